@@ -1,0 +1,406 @@
+#!/usr/bin/env python
+"""Benchmark of the 2DGS Top-K feature rasterizer on the GB300.
+
+Workload (one step = the whole hot path for one 640x480 frame): room scene
+stand-in with 500k surfels and 64-channel BF16 features (K = 8), camera
+cycling over the 16 poses of the circular trajectory; per step:
+project + Precise Tile Intersection binning, per-tile depth sort, Top-K
+forward render, fused L2-feature/L1-RGB loss and gradient, backward render
+(geometric and feature gradients).  Metric: frames/s of forward+backward.
+
+Also reported: the plain FP32 full-accumulation path on the same frames,
+per-call times, the roofline of the dominant kernel, an end-to-end number
+through the C ABI with host buffers, and the FP64 checker on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s & fwd+bwd ms at 640x480 C=64 K=8; % HBM roofline vs plain FP32 path"
+N_SPLATS, C_FEAT, K_TOP, SEED = 500_000, 64, 8, 3
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=64)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip baseline/e2e/cpu legs (profiling runs)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing: one process per GPU, views sharded, no collective on
+# the data path (weak scaling); a barrier and a max-reduce of the time only
+# ---------------------------------------------------------------------------
+class Dist:
+    def __init__(self, backend):
+        import torch
+        import torch.distributed as dist
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = dist if self.world > 1 else None
+        if self.dist:
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend)
+        self.torch = torch
+
+    def barrier(self):
+        if self.dist:
+            self.dist.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.dist:
+            return v
+        t = self.torch.tensor([v], dtype=self.torch.float64,
+                              device="cuda" if self.dist.get_backend() == "nccl" else "cpu")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist:
+            self.dist.destroy_process_group()
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    def __init__(self, gpu: int):
+        self.gpu, self.proc, self.lines = gpu, None, []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    D = Dist("nccl")
+    torch.cuda.set_device(D.local)
+    from paper_2604_10951_gb300 import _lib as L
+    from paper_2604_10951_gb300 import scenes
+    from paper_2604_10951_gb300.build import build
+    from paper_2604_10951_gb300.raster import Frame, make_cams, make_params
+
+    build()
+    dev = torch.device("cuda", D.local)
+    sc = scenes.room_scene(n=N_SPLATS, C=C_FEAT, seed=SEED)
+    poses = scenes.circle_poses(16)
+    cams_c = [make_cams([c]) for c in poses]
+    H, W = poses[0].height, poses[0].width
+    npx = H * W
+    t32 = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev)
+    means, scales, quats, opac, rgb = (t32(x) for x in (sc.means, sc.scales, sc.quats, sc.opacities, sc.rgb))
+    feats = {torch.bfloat16: t32(sc.feats).bfloat16(), torch.float32: t32(sc.feats)}
+    F_tgt_np, rgb_tgt_np = scenes.targets(4, npx, C_FEAT)
+    rgb_tgt = t32(rgb_tgt_np)
+    F_tgt = {torch.bfloat16: t32(F_tgt_np).bfloat16(), torch.float32: t32(F_tgt_np)}
+    stream = torch.cuda.current_stream()
+    sp = C.c_void_p(stream.cuda_stream)
+    ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    class Path:
+        """Buffers and the step of one configuration (all calls via the C ABI)."""
+
+        def __init__(self, K, dtype, stop):
+            self.dtype = dtype
+            self.params = make_params(C=C_FEAT, K=K, tile_size=16, bin_mode="accu", stop_rule=stop,
+                                      feat_dtype=dtype, out_dtype=dtype)
+            self.frame = Frame([poses[0]], N_SPLATS, self.params, pair_capacity=1 << 20, device=dev)
+            cap = 0
+            for c in cams_c:  # size the pair capacity from the 16 poses, with margin
+                self.frame.cams = c
+                cap = max(cap, self.frame.bin_and_sort(means, scales, quats, opac))
+            self.frame._alloc(int(cap * 1.3) + 4096)
+            self.max_pairs = cap
+            self.F, self.rgb_o, self.T, self.ids = self.frame.new_outputs()
+            self.dF = torch.empty_like(self.F)
+            self.drgb = torch.empty_like(self.rgb_o)
+            self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
+            self.g = [torch.empty(N_SPLATS, k, device=dev) for k in (3, 2, 4)] + \
+                     [torch.empty(N_SPLATS, device=dev), torch.empty(N_SPLATS, 3, device=dev)]
+            self.gfeat = torch.empty(N_SPLATS, C_FEAT, dtype=dtype, device=dev)
+            self.feats = feats[dtype]
+            self.F_tgt = F_tgt[dtype]
+            self.ev = None
+
+        def step(self, i, events=None):
+            fr, p, ws = self.frame, self.params, ptr(self.frame.ws)
+            cams = cams_c[i % len(cams_c)]
+            a = (p, cams, 1, N_SPLATS)
+            rec = (lambda k: events[k].record(stream)) if events else (lambda k: None)
+            rec(0)
+            L.fss_project_bin(*a, ptr(means), ptr(scales), ptr(quats), ptr(opac), ws, fr.cap, sp)
+            rec(1)
+            L.fss_sort(*a, ws, fr.cap, sp)
+            rec(2)
+            L.fss_render_forward(*a, ws, fr.cap, ptr(rgb), ptr(self.feats), ptr(self.F), ptr(self.rgb_o),
+                                 ptr(self.T), ptr(self.ids), ptr(fr.saved), sp)
+            rec(3)
+            L.fss_loss_l2_l1(p, npx, ptr(self.F), ptr(self.rgb_o), ptr(self.F_tgt), ptr(rgb_tgt), 1.0, 1.0,
+                             ptr(self.dF), ptr(self.drgb), ptr(self.loss), sp)
+            rec(4)
+            L.fss_render_backward(*a, ws, fr.cap, ptr(means), ptr(scales), ptr(quats), ptr(opac), ptr(rgb),
+                                  ptr(self.feats), ptr(fr.saved), ptr(self.T), ptr(self.dF), ptr(self.drgb), None,
+                                  *(ptr(g) for g in self.g), ptr(self.gfeat), sp)
+            rec(5)
+
+        def check(self):
+            for c in cams_c:
+                self.frame.cams = c
+                s, n = self.frame.read_status()
+                if s != L.FSS_OK:
+                    raise RuntimeError(f"device status {s}: {L.last_error()}")
+
+        def time_steps(self, steps, warmup, per_call=True):
+            for i in range(warmup):
+                self.step(i)
+            torch.cuda.synchronize()
+            D.barrier()
+            names = ["project_bin", "sort", "render_forward", "loss", "render_backward"]
+            calls = {n: [] for n in names}
+            step_ms = []
+            evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(steps)]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for i in range(steps):
+                flush.zero_()  # L2 flush between timed steps (outside the events)
+                self.step(i, evs[i])
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            for e in evs:
+                step_ms.append(e[0].elapsed_time(e[5]))
+                for k, n in enumerate(names):
+                    calls[n].append(e[k].elapsed_time(e[k + 1]))
+            self.check()
+            return step_ms, {n: float(np.mean(v)) for n, v in calls.items()}, wall
+
+    ours = Path(K_TOP, torch.bfloat16, "exact_topk")
+    with ClockSampler(D.local) as clk:
+        step_ms, calls, wall = ours.time_steps(args.steps, args.warmup)
+    total_ms = D.max(float(np.sum(step_ms)))
+    ms_step = total_ms / args.steps
+    frames = args.steps * D.world
+    value = frames / (total_ms / 1e3)
+    launches_per_step = 4 + 1 + 1 + 1 + 5  # project(4) sort(1) forward(1) loss(1) backward(5)
+
+    out = {"metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": D.world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+           "data": "synthetic (seeded room stand-in for the paper's ScanNet scenes)",
+           "config": {"workload": "room 500k surfels, 640x480 (fx=fy=525), C=64 BF16 features, K=8 Top-K "
+                                  "(exact early stop), 16x16 tiles, AccuTile binning, forward+backward incl. "
+                                  "L2-feature/L1-RGB loss; one frame per step over 16 poses",
+                      "global_batch": D.world, "seq_len": npx, "parallelism": f"views sharded x{D.world}",
+                      "l2": "flushed between timed steps (512 MB write)"},
+           "gpu_launches": launches_per_step * args.steps,
+           "calls_ms": {k: round(v, 4) for k, v in calls.items()},
+           "pairs_per_frame_max": ours.max_pairs}
+    clocks = clk.summary()
+    if clocks:
+        out["clocks"] = clocks
+    if not args.no_extras:
+        # the plain FP32 full-accumulation path on the same frames
+        base = Path(0, torch.float32, "tmin")
+        b_ms, b_calls, _ = base.time_steps(max(8, args.steps // 4), 3)
+        b_ms_step = D.max(float(np.sum(b_ms))) / len(b_ms)
+        out["fp32_full_path"] = {"ms_per_step": round(b_ms_step, 4), "frames_per_s": round(1e3 / b_ms_step, 2),
+                                 "calls_ms": {k: round(v, 4) for k, v in b_calls.items()},
+                                 "speedup_of_bf16_topk": round(b_ms_step / ms_step, 3)}
+        fwd_ms = calls["project_bin"] + calls["sort"] + calls["render_forward"]
+        out["forward_only"] = {"ms": round(fwd_ms, 4), "frames_per_s": round(1e3 / fwd_ms, 2)}
+        out["roofline"] = roofline(ours, calls, torch)
+        out["e2e"] = e2e(ours, torch, dev, stream, sp, ptr, L, args)
+        del base
+    if D.rank == 0 and not args.no_extras:
+        out["cpu_baseline"] = cpu_baseline(sc, poses, sample_frames=1)
+    if D.rank == 0:
+        print(json.dumps(out))
+    D.close()
+
+
+def roofline(path, calls, torch):
+    """Forward render kernel: algorithmic bytes per launch / its event time."""
+    peak, src = measured_peaks()
+    fr = path.frame
+    fr.cams = fr.cams  # last pose rendered; recount on pose 0 for the byte model
+    ids = path.ids.cpu().numpy()
+    ranges = fr.region(3 + 1).view(torch.int32).view(-1, 2).cpu().numpy()
+    P = int((ranges[:, 1] - ranges[:, 0]).sum())
+    tiles = ranges.shape[0]
+    H, W = 480, 640
+    ts = 16
+    idv = ids.reshape(H, W, -1)
+    U = 0
+    for ty in range(0, H, ts):
+        for tx in range(0, W, ts):
+            blk = idv[ty:ty + ts, tx:tx + ts].reshape(-1)
+            U += np.unique(blk[blk >= 0]).size
+    s, K, Cc = 2, K_TOP, C_FEAT
+    npx = H * W
+    bytes_ = tiles * 8 + P * (4 + 48 + 4 + 12) + U * Cc * s + npx * (Cc * s + 12 + 4 + 4 * K + 4 * K + 4 * K + 4)
+    t = calls["render_forward"] * 1e-3
+    ach = bytes_ / t / 1e9
+    return {"kernel": "k_render_topk (fss_render_forward)", "bound": "hbm", "achieved": round(ach, 1),
+            "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
+            "peak_source": src, "algorithmic_bytes": int(bytes_), "pairs": P, "unique_rows": int(U)}
+
+
+def e2e(path, torch, dev, stream, sp, ptr, L, args):
+    """Same step through the C ABI with host buffers: per step the targets go
+    host->device from pinned memory and the loss comes back."""
+    F_h = path.F_tgt.cpu().pin_memory()
+    r_h = torch.empty(path.frame.total_pix, 3).pin_memory()
+    r_h.copy_(torch.rand(path.frame.total_pix, 3))
+    loss_h = torch.empty(1, dtype=torch.float64).pin_memory()
+    F_d, r_d = torch.empty_like(path.F_tgt), torch.empty(path.frame.total_pix, 3, device=dev)
+    steps = max(8, args.steps // 4)
+    old_F, old_r = path.F_tgt, None
+
+    def step(i):
+        F_d.copy_(F_h, non_blocking=True)
+        r_d.copy_(r_h, non_blocking=True)
+        path.F_tgt = F_d
+        path.step(i)
+        loss_h.copy_(path.loss, non_blocking=True)
+
+    for i in range(3):
+        step(i)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        step(i)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    path.F_tgt = old_F
+    return {"value": round(steps / dt, 2), "unit": "frames/s",
+            "h2d_bytes_per_step": int(F_h.numel() * F_h.element_size() + r_h.numel() * 4),
+            "d2h_bytes_per_step": 8}
+
+
+def cpu_baseline(sc, poses, sample_frames=1):
+    """The FP64 checker as it stands on this host's cores, on a bounded
+    sample of the same workload (whole 640x480 frames, forward + backward)."""
+    import oracle as O
+
+    O.build()
+    p = O.make_params(K=K_TOP, stop_rule=O.EXACT_TOPK)
+    threads = O.num_threads()
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    for f in range(sample_frames):
+        cam = poses[f]
+        b = O.binning(sc, cam, p)
+        ref = O.render(sc, cam, p, binned=b, threads=threads)
+        gF = rng.normal(size=ref["F"].shape) * 1e-3
+        grgb = rng.normal(size=ref["rgb"].shape) * 1e-3
+        O.render_backward(sc, cam, p, gF, grgb, None, binned=b)
+    dt = time.perf_counter() - t0
+    return {"value": round(sample_frames / dt, 4), "unit": "frames/s", "cores": threads, "kind": "oracle",
+            "sample": f"{sample_frames} full 640x480 frame(s) of the same workload, FP64 forward "
+                      f"(OpenMP, {threads} threads) + backward (1 thread)", "seconds": round(dt, 2)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 checker on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2604_10951_gb300 import scenes
+
+    sc = scenes.room_scene(n=N_SPLATS, C=C_FEAT, seed=SEED)
+    poses = scenes.circle_poses(16)
+    for _ in range(args.warmup and 1):
+        pass
+    res = cpu_baseline(sc, poses, sample_frames=max(1, min(args.steps, 2)))
+    out = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": "frames/s",
+           "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1e3 / res["value"], 2), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "room 500k surfels, 640x480, C=64, K=8, forward+backward (FP64 checker)"},
+           "cpu_baseline": res,
+           "e2e": {"value": res["value"], "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,203 @@
+/*
+ * fss.h -- C ABI of the GB300 (sm_103a) 2D Gaussian Splatting feature
+ * rasterizer with Precise Tile Intersection and Top-K Hard Selection
+ * (Fast-SegSim, arXiv 2604.10951).
+ *
+ * All device memory is owned by the caller.  The library allocates nothing:
+ * every entry point works inside a caller-provided `workspace` (size from
+ * fss_workspace_size) and caller-provided outputs.  Every compute call is
+ * asynchronous on the given CUDA stream (`fss_stream_t` is the same type as
+ * cudaStream_t; NULL means the legacy default stream) and can be captured in
+ * a CUDA graph.  Only fss_read_status synchronises with the host.
+ *
+ * Conventions shared by all calls:
+ *   - surfel parameters are float32, row-major, N rows:
+ *       means [N,3] world position p_i; scales [N,2] (r_u, r_v) > 0 (already
+ *       activated); quats [N,4] (w,x,y,z), any non-zero length (normalised
+ *       inside); opac [N] opacity o_i in [0,1] (already activated);
+ *       rgb [N,3]; feats [N,C] (float32 or bfloat16, params->feat_dtype)
+ *     (Sec. 3.1, Eq. 1: p(u) = p_i + r_u t_u u + r_v t_v v, t_u and t_v the
+ *     first two columns of R(q)).
+ *   - cameras: OpenCV pinhole (x right, y down, z forward); viewmat is the
+ *     row-major 3x4 world->camera [R | t]; pixel (px,py) is sampled at its
+ *     centre (px+0.5, py+0.5).  Up to FSS_MAX_CAMS views per call; view v
+ *     owns pixels [pix_off(v), pix_off(v) + H_v*W_v) of every per-pixel
+ *     output, pix_off(v) = sum over u < v of H_u*W_u (views concatenated).
+ *   - per-pixel outputs are row-major [H, W, ...] per view.
+ *   - the workspace layout depends on (params->tile_size, K, C, feat dtype,
+ *     cameras, N, pair_capacity): pass identical values to every call that
+ *     shares a workspace.
+ *
+ * Errors: a call returns FSS_ERR_INVALID_ARG or FSS_ERR_UNSUPPORTED without
+ * launching anything when its arguments are bad, FSS_ERR_CUDA when a launch
+ * fails; fss_last_error() then holds a message for the calling thread.
+ * Errors found on the device (too many tile-surfel pairs, a bounded wait
+ * that ran out) are recorded in the workspace, make later kernels of the
+ * same frame do nothing, and are returned by fss_read_status.
+ */
+#ifndef FSS_H
+#define FSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *fss_stream_t; /* == cudaStream_t */
+
+typedef enum {
+    FSS_OK = 0,
+    FSS_ERR_INVALID_ARG = 1,
+    FSS_ERR_UNSUPPORTED = 2,
+    FSS_ERR_CAPACITY = 3, /* more tile-surfel pairs than pair_capacity */
+    FSS_ERR_CUDA = 4,
+    FSS_ERR_TIMEOUT = 5   /* a bounded device-side wait gave up */
+} fss_status;
+
+enum { FSS_BIN_AABB = 0, FSS_BIN_SNUG = 1, FSS_BIN_ACCU = 2 };
+enum { FSS_STOP_TMIN = 0, FSS_STOP_EXACT_TOPK = 1 };
+enum { FSS_F32 = 0, FSS_BF16 = 1 };
+
+#define FSS_MAX_CAMS 64
+#define FSS_MAX_K 32
+
+typedef struct {
+    float fx, fy, cx, cy;  /* pinhole intrinsics in pixels */
+    int32_t width, height; /* image size in pixels, 1..16384 */
+    float viewmat[12];     /* row-major 3x4 world->camera [R | t] */
+    float near_plane;      /* hits at camera depth <= near_plane are skipped */
+} fss_camera;
+
+typedef struct {
+    int32_t tile_size;  /* 8, 16 or 32 pixels per tile side */
+    int32_t K;          /* 0: full accumulation (Eq. 2); 1..32: Top-K (Eq. 7) */
+    int32_t bin_mode;   /* FSS_BIN_AABB | FSS_BIN_SNUG | FSS_BIN_ACCU (Sec. 3.2) */
+    int32_t stop_rule;  /* FSS_STOP_TMIN | FSS_STOP_EXACT_TOPK */
+    float alpha_min;    /* contributions below are skipped (default 1/255) */
+    float alpha_max;    /* alpha clamp (default 0.99) */
+    float T_min;        /* stop before transmittance would fall below (1e-4) */
+    int32_t feat_dtype; /* FSS_F32 | FSS_BF16: storage of feats and of their gradient */
+    int32_t out_dtype;  /* FSS_F32 | FSS_BF16: storage of the rendered features */
+    int32_t C;          /* feature channels: multiple of 4 (F32) / 8 (BF16), 4..512 */
+    float bg_rgb[3];    /* background colour added as T_final * bg */
+    int32_t reserved;   /* must be 0 */
+} fss_params;
+
+/* Fills the defaults listed above (tile 16, K 8, ACCU, TMIN, F32, C 16). */
+fss_status fss_default_params(fss_params *params);
+
+/* Bytes of device workspace needed for these cameras, N surfels and at most
+ * `pair_capacity` tile-surfel pairs (the paper's RN-Total, Table 2). */
+fss_status fss_workspace_size(const fss_params *params, const fss_camera *cams, int32_t n_cams,
+                              int64_t N, int64_t pair_capacity, size_t *bytes);
+
+/* Bytes of the `saved` buffer that fss_render_forward fills for the
+ * backward pass (per pixel: Top-K list positions and weights, traversal
+ * length). */
+fss_status fss_saved_size(const fss_params *params, const fss_camera *cams, int32_t n_cams, size_t *bytes);
+
+/*
+ * Projection and Precise Tile Intersection binning (Sec. 3.2).
+ * Per surfel and view: the homogeneous transform T (x' = T u), its
+ * adjugate (ray-splat intersection), the opacity-aware cutoff
+ * k^2 = 2 ln(o / alpha_min), the screen conic of the cutoff disc, its tight
+ * box (SnugBox) and, in ACCU mode, the exact tile interval of every tile row
+ * (or column, whichever span is smaller) from the quadratic
+ * A x^2 + (2B y + 2D) x + (C y^2 + 2E y + F) = 0 (AccuTile).  Writes the
+ * unsorted per-tile surfel lists into the workspace.  If more than
+ * pair_capacity pairs are needed, records FSS_ERR_CAPACITY and the needed
+ * count (see fss_read_status); the following calls then do nothing.
+ * Inputs are device pointers (layout above); culled surfels (camera depth
+ * <= near, o < alpha_min, seen edge-on) produce no pairs.
+ */
+fss_status fss_project_bin(const fss_params *params, const fss_camera *cams, int32_t n_cams, int64_t N,
+                           const float *means, const float *scales, const float *quats, const float *opac,
+                           void *workspace, int64_t pair_capacity, fss_stream_t stream);
+
+/*
+ * Depth sort ("surfels are depth-sorted", Sec. 3.1): orders each tile's
+ * list by (binary32 bits of the surfel centre's camera depth, surfel index),
+ * a total order, so the result is deterministic.
+ */
+fss_status fss_sort(const fss_params *params, const fss_camera *cams, int32_t n_cams, int64_t N,
+                    void *workspace, int64_t pair_capacity, fss_stream_t stream);
+
+/*
+ * Forward render (Eq. 2 with Top-K Hard Selection, Eq. 7).  For every
+ * pixel, front to back over its tile's sorted list: ray-splat intersection
+ * (u,v), alpha = min(alpha_max, o exp(-(u^2+v^2)/2)), skip if
+ * alpha < alpha_min, stop by params->stop_rule, w = alpha T, T *= 1 - alpha.
+ * K = 0: F = sum_i w_i c_i over all contributors.  K > 0: F = sum over the K
+ * largest w_i (ties: earlier wins), no renormalisation.
+ * Device inputs: rgb [N,3] f32, feats [N,C] (feat_dtype).
+ * Device outputs (any may be NULL except as noted; per view concatenated):
+ *   out_feat [pix, C] in out_dtype; out_rgb [pix, 3] = sum w rgb + T bg;
+ *   out_T [pix] final transmittance; out_topk_id [pix, K] surfel indices in
+ *   front-to-back order, -1 padded (K > 0 only);
+ *   saved: fss_saved_size bytes, required if fss_render_backward follows.
+ */
+fss_status fss_render_forward(const fss_params *params, const fss_camera *cams, int32_t n_cams, int64_t N,
+                              void *workspace, int64_t pair_capacity, const float *rgb, const void *feats,
+                              void *out_feat, float *out_rgb, float *out_T, int32_t *out_topk_id,
+                              void *saved, fss_stream_t stream);
+
+/*
+ * Backward render: vector-Jacobian product of fss_render_forward for the
+ * upstream gradients d_feat [pix, C] (out_dtype), d_rgb [pix, 3] f32 and
+ * d_T [pix] f32 (may be NULL).  Replays each pixel back to front from the
+ * saved traversal length and final transmittance; the Top-K set, skips,
+ * stops and clamps are held fixed.  Outputs (overwritten, device):
+ *   g_means [N,3], g_scales [N,2], g_quats [N,4], g_opac [N], g_rgb [N,3]
+ *   (float32) and g_feat [N,C] (feat_dtype; FP32 accumulation inside).
+ * Gradients are summed over all views of the call.
+ */
+fss_status fss_render_backward(const fss_params *params, const fss_camera *cams, int32_t n_cams, int64_t N,
+                               void *workspace, int64_t pair_capacity,
+                               const float *means, const float *scales, const float *quats, const float *opac,
+                               const float *rgb, const void *feats, const void *saved, const float *out_T,
+                               const void *d_feat, const float *d_rgb, const float *d_T,
+                               float *g_means, float *g_scales, float *g_quats, float *g_opac, float *g_rgb,
+                               void *g_feat, fss_stream_t stream);
+
+/*
+ * Synchronises `stream`, then reports device-side errors of the frames
+ * processed in `workspace`: FSS_ERR_CAPACITY (with *num_pairs = the number
+ * of pairs needed), FSS_ERR_TIMEOUT, or FSS_OK (with *num_pairs = pairs
+ * used).  Clears the error flags.  `num_pairs` may be NULL.
+ */
+fss_status fss_read_status(const fss_params *params, const fss_camera *cams, int32_t n_cams, int64_t N,
+                           void *workspace, int64_t pair_capacity, int64_t *num_pairs, fss_stream_t stream);
+
+/*
+ * Loss of the forward+backward workload and its gradient in one pass:
+ *   L = w_feat * mean((F - F_t)^2) + w_rgb * mean(|rgb - rgb_t|)
+ * over n_pix pixels (feature L2 standing in for the segmentation losses,
+ * RGB L1 as in the photometric loss, Sec. 3.5).  Device inputs: feat and
+ * feat_target [n_pix, C] in params->out_dtype, rgb and rgb_target [n_pix,3]
+ * f32.  Device outputs: d_feat [n_pix, C] (out_dtype) and d_rgb [n_pix, 3]
+ * ready for fss_render_backward, and *loss (one double, overwritten).
+ */
+fss_status fss_loss_l2_l1(const fss_params *params, int64_t n_pix, const void *feat, const float *rgb,
+                          const void *feat_target, const float *rgb_target, float w_feat, float w_rgb,
+                          void *d_feat, float *d_rgb, double *loss, fss_stream_t stream);
+
+/* Message of the last error returned to the calling thread ("" if none). */
+const char *fss_last_error(void);
+
+/*
+ * Offset and size of a named region inside the workspace (for inspection
+ * and tests).  Regions: 0 status, 1 per-(view,surfel) render records
+ * (4 x float4: adjugate rows with centre/det, opacity/depth/cutoff),
+ * 2 binning records, 3 tile counts per (view,surfel), 4 tile ranges
+ * (int32 [tiles,2]), 5 tile lists (uint32 item ids), 6 counters (uint64),
+ * 7 per-tile pair counts (uint32).
+ */
+fss_status fss_workspace_region(const fss_params *params, const fss_camera *cams, int32_t n_cams, int64_t N,
+                                int64_t pair_capacity, int32_t which, size_t *offset, size_t *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSS_H */

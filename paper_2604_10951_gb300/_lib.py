@@ -1,0 +1,158 @@
+"""ctypes binding of ``libfss.so`` (the C ABI in ``include/fss.h``).
+
+Functions keep the C names and take plain integers / pointers; this module
+only marshals arguments.  Importing it never compiles anything: the library
+must have been built (``paper_2604_10951_gb300.build.build()``), else
+:func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from .build import LIB
+
+FSS_OK, FSS_ERR_INVALID_ARG, FSS_ERR_UNSUPPORTED, FSS_ERR_CAPACITY, FSS_ERR_CUDA, FSS_ERR_TIMEOUT = range(6)
+FSS_BIN_AABB, FSS_BIN_SNUG, FSS_BIN_ACCU = 0, 1, 2
+FSS_STOP_TMIN, FSS_STOP_EXACT_TOPK = 0, 1
+FSS_F32, FSS_BF16 = 0, 1
+FSS_MAX_CAMS = 64
+FSS_MAX_K = 32
+STATUS_NAMES = {0: "FSS_OK", 1: "FSS_ERR_INVALID_ARG", 2: "FSS_ERR_UNSUPPORTED", 3: "FSS_ERR_CAPACITY",
+                4: "FSS_ERR_CUDA", 5: "FSS_ERR_TIMEOUT"}
+
+# workspace regions (fss_workspace_region)
+REG_STATUS, REG_REC, REG_BINREC, REG_COUNT, REG_RANGES, REG_LIST, REG_COUNTERS, REG_TILECNT = range(8)
+REG_SORTTMP, REG_GRAD_ITEM, REG_FEAT_ACC, REG_DOTS, REG_VIS, REG_UNB, REG_SLOT = range(8, 15)
+
+EXPORTS = ["fss_default_params", "fss_workspace_size", "fss_saved_size", "fss_project_bin", "fss_sort",
+           "fss_render_forward", "fss_render_backward", "fss_read_status", "fss_last_error",
+           "fss_workspace_region", "fss_loss_l2_l1"]
+
+
+class fss_camera(C.Structure):
+    _fields_ = [("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32), ("viewmat", C.c_float * 12),
+                ("near_plane", C.c_float)]
+
+
+class fss_params(C.Structure):
+    _fields_ = [("tile_size", C.c_int32), ("K", C.c_int32), ("bin_mode", C.c_int32), ("stop_rule", C.c_int32),
+                ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("T_min", C.c_float),
+                ("feat_dtype", C.c_int32), ("out_dtype", C.c_int32), ("C", C.c_int32),
+                ("bg_rgb", C.c_float * 3), ("reserved", C.c_int32)]
+
+
+class FssError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB):
+                raise ImportError(f"libfss.so not built ({LIB}); run paper_2604_10951_gb300.build.build()")
+            L = C.CDLL(LIB)
+            P, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+            pp, pc = C.POINTER(fss_params), C.POINTER(fss_camera)
+            sig = {
+                "fss_default_params": [pp],
+                "fss_workspace_size": [pp, pc, i32, i64, i64, C.POINTER(C.c_size_t)],
+                "fss_saved_size": [pp, pc, i32, C.POINTER(C.c_size_t)],
+                "fss_project_bin": [pp, pc, i32, i64, P, P, P, P, P, i64, P],
+                "fss_sort": [pp, pc, i32, i64, P, i64, P],
+                "fss_render_forward": [pp, pc, i32, i64, P, i64, P, P, P, P, P, P, P, P],
+                "fss_render_backward": [pp, pc, i32, i64, P, i64, P, P, P, P, P, P, P, P, P, P, P,
+                                        P, P, P, P, P, P, P],
+                "fss_read_status": [pp, pc, i32, i64, P, i64, C.POINTER(C.c_int64), P],
+                "fss_workspace_region": [pp, pc, i32, i64, i64, i32, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)],
+                "fss_loss_l2_l1": [pp, i64, P, P, P, P, C.c_float, C.c_float, P, P, P, P],
+            }
+            for name, args in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = C.c_int
+            L.fss_last_error.argtypes = []
+            L.fss_last_error.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().fss_last_error().decode()
+
+
+def check(status: int) -> int:
+    if status != FSS_OK:
+        raise FssError(status, last_error())
+    return status
+
+
+# -- same-name wrappers (marshalling only) ----------------------------------
+
+def fss_default_params() -> fss_params:
+    p = fss_params()
+    check(lib().fss_default_params(C.byref(p)))
+    return p
+
+
+def fss_workspace_size(params, cams, n_cams, N, pair_capacity) -> int:
+    out = C.c_size_t()
+    check(lib().fss_workspace_size(C.byref(params), cams, n_cams, N, pair_capacity, C.byref(out)))
+    return out.value
+
+
+def fss_saved_size(params, cams, n_cams) -> int:
+    out = C.c_size_t()
+    check(lib().fss_saved_size(C.byref(params), cams, n_cams, C.byref(out)))
+    return out.value
+
+
+def fss_workspace_region(params, cams, n_cams, N, pair_capacity, which):
+    off, size = C.c_size_t(), C.c_size_t()
+    check(lib().fss_workspace_region(C.byref(params), cams, n_cams, N, pair_capacity, which,
+                                     C.byref(off), C.byref(size)))
+    return off.value, size.value
+
+
+def fss_project_bin(params, cams, n_cams, N, means, scales, quats, opac, workspace, pair_capacity, stream):
+    return check(lib().fss_project_bin(C.byref(params), cams, n_cams, N, means, scales, quats, opac,
+                                       workspace, pair_capacity, stream))
+
+
+def fss_sort(params, cams, n_cams, N, workspace, pair_capacity, stream):
+    return check(lib().fss_sort(C.byref(params), cams, n_cams, N, workspace, pair_capacity, stream))
+
+
+def fss_render_forward(params, cams, n_cams, N, workspace, pair_capacity, rgb, feats, out_feat, out_rgb, out_T,
+                       out_topk_id, saved, stream):
+    return check(lib().fss_render_forward(C.byref(params), cams, n_cams, N, workspace, pair_capacity, rgb, feats,
+                                          out_feat, out_rgb, out_T, out_topk_id, saved, stream))
+
+
+def fss_render_backward(params, cams, n_cams, N, workspace, pair_capacity, means, scales, quats, opac, rgb, feats,
+                        saved, out_T, d_feat, d_rgb, d_T, g_means, g_scales, g_quats, g_opac, g_rgb, g_feat, stream):
+    return check(lib().fss_render_backward(C.byref(params), cams, n_cams, N, workspace, pair_capacity, means, scales,
+                                           quats, opac, rgb, feats, saved, out_T, d_feat, d_rgb, d_T, g_means,
+                                           g_scales, g_quats, g_opac, g_rgb, g_feat, stream))
+
+
+def fss_loss_l2_l1(params, n_pix, feat, rgb, feat_target, rgb_target, w_feat, w_rgb, d_feat, d_rgb, loss, stream):
+    return check(lib().fss_loss_l2_l1(C.byref(params), n_pix, feat, rgb, feat_target, rgb_target, float(w_feat),
+                                      float(w_rgb), d_feat, d_rgb, loss, stream))
+
+
+def fss_read_status(params, cams, n_cams, N, workspace, pair_capacity, stream):
+    """Returns (status, num_pairs) without raising on device-side errors."""
+    n = C.c_int64()
+    s = lib().fss_read_status(C.byref(params), cams, n_cams, N, workspace, pair_capacity, C.byref(n), stream)
+    return s, n.value

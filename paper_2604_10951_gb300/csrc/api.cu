@@ -1,0 +1,398 @@
+// C ABI of the rasterizer library (include/fss.h): argument validation,
+// workspace layout and kernel launches.  No entry point allocates memory.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "fss_internal.cuh"
+#include "kernels.cuh"
+
+namespace fss {
+namespace {
+
+thread_local std::string g_err;
+
+fss_status fail(fss_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+fss_status fail(fss_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+fss_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(FSS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+int num_sms_current() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 148;
+    return n;
+}
+
+fss_status check_params(const fss_params* p) {
+    if (!p) return fail(FSS_ERR_INVALID_ARG, "params is NULL");
+    if (p->tile_size != 8 && p->tile_size != 16 && p->tile_size != 32)
+        return fail(FSS_ERR_UNSUPPORTED, "tile_size %d not in {8,16,32}", p->tile_size);
+    if (p->K < 0 || p->K > FSS_MAX_K) return fail(FSS_ERR_UNSUPPORTED, "K %d not in [0,%d]", p->K, FSS_MAX_K);
+    if (p->bin_mode < FSS_BIN_AABB || p->bin_mode > FSS_BIN_ACCU)
+        return fail(FSS_ERR_INVALID_ARG, "bin_mode %d", p->bin_mode);
+    if (p->stop_rule != FSS_STOP_TMIN && p->stop_rule != FSS_STOP_EXACT_TOPK)
+        return fail(FSS_ERR_INVALID_ARG, "stop_rule %d", p->stop_rule);
+    if ((p->feat_dtype != FSS_F32 && p->feat_dtype != FSS_BF16) || (p->out_dtype != FSS_F32 && p->out_dtype != FSS_BF16))
+        return fail(FSS_ERR_INVALID_ARG, "feat_dtype/out_dtype must be FSS_F32 or FSS_BF16");
+    const int vec = (p->feat_dtype == FSS_BF16 || p->out_dtype == FSS_BF16) ? 8 : 4;
+    if (p->C < 4 || p->C > 512 || p->C % vec)
+        return fail(FSS_ERR_UNSUPPORTED, "C %d must be a multiple of %d in [4,512]", p->C, vec);
+    if (p->K == 0 && p->C > 128) return fail(FSS_ERR_UNSUPPORTED, "full accumulation (K=0) supports C <= 128");
+    if (!(p->alpha_min > 0.0f) || !(p->alpha_max > p->alpha_min) || !(p->alpha_max < 1.0f))
+        return fail(FSS_ERR_INVALID_ARG, "need 0 < alpha_min < alpha_max < 1");
+    if (!(p->T_min >= 0.0f) || !(p->T_min < 1.0f)) return fail(FSS_ERR_INVALID_ARG, "need 0 <= T_min < 1");
+    if (p->reserved != 0) return fail(FSS_ERR_INVALID_ARG, "reserved must be 0");
+    return FSS_OK;
+}
+
+fss_status make_cams(const fss_camera* cams, int32_t n, int ts, Cams& out) {
+    if (!cams) return fail(FSS_ERR_INVALID_ARG, "cams is NULL");
+    if (n < 1 || n > FSS_MAX_CAMS) return fail(FSS_ERR_UNSUPPORTED, "n_cams %d not in [1,%d]", n, FSS_MAX_CAMS);
+    std::memset(&out, 0, sizeof out);
+    out.n = n;
+    int64_t tiles = 0, pix = 0;
+    for (int v = 0; v < n; ++v) {
+        const fss_camera& c = cams[v];
+        if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384)
+            return fail(FSS_ERR_UNSUPPORTED, "camera %d: size %dx%d not in [1,16384]^2", v, c.width, c.height);
+        if (!(c.fx > 0.0f) || !(c.fy > 0.0f) || !(c.near_plane > 0.0f))
+            return fail(FSS_ERR_INVALID_ARG, "camera %d: need fx, fy, near_plane > 0", v);
+        CamDev& d = out.c[v];
+        d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+        for (int r = 0; r < 3; ++r) {
+            for (int k = 0; k < 3; ++k) d.R[3 * r + k] = c.viewmat[4 * r + k];
+            d.t[r] = c.viewmat[4 * r + 3];
+        }
+        d.near_plane = c.near_plane;
+        d.W = c.width; d.H = c.height;
+        d.tiles_x = (c.width + ts - 1) / ts;
+        d.tiles_y = (c.height + ts - 1) / ts;
+        d.tile_off = (int32_t)tiles;
+        d.pix_off = pix;
+        tiles += (int64_t)d.tiles_x * d.tiles_y;
+        pix += (int64_t)c.width * c.height;
+    }
+    if (tiles > (1 << 30)) return fail(FSS_ERR_UNSUPPORTED, "too many tiles");
+    out.total_tiles = (int32_t)tiles;
+    out.total_pix = pix;
+    return FSS_OK;
+}
+
+RParams make_rparams(const fss_params* p, const Cams& cams, int64_t N, int64_t cap) {
+    RParams r;
+    r.ts = p->tile_size; r.K = p->K; r.bin_mode = p->bin_mode; r.stop_rule = p->stop_rule;
+    r.alpha_min = p->alpha_min; r.alpha_max = p->alpha_max; r.T_min = p->T_min;
+    r.feat_dtype = p->feat_dtype; r.out_dtype = p->out_dtype; r.C = p->C;
+    for (int k = 0; k < 3; ++k) r.bg[k] = p->bg_rgb[k];
+    r.N = N;
+    r.n_items = N * cams.n;
+    r.pair_cap = cap;
+    return r;
+}
+
+Layout make_layout(const RParams& P, const Cams& cams) {
+    Layout L;
+    size_t sz[REG_COUNT_ALL] = {};
+    const size_t ni = (size_t)P.n_items, N = (size_t)P.N, cap = (size_t)P.pair_cap;
+    sz[REG_STATUS] = sizeof(Status);
+    sz[REG_REC] = ni * 64;
+    sz[REG_BINREC] = ni * sizeof(BinRec);
+    sz[REG_COUNT] = ni * 4;
+    sz[REG_RANGES] = (size_t)cams.total_tiles * 8;
+    sz[REG_LIST] = cap * 4;
+    sz[REG_COUNTERS] = 0;  // inside the status block
+    sz[REG_TILECNT] = (size_t)cams.total_tiles * 4;
+    sz[REG_SORTTMP] = cap * 16;
+    sz[REG_GRAD_ITEM] = (size_t)cams.n * N * GRAD_STRIDE * 4;
+    sz[REG_FEAT_ACC] = N * (size_t)P.C * 4;
+    sz[REG_DOTS] = (size_t)cams.total_pix * (size_t)P.K * 4;
+    sz[REG_VIS] = ni * 4;
+    sz[REG_UNB] = ni * 4;
+    sz[REG_SLOT] = N * 4;
+    size_t off = 0;
+    for (int r = 0; r < REG_COUNT_ALL; ++r) {
+        L.off[r] = off;
+        L.size[r] = sz[r];
+        off += align256(sz[r]);
+    }
+    L.off[REG_COUNTERS] = L.off[REG_STATUS] + STATUS_CLEAR_OFF;
+    L.size[REG_COUNTERS] = sizeof(((Status*)0)->counters);
+    L.total = off;
+    return L;
+}
+
+struct Ctx {
+    Cams cams;
+    RParams P;
+    Layout L;
+    unsigned char* ws;
+    template <typename T>
+    T* at(int r) const { return reinterpret_cast<T*>(ws + L.off[r]); }
+};
+
+fss_status prepare(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N, int64_t cap,
+                   void* workspace, Ctx& ctx) {
+    fss_status s = check_params(params);
+    if (s != FSS_OK) return s;
+    if ((s = make_cams(cams, n_cams, params->tile_size, ctx.cams)) != FSS_OK) return s;
+    if (N < 0 || N > ((int64_t)1 << 30)) return fail(FSS_ERR_UNSUPPORTED, "N %lld not in [0, 2^30]", (long long)N);
+    if (N * n_cams >= ((int64_t)1 << 32)) return fail(FSS_ERR_UNSUPPORTED, "N * n_cams must be < 2^32");
+    if (cap < 0 || cap >= ((int64_t)1 << 31)) return fail(FSS_ERR_UNSUPPORTED, "pair_capacity not in [0, 2^31)");
+    ctx.P = make_rparams(params, ctx.cams, N, cap);
+    ctx.L = make_layout(ctx.P, ctx.cams);
+    ctx.ws = reinterpret_cast<unsigned char*>(workspace);
+    if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return fail(FSS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    return FSS_OK;
+}
+
+bool misaligned16(const void* p) { return p && (reinterpret_cast<uintptr_t>(p) & 15); }
+
+}  // namespace
+}  // namespace fss
+
+using namespace fss;
+
+extern "C" {
+
+fss_status fss_default_params(fss_params* p) {
+    if (!p) return fail(FSS_ERR_INVALID_ARG, "params is NULL");
+    std::memset(p, 0, sizeof *p);
+    p->tile_size = 16;
+    p->K = 8;
+    p->bin_mode = FSS_BIN_ACCU;
+    p->stop_rule = FSS_STOP_TMIN;
+    p->alpha_min = 1.0f / 255.0f;
+    p->alpha_max = 0.99f;
+    p->T_min = 1e-4f;
+    p->feat_dtype = FSS_F32;
+    p->out_dtype = FSS_F32;
+    p->C = 16;
+    return FSS_OK;
+}
+
+fss_status fss_workspace_size(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N,
+                              int64_t pair_capacity, size_t* bytes) {
+    Ctx ctx;
+    fss_status s = prepare(params, cams, n_cams, N, pair_capacity, nullptr, ctx);
+    if (s != FSS_OK) return s;
+    if (!bytes) return fail(FSS_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = ctx.L.total;
+    return FSS_OK;
+}
+
+fss_status fss_saved_size(const fss_params* params, const fss_camera* cams, int32_t n_cams, size_t* bytes) {
+    fss_status s = check_params(params);
+    if (s != FSS_OK) return s;
+    Cams c;
+    if ((s = make_cams(cams, n_cams, params->tile_size, c)) != FSS_OK) return s;
+    if (!bytes) return fail(FSS_ERR_INVALID_ARG, "bytes is NULL");
+    const size_t px = (size_t)c.total_pix;
+    *bytes = align256(px * params->K * 4) * 2 + align256(px * 4);
+    return FSS_OK;
+}
+
+fss_status fss_workspace_region(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N,
+                                int64_t pair_capacity, int32_t which, size_t* offset, size_t* bytes) {
+    Ctx ctx;
+    fss_status s = prepare(params, cams, n_cams, N, pair_capacity, nullptr, ctx);
+    if (s != FSS_OK) return s;
+    if (which < 0 || which >= REG_COUNT_ALL) return fail(FSS_ERR_INVALID_ARG, "region %d", which);
+    if (offset) *offset = ctx.L.off[which];
+    if (bytes) *bytes = ctx.L.size[which];
+    return FSS_OK;
+}
+
+fss_status fss_project_bin(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N,
+                           const float* means, const float* scales, const float* quats, const float* opac,
+                           void* workspace, int64_t pair_capacity, fss_stream_t stream) {
+    Ctx ctx;
+    fss_status s = prepare(params, cams, n_cams, N, pair_capacity, workspace, ctx);
+    if (s != FSS_OK) return s;
+    if (!workspace) return fail(FSS_ERR_INVALID_ARG, "workspace is NULL");
+    if (N > 0 && (!means || !scales || !quats || !opac)) return fail(FSS_ERR_INVALID_ARG, "NULL surfel input");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    // clear the per-frame part of the status block and the gradient slots
+    e = cudaMemsetAsync(ctx.ws + ctx.L.off[REG_STATUS] + STATUS_CLEAR_OFF, 0, sizeof(Status) - STATUS_CLEAR_OFF, st);
+    if (e != cudaSuccess) return cuda_fail(e, "memset status");
+    if (N > 0) {
+        e = cudaMemsetAsync(ctx.ws + ctx.L.off[REG_SLOT], 0xff, (size_t)N * 4, st);
+        if (e != cudaSuccess) return cuda_fail(e, "memset slots");
+    }
+    const int sms = num_sms_current();
+    Status* stp = ctx.at<Status>(REG_STATUS);
+    const int64_t items = ctx.P.n_items;
+    const int64_t blocks = std::max<int64_t>(1, std::max<int64_t>((items + 255) / 256, 1));
+    k_project<<<(unsigned)blocks, 256, 0, st>>>(ctx.cams, ctx.P, means, scales, quats, opac, ctx.at<float4>(REG_REC),
+                                               ctx.at<BinRec>(REG_BINREC), ctx.at<uint32_t>(REG_COUNT),
+                                               ctx.at<uint32_t>(REG_TILECNT), ctx.at<uint32_t>(REG_VIS),
+                                               ctx.at<uint32_t>(REG_UNB), ctx.at<int32_t>(REG_SLOT), stp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_project");
+    k_count<<<sms * 8, 256, 0, st>>>(ctx.cams, ctx.P, ctx.at<BinRec>(REG_BINREC), ctx.at<uint32_t>(REG_VIS),
+                                     ctx.at<uint32_t>(REG_COUNT), ctx.at<uint32_t>(REG_TILECNT), stp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_count");
+    k_scan<<<1, 1024, 0, st>>>(ctx.cams, ctx.P, ctx.at<uint32_t>(REG_TILECNT), ctx.at<int2>(REG_RANGES), stp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_scan");
+    k_emit<<<sms * 8, 256, 0, st>>>(ctx.cams, ctx.P, ctx.at<BinRec>(REG_BINREC), ctx.at<uint32_t>(REG_VIS),
+                                    ctx.at<uint32_t>(REG_TILECNT), ctx.at<uint32_t>(REG_LIST), stp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_emit");
+    return FSS_OK;
+}
+
+fss_status fss_sort(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N, void* workspace,
+                    int64_t pair_capacity, fss_stream_t stream) {
+    Ctx ctx;
+    fss_status s = prepare(params, cams, n_cams, N, pair_capacity, workspace, ctx);
+    if (s != FSS_OK) return s;
+    if (!workspace) return fail(FSS_ERR_INVALID_ARG, "workspace is NULL");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    k_tile_sort<<<ctx.cams.total_tiles, 256, 0, st>>>(ctx.cams, ctx.P, ctx.at<float4>(REG_REC), ctx.at<int2>(REG_RANGES),
+                                                      ctx.at<uint32_t>(REG_LIST), ctx.at<uint32_t>(REG_UNB),
+                                                      ctx.at<uint64_t>(REG_SORTTMP), ctx.at<Status>(REG_STATUS));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_tile_sort");
+    return FSS_OK;
+}
+
+fss_status fss_render_forward(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N,
+                              void* workspace, int64_t pair_capacity, const float* rgb, const void* feats,
+                              void* out_feat, float* out_rgb, float* out_T, int32_t* out_topk_id, void* saved,
+                              fss_stream_t stream) {
+    Ctx ctx;
+    fss_status s = prepare(params, cams, n_cams, N, pair_capacity, workspace, ctx);
+    if (s != FSS_OK) return s;
+    if (!workspace) return fail(FSS_ERR_INVALID_ARG, "workspace is NULL");
+    if (N > 0 && !rgb) return fail(FSS_ERR_INVALID_ARG, "rgb is NULL");
+    if (out_feat && N > 0 && !feats) return fail(FSS_ERR_INVALID_ARG, "feats is NULL while out_feat is given");
+    if (misaligned16(feats) || misaligned16(out_feat))
+        return fail(FSS_ERR_INVALID_ARG, "feats and out_feat must be 16-byte aligned");
+    FwdArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.rec = ctx.at<float4>(REG_REC);
+    a.ranges = ctx.at<int2>(REG_RANGES);
+    a.list = ctx.at<uint32_t>(REG_LIST);
+    a.rgb = rgb;
+    a.feats = feats;
+    a.out_feat = out_feat;
+    a.out_rgb = out_rgb;
+    a.out_T = out_T;
+    a.out_ids = params->K > 0 ? out_topk_id : nullptr;
+    if (saved) {
+        const size_t px = (size_t)ctx.cams.total_pix;
+        unsigned char* sv = reinterpret_cast<unsigned char*>(saved);
+        a.saved_pos = params->K > 0 ? reinterpret_cast<int32_t*>(sv) : nullptr;
+        a.saved_w = params->K > 0 ? reinterpret_cast<float*>(sv + align256(px * params->K * 4)) : nullptr;
+        a.saved_nstop = reinterpret_cast<int32_t*>(sv + 2 * align256(px * params->K * 4));
+    }
+    a.st = ctx.at<Status>(REG_STATUS);
+    a.persistent = 0;
+    cudaError_t e = launch_render_forward(ctx.cams, ctx.P, a, num_sms_current(), reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "render_forward");
+    return FSS_OK;
+}
+
+fss_status fss_render_backward(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N,
+                               void* workspace, int64_t pair_capacity, const float* means, const float* scales,
+                               const float* quats, const float* opac, const float* rgb, const void* feats,
+                               const void* saved, const float* out_T, const void* d_feat, const float* d_rgb,
+                               const float* d_T, float* g_means, float* g_scales, float* g_quats, float* g_opac,
+                               float* g_rgb, void* g_feat, fss_stream_t stream) {
+    Ctx ctx;
+    fss_status s = prepare(params, cams, n_cams, N, pair_capacity, workspace, ctx);
+    if (s != FSS_OK) return s;
+    if (!workspace || !saved || !out_T || !d_rgb) return fail(FSS_ERR_INVALID_ARG, "NULL workspace/saved/out_T/d_rgb");
+    if (params->out_dtype != params->feat_dtype)
+        return fail(FSS_ERR_UNSUPPORTED, "backward needs out_dtype == feat_dtype");
+    if (N > 0 && (!means || !scales || !quats || !opac || !rgb || !feats || !d_feat))
+        return fail(FSS_ERR_INVALID_ARG, "NULL surfel input or d_feat");
+    if (misaligned16(feats) || misaligned16(d_feat) || misaligned16(g_feat))
+        return fail(FSS_ERR_INVALID_ARG, "feats, d_feat and g_feat must be 16-byte aligned");
+    BwdArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.rec = ctx.at<float4>(REG_REC);
+    a.ranges = ctx.at<int2>(REG_RANGES);
+    a.list = ctx.at<uint32_t>(REG_LIST);
+    a.rgb = rgb;
+    a.feats = feats;
+    const size_t px = (size_t)ctx.cams.total_pix;
+    const unsigned char* sv = reinterpret_cast<const unsigned char*>(saved);
+    a.saved_pos = params->K > 0 ? reinterpret_cast<const int32_t*>(sv) : nullptr;
+    a.saved_w = params->K > 0 ? reinterpret_cast<const float*>(sv + align256(px * params->K * 4)) : nullptr;
+    a.saved_nstop = reinterpret_cast<const int32_t*>(sv + 2 * align256(px * params->K * 4));
+    a.out_T = out_T;
+    a.d_feat = d_feat;
+    a.d_rgb = d_rgb;
+    a.d_T = d_T;
+    a.dots = ctx.at<float>(REG_DOTS);
+    a.grad_item = ctx.at<float>(REG_GRAD_ITEM);
+    a.feat_acc = ctx.at<float>(REG_FEAT_ACC);
+    a.splat_slot = ctx.at<int32_t>(REG_SLOT);
+    a.means = means; a.scales = scales; a.quats = quats; a.opac = opac;
+    a.g_means = g_means; a.g_scales = g_scales; a.g_quats = g_quats; a.g_opac = g_opac; a.g_rgb = g_rgb;
+    a.g_feat = g_feat;
+    a.st = ctx.at<Status>(REG_STATUS);
+    if (N == 0) return FSS_OK;
+    cudaError_t e = launch_render_backward(ctx.cams, ctx.P, a, num_sms_current(), reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "render_backward");
+    return FSS_OK;
+}
+
+fss_status fss_read_status(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N,
+                           void* workspace, int64_t pair_capacity, int64_t* num_pairs, fss_stream_t stream) {
+    Ctx ctx;
+    fss_status s = prepare(params, cams, n_cams, N, pair_capacity, workspace, ctx);
+    if (s != FSS_OK) return s;
+    if (!workspace) return fail(FSS_ERR_INVALID_ARG, "workspace is NULL");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Status h;
+    cudaError_t e = cudaMemcpyAsync(&h, ctx.ws + ctx.L.off[REG_STATUS], sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "read status");
+    if (num_pairs) *num_pairs = h.pairs_needed;
+    if (h.err) {
+        e = cudaMemsetAsync(ctx.ws + ctx.L.off[REG_STATUS], 0, sizeof(int32_t), st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "clear status");
+        if (h.err & ERR_TIMEOUT) return fail(FSS_ERR_TIMEOUT, "a bounded device wait gave up");
+        return fail(FSS_ERR_CAPACITY, "%lld tile-surfel pairs needed, capacity %lld", (long long)h.pairs_needed,
+                    (long long)pair_capacity);
+    }
+    return FSS_OK;
+}
+
+fss_status fss_loss_l2_l1(const fss_params* params, int64_t n_pix, const void* feat, const float* rgb,
+                          const void* feat_target, const float* rgb_target, float w_feat, float w_rgb, void* d_feat,
+                          float* d_rgb, double* loss, fss_stream_t stream) {
+    fss_status s = check_params(params);
+    if (s != FSS_OK) return s;
+    if (n_pix < 0) return fail(FSS_ERR_INVALID_ARG, "n_pix < 0");
+    if (n_pix > 0 && (!feat || !rgb || !feat_target || !rgb_target || !d_feat || !d_rgb))
+        return fail(FSS_ERR_INVALID_ARG, "NULL loss argument");
+    if (!loss) return fail(FSS_ERR_INVALID_ARG, "loss is NULL");
+    if (misaligned16(feat) || misaligned16(feat_target) || misaligned16(d_feat))
+        return fail(FSS_ERR_INVALID_ARG, "feature buffers must be 16-byte aligned");
+    cudaError_t e = launch_loss(n_pix, params->C, params->out_dtype, feat, rgb, feat_target, rgb_target, w_feat, w_rgb,
+                                d_feat, d_rgb, loss, num_sms_current(), reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "loss");
+    return FSS_OK;
+}
+
+const char* fss_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// Internal declarations of the sm_103a rasterizer library: device-side
+// camera and parameter blocks, record layouts and the workspace layout.
+// Not part of the public ABI (include/fss.h).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fss.h"
+
+namespace fss {
+
+// ---------------------------------------------------------------------------
+// launch-time constant blocks (passed by value as kernel parameters, so a
+// captured CUDA graph carries them and no host->device copy is needed)
+// ---------------------------------------------------------------------------
+struct CamDev {
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    float near_plane;
+    int32_t W, H;
+    int32_t tiles_x, tiles_y;
+    int32_t tile_off;  // first global tile id of this view
+    int64_t pix_off;   // first pixel of this view in the concatenated outputs
+};
+
+struct Cams {
+    int32_t n;
+    int32_t total_tiles;
+    int64_t total_pix;
+    CamDev c[FSS_MAX_CAMS];
+};
+
+struct RParams {
+    int32_t ts, K, bin_mode, stop_rule;
+    float alpha_min, alpha_max, T_min;
+    int32_t feat_dtype, out_dtype, C;
+    float bg[3];
+    int64_t N;
+    int64_t n_items;
+    int64_t pair_cap;
+};
+
+// ---------------------------------------------------------------------------
+// records
+// ---------------------------------------------------------------------------
+// Render record of one (view, surfel) item, 4 x float4:
+//   r0 = (m0, xc), r1 = (m1, yc), r2 = (m2, det), r3 = (o, z, k2, s)
+// s = 2^-e is the exact rescale applied to adj(T') (and det).
+// m0..m2: rows of adj(T') (power-of-two rescaled), T' the homogeneous
+// transform expressed about the local pixel origin (xc, yc); for a pixel
+// point X = (x - xc, y - yc, 1): c = (m0.X, m1.X, m2.X), (u, v) = c01 / c2,
+// hit depth = det / c2.
+struct alignas(16) BinRec {
+    float A, B, C, D, E, F;  // conic of the binning cutoff, local coordinates
+    float X0, Y0, hx, hy;    // ellipse centre and half extents (local)
+    float xc, yc;            // local origin (pixels)
+    int16_t px0, px1, py0, py1;  // SnugBox pixel-centre range (inclusive)
+    int16_t tx0, tx1, ty0, ty1;  // outer tile rectangle of the bin mode
+    int32_t flags;           // BR_VISIBLE | BR_UNBOUNDED
+    int32_t pad[3];
+};
+static_assert(sizeof(BinRec) == 80, "BinRec layout");
+enum { BR_VISIBLE = 1, BR_UNBOUNDED = 2 };
+
+// status block at the head of the workspace; everything from `counters` on
+// is cleared at the start of each frame, `err` only by fss_read_status
+struct Status {
+    int32_t err;           // ERR_CAPACITY | ERR_TIMEOUT
+    int32_t pad0;
+    int64_t pairs_needed;  // pairs of the last binning (the paper's RN-Total)
+    uint64_t counters[8];  // 0 evaluations, 1 contributions, 2 pixels stopped early
+    uint32_t nvis;         // bounded visible items listed by k_project
+    uint32_t work;         // persistent work-queue head
+    uint32_t nslot;        // surfels visible in at least one view (gradient slots)
+    uint32_t pad2;
+    uint32_t unb_cnt[FSS_MAX_CAMS];  // unbounded items per view
+};
+enum { ERR_CAPACITY = 1, ERR_TIMEOUT = 2 };
+constexpr size_t STATUS_CLEAR_OFF = 16;  // offsetof(Status, counters)
+
+// ---------------------------------------------------------------------------
+// workspace layout (host computed, identical for every call of a frame)
+// ---------------------------------------------------------------------------
+enum Region {
+    REG_STATUS = 0,
+    REG_REC = 1,
+    REG_BINREC = 2,
+    REG_COUNT = 3,
+    REG_RANGES = 4,
+    REG_LIST = 5,
+    REG_COUNTERS = 6,
+    REG_TILECNT = 7,
+    REG_SORTTMP = 8,
+    REG_GRAD_ITEM = 9,
+    REG_FEAT_ACC = 10,
+    REG_DOTS = 11,
+    REG_VIS = 12,
+    REG_UNB = 13,
+    REG_SLOT = 14,   // int32 [N]: gradient slot of each surfel, -1 if culled in every view
+    REG_COUNT_ALL
+};
+
+struct Layout {
+    size_t off[REG_COUNT_ALL];
+    size_t size[REG_COUNT_ALL];
+    size_t total;
+};
+
+constexpr int GRAD_STRIDE = 16;  // floats per item in the geometric gradient buffer
+
+// view that owns global tile t (views are laid out by increasing tile_off)
+__device__ __forceinline__ int view_of_tile(const Cams& cams, int t) {
+    int lo = 0, hi = cams.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cams.c[mid].tile_off <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace fss

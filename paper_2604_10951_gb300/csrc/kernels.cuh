@@ -1,0 +1,89 @@
+// Kernel declarations shared between the translation units of the library.
+#pragma once
+
+#include "fss_internal.cuh"
+
+namespace fss {
+
+constexpr int SORT_CAP = 4096;  // longest tile list sorted in shared memory
+
+__global__ void k_project(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
+                          const float* __restrict__ means, const float* __restrict__ scales,
+                          const float* __restrict__ quats, const float* __restrict__ opac, float4* __restrict__ rec,
+                          BinRec* __restrict__ binrec, uint32_t* __restrict__ count, uint32_t* __restrict__ tile_cnt,
+                          uint32_t* __restrict__ vis_list, uint32_t* __restrict__ unb_list,
+                          int32_t* __restrict__ splat_slot, Status* __restrict__ st);
+__global__ void k_count(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
+                        const BinRec* __restrict__ binrec, const uint32_t* __restrict__ vis_list,
+                        uint32_t* __restrict__ count, uint32_t* __restrict__ tile_cnt, const Status* __restrict__ st);
+__global__ void k_scan(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
+                       uint32_t* __restrict__ tile_cnt, int2* __restrict__ ranges, Status* __restrict__ st);
+__global__ void k_emit(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
+                       const BinRec* __restrict__ binrec, const uint32_t* __restrict__ vis_list,
+                       uint32_t* __restrict__ cursor, uint32_t* __restrict__ list, const Status* __restrict__ st);
+__global__ void k_tile_sort(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
+                            const float4* __restrict__ rec, const int2* __restrict__ ranges,
+                            uint32_t* __restrict__ list, const uint32_t* __restrict__ unb_list,
+                            uint64_t* __restrict__ scratch, const Status* __restrict__ st);
+
+// forward render arguments (one struct so the template instances share a
+// signature)
+struct FwdArgs {
+    const float4* rec;
+    const int2* ranges;
+    const uint32_t* list;
+    const float* rgb;
+    const void* feats;
+    void* out_feat;
+    float* out_rgb;
+    float* out_T;
+    int32_t* out_ids;
+    int32_t* saved_pos;  // [pix, K]
+    float* saved_w;      // [pix, K]
+    int32_t* saved_nstop;  // [pix]
+    Status* st;
+    int persistent;
+};
+
+// launchers (defined in render_fwd.cu / render_bwd.cu); return a cudaError_t
+cudaError_t launch_render_forward(const Cams& cams, const RParams& P, const FwdArgs& a, int num_sms,
+                                  cudaStream_t stream);
+
+struct BwdArgs {
+    const float4* rec;
+    const int2* ranges;
+    const uint32_t* list;
+    const float* rgb;
+    const void* feats;
+    const int32_t* saved_pos;
+    const float* saved_w;
+    const int32_t* saved_nstop;
+    const float* out_T;
+    const void* d_feat;
+    const float* d_rgb;
+    const float* d_T;
+    float* dots;        // [pix, K] c_i . dL/dF for the selected surfels
+    float* grad_item;   // [n_cams * N, GRAD_STRIDE] per (view, slot)
+    float* feat_acc;    // [N, C] f32 accumulation per slot
+    const int32_t* splat_slot;  // [N]
+    const float* means;
+    const float* scales;
+    const float* quats;
+    const float* opac;
+    float* g_means;
+    float* g_scales;
+    float* g_quats;
+    float* g_opac;
+    float* g_rgb;
+    void* g_feat;
+    Status* st;
+};
+
+cudaError_t launch_render_backward(const Cams& cams, const RParams& P, const BwdArgs& a, int num_sms,
+                                   cudaStream_t stream);
+
+cudaError_t launch_loss(int64_t n_pix, int C, int dtype, const void* F, const float* rgb, const void* Ft,
+                        const float* rgbt, float wf, float wc, void* dF, float* drgb, double* loss, int num_sms,
+                        cudaStream_t s);
+
+}  // namespace fss

@@ -1,0 +1,520 @@
+// Projection and Precise Tile Intersection binning (Sec. 3.2) for sm_103a.
+//
+// k_project   one thread per (view, surfel) item: homogeneous transform T,
+//             its adjugate about the projected centre, opacity-aware cutoff,
+//             screen conic, SnugBox pixel range; appends visible items to a
+//             compact list (unbounded conics to a per-view list instead).
+// k_count     one warp per visible item: AccuTile per-row (or per-column)
+//             tile intervals, pair counts per tile (fire-and-forget adds).
+// k_scan      per-tile exclusive scan -> tile ranges, total pairs, capacity.
+// k_emit      one warp per visible item: writes the item into a slot of each
+//             of its tiles (slot order is arbitrary; the per-tile sort
+//             restores a total order).
+//
+// Every tile decision is taken in binary32 with the fixed operation order
+// that the FP64 checker's binning mirror also follows, so tile lists compare
+// bit for bit.  This translation unit is compiled with -fmad=false and
+// spells each rounding with an _rn intrinsic, so no multiply-add is fused.
+#include "fss_internal.cuh"
+#include "kernels.cuh"
+
+namespace fss {
+
+namespace {
+
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fdv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fq(float a) { return __fsqrt_rn(a); }
+
+// (R v)_r = (R_r0 v0 + R_r1 v1) + R_r2 v2
+__device__ __forceinline__ void mvec(const float* R, const float v[3], float o[3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) o[r] = fa(fa(fm(R[3 * r], v[0]), fm(R[3 * r + 1], v[1])), fm(R[3 * r + 2], v[2]));
+}
+
+__device__ __forceinline__ void crossf(const float a[3], const float b[3], float o[3]) {
+    o[0] = fs(fm(a[1], b[2]), fm(a[2], b[1]));
+    o[1] = fs(fm(a[2], b[0]), fm(a[0], b[2]));
+    o[2] = fs(fm(a[0], b[1]), fm(a[1], b[0]));
+}
+
+// Q_ab = (m0_a m0_b + m1_a m1_b) - kk (m2_a m2_b), (A,B,C,D,E,F) = (Q00,Q01,Q11,Q02,Q12,Q22)
+__device__ __forceinline__ void conic(const float m[9], float kk, float q[6]) {
+    const int ia[6] = {0, 0, 1, 0, 1, 2}, ib[6] = {0, 1, 1, 2, 2, 2};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const int a = ia[k], b = ib[k];
+        const float s = fa(fm(m[a], m[b]), fm(m[3 + a], m[3 + b]));
+        const float t = fm(kk, fm(m[6 + a], m[6 + b]));
+        q[k] = fs(s, t);
+    }
+}
+
+// centre and half extents of the ellipse q <= 0; false if it is empty
+__device__ __forceinline__ bool ellipse(const float q[6], float& X0, float& Y0, float& hx, float& hy) {
+    const float A = q[0], B = q[1], C = q[2], D = q[3], E = q[4], F = q[5];
+    const float g = fs(fm(A, C), fm(B, B));
+    X0 = fdv(fs(fm(B, E), fm(C, D)), g);
+    Y0 = fdv(fs(fm(B, D), fm(A, E)), g);
+    const float Fp = fa(fa(F, fm(D, X0)), fm(E, Y0));
+    if (!(Fp < 0.0f)) return false;
+    const float nF = -Fp;
+    hx = fq(fdv(fm(nF, C), g));
+    hy = fq(fdv(fm(nF, A), g));
+    return true;
+}
+
+// pixel indices whose centres lie in [lo + 0.5, hi + 0.5], clipped to [0, n-1]
+__device__ __forceinline__ bool pix_range(float lo, float hi, int n, int& a, int& b) {
+    const float fl = ceilf(lo), fh = floorf(hi);
+    if (!(fl <= fh)) return false;
+    if (fh < 0.0f || fl > (float)(n - 1)) return false;
+    a = fl < 0.0f ? 0 : (int)fl;
+    b = fh > (float)(n - 1) ? n - 1 : (int)fh;
+    return a <= b;
+}
+
+// AccuTile, outer loop over tile rows: tile-column interval of row ty.  The
+// strip's extreme abscissae are the ellipse's left/right tangent points when
+// these fall inside the strip, else the roots of
+// A x^2 + 2(B y + D) x + (C y^2 + 2 E y + F) = 0 at the nearer strip edge.
+__device__ __forceinline__ bool accu_row(const BinRec& r, int ts, int ty, int& ta, int& tb) {
+    const int ra = max(ty * ts, (int)r.py0), rb = min(ty * ts + ts - 1, (int)r.py1);
+    if (ra > rb) return false;
+    const float Ya = fs(fa((float)ra, 0.5f), r.yc), Yb = fs(fa((float)rb, 0.5f), r.yc);
+    float ext[2];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const float Xs = side == 0 ? fs(r.X0, r.hx) : fa(r.X0, r.hx);
+        const float t = fa(fm(r.B, Xs), r.E);
+        const float Yt = fdv(-t, r.C);
+        if (Yt >= Ya && Yt <= Yb) { ext[side] = Xs; continue; }
+        const float Y = Yt < Ya ? Ya : Yb;
+        const float bb = fa(fm(r.B, Y), r.D);
+        const float cc = fa(fa(fm(fm(r.C, Y), Y), fm(fm(2.0f, r.E), Y)), r.F);
+        float disc = fs(fm(bb, bb), fm(r.A, cc));
+        if (disc < 0.0f) disc = 0.0f;
+        const float sq = fq(disc), nb = -bb;
+        ext[side] = fdv(side == 0 ? fs(nb, sq) : fa(nb, sq), r.A);
+    }
+    const float fl = ceilf(fs(fa(ext[0], r.xc), 0.5f)), fh = floorf(fs(fa(ext[1], r.xc), 0.5f));
+    if (!(fl <= fh)) return false;
+    if (fh < (float)r.px0 || fl > (float)r.px1) return false;
+    const int a = fl < (float)r.px0 ? r.px0 : (int)fl;
+    const int b = fh > (float)r.px1 ? r.px1 : (int)fh;
+    ta = a / ts;
+    tb = b / ts;
+    return true;
+}
+
+// AccuTile, outer loop over tile columns: tile-row interval of column tx
+__device__ __forceinline__ bool accu_col(const BinRec& r, int ts, int tx, int& ta, int& tb) {
+    const int ca = max(tx * ts, (int)r.px0), cb = min(tx * ts + ts - 1, (int)r.px1);
+    if (ca > cb) return false;
+    const float Xa = fs(fa((float)ca, 0.5f), r.xc), Xb = fs(fa((float)cb, 0.5f), r.xc);
+    float ext[2];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const float Ys = side == 0 ? fs(r.Y0, r.hy) : fa(r.Y0, r.hy);
+        const float t = fa(fm(r.B, Ys), r.D);
+        const float Xt = fdv(-t, r.A);
+        if (Xt >= Xa && Xt <= Xb) { ext[side] = Ys; continue; }
+        const float X = Xt < Xa ? Xa : Xb;
+        const float bb = fa(fm(r.B, X), r.E);
+        const float cc = fa(fa(fm(fm(r.A, X), X), fm(fm(2.0f, r.D), X)), r.F);
+        float disc = fs(fm(bb, bb), fm(r.C, cc));
+        if (disc < 0.0f) disc = 0.0f;
+        const float sq = fq(disc), nb = -bb;
+        ext[side] = fdv(side == 0 ? fs(nb, sq) : fa(nb, sq), r.C);
+    }
+    const float fl = ceilf(fs(fa(ext[0], r.yc), 0.5f)), fh = floorf(fs(fa(ext[1], r.yc), 0.5f));
+    if (!(fl <= fh)) return false;
+    if (fh < (float)r.py0 || fl > (float)r.py1) return false;
+    const int a = fl < (float)r.py0 ? r.py0 : (int)fl;
+    const int b = fh > (float)r.py1 ? r.py1 : (int)fh;
+    ta = a / ts;
+    tb = b / ts;
+    return true;
+}
+
+// Outer lines of an item's tile set: rows if the tile span in y does not
+// exceed the span in x (or for the box modes), else columns (SnugBox's
+// "smaller span" traversal).
+struct Lines {
+    int n;          // number of outer lines
+    int first;      // first outer coordinate
+    bool rows;      // outer loop over tile rows
+    bool accurate;  // per-line AccuTile interval (else the full rectangle)
+};
+
+__device__ __forceinline__ Lines lines_of(const BinRec& r, int bin_mode) {
+    Lines L;
+    const int xs = r.tx1 - r.tx0 + 1, ys = r.ty1 - r.ty0 + 1;
+    L.accurate = bin_mode == FSS_BIN_ACCU;
+    L.rows = !L.accurate || ys <= xs;
+    L.n = L.rows ? ys : xs;
+    L.first = L.rows ? r.ty0 : r.tx0;
+    return L;
+}
+
+// inner tile interval [a, b] of outer line `o` (an absolute tile row/column)
+__device__ __forceinline__ bool line_interval(const BinRec& r, const Lines& L, int ts, int o, int& a, int& b) {
+    if (!L.accurate) {
+        a = L.rows ? r.tx0 : r.ty0;
+        b = L.rows ? r.tx1 : r.ty1;
+        return true;
+    }
+    return L.rows ? accu_row(r, ts, o, a, b) : accu_col(r, ts, o, a, b);
+}
+
+__device__ __forceinline__ int view_of_item(int64_t item, int64_t N) { return (int)(item / N); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// k_project
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_project(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
+                                                 const float* __restrict__ means, const float* __restrict__ scales,
+                                                 const float* __restrict__ quats, const float* __restrict__ opac,
+                                                 float4* __restrict__ rec, BinRec* __restrict__ binrec,
+                                                 uint32_t* __restrict__ count, uint32_t* __restrict__ tile_cnt,
+                                                 uint32_t* __restrict__ vis_list, uint32_t* __restrict__ unb_list,
+                                                 int32_t* __restrict__ splat_slot, Status* __restrict__ st) {
+    const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // clear the per-tile counters of this frame (k_count runs after this kernel)
+    for (int64_t t = item; t < cams.total_tiles; t += (int64_t)gridDim.x * blockDim.x) tile_cnt[t] = 0u;
+    if (st->err) return;
+    bool vis = false, unb = false;
+    int view = 0;
+    if (item < P.n_items) {
+        view = view_of_item(item, P.N);
+        const int64_t s = item - (int64_t)view * P.N;
+        const CamDev& cam = cams.c[view];
+        BinRec br;
+        br.flags = 0;
+        br.px0 = br.py0 = br.tx0 = br.ty0 = 1;
+        br.px1 = br.py1 = br.tx1 = br.ty1 = 0;
+        br.A = br.B = br.C = br.D = br.E = br.F = 0.0f;
+        br.X0 = br.Y0 = br.hx = br.hy = br.xc = br.yc = 0.0f;
+        br.pad[0] = br.pad[1] = br.pad[2] = 0;
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
+        do {
+            // S1
+            const float qw = quats[4 * s], qx = quats[4 * s + 1], qy = quats[4 * s + 2], qz = quats[4 * s + 3];
+            const float n2 = fa(fa(fa(fm(qw, qw), fm(qx, qx)), fm(qy, qy)), fm(qz, qz));
+            const float o = opac[s];
+            r3.x = o;
+            if (!(n2 > 0.0f)) break;
+            const float nn = fq(n2);
+            const float w = fdv(qw, nn), x = fdv(qx, nn), y = fdv(qy, nn), z = fdv(qz, nn);
+            // S2
+            float tu[3], tv[3];
+            tu[0] = fs(1.0f, fm(2.0f, fa(fm(y, y), fm(z, z))));
+            tu[1] = fm(2.0f, fa(fm(x, y), fm(w, z)));
+            tu[2] = fm(2.0f, fs(fm(x, z), fm(w, y)));
+            tv[0] = fm(2.0f, fs(fm(x, y), fm(w, z)));
+            tv[1] = fs(1.0f, fm(2.0f, fa(fm(x, x), fm(z, z))));
+            tv[2] = fm(2.0f, fa(fm(y, z), fm(w, x)));
+            // S3
+            const float su = scales[2 * s], sv = scales[2 * s + 1];
+            float e[3], au[3], av[3], pc[3];
+            mvec(cam.R, tu, e);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) au[i] = fm(su, e[i]);
+            mvec(cam.R, tv, e);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) av[i] = fm(sv, e[i]);
+            const float pm[3] = {means[3 * s], means[3 * s + 1], means[3 * s + 2]};
+            mvec(cam.R, pm, e);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) pc[i] = fa(e[i], cam.t[i]);
+            // S4, S5
+            r3.y = pc[2];
+            if (!(pc[2] > cam.near_plane)) break;
+            if (!(o >= P.alpha_min)) break;
+            // S6: k^2 = 2 ln(o / alpha_min), rounded once to binary32
+            const float k2 = (float)(2.0 * log(__ddiv_rn((double)o, (double)P.alpha_min)));
+            r3.z = k2;
+            // S7
+            float c[3][3];
+            const float* src[3] = {au, av, pc};
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                c[j][0] = fa(fm(cam.fx, src[j][0]), fm(cam.cx, src[j][2]));
+                c[j][1] = fa(fm(cam.fy, src[j][1]), fm(cam.cy, src[j][2]));
+                c[j][2] = src[j][2];
+            }
+            // S8
+            const float xc = fdv(c[2][0], c[2][2]);
+            const float yc = fdv(c[2][1], c[2][2]);
+            // S9
+            float d[3][3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                d[j][0] = fs(c[j][0], fm(xc, c[j][2]));
+                d[j][1] = fs(c[j][1], fm(yc, c[j][2]));
+                d[j][2] = c[j][2];
+            }
+            // S10
+            float m[9];
+            crossf(d[1], d[2], &m[0]);
+            crossf(d[2], d[0], &m[3]);
+            crossf(d[0], d[1], &m[6]);
+            // S11
+            float det = fa(fa(fm(d[0][0], m[0]), fm(d[0][1], m[1])), fm(d[0][2], m[2]));
+            // S12: edge-on cull
+            const float pn = fq(fa(fa(fm(pc[0], pc[0]), fm(pc[1], pc[1])), fm(pc[2], pc[2])));
+            const float lim = fm(1e-3f, fm(fm(fm(fm(cam.fx, cam.fy), su), sv), pn));
+            if (!(fabsf(det) > lim)) break;
+            // S13: exact power-of-two rescale
+            float mx = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) mx = fabsf(m[i]) > mx ? fabsf(m[i]) : mx;
+            if (!(mx > 0.0f)) break;
+            int ex;
+            frexpf(mx, &ex);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) m[i] = ldexpf(m[i], -ex);
+            det = ldexpf(det, -ex);
+            r3.w = ldexpf(1.0f, -ex);  // the rescale, needed by the backward pass
+            r0 = make_float4(m[0], m[1], m[2], xc);
+            r1 = make_float4(m[3], m[4], m[5], yc);
+            r2 = make_float4(m[6], m[7], m[8], det);
+            br.xc = xc;
+            br.yc = yc;
+            // S14
+            const float kb = fm(k2, 1.0009765625f);
+            float q[6];
+            conic(m, kb, q);
+            br.A = q[0]; br.B = q[1]; br.C = q[2]; br.D = q[3]; br.E = q[4]; br.F = q[5];
+            int px0, px1, py0, py1;
+            // S15
+            const float g = fs(fm(q[0], q[2]), fm(q[1], q[1]));
+            if (!(q[0] > 0.0f && g > 0.0f)) {
+                br.flags |= BR_UNBOUNDED;
+                px0 = 0; px1 = cam.W - 1; py0 = 0; py1 = cam.H - 1;
+            } else {
+                // S16
+                if (!ellipse(q, br.X0, br.Y0, br.hx, br.hy)) break;
+                // S17
+                if (!pix_range(fs(fa(fs(br.X0, br.hx), xc), 0.5f), fs(fa(fa(br.X0, br.hx), xc), 0.5f), cam.W, px0, px1))
+                    break;
+                if (!pix_range(fs(fa(fs(br.Y0, br.hy), yc), 0.5f), fs(fa(fa(br.Y0, br.hy), yc), 0.5f), cam.H, py0, py1))
+                    break;
+            }
+            br.flags |= BR_VISIBLE;
+            br.px0 = (int16_t)px0; br.px1 = (int16_t)px1; br.py0 = (int16_t)py0; br.py1 = (int16_t)py1;
+            // S18
+            const int ts = P.ts;
+            int tx0 = px0 / ts, tx1 = px1 / ts, ty0 = py0 / ts, ty1 = py1 / ts;
+            // S19
+            if (P.bin_mode == FSS_BIN_AABB && !(br.flags & BR_UNBOUNDED)) {
+                float k2a = (float)(2.0 * log(__ddiv_rn(1.0, (double)P.alpha_min)));
+                if (kb > k2a) k2a = kb;
+                float qa[6], X0, Y0, hx, hy;
+                conic(m, k2a, qa);
+                const float ga = fs(fm(qa[0], qa[2]), fm(qa[1], qa[1]));
+                int ax0 = 0, ax1 = cam.W - 1, ay0 = 0, ay1 = cam.H - 1;
+                if (qa[0] > 0.0f && ga > 0.0f && ellipse(qa, X0, Y0, hx, hy)) {
+                    const float h = hx > hy ? hx : hy;
+                    if (!pix_range(fs(fa(fs(X0, h), xc), 0.5f), fs(fa(fa(X0, h), xc), 0.5f), cam.W, ax0, ax1)) {
+                        ax0 = px0; ax1 = px1;
+                    }
+                    if (!pix_range(fs(fa(fs(Y0, h), yc), 0.5f), fs(fa(fa(Y0, h), yc), 0.5f), cam.H, ay0, ay1)) {
+                        ay0 = py0; ay1 = py1;
+                    }
+                }
+                ax0 = min(ax0, px0); ax1 = max(ax1, px1);
+                ay0 = min(ay0, py0); ay1 = max(ay1, py1);
+                tx0 = ax0 / ts; tx1 = ax1 / ts; ty0 = ay0 / ts; ty1 = ay1 / ts;
+            }
+            br.tx0 = (int16_t)tx0; br.tx1 = (int16_t)tx1; br.ty0 = (int16_t)ty0; br.ty1 = (int16_t)ty1;
+        } while (0);
+        vis = (br.flags & BR_VISIBLE) && !(br.flags & BR_UNBOUNDED);
+        unb = (br.flags & BR_VISIBLE) && (br.flags & BR_UNBOUNDED);
+        if (vis || unb) {  // records of culled items are never read
+            float4* rr = rec + 4 * item;
+            rr[0] = r0; rr[1] = r1; rr[2] = r2; rr[3] = r3;
+            binrec[item] = br;
+            count[item] = 0u;
+            // one gradient slot per surfel visible in any view (-1 -> -2 claims it)
+            if (atomicCAS(&splat_slot[s], -1, -2) == -1) splat_slot[s] = (int32_t)atomicAdd(&st->nslot, 1u);
+        }
+    }
+    // warp-aggregated append of bounded visible items (unordered)
+    const unsigned mvis = __ballot_sync(0xffffffffu, vis);
+    if (mvis) {
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(mvis) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(&st->nvis, (uint32_t)__popc(mvis));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (vis) vis_list[base + __popc(mvis & ((1u << lane) - 1u))] = (uint32_t)item;
+    }
+    if (unb) {
+        const uint32_t k = atomicAdd(&st->unb_cnt[view], 1u);
+        unb_list[(int64_t)view * P.N + k] = (uint32_t)item;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_count: one warp per bounded visible item
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_count(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
+                                               const BinRec* __restrict__ binrec, const uint32_t* __restrict__ vis_list,
+                                               uint32_t* __restrict__ count, uint32_t* __restrict__ tile_cnt,
+                                               const Status* __restrict__ st) {
+    if (st->err) return;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nvis = st->nvis;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t wi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wi < nvis; wi += warps) {
+        const uint32_t item = vis_list[wi];
+        const BinRec r = binrec[item];
+        const CamDev& cam = cams.c[view_of_item(item, P.N)];
+        const Lines L = lines_of(r, P.bin_mode);
+        uint32_t cnt = 0;
+        for (int li = lane; li < L.n; li += 32) {
+            const int o = L.first + li;
+            int a, b;
+            if (!line_interval(r, L, P.ts, o, a, b)) continue;
+            for (int k = a; k <= b; ++k) {
+                const int tx = L.rows ? k : o, ty = L.rows ? o : k;
+                atomicAdd(&tile_cnt[cam.tile_off + ty * cam.tiles_x + tx], 1u);
+            }
+            cnt += (uint32_t)(b - a + 1);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+        if (lane == 0) count[item] = cnt;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_scan: one CTA; per-tile totals (bounded pairs + the view's unbounded
+// items) -> exclusive scan -> ranges; tile_cnt becomes the emit cursor
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
+                                               uint32_t* __restrict__ tile_cnt, int2* __restrict__ ranges,
+                                               Status* __restrict__ st) {
+    __shared__ uint32_t warp_tot[32];
+    __shared__ uint64_t carry_s;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nt = cams.total_tiles;
+    constexpr int ITEMS = 4;
+    for (int base = 0; base < nt; base += 1024 * ITEMS) {
+        uint32_t v[ITEMS], bounded[ITEMS];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            const int t = base + threadIdx.x * ITEMS + k;
+            uint32_t c = 0, b = 0;
+            if (t < nt) {
+                b = tile_cnt[t];
+                c = b + st->unb_cnt[view_of_tile(cams, t)];
+            }
+            v[k] = c;
+            bounded[k] = b;
+            sum += c;
+        }
+        // block exclusive scan of per-thread sums
+        uint32_t incl = sum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane == 31) warp_tot[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            uint32_t w = warp_tot[lane], wi = w;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, wi, off);
+                if (lane >= off) wi += y;
+            }
+            warp_tot[lane] = wi - w;  // exclusive
+        }
+        __syncthreads();
+        uint64_t run = carry_s + warp_tot[wid] + (incl - sum);
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            const int t = base + threadIdx.x * ITEMS + k;
+            if (t < nt) {
+                const uint64_t s0 = run;
+                run += v[k];
+                const bool fits = run <= (uint64_t)P.pair_cap;
+                ranges[t] = make_int2(fits ? (int)s0 : 0, fits ? (int)run : 0);
+                tile_cnt[t] = fits ? (uint32_t)s0 : 0u;  // emit cursor
+                (void)bounded[k];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) carry_s = run;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        st->pairs_needed = (int64_t)carry_s;
+        if (carry_s > (uint64_t)P.pair_cap) st->err |= ERR_CAPACITY;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_emit: one warp per bounded visible item; the warp's lanes take the
+// flattened (line, tile) pairs so a wide item costs few rounds
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
+                                              const BinRec* __restrict__ binrec, const uint32_t* __restrict__ vis_list,
+                                              uint32_t* __restrict__ cursor, uint32_t* __restrict__ list,
+                                              const Status* __restrict__ st) {
+    if (st->err) return;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nvis = st->nvis;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t wi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wi < nvis; wi += warps) {
+        const uint32_t item = vis_list[wi];
+        const BinRec r = binrec[item];
+        const CamDev& cam = cams.c[view_of_item(item, P.N)];
+        const Lines L = lines_of(r, P.bin_mode);
+        for (int lb = 0; lb < L.n; lb += 32) {
+            const int li = lb + lane;
+            int a = 0, b = -1;
+            if (li < L.n && !line_interval(r, L, P.ts, L.first + li, a, b)) { a = 0; b = -1; }
+            const int len = b - a + 1;
+            int incl = len;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int k0 = 0; k0 < total; k0 += 32) {
+                const int k = k0 + lane;
+                // owner lane: the first lane whose inclusive count exceeds k
+                int lo = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int probe = __shfl_sync(0xffffffffu, incl, lo + step - 1);
+                    if (probe <= k) lo += step;
+                }
+                const int own_incl = __shfl_sync(0xffffffffu, incl, lo);
+                const int own_len = __shfl_sync(0xffffffffu, len, lo);
+                const int own_a = __shfl_sync(0xffffffffu, a, lo);
+                if (k < total) {
+                    const int inner = own_a + (k - (own_incl - own_len));
+                    const int o = L.first + lb + lo;
+                    const int tx = L.rows ? inner : o, ty = L.rows ? o : inner;
+                    const uint32_t pos = atomicAdd(&cursor[cam.tile_off + ty * cam.tiles_x + tx], 1u);
+                    if (pos < (uint32_t)P.pair_cap) list[pos] = item;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace fss

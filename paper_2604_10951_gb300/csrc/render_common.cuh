@@ -1,0 +1,110 @@
+// Device helpers shared by the forward and backward render kernels.  The
+// per-evaluation arithmetic lives here once, so the backward replay takes
+// exactly the forward's skip decisions.
+#pragma once
+
+#include "fss_internal.cuh"
+
+namespace fss {
+
+constexpr int BATCH = 256;   // staged records per batch (Top-K kernels)
+constexpr int FBATCH = 64;   // staged records + feature rows per batch (full kernels)
+constexpr float NEG_HALF_LOG2E = -0.72134752044448170f;  // exp(-r/2) = 2^(r * this)
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Ray-splat intersection and opacity of one staged surfel at pixel point
+// (pxf, pyf) (Eq. 2 density, alpha before the clamp).  Returns false when
+// the surfel is skipped (alpha below alpha_min, hit at or behind the near
+// plane, or a non-finite intersection).
+struct Hit {
+    float X, Y, u, v, inv, alpha_raw;
+};
+
+__device__ __forceinline__ bool eval_splat(const float4& A, const float4& B, const float4& Cq, float o, float pxf,
+                                           float pyf, float alpha_min, float near_plane, Hit& h) {
+    h.X = pxf - A.w;
+    h.Y = pyf - B.w;
+    const float c0 = fmaf(A.x, h.X, fmaf(A.y, h.Y, A.z));
+    const float c1 = fmaf(B.x, h.X, fmaf(B.y, h.Y, B.z));
+    const float c2 = fmaf(Cq.x, h.X, fmaf(Cq.y, h.Y, Cq.z));
+    h.inv = rcp_approx(c2);
+    h.u = c0 * h.inv;
+    h.v = c1 * h.inv;
+    const float rho = fmaf(h.u, h.u, h.v * h.v);
+    h.alpha_raw = o * ex2_approx(NEG_HALF_LOG2E * rho);
+    return (h.alpha_raw >= alpha_min) && (Cq.w * h.inv > near_plane);
+}
+
+template <typename FT>
+struct FeatVec;
+
+template <>
+struct FeatVec<float> {
+    static constexpr int E = 4;  // channels per 16-byte load
+    __device__ static __forceinline__ void load(const float* p, float* o) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+    __device__ static __forceinline__ float one(const float* p) { return __ldg(p); }
+};
+
+template <>
+struct FeatVec<__nv_bfloat16> {
+    static constexpr int E = 8;
+    __device__ static __forceinline__ void load(const __nv_bfloat16* p, float* o) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            o[2 * k] = __uint_as_float(w[k] << 16);
+            o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+        }
+    }
+    __device__ static __forceinline__ float one(const __nv_bfloat16* p) {
+        return __uint_as_float(((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p))) << 16);
+    }
+};
+
+// store E channels (E = 4 or 8) in the output dtype
+template <int E>
+__device__ __forceinline__ void store_vec(void* out, int64_t elem, const float* acc, int out_dtype) {
+    if (out_dtype == FSS_F32) {
+        float4* p = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + elem);
+#pragma unroll
+        for (int k = 0; k < E / 4; ++k) p[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+    } else {
+        uint32_t w[E / 2];
+#pragma unroll
+        for (int k = 0; k < E / 2; ++k) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(acc[2 * k], acc[2 * k + 1]);
+            w[k] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        __nv_bfloat16* b = reinterpret_cast<__nv_bfloat16*>(out) + elem;
+        if (E == 8) *reinterpret_cast<uint4*>(b) = make_uint4(w[0], w[1], w[2], w[3]);
+        else *reinterpret_cast<uint2*>(b) = make_uint2(w[0], w[1]);
+    }
+}
+
+__device__ __forceinline__ void warp_count(uint64_t* ctr, uint32_t v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(reinterpret_cast<unsigned long long*>(ctr), (unsigned long long)v);
+}
+
+// vector reduction into global memory (sm_90+): four floats, one request
+__device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+}  // namespace fss

@@ -1,0 +1,413 @@
+// Forward render for sm_103a: front-to-back alpha compositing of the
+// depth-sorted tile lists (Sec. 3.1, Eq. 2) with Top-K Hard Selection before
+// the C-channel feature accumulation (Sec. 3.4, Eq. 7).
+//
+// One CTA renders one TS x TS tile, one thread per pixel.
+// Phase 1: batches of BATCH surfel records are staged in shared memory by the
+//   CTA; every thread intersects its pixel ray with each staged surfel,
+//   composites colour and transmittance and keeps its K largest blending
+//   weights in a register min-heap (ties keep the earlier surfel).  A warp
+//   leaves the batch loop as soon as all its pixels have stopped; the CTA
+//   stops staging once every pixel has.
+// Phase 2: the CTA gathers only the K selected feature rows per pixel
+//   (16-byte loads: 8 bf16 or 4 f32 channels), weights them in FP32 and writes
+//   channel-last output with consecutive lanes on consecutive 16-byte chunks.
+// The full-accumulation kernel (K = 0, the plain path) instead stages the
+// feature rows of every batch and accumulates all C channels per contributor
+// in registers.
+//
+// The accumulation is a sparse gather-weighted sum, not a dense contraction,
+// so no tensor cores are involved.
+#include "fss_internal.cuh"
+#include "kernels.cuh"
+#include "render_common.cuh"
+
+#include <algorithm>
+#include <climits>
+
+namespace fss {
+
+namespace {
+
+// next tile of this CTA: its own index, or the head of the work queue
+__device__ __forceinline__ int next_tile(const FwdArgs& a, int* s_tile, bool first) {
+    if (!a.persistent) return first ? (int)blockIdx.x : INT_MAX;
+    __syncthreads();
+    if (threadIdx.x == 0) *s_tile = (int)atomicAdd(&a.st->work, 1u);
+    __syncthreads();
+    return *s_tile;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Top-K kernel
+// ---------------------------------------------------------------------------
+template <int TS, int KCAP, typename FT>
+__global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__ Cams cams,
+                                                         const __grid_constant__ RParams P, const FwdArgs a) {
+    constexpr int NT = TS * TS;
+    constexpr int PC = (NT < 65536 / (KCAP * 8 + 4)) ? NT : 65536 / (KCAP * 8 + 4);  // phase-2 pixel chunk
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4* s_r0 = reinterpret_cast<float4*>(smem);
+    float4* s_r1 = s_r0 + BATCH;
+    float4* s_r2 = s_r1 + BATCH;
+    float* s_o = reinterpret_cast<float*>(s_r2 + BATCH);
+    float* s_c0 = s_o + BATCH;
+    float* s_c1 = s_c0 + BATCH;
+    float* s_c2 = s_c1 + BATCH;
+    int32_t* s_id = reinterpret_cast<int32_t*>(smem);  // phase 2 reuse
+    float* s_w = reinterpret_cast<float*>(s_id + PC * KCAP);
+    int32_t* s_n = reinterpret_cast<int32_t*>(s_w + PC * KCAP);
+    __shared__ int s_tile;
+
+    const int tid = threadIdx.x;
+    if (a.st->err) return;
+    const int K = P.K;
+    const FT* __restrict__ feats = reinterpret_cast<const FT*>(a.feats);
+    for (int t = next_tile(a, &s_tile, true); t < cams.total_tiles; t = next_tile(a, &s_tile, false)) {
+        const int view = view_of_tile(cams, t);
+        const CamDev& cam = cams.c[view];
+        const int lt = t - cam.tile_off;
+        const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
+        const int px = tx * TS + (tid % TS), py = ty * TS + (tid / TS);
+        const bool inside = px < cam.W && py < cam.H;
+        const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
+        const int2 rg = a.ranges[t];
+        const int n = rg.y - rg.x;
+        const int64_t vbase = (int64_t)view * P.N;
+
+        float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
+        bool done = !inside;
+        int last = -1;
+        float hw[KCAP];
+        int hp[KCAP];
+#pragma unroll
+        for (int k = 0; k < KCAP; ++k) { hw[k] = 0.0f; hp[k] = INT_MAX; }
+        int hc = 0, imin = 0;
+        float wmin = 0.0f;
+        uint32_t n_eval = 0, n_contrib = 0;
+
+        for (int b0 = 0; b0 < n; b0 += BATCH) {
+            if (__syncthreads_and(done)) break;
+            const int cnt = min(BATCH, n - b0);
+            for (int j = tid; j < cnt; j += NT) {
+                const uint32_t item = a.list[rg.x + b0 + j];
+                const float4* r = a.rec + 4 * (size_t)item;
+                s_r0[j] = r[0];
+                s_r1[j] = r[1];
+                s_r2[j] = r[2];
+                s_o[j] = r[3].x;
+                const int64_t sp = (int64_t)item - vbase;
+                s_c0[j] = a.rgb[3 * sp];
+                s_c1[j] = a.rgb[3 * sp + 1];
+                s_c2[j] = a.rgb[3 * sp + 2];
+            }
+            __syncthreads();
+            if (done) continue;
+            for (int j = 0; j < cnt; ++j) {
+                ++n_eval;
+                Hit h;
+                if (!eval_splat(s_r0[j], s_r1[j], s_r2[j], s_o[j], pxf, pyf, P.alpha_min, cam.near_plane, h)) continue;
+                const float alpha = fminf(h.alpha_raw, P.alpha_max);
+                const float Tn = T * (1.0f - alpha);
+                if (Tn < P.T_min) { done = true; break; }
+                const float w = alpha * T;
+                cr = fmaf(w, s_c0[j], cr);
+                cg = fmaf(w, s_c1[j], cg);
+                cb = fmaf(w, s_c2[j], cb);
+                ++n_contrib;
+                const int pos = b0 + j;
+                // register min-heap of the K largest weights (ties: earlier wins)
+                int slot = -1;
+                if (hc < K) slot = hc++;
+                else if (w > wmin) slot = imin;
+                if (slot >= 0) {
+#pragma unroll
+                    for (int k = 0; k < KCAP; ++k)
+                        if (k == slot) { hw[k] = w; hp[k] = pos; }
+                    if (hc == K) {
+                        wmin = hw[0]; imin = 0;
+                        int pmin = hp[0];
+#pragma unroll
+                        for (int k = 1; k < KCAP; ++k) {
+                            if (k < K && (hw[k] < wmin || (hw[k] == wmin && hp[k] > pmin))) {
+                                wmin = hw[k]; imin = k; pmin = hp[k];
+                            }
+                        }
+                    }
+                }
+                T = Tn;
+                last = pos;
+                if (P.stop_rule == FSS_STOP_EXACT_TOPK && hc == K && P.alpha_max * T <= wmin) { done = true; break; }
+            }
+        }
+
+        // per-pixel outputs; Top-K entries in front-to-back order
+        const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
+        int rank[KCAP];
+#pragma unroll
+        for (int k = 0; k < KCAP; ++k) {
+            int r = 0;
+#pragma unroll
+            for (int j = 0; j < KCAP; ++j) r += (j < hc && hp[j] < hp[k]) ? 1 : 0;
+            rank[k] = r;
+        }
+        if (inside) {
+            if (a.out_rgb) {
+                a.out_rgb[3 * pix] = fmaf(T, P.bg[0], cr);
+                a.out_rgb[3 * pix + 1] = fmaf(T, P.bg[1], cg);
+                a.out_rgb[3 * pix + 2] = fmaf(T, P.bg[2], cb);
+            }
+            if (a.out_T) a.out_T[pix] = T;
+            if (a.saved_nstop) a.saved_nstop[pix] = last + 1;
+#pragma unroll
+            for (int k = 0; k < KCAP; ++k) {
+                if (k < hc) {
+                    const int64_t o = pix * K + rank[k];
+                    const int32_t id = (int32_t)((int64_t)a.list[rg.x + hp[k]] - vbase);
+                    if (a.out_ids) a.out_ids[o] = id;
+                    if (a.saved_pos) a.saved_pos[o] = hp[k];
+                    if (a.saved_w) a.saved_w[o] = hw[k];
+                }
+            }
+            for (int k = hc; k < K; ++k) {
+                const int64_t o = pix * K + k;
+                if (a.out_ids) a.out_ids[o] = -1;
+                if (a.saved_pos) a.saved_pos[o] = -1;
+                if (a.saved_w) a.saved_w[o] = 0.0f;
+            }
+        }
+        warp_count(&a.st->counters[0], n_eval);
+        warp_count(&a.st->counters[1], n_contrib);
+
+        // phase 2: gather-accumulate the selected feature rows
+        if (a.out_feat) {
+            constexpr int E = FeatVec<FT>::E;
+            const int nvec = P.C / E;
+            for (int p0 = 0; p0 < NT; p0 += PC) {
+                __syncthreads();
+                if (tid >= p0 && tid < p0 + PC) {
+                    const int q = tid - p0;
+                    s_n[q] = inside ? hc : 0;
+#pragma unroll
+                    for (int k = 0; k < KCAP; ++k) {
+                        if (k < hc) {
+                            s_id[q * KCAP + rank[k]] = (int32_t)((int64_t)a.list[rg.x + hp[k]] - vbase);
+                            s_w[q * KCAP + rank[k]] = hw[k];
+                        }
+                    }
+                }
+                __syncthreads();
+                const int npx = min(PC, NT - p0);
+                for (int it = tid; it < npx * nvec; it += NT) {
+                    const int q = it / nvec, vv = it - q * nvec;
+                    const int p = p0 + q;
+                    const int qx = tx * TS + (p % TS), qy = ty * TS + (p / TS);
+                    if (qx >= cam.W || qy >= cam.H) continue;
+                    float acc[E];
+#pragma unroll
+                    for (int e = 0; e < E; ++e) acc[e] = 0.0f;
+                    const int c = s_n[q];
+                    for (int k = 0; k < c; ++k) {
+                        const int id = s_id[q * KCAP + k];
+                        const float w = s_w[q * KCAP + k];
+                        float f[E];
+                        FeatVec<FT>::load(feats + (size_t)id * P.C + vv * E, f);
+#pragma unroll
+                        for (int e = 0; e < E; ++e) acc[e] = fmaf(w, f[e], acc[e]);
+                    }
+                    const int64_t qpix = cam.pix_off + (int64_t)qy * cam.W + qx;
+                    store_vec<E>(a.out_feat, qpix * P.C + vv * E, acc, P.out_dtype);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// full-accumulation kernel (K = 0): all contributors, all channels
+// ---------------------------------------------------------------------------
+template <int TS, int CMAX, typename FT>
+__global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__ Cams cams,
+                                                         const __grid_constant__ RParams P, const FwdArgs a) {
+    constexpr int NT = TS * TS;
+    constexpr int E = FeatVec<FT>::E;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4* s_r0 = reinterpret_cast<float4*>(smem);
+    float4* s_r1 = s_r0 + FBATCH;
+    float4* s_r2 = s_r1 + FBATCH;
+    float* s_o = reinterpret_cast<float*>(s_r2 + FBATCH);
+    float* s_c0 = s_o + FBATCH;
+    float* s_c1 = s_c0 + FBATCH;
+    float* s_c2 = s_c1 + FBATCH;
+    float* s_f = s_c2 + FBATCH;  // [FBATCH][C] f32
+    __shared__ int s_tile;
+
+    const int tid = threadIdx.x;
+    if (a.st->err) return;
+    const int C = P.C;
+    const FT* __restrict__ feats = reinterpret_cast<const FT*>(a.feats);
+    for (int t = next_tile(a, &s_tile, true); t < cams.total_tiles; t = next_tile(a, &s_tile, false)) {
+        const int view = view_of_tile(cams, t);
+        const CamDev& cam = cams.c[view];
+        const int lt = t - cam.tile_off;
+        const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
+        const int px = tx * TS + (tid % TS), py = ty * TS + (tid / TS);
+        const bool inside = px < cam.W && py < cam.H;
+        const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
+        const int2 rg = a.ranges[t];
+        const int n = rg.y - rg.x;
+        const int64_t vbase = (int64_t)view * P.N;
+
+        float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
+        float acc[CMAX];
+#pragma unroll
+        for (int c = 0; c < CMAX; ++c) acc[c] = 0.0f;
+        bool done = !inside;
+        int last = -1;
+        uint32_t n_eval = 0, n_contrib = 0;
+        const int nvec = C / E;
+
+        for (int b0 = 0; b0 < n; b0 += FBATCH) {
+            if (__syncthreads_and(done)) break;
+            const int cnt = min(FBATCH, n - b0);
+            for (int j = tid; j < cnt; j += NT) {
+                const uint32_t item = a.list[rg.x + b0 + j];
+                const float4* r = a.rec + 4 * (size_t)item;
+                s_r0[j] = r[0];
+                s_r1[j] = r[1];
+                s_r2[j] = r[2];
+                s_o[j] = r[3].x;
+                const int64_t sp = (int64_t)item - vbase;
+                s_c0[j] = a.rgb[3 * sp];
+                s_c1[j] = a.rgb[3 * sp + 1];
+                s_c2[j] = a.rgb[3 * sp + 2];
+            }
+            for (int it = tid; it < cnt * nvec; it += NT) {
+                const int j = it / nvec, vv = it - j * nvec;
+                const int64_t sp = (int64_t)a.list[rg.x + b0 + j] - vbase;
+                float f[E];
+                FeatVec<FT>::load(feats + (size_t)sp * C + vv * E, f);
+#pragma unroll
+                for (int e = 0; e < E; ++e) s_f[j * C + vv * E + e] = f[e];
+            }
+            __syncthreads();
+            if (done) continue;
+            for (int j = 0; j < cnt; ++j) {
+                ++n_eval;
+                Hit h;
+                if (!eval_splat(s_r0[j], s_r1[j], s_r2[j], s_o[j], pxf, pyf, P.alpha_min, cam.near_plane, h)) continue;
+                const float alpha = fminf(h.alpha_raw, P.alpha_max);
+                const float Tn = T * (1.0f - alpha);
+                if (Tn < P.T_min) { done = true; break; }
+                const float w = alpha * T;
+                cr = fmaf(w, s_c0[j], cr);
+                cg = fmaf(w, s_c1[j], cg);
+                cb = fmaf(w, s_c2[j], cb);
+                ++n_contrib;
+                const float4* fr = reinterpret_cast<const float4*>(s_f + j * C);
+#pragma unroll
+                for (int c4 = 0; c4 < CMAX / 4; ++c4) {
+                    if (4 * c4 < C) {
+                        const float4 f = fr[c4];
+                        acc[4 * c4] = fmaf(w, f.x, acc[4 * c4]);
+                        acc[4 * c4 + 1] = fmaf(w, f.y, acc[4 * c4 + 1]);
+                        acc[4 * c4 + 2] = fmaf(w, f.z, acc[4 * c4 + 2]);
+                        acc[4 * c4 + 3] = fmaf(w, f.w, acc[4 * c4 + 3]);
+                    }
+                }
+                T = Tn;
+                last = b0 + j;
+            }
+        }
+        if (inside) {
+            const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
+            if (a.out_rgb) {
+                a.out_rgb[3 * pix] = fmaf(T, P.bg[0], cr);
+                a.out_rgb[3 * pix + 1] = fmaf(T, P.bg[1], cg);
+                a.out_rgb[3 * pix + 2] = fmaf(T, P.bg[2], cb);
+            }
+            if (a.out_T) a.out_T[pix] = T;
+            if (a.saved_nstop) a.saved_nstop[pix] = last + 1;
+            if (a.out_feat) {
+#pragma unroll
+                for (int c4 = 0; c4 < CMAX / 4; ++c4)
+                    if (4 * c4 < C) store_vec<4>(a.out_feat, pix * C + 4 * c4, &acc[4 * c4], P.out_dtype);
+            }
+        }
+        warp_count(&a.st->counters[0], n_eval);
+        warp_count(&a.st->counters[1], n_contrib);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launcher
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename KernelT>
+cudaError_t launch(KernelT kern, int threads, size_t smem, const Cams& cams, const RParams& P, const FwdArgs& a,
+                   int num_sms, cudaStream_t stream) {
+    cudaError_t e = cudaSuccess;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int grid = cams.total_tiles;
+    if (a.persistent) {
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+        if (e != cudaSuccess) return e;
+        grid = max(1, per_sm) * num_sms;
+    }
+    if (grid <= 0) return cudaSuccess;
+    kern<<<grid, threads, smem, stream>>>(cams, P, a);
+    return cudaGetLastError();
+}
+
+template <int TS, typename FT>
+cudaError_t launch_topk(const Cams& cams, const RParams& P, const FwdArgs& a, int num_sms, cudaStream_t s) {
+    constexpr int NT = TS * TS;
+    const size_t p1 = (size_t)BATCH * (3 * 16 + 4 * 4);
+    auto p2 = [](int kcap) {
+        const int pc = (NT < 65536 / (kcap * 8 + 4)) ? NT : 65536 / (kcap * 8 + 4);
+        return (size_t)pc * (kcap * 8 + 4);
+    };
+    if (P.K <= 4) return launch(k_render_topk<TS, 4, FT>, NT, std::max(p1, p2(4)), cams, P, a, num_sms, s);
+    if (P.K <= 8) return launch(k_render_topk<TS, 8, FT>, NT, std::max(p1, p2(8)), cams, P, a, num_sms, s);
+    if (P.K <= 16) return launch(k_render_topk<TS, 16, FT>, NT, std::max(p1, p2(16)), cams, P, a, num_sms, s);
+    return launch(k_render_topk<TS, 32, FT>, NT, std::max(p1, p2(32)), cams, P, a, num_sms, s);
+}
+
+template <int TS, typename FT>
+cudaError_t launch_full(const Cams& cams, const RParams& P, const FwdArgs& a, int num_sms, cudaStream_t s) {
+    constexpr int NT = TS * TS;
+    const size_t smem = (size_t)FBATCH * (3 * 16 + 4 * 4) + (size_t)FBATCH * P.C * 4;
+    if (P.C <= 16) return launch(k_render_full<TS, 16, FT>, NT, smem, cams, P, a, num_sms, s);
+    if (P.C <= 32) return launch(k_render_full<TS, 32, FT>, NT, smem, cams, P, a, num_sms, s);
+    if (P.C <= 64) return launch(k_render_full<TS, 64, FT>, NT, smem, cams, P, a, num_sms, s);
+    return launch(k_render_full<TS, 128, FT>, NT, smem, cams, P, a, num_sms, s);
+}
+
+template <typename FT>
+cudaError_t launch_dtype(const Cams& cams, const RParams& P, const FwdArgs& a, int num_sms, cudaStream_t s) {
+    if (P.K == 0) {
+        if (P.ts == 8) return launch_full<8, FT>(cams, P, a, num_sms, s);
+        if (P.ts == 16) return launch_full<16, FT>(cams, P, a, num_sms, s);
+        return launch_full<32, FT>(cams, P, a, num_sms, s);
+    }
+    if (P.ts == 8) return launch_topk<8, FT>(cams, P, a, num_sms, s);
+    if (P.ts == 16) return launch_topk<16, FT>(cams, P, a, num_sms, s);
+    return launch_topk<32, FT>(cams, P, a, num_sms, s);
+}
+
+}  // namespace
+
+cudaError_t launch_render_forward(const Cams& cams, const RParams& P, const FwdArgs& a, int num_sms,
+                                  cudaStream_t stream) {
+    if (P.feat_dtype == FSS_BF16) return launch_dtype<__nv_bfloat16>(cams, P, a, num_sms, stream);
+    return launch_dtype<float>(cams, P, a, num_sms, stream);
+}
+
+}  // namespace fss

@@ -1,0 +1,131 @@
+"""GPU parity of projection, Precise Tile Intersection and the depth sort.
+
+Every integer result (culling, pixel and tile ranges, per-surfel tile
+counts, the tile lists and their order) is bit-exact against the oracle's
+binary32 binning mirror, and so are the binary32 values the decisions are
+taken from (adjugate rows, centre, conic, ellipse extents, depth, cutoff).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2604_10951_gb300 import scenes
+from tests._scenes import ident_cam, make_scene
+
+pytestmark = pytest.mark.gpu
+
+MODES = {"aabb": O.AABB, "snug": O.SNUG, "accu": O.ACCU}
+
+
+def _check_view(run, scene, cam, ts, mode, view=0):
+    p = O.make_params(tile_size=ts, K=run.params.K)
+    recf, reci, cnt = O.mirror_project(scene, cam, p, MODES[mode])
+    N = scene.n
+    sl = slice(view * N, (view + 1) * N)
+    rec = run.rec()[sl]            # r0=(m0,xc) r1=(m1,yc) r2=(m2,det) r3=(o,z,k2,s)
+    bf, bi, flags = run.binrec()
+    bf, bi, flags = bf[sl], bi[sl], flags[sl]
+    vis = reci[:, 0] == 1
+    np.testing.assert_array_equal((flags & 1) == 1, vis)
+    m = vis
+    # binary32 values behind every decision, bit for bit
+    np.testing.assert_array_equal(rec[m, 13], recf[m, 0])   # centre depth z
+    np.testing.assert_array_equal(rec[m, 14], recf[m, 1])   # cutoff k^2
+    np.testing.assert_array_equal(rec[m, 3], recf[m, 2])    # xc
+    np.testing.assert_array_equal(rec[m, 7], recf[m, 3])    # yc
+    np.testing.assert_array_equal(rec[m, 11], recf[m, 4])   # det (rescaled)
+    np.testing.assert_array_equal(rec[m][:, [0, 1, 2, 4, 5, 6, 8, 9, 10]], recf[m, 5:14])  # adjugate rows
+    np.testing.assert_array_equal(rec[m, 12], scene.opacities[m])
+    np.testing.assert_array_equal(bf[m][:, 0:6], recf[m, 14:20])      # conic A..F
+    bounded = m & (reci[:, 2] == 0)
+    np.testing.assert_array_equal(bf[bounded][:, 6:10], recf[bounded, 20:24])  # X0, Y0, hx, hy
+    np.testing.assert_array_equal((flags[m] & 2) != 0, reci[m, 2] == 1)       # unbounded
+    np.testing.assert_array_equal(bi[m][:, 0:4], reci[m][:, [3, 4, 5, 6]])   # pixel range
+    np.testing.assert_array_equal(bi[m][:, 4:8], reci[m][:, [7, 8, 9, 10]])  # tile rectangle
+    # tile counts per surfel (bounded ones; unbounded ones use the per-view list)
+    gc = run.count()[sl]
+    np.testing.assert_array_equal(gc[bounded], cnt[bounded])
+    return recf, reci
+
+
+def _check_lists(run, scene, cams, ts, mode):
+    """Sorted per-tile lists of all views equal the oracle's, bit for bit."""
+    tile_off = 0
+    all_ranges = run.ranges()
+    lists = run.lists()
+    N = scene.n
+    for v, cam in enumerate(cams):
+        p = O.make_params(tile_size=ts)
+        b = O.binning(scene, cam, p, MODES[mode])
+        nt = O.n_tiles(cam, ts)
+        rng = all_ranges[tile_off:tile_off + nt]
+        for t in range(nt):
+            mine = lists[rng[t, 0]:rng[t, 1]] - v * N
+            ref = b["ids"][b["ranges"][t, 0]:b["ranges"][t, 1]]
+            np.testing.assert_array_equal(mine, ref, err_msg=f"view {v} tile {t}")
+        tile_off += nt
+
+
+@pytest.mark.parametrize("mode", ["aabb", "snug", "accu"])
+@pytest.mark.parametrize("ts", [8, 16, 32])
+def test_tiny_scene_binning_bit_exact(mode, ts):
+    from tests.gpu_util import GpuRun
+    sc, cam = scenes.tiny_scene(seed=0)
+    run = GpuRun(sc, [cam], K=4, tile_size=ts, bin_mode=mode, render=False)
+    _check_view(run, sc, cam, ts, mode)
+    _check_lists(run, sc, [cam], ts, mode)
+    b = O.binning(sc, cam, O.make_params(tile_size=ts), MODES[mode])
+    assert run.P == b["P"]
+
+
+def test_room_view_binning_bit_exact():
+    from tests.gpu_util import GpuRun
+    sc = scenes.room_scene(n=200_000, C=8, seed=1)
+    cams = scenes.circle_poses(16)[:2]
+    run = GpuRun(sc, cams, K=8, tile_size=16, render=False, cap=1 << 20)
+    for v, cam in enumerate(cams):
+        _check_view(run, sc, cam, 16, "accu", view=v)
+    _check_lists(run, sc, cams, 16, "accu")
+
+
+def test_ragged_image_and_small_scene():
+    from tests.gpu_util import GpuRun
+    sc, _ = scenes.tiny_scene(seed=3, n=300)
+    cam = ident_cam(W=100, H=75, f=90.0)
+    cam.viewmat[2, 3] = 3.0
+    run = GpuRun(sc, [cam], K=4, tile_size=16, render=False)
+    _check_view(run, sc, cam, 16, "accu")
+    _check_lists(run, sc, [cam], 16, "accu")
+
+
+def test_capacity_overflow_reports_needed_pairs_and_recovers():
+    from paper_2604_10951_gb300 import _lib as L
+    from tests.gpu_util import GpuRun, dev
+    sc, cam = scenes.tiny_scene(seed=0)
+    run = GpuRun(sc, [cam], K=4, render=False, cap=1 << 16)
+    need = run.P
+    fr = run.frame
+    fr._alloc(100)
+    fr.project_bin(run.means, run.scales, run.quats, run.opac)
+    status, got = fr.read_status()
+    assert status == L.FSS_ERR_CAPACITY and got == need
+    status, _ = fr.read_status()  # flags are cleared by the read
+    assert status == L.FSS_OK
+    assert fr.bin_and_sort(run.means, run.scales, run.quats, run.opac) == need
+
+
+def test_invalid_arguments_are_rejected_without_launch():
+    from paper_2604_10951_gb300 import _lib as L
+    from paper_2604_10951_gb300.raster import make_cams, make_params
+    sc, cam = scenes.tiny_scene(seed=0)
+    cams = make_cams([cam])
+    bad = [dict(tile_size=12), dict(K=33), dict(C=6, feat_dtype=None), dict(alpha_min=0.0)]
+    for kw in bad:
+        kw2 = {k: v for k, v in kw.items() if v is not None}
+        p = make_params(C=kw2.pop("C", 16), **kw2)
+        with pytest.raises(L.FssError) as ei:
+            L.fss_workspace_size(p, cams, 1, sc.n, 1000)
+        assert ei.value.status in (L.FSS_ERR_INVALID_ARG, L.FSS_ERR_UNSUPPORTED)
+    p = make_params(C=16)
+    with pytest.raises(L.FssError):
+        L.fss_project_bin(p, cams, 1, sc.n, None, None, None, None, None, 1000, None)
