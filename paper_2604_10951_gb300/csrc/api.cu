@@ -252,6 +252,9 @@ fss_status fss_project_bin(const fss_params* params, const fss_camera* cams, int
     k_emit<<<sms * 8, 256, 0, st>>>(ctx.cams, ctx.P, ctx.at<BinRec>(REG_BINREC), ctx.at<uint32_t>(REG_VIS),
                                     ctx.at<uint32_t>(REG_TILECNT), ctx.at<uint32_t>(REG_LIST), stp);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_emit");
+    k_record<<<sms * 4, 256, 0, st>>>(ctx.cams, ctx.P, means, scales, quats, ctx.at<float4>(REG_REC),
+                                      ctx.at<uint32_t>(REG_VIS), ctx.at<uint32_t>(REG_UNB), stp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_record");
     return FSS_OK;
 }
 

@@ -21,6 +21,11 @@ __global__ void k_scan(const __grid_constant__ Cams cams, const __grid_constant_
 __global__ void k_emit(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                        const BinRec* __restrict__ binrec, const uint32_t* __restrict__ vis_list,
                        uint32_t* __restrict__ cursor, uint32_t* __restrict__ list, const Status* __restrict__ st);
+__global__ void k_record(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
+                         const float* __restrict__ means, const float* __restrict__ scales,
+                         const float* __restrict__ quats, float4* __restrict__ rec,
+                         const uint32_t* __restrict__ vis_list, const uint32_t* __restrict__ unb_list,
+                         const Status* __restrict__ st);
 __global__ void k_tile_sort(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                             const float4* __restrict__ rec, const int2* __restrict__ ranges,
                             uint32_t* __restrict__ list, const uint32_t* __restrict__ unb_list,

@@ -28,6 +28,52 @@ __device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); 
 __device__ __forceinline__ float fdv(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ float fq(float a) { return __fsqrt_rn(a); }
 
+// ---- double-float arithmetic (hi + lo, ~48 significant bits) ----------------
+// Error-free sums (Knuth's two-sum, 6 operations) and products (the exact
+// low part of a*b from one fused multiply-add), renormalised after every
+// operation.  Used only for the per-surfel render record, whose ray-splat
+// homography is ill-conditioned for surfels seen close to edge-on.
+struct df {
+    float hi, lo;
+};
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = fa(a, b), bb = fs(s, a);
+    return {s, fa(fs(a, fs(s, bb)), fs(b, bb))};
+}
+__device__ __forceinline__ df quick_two_sum(float s, float e) {
+    const float h = fa(s, e);
+    return {h, fs(e, fs(h, s))};
+}
+__device__ __forceinline__ df two_prod(float a, float b) {
+    const float p = fm(a, b);
+    return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ df dadd(df x, df y) {
+    const df s = two_sum(x.hi, y.hi);
+    return quick_two_sum(s.hi, fa(s.lo, fa(x.lo, y.lo)));
+}
+__device__ __forceinline__ df dneg(df x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ df dsub(df x, df y) { return dadd(x, dneg(y)); }
+__device__ __forceinline__ df dmul(df x, df y) {
+    const df p = two_prod(x.hi, y.hi);
+    return quick_two_sum(p.hi, fa(p.lo, fa(fm(x.hi, y.lo), fm(x.lo, y.hi))));
+}
+__device__ __forceinline__ df dmulf(df x, float f) {
+    const df p = two_prod(x.hi, f);
+    return quick_two_sum(p.hi, fa(p.lo, fm(x.lo, f)));
+}
+__device__ __forceinline__ df dfrom(float a) { return {a, 0.0f}; }
+// (R v)_r with binary32 R and double-float v
+__device__ __forceinline__ void dmvec(const float* R, const df v[3], df o[3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) o[r] = dadd(dadd(dmulf(v[0], R[3 * r]), dmulf(v[1], R[3 * r + 1])), dmulf(v[2], R[3 * r + 2]));
+}
+__device__ __forceinline__ void dcross(const df a[3], const df b[3], df o[3]) {
+    o[0] = dsub(dmul(a[1], b[2]), dmul(a[2], b[1]));
+    o[1] = dsub(dmul(a[2], b[0]), dmul(a[0], b[2]));
+    o[2] = dsub(dmul(a[0], b[1]), dmul(a[1], b[0]));
+}
+
 // (R v)_r = (R_r0 v0 + R_r1 v1) + R_r2 v2
 __device__ __forceinline__ void mvec(const float* R, const float v[3], float o[3]) {
 #pragma unroll
@@ -514,6 +560,97 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Cams cams,
                 }
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_record: precise render record of every listed item (thread per item)
+//
+// The ray-splat solve u ~ adj(T') (x - xc, y - yc, 1) is evaluated per pixel
+// in binary32, but the adjugate itself is computed here in double-float from
+// the binary32 inputs and rounded once: for a surfel seen nearly edge-on the
+// intersection amplifies a relative error e in T by about (depth / size) /
+// cos(view angle), so a binary32 chain (the binning mirror above) would put
+// ~1e-3 relative error into alpha.  The binning record keeps the binary32
+// values; only the render record r0..r2 and the rescale r3.w change.
+// With n2 = |q|^2, R(q/|q|) = R'(q) / n2 where R' is the homogeneous
+// (unnormalised) rotation polynomial, so n2 * T = K [r_u Rv t_u', r_v Rv t_v',
+// n2 (Rv p + t)] needs no square root; its adjugate is n2^2 adj(T).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_record(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
+                                                const float* __restrict__ means, const float* __restrict__ scales,
+                                                const float* __restrict__ quats, float4* __restrict__ rec,
+                                                const uint32_t* __restrict__ vis_list,
+                                                const uint32_t* __restrict__ unb_list, const Status* __restrict__ st) {
+    if (st->err) return;
+    const uint32_t nvis = st->nvis;
+    uint32_t total = nvis;
+    for (int v = 0; v < cams.n; ++v) total += st->unb_cnt[v];
+    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        uint32_t item;
+        if (idx < nvis) {
+            item = vis_list[idx];
+        } else {
+            uint32_t k = idx - nvis;
+            int v = 0;
+            while (k >= st->unb_cnt[v]) k -= st->unb_cnt[v++];
+            item = unb_list[(int64_t)v * P.N + k];
+        }
+        const int view = view_of_item(item, P.N);
+        const int64_t s = (int64_t)item - (int64_t)view * P.N;
+        const CamDev& cam = cams.c[view];
+        float4* rr = rec + 4 * (size_t)item;
+        const float xc = rr[0].w, yc = rr[1].w;
+        const float qw = quats[4 * s], qx = quats[4 * s + 1], qy = quats[4 * s + 2], qz = quats[4 * s + 3];
+        const df ww = two_prod(qw, qw), xx = two_prod(qx, qx), yy = two_prod(qy, qy), zz = two_prod(qz, qz);
+        const df xy = two_prod(qx, qy), wz = two_prod(qw, qz), xz = two_prod(qx, qz), wy = two_prod(qw, qy);
+        const df yz = two_prod(qy, qz), wx = two_prod(qw, qx);
+        const df n2 = dadd(dadd(ww, xx), dadd(yy, zz));
+        const df tu[3] = {dsub(dadd(ww, xx), dadd(yy, zz)), dmulf(dadd(xy, wz), 2.0f), dmulf(dsub(xz, wy), 2.0f)};
+        const df tv[3] = {dmulf(dsub(xy, wz), 2.0f), dsub(dadd(ww, yy), dadd(xx, zz)), dmulf(dadd(yz, wx), 2.0f)};
+        df eu[3], ev[3], pc[3];
+        dmvec(cam.R, tu, eu);
+        dmvec(cam.R, tv, ev);
+        const df pm[3] = {dfrom(means[3 * s]), dfrom(means[3 * s + 1]), dfrom(means[3 * s + 2])};
+        dmvec(cam.R, pm, pc);
+        const float su = scales[2 * s], sv = scales[2 * s + 1];
+        df col[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            col[0][i] = dmulf(eu[i], su);
+            col[1][i] = dmulf(ev[i], sv);
+            col[2][i] = dmul(dadd(pc[i], dfrom(cam.t[i])), n2);
+        }
+        // columns of n2 * T, then shifted about (xc, yc)
+        df d[3][3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const df cx = dadd(dmulf(col[j][0], cam.fx), dmulf(col[j][2], cam.cx));
+            const df cy = dadd(dmulf(col[j][1], cam.fy), dmulf(col[j][2], cam.cy));
+            d[j][0] = dsub(cx, dmulf(col[j][2], xc));
+            d[j][1] = dsub(cy, dmulf(col[j][2], yc));
+            d[j][2] = col[j][2];
+        }
+        df m[3][3];
+        dcross(d[1], d[2], m[0]);
+        dcross(d[2], d[0], m[1]);
+        dcross(d[0], d[1], m[2]);
+        const df det = dadd(dadd(dmul(d[0][0], m[0][0]), dmul(d[0][1], m[0][1])), dmul(d[0][2], m[0][2]));
+        float mx = 0.0f;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) mx = fmaxf(mx, fabsf(m[r][c].hi));
+        if (!(mx > 0.0f)) continue;
+        int ex;
+        frexpf(mx, &ex);
+        // hit depth det(T') / c2: with M = 2^-ex n2^2 adj(T'), store 2^-ex det(n2 T') / n2
+        const float detr = ldexpf(fdv(det.hi, n2.hi), -ex);
+        rr[0] = make_float4(ldexpf(m[0][0].hi, -ex), ldexpf(m[0][1].hi, -ex), ldexpf(m[0][2].hi, -ex), xc);
+        rr[1] = make_float4(ldexpf(m[1][0].hi, -ex), ldexpf(m[1][1].hi, -ex), ldexpf(m[1][2].hi, -ex), yc);
+        rr[2] = make_float4(ldexpf(m[2][0].hi, -ex), ldexpf(m[2][1].hi, -ex), ldexpf(m[2][2].hi, -ex), detr);
+        // total scale of M relative to adj(T' of the normalised surfel)
+        rr[3].w = ldexpf(fm(n2.hi, n2.hi), -ex);
     }
 }
 
