@@ -288,6 +288,7 @@ fss_status fss_render_forward(const fss_params* params, const fss_camera* cams, 
     FwdArgs a;
     std::memset(&a, 0, sizeof a);
     a.rec = ctx.at<float4>(REG_REC);
+    a.binrec = ctx.at<BinRec>(REG_BINREC);
     a.ranges = ctx.at<int2>(REG_RANGES);
     a.list = ctx.at<uint32_t>(REG_LIST);
     a.rgb = rgb;
@@ -329,6 +330,7 @@ fss_status fss_render_backward(const fss_params* params, const fss_camera* cams,
     BwdArgs a;
     std::memset(&a, 0, sizeof a);
     a.rec = ctx.at<float4>(REG_REC);
+    a.binrec = ctx.at<BinRec>(REG_BINREC);
     a.ranges = ctx.at<int2>(REG_RANGES);
     a.list = ctx.at<uint32_t>(REG_LIST);
     a.rgb = rgb;

@@ -35,6 +35,7 @@ __global__ void k_tile_sort(const __grid_constant__ Cams cams, const __grid_cons
 // signature)
 struct FwdArgs {
     const float4* rec;
+    const BinRec* binrec;
     const int2* ranges;
     const uint32_t* list;
     const float* rgb;
@@ -56,6 +57,7 @@ cudaError_t launch_render_forward(const Cams& cams, const RParams& P, const FwdA
 
 struct BwdArgs {
     const float4* rec;
+    const BinRec* binrec;
     const int2* ranges;
     const uint32_t* list;
     const float* rgb;

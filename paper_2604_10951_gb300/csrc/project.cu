@@ -28,6 +28,23 @@ __device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); 
 __device__ __forceinline__ float fdv(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ float fq(float a) { return __fsqrt_rn(a); }
 
+// natural logarithm of x > 0 in binary32, the same operation sequence as the
+// checker's binning mirror: x = m 2^e with m in [sqrt(1/2), sqrt(2)),
+// ln m = 2 atanh(s), s = (m - 1)/(m + 1), series to s^9 (|s| <= 0.1716).
+__device__ __forceinline__ float ln32(float x) {
+    int e;
+    float m = frexpf(x, &e);
+    if (m < 0.70710677f) { m = fm(m, 2.0f); e = e - 1; }
+    const float s = fdv(fs(m, 1.0f), fa(m, 1.0f));
+    const float s2 = fm(s, s);
+    float p = fm(s2, 1.0f / 9.0f);
+    p = fm(fa(p, 1.0f / 7.0f), s2);
+    p = fm(fa(p, 1.0f / 5.0f), s2);
+    p = fm(fa(p, 1.0f / 3.0f), s2);
+    p = fa(p, 1.0f);
+    return fa(fm((float)e, 0.6931472f), fm(fm(2.0f, s), p));
+}
+
 // ---- double-float arithmetic (hi + lo, ~48 significant bits) ----------------
 // Error-free sums (Knuth's two-sum, 6 operations) and products (the exact
 // low part of a*b from one fused multiply-add), renormalised after every
@@ -281,8 +298,8 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ Cams ca
             r3.y = pc[2];
             if (!(pc[2] > cam.near_plane)) break;
             if (!(o >= P.alpha_min)) break;
-            // S6: k^2 = 2 ln(o / alpha_min), rounded once to binary32
-            const float k2 = (float)(2.0 * log(__ddiv_rn((double)o, (double)P.alpha_min)));
+            // S6: k^2 = 2 ln(o / alpha_min)
+            const float k2 = fm(2.0f, ln32(fdv(o, P.alpha_min)));
             r3.z = k2;
             // S7
             float c[3][3];
@@ -358,7 +375,7 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ Cams ca
             int tx0 = px0 / ts, tx1 = px1 / ts, ty0 = py0 / ts, ty1 = py1 / ts;
             // S19
             if (P.bin_mode == FSS_BIN_AABB && !(br.flags & BR_UNBOUNDED)) {
-                float k2a = (float)(2.0 * log(__ddiv_rn(1.0, (double)P.alpha_min)));
+                float k2a = fm(2.0f, ln32(fdv(1.0f, P.alpha_min)));
                 if (kb > k2a) k2a = kb;
                 float qa[6], X0, Y0, hx, hy;
                 conic(m, k2a, qa);

@@ -34,7 +34,6 @@ namespace fss {
 namespace {
 
 constexpr int BB = 128;      // staged surfels per backward batch
-constexpr int PCAP = 2048;   // list positions per k_bwd_feat pass
 constexpr int BWD_FEAT_THREADS = 256;
 
 // reduce-scatter of V values (power of two, 2..32 per lane...) across a warp:
@@ -73,23 +72,54 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 // ---------------------------------------------------------------------------
 // k_bwd_feat (Top-K): dots and feature gradients, grouped per tile
+//
+// Per tile (and per chunk of at most ECAP (pixel, k) entries): the tile's
+// dL/dF rows and the feature rows of the distinct selected surfels are
+// staged in shared memory (rows padded by 16 bytes so 16-byte loads from
+// different rows hit different banks); a counting sort groups the entries
+// by surfel (CSR).  Then
+//   dots   one thread per entry: c_i . dL/dF(x) -> dots[pixel, k];
+//   grads  one thread per (surfel, 4 channels): sum_x w_i(x) dL/dF(x)
+//          over the surfel's entries -> one 16-byte vector reduction.
 // ---------------------------------------------------------------------------
-template <int CPL, typename FT>
+constexpr int ECAP = 2048;  // (pixel, k) entries per pass
+constexpr int PTAB = 2048;  // list positions per pass
+
+template <typename FT>
+__device__ __forceinline__ void lds4(const FT* p, float* o);
+template <>
+__device__ __forceinline__ void lds4<float>(const float* p, float* o) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void lds4<__nv_bfloat16>(const __nv_bfloat16* p, float* o) {
+    const uint2 v = *reinterpret_cast<const uint2*>(p);
+    o[0] = __uint_as_float(v.x << 16); o[1] = __uint_as_float(v.x & 0xffff0000u);
+    o[2] = __uint_as_float(v.y << 16); o[3] = __uint_as_float(v.y & 0xffff0000u);
+}
+
+template <typename FT>
 __global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_constant__ Cams cams,
                                                               const __grid_constant__ RParams P, const BwdArgs a,
-                                                              int ucap) {
+                                                              int pch, int ucap, int rowe) {
+    constexpr int E = FeatVec<FT>::E;
     extern __shared__ __align__(16) unsigned char smem[];
-    int32_t* s_slot = reinterpret_cast<int32_t*>(smem);  // [PCAP] flag -> slot
-    int32_t* s_inv = s_slot + PCAP;                      // [PCAP] slot -> position
-    float* s_feat = reinterpret_cast<float*>(s_inv + PCAP);  // [ucap][C]
-    float* s_acc = s_feat + (size_t)ucap * P.C;              // [ucap][C]
-    __shared__ int s_red[32];
+    int* s_tab = reinterpret_cast<int*>(smem);  // [PTAB] position -> slot
+    int* s_off = s_tab + PTAB;                  // [ECAP + 1] per-slot counts -> offsets
+    int* s_cur = s_off + ECAP + 1;              // [ECAP] scatter cursors
+    int* s_inv = s_cur + ECAP;                  // [ECAP] slot -> position
+    int* s_ent = s_inv + ECAP;                  // [ECAP] (slot << 16) | entry, grouped by slot
+    float* s_ew = reinterpret_cast<float*>(s_ent + ECAP);  // [ECAP] weights, grouped by slot
+    FT* s_df = reinterpret_cast<FT*>(smem + (((size_t)(PTAB + 5 * ECAP + 1) * 4 + 15) & ~(size_t)15));
+    FT* s_ft = s_df + (size_t)pch * rowe;
+    __shared__ int s_red[33];
     __shared__ int s_max;
 
     if (a.st->err) return;
     const int t = blockIdx.x;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int K = P.K, C = P.C, ts = P.ts, npx = ts * ts;
+    const int tid = threadIdx.x;
+    const int K = P.K, C = P.C, ts = P.ts, npx = ts * ts, nvec = C / E, nc4 = C / 4;
     const int view = view_of_tile(cams, t);
     const CamDev& cam = cams.c[view];
     const int lt = t - cam.tile_off;
@@ -98,15 +128,18 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_cons
     const int64_t vbase = (int64_t)view * P.N;
     const FT* __restrict__ feats = reinterpret_cast<const FT*>(a.feats);
     const FT* __restrict__ dF = reinterpret_cast<const FT*>(a.d_feat);
+    auto pix_of = [&](int p, int64_t& pix) {  // tile pixel p -> global pixel; false if outside
+        const int px = tx * ts + p % ts, py = ty * ts + p / ts;
+        pix = cam.pix_off + (int64_t)py * cam.W + px;
+        return px < cam.W && py < cam.H;
+    };
 
-    // longest selected position + 1 over the tile's pixels
     if (tid == 0) s_max = 0;
     __syncthreads();
     int lmax = 0;
     for (int p = tid; p < npx; p += BWD_FEAT_THREADS) {
-        const int px = tx * ts + p % ts, py = ty * ts + p / ts;
-        if (px >= cam.W || py >= cam.H) continue;
-        const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
+        int64_t pix;
+        if (!pix_of(p, pix)) continue;
         for (int k = K - 1; k >= 0; --k) {
             const int pos = a.saved_pos[pix * K + k];
             if (pos >= 0) { lmax = max(lmax, pos + 1); break; }
@@ -115,119 +148,110 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_cons
     atomicMax(&s_max, lmax);
     __syncthreads();
     const int L = s_max;
+    if (L == 0) return;
 
-    for (int p0 = 0; p0 < L; p0 += PCAP) {
-        for (int i = tid; i < PCAP; i += BWD_FEAT_THREADS) s_slot[i] = 0;
-        __syncthreads();
-        for (int p = tid; p < npx; p += BWD_FEAT_THREADS) {
-            const int px = tx * ts + p % ts, py = ty * ts + p / ts;
-            if (px >= cam.W || py >= cam.H) continue;
-            const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
-            for (int k = 0; k < K; ++k) {
-                const int pos = a.saved_pos[pix * K + k];
-                if (pos >= p0 && pos < p0 + PCAP) s_slot[pos - p0] = 1;
-            }
+    for (int pc0 = 0; pc0 < npx; pc0 += pch) {
+        const int np = min(pch, npx - pc0);
+        const int ne = np * K;
+        // stage the chunk's dL/dF rows (zeros outside the image)
+        for (int idx = tid; idx < np * nvec; idx += BWD_FEAT_THREADS) {
+            const int q = idx / nvec, v = idx - q * nvec;
+            int64_t pix;
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (pix_of(pc0 + q, pix)) val = __ldg(reinterpret_cast<const uint4*>(dF + pix * C + v * E));
+            *reinterpret_cast<uint4*>(s_df + (size_t)q * rowe + v * E) = val;
         }
-        __syncthreads();
-        // exclusive scan of the flags (PCAP / 256 = 8 per thread)
-        constexpr int PER = PCAP / BWD_FEAT_THREADS;
-        int f[PER], sum = 0;
-#pragma unroll
-        for (int k = 0; k < PER; ++k) { f[k] = s_slot[tid * PER + k]; sum += f[k]; }
-        int incl = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) s_red[wid] = incl;
-        __syncthreads();
-        if (wid == 0) {
-            const int w = lane < BWD_FEAT_THREADS / 32 ? s_red[lane] : 0;
-            int wi = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, wi, o);
-                if (lane >= o) wi += y;
-            }
-            if (lane < BWD_FEAT_THREADS / 32) s_red[lane] = wi - w;
-            if (lane == BWD_FEAT_THREADS / 32 - 1) s_red[31] = wi;  // total
-        }
-        __syncthreads();
-        int run = s_red[wid] + incl - sum;
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int pos = tid * PER + k;
-            if (f[k]) { s_slot[pos] = run; s_inv[run] = pos; ++run; }
-            else s_slot[pos] = -1;
-        }
-        __syncthreads();
-        const int U = s_red[31];
-
-        for (int u0 = 0; u0 < U; u0 += ucap) {
-            const int u1 = min(U, u0 + ucap);
-            // stage the feature rows of slots [u0, u1) and clear their accumulators
-            for (int idx = tid; idx < (u1 - u0) * C; idx += BWD_FEAT_THREADS) {
-                const int sl = idx / C, ch = idx - sl * C;
-                const int64_t sp = (int64_t)a.list[rg.x + p0 + s_inv[u0 + sl]] - vbase;
-                s_feat[idx] = FeatVec<FT>::one(feats + sp * C + ch);
-                s_acc[idx] = 0.0f;
+        for (int p0 = 0; p0 < L; p0 += PTAB) {
+            for (int i = tid; i < PTAB; i += BWD_FEAT_THREADS) s_tab[i] = 0;
+            for (int i = tid; i <= ECAP; i += BWD_FEAT_THREADS) s_off[i] = 0;
+            __syncthreads();
+            // mark the selected positions of this pass
+            for (int e = tid; e < ne; e += BWD_FEAT_THREADS) {
+                int64_t pix;
+                if (!pix_of(pc0 + e / K, pix)) continue;
+                const int pos = a.saved_pos[pix * K + e % K];
+                if (pos >= p0 && pos < p0 + PTAB) s_tab[pos - p0] = 1;
             }
             __syncthreads();
-            // one warp per pixel: dL/dF row in registers, then its entries
-            for (int p = wid; p < npx; p += BWD_FEAT_THREADS / 32) {
-                const int px = tx * ts + p % ts, py = ty * ts + p / ts;
-                if (px >= cam.W || py >= cam.H) continue;
-                const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
-                int pos = -1;
-                float w = 0.0f;
-                int sl = -1;
-                if (lane < K) {
-                    pos = a.saved_pos[pix * K + lane];
-                    w = a.saved_w[pix * K + lane];
-                    if (pos >= p0 && pos < p0 + PCAP) {
-                        const int s2 = s_slot[pos - p0];
-                        if (s2 >= u0 && s2 < u1) sl = s2 - u0;
-                    }
+            const int U = block_exscan(s_tab, PTAB, s_red);  // s_tab[pos] = slot where marked
+            if (U == 0) continue;
+            for (int i = tid; i < PTAB; i += BWD_FEAT_THREADS) {
+                const int nxt = i + 1 < PTAB ? s_tab[i + 1] : U;
+                if (nxt - s_tab[i] == 1) s_inv[s_tab[i]] = i;
+            }
+            // count entries per slot, then offsets (CSR)
+            for (int e = tid; e < ne; e += BWD_FEAT_THREADS) {
+                int64_t pix;
+                if (!pix_of(pc0 + e / K, pix)) continue;
+                const int pos = a.saved_pos[pix * K + e % K];
+                if (pos >= p0 && pos < p0 + PTAB) atomicAdd(&s_off[s_tab[pos - p0]], 1);
+            }
+            __syncthreads();
+            const int nsel = block_exscan(s_off, U, s_red);
+            for (int i = tid; i < U; i += BWD_FEAT_THREADS) s_cur[i] = s_off[i];
+            if (tid == 0) s_off[U] = nsel;
+            __syncthreads();
+            for (int e = tid; e < ne; e += BWD_FEAT_THREADS) {
+                int64_t pix;
+                if (!pix_of(pc0 + e / K, pix)) continue;
+                const int pos = a.saved_pos[pix * K + e % K];
+                if (pos >= p0 && pos < p0 + PTAB) {
+                    const int slot = s_tab[pos - p0];
+                    const int at = atomicAdd(&s_cur[slot], 1);
+                    s_ent[at] = (slot << 16) | e;
+                    s_ew[at] = a.saved_w[pix * K + e % K];
                 }
-                unsigned rel = __ballot_sync(0xffffffffu, sl >= 0);
-                if (!rel) continue;
-                float df[CPL];
-#pragma unroll
-                for (int i = 0; i < CPL; ++i) {
-                    const int ch = lane + 32 * i;
-                    df[i] = ch < C ? FeatVec<FT>::one(dF + pix * C + ch) : 0.0f;
+            }
+            __syncthreads();
+            for (int u0 = 0; u0 < U; u0 += ucap) {
+                const int u1 = min(U, u0 + ucap);
+                // stage the feature rows of slots [u0, u1)
+                for (int idx = tid; idx < (u1 - u0) * nvec; idx += BWD_FEAT_THREADS) {
+                    const int sl = idx / nvec, v = idx - sl * nvec;
+                    const int64_t sp = (int64_t)a.list[rg.x + p0 + s_inv[u0 + sl]] - vbase;
+                    *reinterpret_cast<uint4*>(s_ft + (size_t)sl * rowe + v * E) =
+                        __ldg(reinterpret_cast<const uint4*>(feats + sp * C + v * E));
                 }
-                while (rel) {
-                    const int k = __ffs(rel) - 1;
-                    rel &= rel - 1;
-                    const int slk = __shfl_sync(0xffffffffu, sl, k);
-                    const float wk = __shfl_sync(0xffffffffu, w, k);
-                    float dot = 0.0f;
+                __syncthreads();
+                // dots: one thread per entry
+                for (int i = s_off[u0] + tid; i < s_off[u1]; i += BWD_FEAT_THREADS) {
+                    const int ent = s_ent[i], e = ent & 0xffff, sl = (ent >> 16) - u0, q = e / K;
+                    const FT* fr = s_ft + (size_t)sl * rowe;
+                    const FT* gr = s_df + (size_t)q * rowe;
+                    float d0 = 0.0f, d1 = 0.0f;
+                    for (int c = 0; c < C; c += E) {
+                        float f[E], g[E];
+                        FeatVec<FT>::lds(fr + c, f);
+                        FeatVec<FT>::lds(gr + c, g);
 #pragma unroll
-                    for (int i = 0; i < CPL; ++i) {
-                        const int ch = lane + 32 * i;
-                        if (ch < C) {
-                            dot = fmaf(s_feat[slk * C + ch], df[i], dot);
-                            atomicAdd(&s_acc[slk * C + ch], wk * df[i]);
+                        for (int k = 0; k < E; k += 2) {
+                            d0 = fmaf(f[k], g[k], d0);
+                            d1 = fmaf(f[k + 1], g[k + 1], d1);
                         }
                     }
-                    dot = warp_sum(dot);
-                    if (lane == 0) a.dots[pix * K + k] = dot;
+                    int64_t pix;
+                    pix_of(pc0 + q, pix);
+                    a.dots[pix * K + e % K] = d0 + d1;
                 }
+                // feature gradients: one thread per (slot, 4 channels)
+                for (int w2 = tid; w2 < (u1 - u0) * nc4; w2 += BWD_FEAT_THREADS) {
+                    const int sl = w2 / nc4, c4 = w2 - sl * nc4, slot = u0 + sl;
+                    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                    for (int i = s_off[slot]; i < s_off[slot + 1]; ++i) {
+                        const int q = (s_ent[i] & 0xffff) / K;
+                        const float w = s_ew[i];
+                        float g[4];
+                        lds4<FT>(s_df + (size_t)q * rowe + 4 * c4, g);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) acc[k] = fmaf(w, g[k], acc[k]);
+                    }
+                    const int64_t sp = (int64_t)a.list[rg.x + p0 + s_inv[slot]] - vbase;
+                    red_add_v4(a.feat_acc + (int64_t)a.splat_slot[sp] * C + 4 * c4, acc[0], acc[1], acc[2], acc[3]);
+                }
+                __syncthreads();
             }
-            __syncthreads();
-            // flush: one row of 16-byte reductions per surfel
-            const int c4 = C / 4;
-            for (int idx = tid; idx < (u1 - u0) * c4; idx += BWD_FEAT_THREADS) {
-                const int sl = idx / c4, q = idx - sl * c4;
-                const int64_t sp = (int64_t)a.list[rg.x + p0 + s_inv[u0 + sl]] - vbase;
-                const int slot = a.splat_slot[sp];
-                const float* v = s_acc + sl * C + 4 * q;
-                red_add_v4(a.feat_acc + (int64_t)slot * C + 4 * q, v[0], v[1], v[2], v[3]);
-            }
-            __syncthreads();
         }
+        __syncthreads();
     }
 }
 
@@ -243,11 +267,9 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
     float4* s_r0 = reinterpret_cast<float4*>(smem);
     float4* s_r1 = s_r0 + NB;
     float4* s_r2 = s_r1 + NB;
-    float* s_o = reinterpret_cast<float*>(s_r2 + NB);
-    float* s_c0 = s_o + NB;
-    float* s_c1 = s_c0 + NB;
-    float* s_c2 = s_c1 + NB;
-    float* s_g = s_c2 + NB;        // [NB][16] partial derivatives
+    float4* s_oc = s_r2 + NB;                          // (o, r, g, b)
+    int2* s_box = reinterpret_cast<int2*>(s_oc + NB);  // SnugBox pixel range
+    float* s_g = reinterpret_cast<float*>(s_box + NB); // [NB][16] partial derivatives
     float* s_f = s_g + NB * 16;    // FULL: [NB][C] features
     float* s_gf = s_f + (FULL ? NB * P.C : 0);  // FULL: [NB][C] feature gradients
     __shared__ int s_max;
@@ -311,11 +333,10 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
             s_r0[j] = r[0];
             s_r1[j] = r[1];
             s_r2[j] = r[2];
-            s_o[j] = r[3].x;
             const int64_t sp = (int64_t)item - vbase;
-            s_c0[j] = a.rgb[3 * sp];
-            s_c1[j] = a.rgb[3 * sp + 1];
-            s_c2[j] = a.rgb[3 * sp + 2];
+            s_oc[j] = make_float4(r[3].x, a.rgb[3 * sp], a.rgb[3 * sp + 1], a.rgb[3 * sp + 2]);
+            const int16_t* bx = reinterpret_cast<const int16_t*>(a.binrec) + 40 * (size_t)item + 24;
+            s_box[j] = make_int2(((int)bx[0] & 0xffff) | ((int)bx[1] << 16), ((int)bx[2] & 0xffff) | ((int)bx[3] << 16));
         }
         for (int i = tid; i < cnt * 16; i += NT) s_g[i] = 0.0f;
         if (FULL) {
@@ -335,19 +356,23 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
         __syncthreads();
         for (int j = cnt - 1; j >= 0; --j) {
             const int pos = b_start + j;
+            const int2 bx = s_box[j];
+            const bool in_box = pos < nstop && px >= (int)(int16_t)(bx.x & 0xffff) && px <= (bx.x >> 16) &&
+                                py >= (int)(int16_t)(bx.y & 0xffff) && py <= (bx.y >> 16);
+            if (!__any_sync(0xffffffffu, in_box)) continue;
             float g[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) g[k] = 0.0f;
             float w = 0.0f;
             bool contrib = false;
             Hit h;
-            if (pos < nstop &&
-                eval_splat(s_r0[j], s_r1[j], s_r2[j], s_o[j], pxf, pyf, P.alpha_min, cam.near_plane, h)) {
+            const float4 oc = s_oc[j];
+            if (pos < nstop && eval_splat(s_r0[j], s_r1[j], s_r2[j], oc.x, pxf, pyf, P.alpha_min, cam.near_plane, h)) {
                 contrib = true;
                 const float alpha = fminf(h.alpha_raw, P.alpha_max);
                 const float Tj = T / (1.0f - alpha);
                 w = alpha * Tj;
-                float s = s_c0[j] * gr + s_c1[j] * gg + s_c2[j] * gb;
+                float s = oc.y * gr + oc.z * gg + oc.w * gb;
                 if (!FULL) {
                     if (pos == next_pos) {
                         s += next_dot;
@@ -376,7 +401,7 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
                 g[11] = w * gg;
                 g[12] = w * gb;
                 if (h.alpha_raw < P.alpha_max) {
-                    const float G = h.alpha_raw / s_o[j];
+                    const float G = h.alpha_raw / oc.x;
                     g[9] = dal * G;
                     const float drho = -0.5f * alpha * dal;
                     const float du = 2.0f * h.u * drho, dv = 2.0f * h.v * drho;
@@ -606,28 +631,25 @@ cudaError_t set_smem(const void* k, size_t smem) {
 
 template <typename FT>
 cudaError_t launch_feat(const Cams& cams, const RParams& P, const BwdArgs& a, cudaStream_t s) {
-    const size_t row = (size_t)P.C * 8;  // staged feature + accumulator, f32
-    const size_t budget = 96 * 1024 - 2 * PCAP * 4;
-    const int ucap = (int)std::max<size_t>(1, std::min<size_t>(1024, budget / row));
-    const size_t smem = 2 * PCAP * 4 + (size_t)ucap * row;
-    cudaError_t e;
-#define FSS_FEAT(CPL)                                                                        \
-    e = set_smem((const void*)k_bwd_feat<CPL, FT>, smem);                                  \
-    if (e != cudaSuccess) return e;                                                         \
-    k_bwd_feat<CPL, FT><<<cams.total_tiles, BWD_FEAT_THREADS, smem, s>>>(cams, P, a, ucap); \
+    const int rowe = P.C + 16 / (int)sizeof(FT);  // padded row, elements
+    const size_t rowb = (size_t)rowe * sizeof(FT);
+    const size_t fixed = (((size_t)(PTAB + 5 * ECAP + 1) * 4 + 15) & ~(size_t)15);
+    const size_t budget = 112 * 1024;
+    const int npx = P.ts * P.ts;
+    int pch = std::min(npx, ECAP / std::max(1, P.K));
+    pch = (int)std::min<size_t>((size_t)pch, std::max<size_t>(32, (40 * 1024) / rowb));
+    const int ucap = (int)std::max<size_t>(16, std::min<size_t>(ECAP, (budget - fixed - pch * rowb) / rowb));
+    const size_t smem = fixed + (size_t)(pch + ucap) * rowb;
+    cudaError_t e = set_smem((const void*)k_bwd_feat<FT>, smem);
+    if (e != cudaSuccess) return e;
+    k_bwd_feat<FT><<<cams.total_tiles, BWD_FEAT_THREADS, smem, s>>>(cams, P, a, pch, ucap, rowe);
     return cudaGetLastError();
-    if (P.C <= 32) { FSS_FEAT(1) }
-    if (P.C <= 64) { FSS_FEAT(2) }
-    if (P.C <= 128) { FSS_FEAT(4) }
-    if (P.C <= 256) { FSS_FEAT(8) }
-    FSS_FEAT(16)
-#undef FSS_FEAT
 }
 
 template <int TS, bool FULL, int CMAX, typename FT>
 cudaError_t launch_geo_one(const Cams& cams, const RParams& P, const BwdArgs& a, cudaStream_t s) {
     constexpr int NB = FULL ? FBATCH : BB;
-    const size_t smem = (size_t)NB * (3 * 16 + 4 * 4) + (size_t)NB * 16 * 4 + (FULL ? (size_t)NB * P.C * 8 : 0);
+    const size_t smem = (size_t)NB * (4 * 16 + 8) + (size_t)NB * 16 * 4 + (FULL ? (size_t)NB * P.C * 8 : 0);
     cudaError_t e = set_smem((const void*)k_bwd_geo<TS, FULL, CMAX, FT>, smem);
     if (e != cudaSuccess) return e;
     k_bwd_geo<TS, FULL, CMAX, FT><<<cams.total_tiles, TS * TS, smem, s>>>(cams, P, a);

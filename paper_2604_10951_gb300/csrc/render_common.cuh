@@ -56,6 +56,11 @@ struct FeatVec<float> {
         o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
     }
     __device__ static __forceinline__ float one(const float* p) { return __ldg(p); }
+    // 16-byte shared-memory load
+    __device__ static __forceinline__ void lds(const float* p, float* o) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
 };
 
 template <>
@@ -72,6 +77,15 @@ struct FeatVec<__nv_bfloat16> {
     }
     __device__ static __forceinline__ float one(const __nv_bfloat16* p) {
         return __uint_as_float(((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p))) << 16);
+    }
+    __device__ static __forceinline__ void lds(const __nv_bfloat16* p, float* o) {
+        const uint4 v = *reinterpret_cast<const uint4*>(p);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            o[2 * k] = __uint_as_float(w[k] << 16);
+            o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+        }
     }
 };
 
@@ -93,6 +107,50 @@ __device__ __forceinline__ void store_vec(void* out, int64_t elem, const float* 
         if (E == 8) *reinterpret_cast<uint4*>(b) = make_uint4(w[0], w[1], w[2], w[3]);
         else *reinterpret_cast<uint2*>(b) = make_uint2(w[0], w[1]);
     }
+}
+
+// exclusive scan of v[0, n) in shared memory by the whole CTA (n <= 8 *
+// blockDim.x, blockDim.x a multiple of 32, <= 1024); returns the total.
+// `red` is a 33-int shared scratch.  Contains __syncthreads.
+__device__ __forceinline__ int block_exscan(int* v, int n, int* red) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    int loc[8], sum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int i = tid * per + k;
+        loc[k] = (k < per && i < n) ? v[i] : 0;
+        sum += loc[k];
+    }
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) red[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int w = lane < nw ? red[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < nw) red[lane] = wi - w;
+        if (lane == 31) red[32] = wi;
+    }
+    __syncthreads();
+    int run = red[wid] + incl - sum;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int i = tid * per + k;
+        if (k < per && i < n) { v[i] = run; run += loc[k]; }
+    }
+    const int total = red[32];
+    __syncthreads();
+    return total;
 }
 
 __device__ __forceinline__ void warp_count(uint64_t* ctr, uint32_t v) {

@@ -43,6 +43,11 @@ __device__ __forceinline__ int next_tile(const FwdArgs& a, int* s_tile, bool fir
 // ---------------------------------------------------------------------------
 // Top-K kernel
 // ---------------------------------------------------------------------------
+// Shared memory: BATCH staged surfels as 4 x float4 (adjugate rows with the
+// local origin and det; opacity and colour) plus their SnugBox pixel range,
+// then each pixel's K-set as KCAP weights and list positions stored k-major
+// (slot k of thread t at k * NT + t), so that every lane's slot lands in its
+// own bank whatever slot it writes.  Phase 2 reuses the staging area.
 template <int TS, int KCAP, typename FT>
 __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__ Cams cams,
                                                          const __grid_constant__ RParams P, const FwdArgs a) {
@@ -52,12 +57,12 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
     float4* s_r0 = reinterpret_cast<float4*>(smem);
     float4* s_r1 = s_r0 + BATCH;
     float4* s_r2 = s_r1 + BATCH;
-    float* s_o = reinterpret_cast<float*>(s_r2 + BATCH);
-    float* s_c0 = s_o + BATCH;
-    float* s_c1 = s_c0 + BATCH;
-    float* s_c2 = s_c1 + BATCH;
-    int32_t* s_id = reinterpret_cast<int32_t*>(smem);  // phase 2 reuse
-    float* s_w = reinterpret_cast<float*>(s_id + PC * KCAP);
+    float4* s_oc = s_r2 + BATCH;                            // (o, r, g, b)
+    int2* s_box = reinterpret_cast<int2*>(s_oc + BATCH);    // (px0 | px1 << 16, py0 | py1 << 16)
+    float* s_hw = reinterpret_cast<float*>(s_box + BATCH);  // [KCAP][NT] weights
+    int* s_hp = reinterpret_cast<int*>(s_hw + KCAP * NT);   // [KCAP][NT] list positions
+    int32_t* s_id = reinterpret_cast<int32_t*>(smem);       // phase 2: [PC][KCAP] ids
+    float* s_w = reinterpret_cast<float*>(s_id + PC * KCAP);  //          [PC][KCAP] weights
     int32_t* s_n = reinterpret_cast<int32_t*>(s_w + PC * KCAP);
     __shared__ int s_tile;
 
@@ -65,6 +70,7 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
     if (a.st->err) return;
     const int K = P.K;
     const FT* __restrict__ feats = reinterpret_cast<const FT*>(a.feats);
+    const int16_t* __restrict__ boxes = reinterpret_cast<const int16_t*>(a.binrec);
     for (int t = next_tile(a, &s_tile, true); t < cams.total_tiles; t = next_tile(a, &s_tile, false)) {
         const int view = view_of_tile(cams, t);
         const CamDev& cam = cams.c[view];
@@ -79,12 +85,7 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
 
         float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
         bool done = !inside;
-        int last = -1;
-        float hw[KCAP];
-        int hp[KCAP];
-#pragma unroll
-        for (int k = 0; k < KCAP; ++k) { hw[k] = 0.0f; hp[k] = INT_MAX; }
-        int hc = 0, imin = 0;
+        int last = -1, hc = 0, imin = 0, pmin = 0;
         float wmin = 0.0f;
         uint32_t n_eval = 0, n_contrib = 0;
 
@@ -97,43 +98,56 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
                 s_r0[j] = r[0];
                 s_r1[j] = r[1];
                 s_r2[j] = r[2];
-                s_o[j] = r[3].x;
                 const int64_t sp = (int64_t)item - vbase;
-                s_c0[j] = a.rgb[3 * sp];
-                s_c1[j] = a.rgb[3 * sp + 1];
-                s_c2[j] = a.rgb[3 * sp + 2];
+                s_oc[j] = make_float4(r[3].x, a.rgb[3 * sp], a.rgb[3 * sp + 1], a.rgb[3 * sp + 2]);
+                // SnugBox pixel range, int16 at bytes 48..55 of the binning record
+                const int16_t* bx = boxes + 40 * (size_t)item + 24;
+                s_box[j] = make_int2(((int)bx[0] & 0xffff) | ((int)bx[1] << 16), ((int)bx[2] & 0xffff) | ((int)bx[3] << 16));
             }
             __syncthreads();
             if (done) continue;
             for (int j = 0; j < cnt; ++j) {
+                // skip a surfel whose conservative pixel box misses every live pixel of the warp
+                const int2 bx = s_box[j];
+                const bool in_box = px >= (int)(int16_t)(bx.x & 0xffff) && px <= (bx.x >> 16) &&
+                                    py >= (int)(int16_t)(bx.y & 0xffff) && py <= (bx.y >> 16);
+                if (!__any_sync(__activemask(), in_box)) continue;
                 ++n_eval;
                 Hit h;
-                if (!eval_splat(s_r0[j], s_r1[j], s_r2[j], s_o[j], pxf, pyf, P.alpha_min, cam.near_plane, h)) continue;
+                const float4 oc = s_oc[j];
+                if (!eval_splat(s_r0[j], s_r1[j], s_r2[j], oc.x, pxf, pyf, P.alpha_min, cam.near_plane, h)) continue;
                 const float alpha = fminf(h.alpha_raw, P.alpha_max);
                 const float Tn = T * (1.0f - alpha);
                 if (Tn < P.T_min) { done = true; break; }
                 const float w = alpha * T;
-                cr = fmaf(w, s_c0[j], cr);
-                cg = fmaf(w, s_c1[j], cg);
-                cb = fmaf(w, s_c2[j], cb);
+                cr = fmaf(w, oc.y, cr);
+                cg = fmaf(w, oc.z, cg);
+                cb = fmaf(w, oc.w, cb);
                 ++n_contrib;
                 const int pos = b0 + j;
-                // register min-heap of the K largest weights (ties: earlier wins)
-                int slot = -1;
-                if (hc < K) slot = hc++;
-                else if (w > wmin) slot = imin;
-                if (slot >= 0) {
-#pragma unroll
-                    for (int k = 0; k < KCAP; ++k)
-                        if (k == slot) { hw[k] = w; hp[k] = pos; }
-                    if (hc == K) {
-                        wmin = hw[0]; imin = 0;
-                        int pmin = hp[0];
-#pragma unroll
-                        for (int k = 1; k < KCAP; ++k) {
-                            if (k < K && (hw[k] < wmin || (hw[k] == wmin && hp[k] > pmin))) {
-                                wmin = hw[k]; imin = k; pmin = hp[k];
-                            }
+                // K largest weights (ties: the earlier surfel stays)
+                if (hc < K) {
+                    s_hw[hc * NT + tid] = w;
+                    s_hp[hc * NT + tid] = pos;
+                    if (++hc == K) {
+                        wmin = INFINITY;
+                        for (int k = 0; k < K; ++k) {
+                            const float v = s_hw[k * NT + tid];
+                            if (v <= wmin) { wmin = v; imin = k; }  // equal weights: the later slot is later in depth
+                        }
+                        pmin = s_hp[imin * NT + tid];
+                    }
+                } else if (w > wmin) {
+                    s_hw[imin * NT + tid] = w;
+                    s_hp[imin * NT + tid] = pos;
+                    wmin = INFINITY;
+                    pmin = -1;
+                    for (int k = 0; k < K; ++k) {
+                        const float v = s_hw[k * NT + tid];
+                        if (v < wmin || (v == wmin && s_hp[k * NT + tid] > pmin)) {
+                            wmin = v;
+                            imin = k;
+                            pmin = s_hp[k * NT + tid];
                         }
                     }
                 }
@@ -143,16 +157,22 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
             }
         }
 
-        // per-pixel outputs; Top-K entries in front-to-back order
-        const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
-        int rank[KCAP];
+        // per-pixel outputs; the K-set in front-to-back order
+        float hw[KCAP];
+        int hp[KCAP], hid[KCAP], rank[KCAP];
+#pragma unroll
+        for (int k = 0; k < KCAP; ++k) {
+            hw[k] = k < hc ? s_hw[k * NT + tid] : 0.0f;
+            hp[k] = k < hc ? s_hp[k * NT + tid] : INT_MAX;
+        }
 #pragma unroll
         for (int k = 0; k < KCAP; ++k) {
             int r = 0;
 #pragma unroll
-            for (int j = 0; j < KCAP; ++j) r += (j < hc && hp[j] < hp[k]) ? 1 : 0;
+            for (int j = 0; j < KCAP; ++j) r += (hp[j] < hp[k]) ? 1 : 0;
             rank[k] = r;
         }
+        const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
         if (inside) {
             if (a.out_rgb) {
                 a.out_rgb[3 * pix] = fmaf(T, P.bg[0], cr);
@@ -163,10 +183,11 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
             if (a.saved_nstop) a.saved_nstop[pix] = last + 1;
 #pragma unroll
             for (int k = 0; k < KCAP; ++k) {
+                hid[k] = -1;
                 if (k < hc) {
                     const int64_t o = pix * K + rank[k];
-                    const int32_t id = (int32_t)((int64_t)a.list[rg.x + hp[k]] - vbase);
-                    if (a.out_ids) a.out_ids[o] = id;
+                    hid[k] = (int32_t)((int64_t)a.list[rg.x + hp[k]] - vbase);
+                    if (a.out_ids) a.out_ids[o] = hid[k];
                     if (a.saved_pos) a.saved_pos[o] = hp[k];
                     if (a.saved_w) a.saved_w[o] = hw[k];
                 }
@@ -193,7 +214,7 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
 #pragma unroll
                     for (int k = 0; k < KCAP; ++k) {
                         if (k < hc) {
-                            s_id[q * KCAP + rank[k]] = (int32_t)((int64_t)a.list[rg.x + hp[k]] - vbase);
+                            s_id[q * KCAP + rank[k]] = hid[k];
                             s_w[q * KCAP + rank[k]] = hw[k];
                         }
                     }
@@ -237,17 +258,16 @@ __global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__
     float4* s_r0 = reinterpret_cast<float4*>(smem);
     float4* s_r1 = s_r0 + FBATCH;
     float4* s_r2 = s_r1 + FBATCH;
-    float* s_o = reinterpret_cast<float*>(s_r2 + FBATCH);
-    float* s_c0 = s_o + FBATCH;
-    float* s_c1 = s_c0 + FBATCH;
-    float* s_c2 = s_c1 + FBATCH;
-    float* s_f = s_c2 + FBATCH;  // [FBATCH][C] f32
+    float4* s_oc = s_r2 + FBATCH;                           // (o, r, g, b)
+    int2* s_box = reinterpret_cast<int2*>(s_oc + FBATCH);   // SnugBox pixel range
+    float* s_f = reinterpret_cast<float*>(s_box + FBATCH);  // [FBATCH][C] f32
     __shared__ int s_tile;
 
     const int tid = threadIdx.x;
     if (a.st->err) return;
     const int C = P.C;
     const FT* __restrict__ feats = reinterpret_cast<const FT*>(a.feats);
+    const int16_t* __restrict__ boxes = reinterpret_cast<const int16_t*>(a.binrec);
     for (int t = next_tile(a, &s_tile, true); t < cams.total_tiles; t = next_tile(a, &s_tile, false)) {
         const int view = view_of_tile(cams, t);
         const CamDev& cam = cams.c[view];
@@ -278,11 +298,10 @@ __global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__
                 s_r0[j] = r[0];
                 s_r1[j] = r[1];
                 s_r2[j] = r[2];
-                s_o[j] = r[3].x;
                 const int64_t sp = (int64_t)item - vbase;
-                s_c0[j] = a.rgb[3 * sp];
-                s_c1[j] = a.rgb[3 * sp + 1];
-                s_c2[j] = a.rgb[3 * sp + 2];
+                s_oc[j] = make_float4(r[3].x, a.rgb[3 * sp], a.rgb[3 * sp + 1], a.rgb[3 * sp + 2]);
+                const int16_t* bx = boxes + 40 * (size_t)item + 24;
+                s_box[j] = make_int2(((int)bx[0] & 0xffff) | ((int)bx[1] << 16), ((int)bx[2] & 0xffff) | ((int)bx[3] << 16));
             }
             for (int it = tid; it < cnt * nvec; it += NT) {
                 const int j = it / nvec, vv = it - j * nvec;
@@ -295,16 +314,21 @@ __global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__
             __syncthreads();
             if (done) continue;
             for (int j = 0; j < cnt; ++j) {
+                const int2 bx = s_box[j];
+                const bool in_box = px >= (int)(int16_t)(bx.x & 0xffff) && px <= (bx.x >> 16) &&
+                                    py >= (int)(int16_t)(bx.y & 0xffff) && py <= (bx.y >> 16);
+                if (!__any_sync(__activemask(), in_box)) continue;
                 ++n_eval;
                 Hit h;
-                if (!eval_splat(s_r0[j], s_r1[j], s_r2[j], s_o[j], pxf, pyf, P.alpha_min, cam.near_plane, h)) continue;
+                const float4 oc = s_oc[j];
+                if (!eval_splat(s_r0[j], s_r1[j], s_r2[j], oc.x, pxf, pyf, P.alpha_min, cam.near_plane, h)) continue;
                 const float alpha = fminf(h.alpha_raw, P.alpha_max);
                 const float Tn = T * (1.0f - alpha);
                 if (Tn < P.T_min) { done = true; break; }
                 const float w = alpha * T;
-                cr = fmaf(w, s_c0[j], cr);
-                cg = fmaf(w, s_c1[j], cg);
-                cb = fmaf(w, s_c2[j], cb);
+                cr = fmaf(w, oc.y, cr);
+                cg = fmaf(w, oc.z, cg);
+                cb = fmaf(w, oc.w, cb);
                 ++n_contrib;
                 const float4* fr = reinterpret_cast<const float4*>(s_f + j * C);
 #pragma unroll
@@ -369,21 +393,21 @@ cudaError_t launch(KernelT kern, int threads, size_t smem, const Cams& cams, con
 template <int TS, typename FT>
 cudaError_t launch_topk(const Cams& cams, const RParams& P, const FwdArgs& a, int num_sms, cudaStream_t s) {
     constexpr int NT = TS * TS;
-    const size_t p1 = (size_t)BATCH * (3 * 16 + 4 * 4);
-    auto p2 = [](int kcap) {
+    auto smem = [](int kcap) {
+        const size_t p1 = (size_t)BATCH * (4 * 16 + 8) + (size_t)NT * kcap * 8;  // staging + K-sets
         const int pc = (NT < 65536 / (kcap * 8 + 4)) ? NT : 65536 / (kcap * 8 + 4);
-        return (size_t)pc * (kcap * 8 + 4);
+        return std::max(p1, (size_t)pc * (kcap * 8 + 4));
     };
-    if (P.K <= 4) return launch(k_render_topk<TS, 4, FT>, NT, std::max(p1, p2(4)), cams, P, a, num_sms, s);
-    if (P.K <= 8) return launch(k_render_topk<TS, 8, FT>, NT, std::max(p1, p2(8)), cams, P, a, num_sms, s);
-    if (P.K <= 16) return launch(k_render_topk<TS, 16, FT>, NT, std::max(p1, p2(16)), cams, P, a, num_sms, s);
-    return launch(k_render_topk<TS, 32, FT>, NT, std::max(p1, p2(32)), cams, P, a, num_sms, s);
+    if (P.K <= 4) return launch(k_render_topk<TS, 4, FT>, NT, smem(4), cams, P, a, num_sms, s);
+    if (P.K <= 8) return launch(k_render_topk<TS, 8, FT>, NT, smem(8), cams, P, a, num_sms, s);
+    if (P.K <= 16) return launch(k_render_topk<TS, 16, FT>, NT, smem(16), cams, P, a, num_sms, s);
+    return launch(k_render_topk<TS, 32, FT>, NT, smem(32), cams, P, a, num_sms, s);
 }
 
 template <int TS, typename FT>
 cudaError_t launch_full(const Cams& cams, const RParams& P, const FwdArgs& a, int num_sms, cudaStream_t s) {
     constexpr int NT = TS * TS;
-    const size_t smem = (size_t)FBATCH * (3 * 16 + 4 * 4) + (size_t)FBATCH * P.C * 4;
+    const size_t smem = (size_t)FBATCH * (4 * 16 + 8) + (size_t)FBATCH * P.C * 4;
     if (P.C <= 16) return launch(k_render_full<TS, 16, FT>, NT, smem, cams, P, a, num_sms, s);
     if (P.C <= 32) return launch(k_render_full<TS, 32, FT>, NT, smem, cams, P, a, num_sms, s);
     if (P.C <= 64) return launch(k_render_full<TS, 64, FT>, NT, smem, cams, P, a, num_sms, s);
