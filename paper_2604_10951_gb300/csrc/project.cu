@@ -232,7 +232,10 @@ __device__ __forceinline__ bool line_interval(const BinRec& r, const Lines& L, i
     return L.rows ? accu_row(r, ts, o, a, b) : accu_col(r, ts, o, a, b);
 }
 
-__device__ __forceinline__ int view_of_item(int64_t item, int64_t N) { return (int)(item / N); }
+// view of item (items are view-major, view * N + surfel, < 2^32)
+__device__ __forceinline__ int view_of_item(int64_t item, int64_t N) {
+    return N >= ((int64_t)1 << 32) || item < N ? 0 : (int)((uint32_t)item / (uint32_t)N);
+}
 
 }  // namespace
 

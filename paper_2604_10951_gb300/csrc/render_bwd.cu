@@ -99,7 +99,7 @@ __device__ __forceinline__ void lds4<__nv_bfloat16>(const __nv_bfloat16* p, floa
     o[2] = __uint_as_float(v.y << 16); o[3] = __uint_as_float(v.y & 0xffff0000u);
 }
 
-template <typename FT>
+template <int TS, typename FT>
 __global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_constant__ Cams cams,
                                                               const __grid_constant__ RParams P, const BwdArgs a,
                                                               int pch, int ucap, int rowe) {
@@ -119,7 +119,11 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_cons
     if (a.st->err) return;
     const int t = blockIdx.x;
     const int tid = threadIdx.x;
-    const int K = P.K, C = P.C, ts = P.ts, npx = ts * ts, nvec = C / E, nc4 = C / 4;
+    constexpr int ts = TS, npx = TS * TS;
+    const int K = P.K, C = P.C, nvec = C / E, nc4 = C / 4;
+    const FastDiv divK(K);
+    const int rv = BWD_FEAT_THREADS / nvec, r0v = tid / nvec, v0 = tid - r0v * nvec;  // row-chunk mapping
+    const int rc = BWD_FEAT_THREADS / nc4, r0c = tid / nc4, c40 = tid - r0c * nc4;    // slot-channel mapping
     const int view = view_of_tile(cams, t);
     const CamDev& cam = cams.c[view];
     const int lt = t - cam.tile_off;
@@ -154,12 +158,13 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_cons
         const int np = min(pch, npx - pc0);
         const int ne = np * K;
         // stage the chunk's dL/dF rows (zeros outside the image)
-        for (int idx = tid; idx < np * nvec; idx += BWD_FEAT_THREADS) {
-            const int q = idx / nvec, v = idx - q * nvec;
-            int64_t pix;
-            uint4 val = make_uint4(0u, 0u, 0u, 0u);
-            if (pix_of(pc0 + q, pix)) val = __ldg(reinterpret_cast<const uint4*>(dF + pix * C + v * E));
-            *reinterpret_cast<uint4*>(s_df + (size_t)q * rowe + v * E) = val;
+        if (r0v < rv) {
+            for (int q = r0v; q < np; q += rv) {
+                int64_t pix;
+                uint4 val = make_uint4(0u, 0u, 0u, 0u);
+                if (pix_of(pc0 + q, pix)) val = __ldg(reinterpret_cast<const uint4*>(dF + pix * C + v0 * E));
+                *reinterpret_cast<uint4*>(s_df + (size_t)q * rowe + v0 * E) = val;
+            }
         }
         for (int p0 = 0; p0 < L; p0 += PTAB) {
             for (int i = tid; i < PTAB; i += BWD_FEAT_THREADS) s_tab[i] = 0;
@@ -167,9 +172,10 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_cons
             __syncthreads();
             // mark the selected positions of this pass
             for (int e = tid; e < ne; e += BWD_FEAT_THREADS) {
+                const int q = divK.div(e);
                 int64_t pix;
-                if (!pix_of(pc0 + e / K, pix)) continue;
-                const int pos = a.saved_pos[pix * K + e % K];
+                if (!pix_of(pc0 + q, pix)) continue;
+                const int pos = a.saved_pos[pix * K + (e - q * K)];
                 if (pos >= p0 && pos < p0 + PTAB) s_tab[pos - p0] = 1;
             }
             __syncthreads();
@@ -181,9 +187,10 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_cons
             }
             // count entries per slot, then offsets (CSR)
             for (int e = tid; e < ne; e += BWD_FEAT_THREADS) {
+                const int q = divK.div(e);
                 int64_t pix;
-                if (!pix_of(pc0 + e / K, pix)) continue;
-                const int pos = a.saved_pos[pix * K + e % K];
+                if (!pix_of(pc0 + q, pix)) continue;
+                const int pos = a.saved_pos[pix * K + (e - q * K)];
                 if (pos >= p0 && pos < p0 + PTAB) atomicAdd(&s_off[s_tab[pos - p0]], 1);
             }
             __syncthreads();
@@ -192,30 +199,32 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_cons
             if (tid == 0) s_off[U] = nsel;
             __syncthreads();
             for (int e = tid; e < ne; e += BWD_FEAT_THREADS) {
+                const int q = divK.div(e);
                 int64_t pix;
-                if (!pix_of(pc0 + e / K, pix)) continue;
-                const int pos = a.saved_pos[pix * K + e % K];
+                if (!pix_of(pc0 + q, pix)) continue;
+                const int pos = a.saved_pos[pix * K + (e - q * K)];
                 if (pos >= p0 && pos < p0 + PTAB) {
                     const int slot = s_tab[pos - p0];
                     const int at = atomicAdd(&s_cur[slot], 1);
                     s_ent[at] = (slot << 16) | e;
-                    s_ew[at] = a.saved_w[pix * K + e % K];
+                    s_ew[at] = a.saved_w[pix * K + (e - q * K)];
                 }
             }
             __syncthreads();
             for (int u0 = 0; u0 < U; u0 += ucap) {
                 const int u1 = min(U, u0 + ucap);
                 // stage the feature rows of slots [u0, u1)
-                for (int idx = tid; idx < (u1 - u0) * nvec; idx += BWD_FEAT_THREADS) {
-                    const int sl = idx / nvec, v = idx - sl * nvec;
-                    const int64_t sp = (int64_t)a.list[rg.x + p0 + s_inv[u0 + sl]] - vbase;
-                    *reinterpret_cast<uint4*>(s_ft + (size_t)sl * rowe + v * E) =
-                        __ldg(reinterpret_cast<const uint4*>(feats + sp * C + v * E));
+                if (r0v < rv) {
+                    for (int sl = r0v; sl < u1 - u0; sl += rv) {
+                        const int64_t sp = (int64_t)a.list[rg.x + p0 + s_inv[u0 + sl]] - vbase;
+                        *reinterpret_cast<uint4*>(s_ft + (size_t)sl * rowe + v0 * E) =
+                            __ldg(reinterpret_cast<const uint4*>(feats + sp * C + v0 * E));
+                    }
                 }
                 __syncthreads();
                 // dots: one thread per entry
                 for (int i = s_off[u0] + tid; i < s_off[u1]; i += BWD_FEAT_THREADS) {
-                    const int ent = s_ent[i], e = ent & 0xffff, sl = (ent >> 16) - u0, q = e / K;
+                    const int ent = s_ent[i], e = ent & 0xffff, sl = (ent >> 16) - u0, q = divK.div(e);
                     const FT* fr = s_ft + (size_t)sl * rowe;
                     const FT* gr = s_df + (size_t)q * rowe;
                     float d0 = 0.0f, d1 = 0.0f;
@@ -231,14 +240,14 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_cons
                     }
                     int64_t pix;
                     pix_of(pc0 + q, pix);
-                    a.dots[pix * K + e % K] = d0 + d1;
+                    a.dots[pix * K + (e - q * K)] = d0 + d1;
                 }
                 // feature gradients: one thread per (slot, 4 channels)
-                for (int w2 = tid; w2 < (u1 - u0) * nc4; w2 += BWD_FEAT_THREADS) {
-                    const int sl = w2 / nc4, c4 = w2 - sl * nc4, slot = u0 + sl;
+                for (int sl = r0c; r0c < rc && sl < u1 - u0; sl += rc) {
+                    const int c4 = c40, slot = u0 + sl;
                     float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
                     for (int i = s_off[slot]; i < s_off[slot + 1]; ++i) {
-                        const int q = (s_ent[i] & 0xffff) / K;
+                        const int q = divK.div(s_ent[i] & 0xffff);
                         const float w = s_ew[i];
                         float g[4];
                         lds4<FT>(s_df + (size_t)q * rowe + 4 * c4, g);
@@ -267,9 +276,9 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
     float4* s_r0 = reinterpret_cast<float4*>(smem);
     float4* s_r1 = s_r0 + NB;
     float4* s_r2 = s_r1 + NB;
-    float4* s_oc = s_r2 + NB;                          // (o, r, g, b)
-    int2* s_box = reinterpret_cast<int2*>(s_oc + NB);  // SnugBox pixel range
-    float* s_g = reinterpret_cast<float*>(s_box + NB); // [NB][16] partial derivatives
+    float4* s_oc = s_r2 + NB;                                  // (o, r, g, b)
+    uint32_t* s_wm = reinterpret_cast<uint32_t*>(s_oc + NB);   // warps the SnugBox reaches
+    float* s_g = reinterpret_cast<float*>(s_wm + 2 * NB);      // [NB][16] partial derivatives
     float* s_f = s_g + NB * 16;    // FULL: [NB][C] features
     float* s_gf = s_f + (FULL ? NB * P.C : 0);  // FULL: [NB][C] feature gradients
     __shared__ int s_max;
@@ -277,6 +286,7 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
     if (a.st->err) return;
     const int t = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31;
+    const uint32_t wbit = 1u << (tid >> 5);
     const int C = P.C, K = P.K;
     const int view = view_of_tile(cams, t);
     const CamDev& cam = cams.c[view];
@@ -335,31 +345,28 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
             s_r2[j] = r[2];
             const int64_t sp = (int64_t)item - vbase;
             s_oc[j] = make_float4(r[3].x, a.rgb[3 * sp], a.rgb[3 * sp + 1], a.rgb[3 * sp + 2]);
-            const int16_t* bx = reinterpret_cast<const int16_t*>(a.binrec) + 40 * (size_t)item + 24;
-            s_box[j] = make_int2(((int)bx[0] & 0xffff) | ((int)bx[1] << 16), ((int)bx[2] & 0xffff) | ((int)bx[3] << 16));
+            const int16_t* bx = reinterpret_cast<const int16_t*>(a.binrec) + 40 * (size_t)item + 26;
+            s_wm[j] = warp_row_mask<TS>(ty * TS, bx[0], bx[1]);
         }
         for (int i = tid; i < cnt * 16; i += NT) s_g[i] = 0.0f;
         if (FULL) {
-            const int nvec = C / FeatVec<FT>::E;
-            for (int it = tid; it < cnt * nvec; it += NT) {
-                const int j = it / nvec, vv = it - j * nvec;
+            constexpr int E = FeatVec<FT>::E;
+            const int nvec = C / E, rpi = NT / nvec, r0 = tid / nvec, vv = tid - r0 * nvec;
+            for (int j = r0; r0 < rpi && j < cnt; j += rpi) {
                 const int64_t sp = (int64_t)a.list[rg.x + b_start + j] - vbase;
-                float f[FeatVec<FT>::E];
-                FeatVec<FT>::load(feats + sp * C + vv * FeatVec<FT>::E, f);
+                float f[E];
+                FeatVec<FT>::load(feats + sp * C + vv * E, f);
 #pragma unroll
-                for (int e = 0; e < FeatVec<FT>::E; ++e) {
-                    s_f[j * C + vv * FeatVec<FT>::E + e] = f[e];
-                    s_gf[j * C + vv * FeatVec<FT>::E + e] = 0.0f;
+                for (int e = 0; e < E; ++e) {
+                    s_f[j * C + vv * E + e] = f[e];
+                    s_gf[j * C + vv * E + e] = 0.0f;
                 }
             }
         }
         __syncthreads();
         for (int j = cnt - 1; j >= 0; --j) {
             const int pos = b_start + j;
-            const int2 bx = s_box[j];
-            const bool in_box = pos < nstop && px >= (int)(int16_t)(bx.x & 0xffff) && px <= (bx.x >> 16) &&
-                                py >= (int)(int16_t)(bx.y & 0xffff) && py <= (bx.y >> 16);
-            if (!__any_sync(0xffffffffu, in_box)) continue;
+            if (!(s_wm[j] & wbit)) continue;  // warp-uniform: the SnugBox misses this warp's rows
             float g[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) g[k] = 0.0f;
@@ -640,16 +647,21 @@ cudaError_t launch_feat(const Cams& cams, const RParams& P, const BwdArgs& a, cu
     pch = (int)std::min<size_t>((size_t)pch, std::max<size_t>(32, (40 * 1024) / rowb));
     const int ucap = (int)std::max<size_t>(16, std::min<size_t>(ECAP, (budget - fixed - pch * rowb) / rowb));
     const size_t smem = fixed + (size_t)(pch + ucap) * rowb;
-    cudaError_t e = set_smem((const void*)k_bwd_feat<FT>, smem);
-    if (e != cudaSuccess) return e;
-    k_bwd_feat<FT><<<cams.total_tiles, BWD_FEAT_THREADS, smem, s>>>(cams, P, a, pch, ucap, rowe);
-    return cudaGetLastError();
+    auto go = [&](auto kern) {
+        cudaError_t e = set_smem((const void*)kern, smem);
+        if (e != cudaSuccess) return e;
+        kern<<<cams.total_tiles, BWD_FEAT_THREADS, smem, s>>>(cams, P, a, pch, ucap, rowe);
+        return cudaGetLastError();
+    };
+    if (P.ts == 8) return go(k_bwd_feat<8, FT>);
+    if (P.ts == 16) return go(k_bwd_feat<16, FT>);
+    return go(k_bwd_feat<32, FT>);
 }
 
 template <int TS, bool FULL, int CMAX, typename FT>
 cudaError_t launch_geo_one(const Cams& cams, const RParams& P, const BwdArgs& a, cudaStream_t s) {
     constexpr int NB = FULL ? FBATCH : BB;
-    const size_t smem = (size_t)NB * (4 * 16 + 8) + (size_t)NB * 16 * 4 + (FULL ? (size_t)NB * P.C * 8 : 0);
+    const size_t smem = (size_t)NB * (4 * 16 + 8) + (size_t)NB * 16 * 4 + (FULL ? (size_t)NB * P.C * 8 : 0);  // staging, masks, partials, rows
     cudaError_t e = set_smem((const void*)k_bwd_geo<TS, FULL, CMAX, FT>, smem);
     if (e != cudaSuccess) return e;
     k_bwd_geo<TS, FULL, CMAX, FT><<<cams.total_tiles, TS * TS, smem, s>>>(cams, P, a);

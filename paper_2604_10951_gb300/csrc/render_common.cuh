@@ -109,6 +109,34 @@ __device__ __forceinline__ void store_vec(void* out, int64_t elem, const float* 
     }
 }
 
+// Division by a divisor fixed for the whole kernel (d >= 1, 0 <= n < 2^24),
+// without the ~20-instruction integer division: a float reciprocal guess
+// corrected by one step either way.
+struct FastDiv {
+    int d;
+    float r;
+    __device__ __forceinline__ explicit FastDiv(int dd) : d(dd), r(1.0f / (float)dd) {}
+    __device__ __forceinline__ int div(int n) const {
+        int q = __float2int_rz(__int2float_rn(n) * r);
+        q += ((q + 1) * d <= n) ? 1 : 0;
+        q -= (q * d > n) ? 1 : 0;
+        return q;
+    }
+};
+
+// Warps of a TS x TS tile (one thread per pixel, row-major) own R = 32 / TS
+// consecutive pixel rows each (TS <= 32).  Bit w of the mask is set when the
+// pixel-row range [py0, py1] of a surfel meets warp w's rows.
+template <int TS>
+__device__ __forceinline__ uint32_t warp_row_mask(int tile_y0, int py0, int py1) {
+    constexpr int R = 32 / TS, NW = TS * TS / 32;
+    const int r0 = max(py0 - tile_y0, 0), r1 = min(py1 - tile_y0, TS - 1);
+    if (r0 > r1) return 0u;
+    const int w0 = r0 / R, w1 = r1 / R;
+    const uint32_t hi = (w1 >= 31) ? 0xffffffffu : ((2u << w1) - 1u);
+    return (hi & ~((1u << w0) - 1u)) & (NW >= 32 ? 0xffffffffu : ((1u << NW) - 1u));
+}
+
 // exclusive scan of v[0, n) in shared memory by the whole CTA (n <= 8 *
 // blockDim.x, blockDim.x a multiple of 32, <= 1024); returns the total.
 // `red` is a 33-int shared scratch.  Contains __syncthreads.

@@ -44,10 +44,15 @@ __device__ __forceinline__ int next_tile(const FwdArgs& a, int* s_tile, bool fir
 // Top-K kernel
 // ---------------------------------------------------------------------------
 // Shared memory: BATCH staged surfels as 4 x float4 (adjugate rows with the
-// local origin and det; opacity and colour) plus their SnugBox pixel range,
-// then each pixel's K-set as KCAP weights and list positions stored k-major
-// (slot k of thread t at k * NT + t), so that every lane's slot lands in its
-// own bank whatever slot it writes.  Phase 2 reuses the staging area.
+// local origin and det; opacity and colour) and a per-surfel mask of the
+// warps whose pixel rows its SnugBox reaches.  Phase 2 reuses the area.
+//
+// The K-set of a pixel lives in registers as an array sorted by decreasing
+// weight.  A new weight runs down a compare-exchange chain (strictly
+// greater moves ahead, so between equal weights the earlier surfel stays
+// in front and the later one is the first to fall off the end).  For K <
+// KCAP the first KCAP - K slots hold +inf and never move, so the K-th
+// largest weight is always slot KCAP - 1.
 template <int TS, int KCAP, typename FT>
 __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__ Cams cams,
                                                          const __grid_constant__ RParams P, const FwdArgs a) {
@@ -57,20 +62,23 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
     float4* s_r0 = reinterpret_cast<float4*>(smem);
     float4* s_r1 = s_r0 + BATCH;
     float4* s_r2 = s_r1 + BATCH;
-    float4* s_oc = s_r2 + BATCH;                            // (o, r, g, b)
-    int2* s_box = reinterpret_cast<int2*>(s_oc + BATCH);    // (px0 | px1 << 16, py0 | py1 << 16)
-    float* s_hw = reinterpret_cast<float*>(s_box + BATCH);  // [KCAP][NT] weights
-    int* s_hp = reinterpret_cast<int*>(s_hw + KCAP * NT);   // [KCAP][NT] list positions
-    int32_t* s_id = reinterpret_cast<int32_t*>(smem);       // phase 2: [PC][KCAP] ids
-    float* s_w = reinterpret_cast<float*>(s_id + PC * KCAP);  //          [PC][KCAP] weights
+    float4* s_oc = s_r2 + BATCH;                                 // (o, r, g, b)
+    uint32_t* s_wm = reinterpret_cast<uint32_t*>(s_oc + BATCH);  // warps the SnugBox reaches
+    int32_t* s_id = reinterpret_cast<int32_t*>(smem);            // phase 2: [PC][KCAP] ids
+    float* s_w = reinterpret_cast<float*>(s_id + PC * KCAP);     //          [PC][KCAP] weights
     int32_t* s_n = reinterpret_cast<int32_t*>(s_w + PC * KCAP);
     __shared__ int s_tile;
 
     const int tid = threadIdx.x;
+    const uint32_t wbit = 1u << (tid >> 5);
     if (a.st->err) return;
     const int K = P.K;
     const FT* __restrict__ feats = reinterpret_cast<const FT*>(a.feats);
     const int16_t* __restrict__ boxes = reinterpret_cast<const int16_t*>(a.binrec);
+    constexpr int E = FeatVec<FT>::E;
+    const int nvec = P.C / E;
+    const int ppi = NT / nvec;                         // pixels per phase-2 sweep
+    const int q0 = tid / nvec, vv = tid - q0 * nvec;   // this thread's pixel offset and 16-byte chunk
     for (int t = next_tile(a, &s_tile, true); t < cams.total_tiles; t = next_tile(a, &s_tile, false)) {
         const int view = view_of_tile(cams, t);
         const CamDev& cam = cams.c[view];
@@ -85,8 +93,14 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
 
         float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
         bool done = !inside;
-        int last = -1, hc = 0, imin = 0, pmin = 0;
-        float wmin = 0.0f;
+        int last = -1;
+        float hw[KCAP];
+        int hp[KCAP];
+#pragma unroll
+        for (int k = 0; k < KCAP; ++k) {
+            hw[k] = k < KCAP - K ? INFINITY : -INFINITY;
+            hp[k] = -1;
+        }
         uint32_t n_eval = 0, n_contrib = 0;
 
         for (int b0 = 0; b0 < n; b0 += BATCH) {
@@ -100,18 +114,14 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
                 s_r2[j] = r[2];
                 const int64_t sp = (int64_t)item - vbase;
                 s_oc[j] = make_float4(r[3].x, a.rgb[3 * sp], a.rgb[3 * sp + 1], a.rgb[3 * sp + 2]);
-                // SnugBox pixel range, int16 at bytes 48..55 of the binning record
-                const int16_t* bx = boxes + 40 * (size_t)item + 24;
-                s_box[j] = make_int2(((int)bx[0] & 0xffff) | ((int)bx[1] << 16), ((int)bx[2] & 0xffff) | ((int)bx[3] << 16));
+                // SnugBox pixel rows: int16 py0, py1 at bytes 52..55 of the binning record
+                const int16_t* bx = boxes + 40 * (size_t)item + 26;
+                s_wm[j] = warp_row_mask<TS>(ty * TS, bx[0], bx[1]);
             }
             __syncthreads();
             if (done) continue;
             for (int j = 0; j < cnt; ++j) {
-                // skip a surfel whose conservative pixel box misses every live pixel of the warp
-                const int2 bx = s_box[j];
-                const bool in_box = px >= (int)(int16_t)(bx.x & 0xffff) && px <= (bx.x >> 16) &&
-                                    py >= (int)(int16_t)(bx.y & 0xffff) && py <= (bx.y >> 16);
-                if (!__any_sync(__activemask(), in_box)) continue;
+                if (!(s_wm[j] & wbit)) continue;  // warp-uniform: no pixel row of this warp is reached
                 ++n_eval;
                 Hit h;
                 const float4 oc = s_oc[j];
@@ -124,52 +134,35 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
                 cg = fmaf(w, oc.z, cg);
                 cb = fmaf(w, oc.w, cb);
                 ++n_contrib;
-                const int pos = b0 + j;
-                // K largest weights (ties: the earlier surfel stays)
-                if (hc < K) {
-                    s_hw[hc * NT + tid] = w;
-                    s_hp[hc * NT + tid] = pos;
-                    if (++hc == K) {
-                        wmin = INFINITY;
-                        for (int k = 0; k < K; ++k) {
-                            const float v = s_hw[k * NT + tid];
-                            if (v <= wmin) { wmin = v; imin = k; }  // equal weights: the later slot is later in depth
-                        }
-                        pmin = s_hp[imin * NT + tid];
-                    }
-                } else if (w > wmin) {
-                    s_hw[imin * NT + tid] = w;
-                    s_hp[imin * NT + tid] = pos;
-                    wmin = INFINITY;
-                    pmin = -1;
-                    for (int k = 0; k < K; ++k) {
-                        const float v = s_hw[k * NT + tid];
-                        if (v < wmin || (v == wmin && s_hp[k * NT + tid] > pmin)) {
-                            wmin = v;
-                            imin = k;
-                            pmin = s_hp[k * NT + tid];
-                        }
+                if (w > hw[KCAP - 1]) {
+                    float x = w;
+                    int xp = b0 + j;
+#pragma unroll
+                    for (int k = 0; k < KCAP; ++k) {
+                        const bool gt = x > hw[k];
+                        const float nw = gt ? x : hw[k];
+                        const int np = gt ? xp : hp[k];
+                        x = gt ? hw[k] : x;
+                        xp = gt ? hp[k] : xp;
+                        hw[k] = nw;
+                        hp[k] = np;
                     }
                 }
                 T = Tn;
-                last = pos;
-                if (P.stop_rule == FSS_STOP_EXACT_TOPK && hc == K && P.alpha_max * T <= wmin) { done = true; break; }
+                last = b0 + j;
+                if (P.stop_rule == FSS_STOP_EXACT_TOPK && P.alpha_max * T <= hw[KCAP - 1]) { done = true; break; }
             }
         }
 
         // per-pixel outputs; the K-set in front-to-back order
-        float hw[KCAP];
-        int hp[KCAP], hid[KCAP], rank[KCAP];
+        int rank[KCAP], hid[KCAP];
+        int hc = 0;
 #pragma unroll
         for (int k = 0; k < KCAP; ++k) {
-            hw[k] = k < hc ? s_hw[k * NT + tid] : 0.0f;
-            hp[k] = k < hc ? s_hp[k * NT + tid] : INT_MAX;
-        }
-#pragma unroll
-        for (int k = 0; k < KCAP; ++k) {
+            hc += hp[k] >= 0 ? 1 : 0;
             int r = 0;
 #pragma unroll
-            for (int j = 0; j < KCAP; ++j) r += (hp[j] < hp[k]) ? 1 : 0;
+            for (int j = 0; j < KCAP; ++j) r += (hp[j] >= 0 && hp[j] < hp[k]) ? 1 : 0;
             rank[k] = r;
         }
         const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
@@ -184,7 +177,7 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
 #pragma unroll
             for (int k = 0; k < KCAP; ++k) {
                 hid[k] = -1;
-                if (k < hc) {
+                if (hp[k] >= 0) {
                     const int64_t o = pix * K + rank[k];
                     hid[k] = (int32_t)((int64_t)a.list[rg.x + hp[k]] - vbase);
                     if (a.out_ids) a.out_ids[o] = hid[k];
@@ -204,8 +197,6 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
 
         // phase 2: gather-accumulate the selected feature rows
         if (a.out_feat) {
-            constexpr int E = FeatVec<FT>::E;
-            const int nvec = P.C / E;
             for (int p0 = 0; p0 < NT; p0 += PC) {
                 __syncthreads();
                 if (tid >= p0 && tid < p0 + PC) {
@@ -213,7 +204,7 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
                     s_n[q] = inside ? hc : 0;
 #pragma unroll
                     for (int k = 0; k < KCAP; ++k) {
-                        if (k < hc) {
+                        if (hp[k] >= 0) {
                             s_id[q * KCAP + rank[k]] = hid[k];
                             s_w[q * KCAP + rank[k]] = hw[k];
                         }
@@ -221,8 +212,8 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
                 }
                 __syncthreads();
                 const int npx = min(PC, NT - p0);
-                for (int it = tid; it < npx * nvec; it += NT) {
-                    const int q = it / nvec, vv = it - q * nvec;
+                if (q0 >= ppi) continue;
+                for (int q = q0; q < npx; q += ppi) {
                     const int p = p0 + q;
                     const int qx = tx * TS + (p % TS), qy = ty * TS + (p / TS);
                     if (qx >= cam.W || qy >= cam.H) continue;
@@ -258,9 +249,9 @@ __global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__
     float4* s_r0 = reinterpret_cast<float4*>(smem);
     float4* s_r1 = s_r0 + FBATCH;
     float4* s_r2 = s_r1 + FBATCH;
-    float4* s_oc = s_r2 + FBATCH;                           // (o, r, g, b)
-    int2* s_box = reinterpret_cast<int2*>(s_oc + FBATCH);   // SnugBox pixel range
-    float* s_f = reinterpret_cast<float*>(s_box + FBATCH);  // [FBATCH][C] f32
+    float4* s_oc = s_r2 + FBATCH;                                   // (o, r, g, b)
+    uint32_t* s_wm = reinterpret_cast<uint32_t*>(s_oc + FBATCH);    // warps the SnugBox reaches
+    float* s_f = reinterpret_cast<float*>(s_wm + 2 * FBATCH);       // [FBATCH][C] f32 (16-byte aligned)
     __shared__ int s_tile;
 
     const int tid = threadIdx.x;
@@ -268,6 +259,10 @@ __global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__
     const int C = P.C;
     const FT* __restrict__ feats = reinterpret_cast<const FT*>(a.feats);
     const int16_t* __restrict__ boxes = reinterpret_cast<const int16_t*>(a.binrec);
+    const uint32_t wbit = 1u << (tid >> 5);
+    const int nv = C / E;
+    const int rpi = NT / nv;                         // staged rows per sweep
+    const int r0 = tid / nv, vv0 = tid - r0 * nv;    // this thread's row offset and 16-byte chunk
     for (int t = next_tile(a, &s_tile, true); t < cams.total_tiles; t = next_tile(a, &s_tile, false)) {
         const int view = view_of_tile(cams, t);
         const CamDev& cam = cams.c[view];
@@ -287,7 +282,6 @@ __global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__
         bool done = !inside;
         int last = -1;
         uint32_t n_eval = 0, n_contrib = 0;
-        const int nvec = C / E;
 
         for (int b0 = 0; b0 < n; b0 += FBATCH) {
             if (__syncthreads_and(done)) break;
@@ -300,24 +294,22 @@ __global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__
                 s_r2[j] = r[2];
                 const int64_t sp = (int64_t)item - vbase;
                 s_oc[j] = make_float4(r[3].x, a.rgb[3 * sp], a.rgb[3 * sp + 1], a.rgb[3 * sp + 2]);
-                const int16_t* bx = boxes + 40 * (size_t)item + 24;
-                s_box[j] = make_int2(((int)bx[0] & 0xffff) | ((int)bx[1] << 16), ((int)bx[2] & 0xffff) | ((int)bx[3] << 16));
+                const int16_t* bx = boxes + 40 * (size_t)item + 26;
+                s_wm[j] = warp_row_mask<TS>(ty * TS, bx[0], bx[1]);
             }
-            for (int it = tid; it < cnt * nvec; it += NT) {
-                const int j = it / nvec, vv = it - j * nvec;
-                const int64_t sp = (int64_t)a.list[rg.x + b0 + j] - vbase;
-                float f[E];
-                FeatVec<FT>::load(feats + (size_t)sp * C + vv * E, f);
+            if (r0 < rpi) {
+                for (int j = r0; j < cnt; j += rpi) {
+                    const int64_t sp = (int64_t)a.list[rg.x + b0 + j] - vbase;
+                    float f[E];
+                    FeatVec<FT>::load(feats + (size_t)sp * C + vv0 * E, f);
 #pragma unroll
-                for (int e = 0; e < E; ++e) s_f[j * C + vv * E + e] = f[e];
+                    for (int e = 0; e < E; ++e) s_f[j * C + vv0 * E + e] = f[e];
+                }
             }
             __syncthreads();
             if (done) continue;
             for (int j = 0; j < cnt; ++j) {
-                const int2 bx = s_box[j];
-                const bool in_box = px >= (int)(int16_t)(bx.x & 0xffff) && px <= (bx.x >> 16) &&
-                                    py >= (int)(int16_t)(bx.y & 0xffff) && py <= (bx.y >> 16);
-                if (!__any_sync(__activemask(), in_box)) continue;
+                if (!(s_wm[j] & wbit)) continue;  // warp-uniform
                 ++n_eval;
                 Hit h;
                 const float4 oc = s_oc[j];
@@ -394,7 +386,7 @@ template <int TS, typename FT>
 cudaError_t launch_topk(const Cams& cams, const RParams& P, const FwdArgs& a, int num_sms, cudaStream_t s) {
     constexpr int NT = TS * TS;
     auto smem = [](int kcap) {
-        const size_t p1 = (size_t)BATCH * (4 * 16 + 8) + (size_t)NT * kcap * 8;  // staging + K-sets
+        const size_t p1 = (size_t)BATCH * (4 * 16 + 4);  // staging
         const int pc = (NT < 65536 / (kcap * 8 + 4)) ? NT : 65536 / (kcap * 8 + 4);
         return std::max(p1, (size_t)pc * (kcap * 8 + 4));
     };
@@ -407,7 +399,7 @@ cudaError_t launch_topk(const Cams& cams, const RParams& P, const FwdArgs& a, in
 template <int TS, typename FT>
 cudaError_t launch_full(const Cams& cams, const RParams& P, const FwdArgs& a, int num_sms, cudaStream_t s) {
     constexpr int NT = TS * TS;
-    const size_t smem = (size_t)FBATCH * (4 * 16 + 8) + (size_t)FBATCH * P.C * 4;
+    const size_t smem = (size_t)FBATCH * (4 * 16 + 8) + (size_t)FBATCH * P.C * 4;  // staging, masks, rows
     if (P.C <= 16) return launch(k_render_full<TS, 16, FT>, NT, smem, cams, P, a, num_sms, s);
     if (P.C <= 32) return launch(k_render_full<TS, 32, FT>, NT, smem, cams, P, a, num_sms, s);
     if (P.C <= 64) return launch(k_render_full<TS, 64, FT>, NT, smem, cams, P, a, num_sms, s);

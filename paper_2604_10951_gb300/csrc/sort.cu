@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256) k_tile_sort(const __grid_constant__ Cams 
         for (int k = 2; k <= m; k <<= 1) {
             for (int j = k >> 1; j > 0; j >>= 1) {
                 for (int i = tid; i < (m >> 1); i += blockDim.x) {
-                    const int l = 2 * j * (i / j) + (i % j);
+                    const int l = ((i & ~(j - 1)) << 1) | (i & (j - 1));  // j is a power of two
                     const int r = l + j;
                     const bool up = (l & k) == 0;
                     const uint64_t a = sk[l], b = sk[r];
