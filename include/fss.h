@@ -82,10 +82,14 @@ typedef struct {
     int32_t out_dtype;  /* FSS_F32 | FSS_BF16: storage of the rendered features */
     int32_t C;          /* feature channels: multiple of 4 (F32) / 8 (BF16), 4..512 */
     float bg_rgb[3];    /* background colour added as T_final * bg */
-    int32_t reserved;   /* must be 0 */
+    int32_t schedule;   /* FSS_SCHED_GRID: one CTA per tile; FSS_SCHED_PERSISTENT:
+                           one wave of CTAs pulling tiles from a device work
+                           queue (balances views of mixed size) */
 } fss_params;
 
-/* Fills the defaults listed above (tile 16, K 8, ACCU, TMIN, F32, C 16). */
+enum { FSS_SCHED_GRID = 0, FSS_SCHED_PERSISTENT = 1 };
+
+/* Fills the defaults listed above (tile 16, K 8, ACCU, TMIN, F32, C 16, grid). */
 fss_status fss_default_params(fss_params *params);
 
 /* Bytes of device workspace needed for these cameras, N surfels and at most

@@ -17,6 +17,7 @@ FSS_OK, FSS_ERR_INVALID_ARG, FSS_ERR_UNSUPPORTED, FSS_ERR_CAPACITY, FSS_ERR_CUDA
 FSS_BIN_AABB, FSS_BIN_SNUG, FSS_BIN_ACCU = 0, 1, 2
 FSS_STOP_TMIN, FSS_STOP_EXACT_TOPK = 0, 1
 FSS_F32, FSS_BF16 = 0, 1
+FSS_SCHED_GRID, FSS_SCHED_PERSISTENT = 0, 1
 FSS_MAX_CAMS = 64
 FSS_MAX_K = 32
 STATUS_NAMES = {0: "FSS_OK", 1: "FSS_ERR_INVALID_ARG", 2: "FSS_ERR_UNSUPPORTED", 3: "FSS_ERR_CAPACITY",
@@ -24,7 +25,7 @@ STATUS_NAMES = {0: "FSS_OK", 1: "FSS_ERR_INVALID_ARG", 2: "FSS_ERR_UNSUPPORTED",
 
 # workspace regions (fss_workspace_region)
 REG_STATUS, REG_REC, REG_BINREC, REG_COUNT, REG_RANGES, REG_LIST, REG_COUNTERS, REG_TILECNT = range(8)
-REG_SORTTMP, REG_GRAD_ITEM, REG_FEAT_ACC, REG_DOTS, REG_VIS, REG_UNB, REG_SLOT = range(8, 15)
+REG_SORTTMP, REG_GRAD_ITEM, REG_FEAT_ACC, REG_DOTS, REG_VIS, REG_UNB, REG_SLOT, REG_WIDE = range(8, 16)
 
 EXPORTS = ["fss_default_params", "fss_workspace_size", "fss_saved_size", "fss_project_bin", "fss_sort",
            "fss_render_forward", "fss_render_backward", "fss_read_status", "fss_last_error",
@@ -41,7 +42,7 @@ class fss_params(C.Structure):
     _fields_ = [("tile_size", C.c_int32), ("K", C.c_int32), ("bin_mode", C.c_int32), ("stop_rule", C.c_int32),
                 ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("T_min", C.c_float),
                 ("feat_dtype", C.c_int32), ("out_dtype", C.c_int32), ("C", C.c_int32),
-                ("bg_rgb", C.c_float * 3), ("reserved", C.c_int32)]
+                ("bg_rgb", C.c_float * 3), ("schedule", C.c_int32)]
 
 
 class FssError(RuntimeError):

@@ -56,7 +56,8 @@ fss_status check_params(const fss_params* p) {
     if (!(p->alpha_min > 0.0f) || !(p->alpha_max > p->alpha_min) || !(p->alpha_max < 1.0f))
         return fail(FSS_ERR_INVALID_ARG, "need 0 < alpha_min < alpha_max < 1");
     if (!(p->T_min >= 0.0f) || !(p->T_min < 1.0f)) return fail(FSS_ERR_INVALID_ARG, "need 0 <= T_min < 1");
-    if (p->reserved != 0) return fail(FSS_ERR_INVALID_ARG, "reserved must be 0");
+    if (p->schedule != FSS_SCHED_GRID && p->schedule != FSS_SCHED_PERSISTENT)
+        return fail(FSS_ERR_INVALID_ARG, "schedule %d", p->schedule);
     return FSS_OK;
 }
 
@@ -124,6 +125,7 @@ Layout make_layout(const RParams& P, const Cams& cams) {
     sz[REG_VIS] = ni * 4;
     sz[REG_UNB] = ni * 4;
     sz[REG_SLOT] = N * 4;
+    sz[REG_WIDE] = ni * 4;
     size_t off = 0;
     for (int r = 0; r < REG_COUNT_ALL; ++r) {
         L.off[r] = off;
@@ -226,6 +228,8 @@ fss_status fss_project_bin(const fss_params* params, const fss_camera* cams, int
     if (s != FSS_OK) return s;
     if (!workspace) return fail(FSS_ERR_INVALID_ARG, "workspace is NULL");
     if (N > 0 && (!means || !scales || !quats || !opac)) return fail(FSS_ERR_INVALID_ARG, "NULL surfel input");
+    if ((reinterpret_cast<uintptr_t>(quats) & 15) || (reinterpret_cast<uintptr_t>(scales) & 7))
+        return fail(FSS_ERR_INVALID_ARG, "quats must be 16-byte and scales 8-byte aligned");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e;
     // clear the per-frame part of the status block and the gradient slots
@@ -235,26 +239,25 @@ fss_status fss_project_bin(const fss_params* params, const fss_camera* cams, int
         e = cudaMemsetAsync(ctx.ws + ctx.L.off[REG_SLOT], 0xff, (size_t)N * 4, st);
         if (e != cudaSuccess) return cuda_fail(e, "memset slots");
     }
+    e = cudaMemsetAsync(ctx.ws + ctx.L.off[REG_TILECNT], 0, (size_t)ctx.cams.total_tiles * 4, st);
+    if (e != cudaSuccess) return cuda_fail(e, "memset tile counts");
     const int sms = num_sms_current();
     Status* stp = ctx.at<Status>(REG_STATUS);
     const int64_t items = ctx.P.n_items;
-    const int64_t blocks = std::max<int64_t>(1, std::max<int64_t>((items + 255) / 256, 1));
+    const int64_t blocks = std::max<int64_t>(1, (items + 255) / 256);
     k_project<<<(unsigned)blocks, 256, 0, st>>>(ctx.cams, ctx.P, means, scales, quats, opac, ctx.at<float4>(REG_REC),
                                                ctx.at<BinRec>(REG_BINREC), ctx.at<uint32_t>(REG_COUNT),
                                                ctx.at<uint32_t>(REG_TILECNT), ctx.at<uint32_t>(REG_VIS),
-                                               ctx.at<uint32_t>(REG_UNB), ctx.at<int32_t>(REG_SLOT), stp);
+                                               ctx.at<uint32_t>(REG_WIDE), ctx.at<uint32_t>(REG_UNB),
+                                               ctx.at<int32_t>(REG_SLOT), stp);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_project");
-    k_count<<<sms * 8, 256, 0, st>>>(ctx.cams, ctx.P, ctx.at<BinRec>(REG_BINREC), ctx.at<uint32_t>(REG_VIS),
-                                     ctx.at<uint32_t>(REG_COUNT), ctx.at<uint32_t>(REG_TILECNT), stp);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_count");
     k_scan<<<1, 1024, 0, st>>>(ctx.cams, ctx.P, ctx.at<uint32_t>(REG_TILECNT), ctx.at<int2>(REG_RANGES), stp);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_scan");
-    k_emit<<<sms * 8, 256, 0, st>>>(ctx.cams, ctx.P, ctx.at<BinRec>(REG_BINREC), ctx.at<uint32_t>(REG_VIS),
-                                    ctx.at<uint32_t>(REG_TILECNT), ctx.at<uint32_t>(REG_LIST), stp);
+    k_emit<<<sms * 4, 256, 0, st>>>(ctx.cams, ctx.P, ctx.at<BinRec>(REG_BINREC), ctx.at<uint32_t>(REG_VIS),
+                                    ctx.at<uint32_t>(REG_WIDE), ctx.at<uint32_t>(REG_UNB),
+                                    ctx.at<uint32_t>(REG_TILECNT), ctx.at<uint32_t>(REG_LIST), means, scales, quats,
+                                    ctx.at<float4>(REG_REC), stp);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_emit");
-    k_record<<<sms * 4, 256, 0, st>>>(ctx.cams, ctx.P, means, scales, quats, ctx.at<float4>(REG_REC),
-                                      ctx.at<uint32_t>(REG_VIS), ctx.at<uint32_t>(REG_UNB), stp);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_record");
     return FSS_OK;
 }
 
@@ -305,7 +308,7 @@ fss_status fss_render_forward(const fss_params* params, const fss_camera* cams, 
         a.saved_nstop = reinterpret_cast<int32_t*>(sv + 2 * align256(px * params->K * 4));
     }
     a.st = ctx.at<Status>(REG_STATUS);
-    a.persistent = 0;
+    a.persistent = params->schedule == FSS_SCHED_PERSISTENT;
     cudaError_t e = launch_render_forward(ctx.cams, ctx.P, a, num_sms_current(), reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "render_forward");
     return FSS_OK;
@@ -323,6 +326,8 @@ fss_status fss_render_backward(const fss_params* params, const fss_camera* cams,
     if (!workspace || !saved || !out_T || !d_rgb) return fail(FSS_ERR_INVALID_ARG, "NULL workspace/saved/out_T/d_rgb");
     if (params->out_dtype != params->feat_dtype)
         return fail(FSS_ERR_UNSUPPORTED, "backward needs out_dtype == feat_dtype");
+    if (params->K > 0 && params->C / (params->feat_dtype == FSS_BF16 ? 8 : 4) > 32)
+        return fail(FSS_ERR_UNSUPPORTED, "Top-K backward supports C <= %d", params->feat_dtype == FSS_BF16 ? 256 : 128);
     if (N > 0 && (!means || !scales || !quats || !opac || !rgb || !feats || !d_feat))
         return fail(FSS_ERR_INVALID_ARG, "NULL surfel input or d_feat");
     if (misaligned16(feats) || misaligned16(d_feat) || misaligned16(g_feat))
@@ -352,6 +357,7 @@ fss_status fss_render_backward(const fss_params* params, const fss_camera* cams,
     a.g_means = g_means; a.g_scales = g_scales; a.g_quats = g_quats; a.g_opac = g_opac; a.g_rgb = g_rgb;
     a.g_feat = g_feat;
     a.st = ctx.at<Status>(REG_STATUS);
+    a.persistent = params->schedule == FSS_SCHED_PERSISTENT;
     if (N == 0) return FSS_OK;
     cudaError_t e = launch_render_backward(ctx.cams, ctx.P, a, num_sms_current(), reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "render_backward");

@@ -73,9 +73,12 @@ struct Status {
     int64_t pairs_needed;  // pairs of the last binning (the paper's RN-Total)
     uint64_t counters[8];  // 0 evaluations, 1 contributions, 2 pixels stopped early
     uint32_t nvis;         // bounded visible items listed by k_project
-    uint32_t work;         // persistent work-queue head
+    uint32_t work;         // persistent work-queue head of the forward render
     uint32_t nslot;        // surfels visible in at least one view (gradient slots)
-    uint32_t pad2;
+    uint32_t work_feat;    // work-queue heads of the backward tile kernels
+    uint32_t work_geo;
+    uint32_t nwide;        // bounded visible items spanning many tiles
+    uint32_t pad3[2];
     uint32_t unb_cnt[FSS_MAX_CAMS];  // unbounded items per view
 };
 enum { ERR_CAPACITY = 1, ERR_TIMEOUT = 2 };
@@ -100,6 +103,7 @@ enum Region {
     REG_VIS = 12,
     REG_UNB = 13,
     REG_SLOT = 14,   // int32 [N]: gradient slot of each surfel, -1 if culled in every view
+    REG_WIDE = 15,   // uint32 [items]: visible items spanning many tiles
     REG_COUNT_ALL
 };
 

@@ -11,21 +11,16 @@ __global__ void k_project(const __grid_constant__ Cams cams, const __grid_consta
                           const float* __restrict__ means, const float* __restrict__ scales,
                           const float* __restrict__ quats, const float* __restrict__ opac, float4* __restrict__ rec,
                           BinRec* __restrict__ binrec, uint32_t* __restrict__ count, uint32_t* __restrict__ tile_cnt,
-                          uint32_t* __restrict__ vis_list, uint32_t* __restrict__ unb_list,
-                          int32_t* __restrict__ splat_slot, Status* __restrict__ st);
-__global__ void k_count(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
-                        const BinRec* __restrict__ binrec, const uint32_t* __restrict__ vis_list,
-                        uint32_t* __restrict__ count, uint32_t* __restrict__ tile_cnt, const Status* __restrict__ st);
+                          uint32_t* __restrict__ vis_list, uint32_t* __restrict__ wide_list,
+                          uint32_t* __restrict__ unb_list, int32_t* __restrict__ splat_slot, Status* __restrict__ st);
 __global__ void k_scan(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                        uint32_t* __restrict__ tile_cnt, int2* __restrict__ ranges, Status* __restrict__ st);
 __global__ void k_emit(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                        const BinRec* __restrict__ binrec, const uint32_t* __restrict__ vis_list,
-                       uint32_t* __restrict__ cursor, uint32_t* __restrict__ list, const Status* __restrict__ st);
-__global__ void k_record(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
-                         const float* __restrict__ means, const float* __restrict__ scales,
-                         const float* __restrict__ quats, float4* __restrict__ rec,
-                         const uint32_t* __restrict__ vis_list, const uint32_t* __restrict__ unb_list,
-                         const Status* __restrict__ st);
+                       const uint32_t* __restrict__ wide_list, const uint32_t* __restrict__ unb_list,
+                       uint32_t* __restrict__ cursor, uint32_t* __restrict__ list, const float* __restrict__ means,
+                       const float* __restrict__ scales, const float* __restrict__ quats, float4* __restrict__ rec,
+                       const Status* __restrict__ st);
 __global__ void k_tile_sort(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                             const float4* __restrict__ rec, const int2* __restrict__ ranges,
                             uint32_t* __restrict__ list, const uint32_t* __restrict__ unb_list,
@@ -77,6 +72,7 @@ struct BwdArgs {
     const float* scales;
     const float* quats;
     const float* opac;
+    int persistent;  // tile kernels pull tiles from the status block's queues
     float* g_means;
     float* g_scales;
     float* g_quats;

@@ -4,12 +4,12 @@
 //             its adjugate about the projected centre, opacity-aware cutoff,
 //             screen conic, SnugBox pixel range; appends visible items to a
 //             compact list (unbounded conics to a per-view list instead).
-// k_count     one warp per visible item: AccuTile per-row (or per-column)
-//             tile intervals, pair counts per tile (fire-and-forget adds).
+//             Also counts each item's tiles (AccuTile per-row or per-column
+//             intervals) into per-tile counters.
 // k_scan      per-tile exclusive scan -> tile ranges, total pairs, capacity.
-// k_emit      one warp per visible item: writes the item into a slot of each
-//             of its tiles (slot order is arbitrary; the per-tile sort
-//             restores a total order).
+// k_emit      writes each item into a slot of each of its tiles (slot order
+//             is arbitrary; the per-tile sort restores a total order) and
+//             computes the double-float render records.
 //
 // Every tile decision is taken in binary32 with the fixed operation order
 // that the FP64 checker's binning mirror also follows, so tile lists compare
@@ -240,20 +240,30 @@ __device__ __forceinline__ int view_of_item(int64_t item, int64_t N) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// k_project
+// k_project: one thread per (view, surfel) item
+//
+// Culls on depth first (the camera-space centre needs only the mean), then
+// loads the rest of the surfel.  A visible item with a bounded conic counts
+// its tiles (fire-and-forget adds into the per-tile counters, cleared by the
+// host call before this kernel) and is appended to the narrow list, or to
+// the wide list when it spans more than WIDE_TILES tiles; an unbounded item
+// goes to its view's list instead (every tile of the view includes it).
+// Appends and gradient-slot claims are aggregated per CTA.
 // ---------------------------------------------------------------------------
+constexpr uint32_t WIDE_TILES = 32;
+
 __global__ void __launch_bounds__(256) k_project(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                                                  const float* __restrict__ means, const float* __restrict__ scales,
                                                  const float* __restrict__ quats, const float* __restrict__ opac,
                                                  float4* __restrict__ rec, BinRec* __restrict__ binrec,
                                                  uint32_t* __restrict__ count, uint32_t* __restrict__ tile_cnt,
-                                                 uint32_t* __restrict__ vis_list, uint32_t* __restrict__ unb_list,
-                                                 int32_t* __restrict__ splat_slot, Status* __restrict__ st) {
+                                                 uint32_t* __restrict__ vis_list, uint32_t* __restrict__ wide_list,
+                                                 uint32_t* __restrict__ unb_list, int32_t* __restrict__ splat_slot,
+                                                 Status* __restrict__ st) {
     const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    // clear the per-tile counters of this frame (k_count runs after this kernel)
-    for (int64_t t = item; t < cams.total_tiles; t += (int64_t)gridDim.x * blockDim.x) tile_cnt[t] = 0u;
     if (st->err) return;
-    bool vis = false, unb = false;
+    bool vis = false, wide = false, unb = false, claim = false;
+    int64_t claim_s = 0;
     int view = 0;
     if (item < P.n_items) {
         view = view_of_item(item, P.N);
@@ -268,11 +278,22 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ Cams ca
         br.pad[0] = br.pad[1] = br.pad[2] = 0;
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
         do {
-            // S1
-            const float qw = quats[4 * s], qx = quats[4 * s + 1], qy = quats[4 * s + 2], qz = quats[4 * s + 3];
-            const float n2 = fa(fa(fa(fm(qw, qw), fm(qx, qx)), fm(qy, qy)), fm(qz, qz));
-            const float o = opac[s];
+            // S3 (centre) and S4 first: the order of the cull tests does not change the result
+            float e[3], pc[3];
+            const float pm[3] = {__ldg(means + 3 * s), __ldg(means + 3 * s + 1), __ldg(means + 3 * s + 2)};
+            mvec(cam.R, pm, e);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) pc[i] = fa(e[i], cam.t[i]);
+            r3.y = pc[2];
+            if (!(pc[2] > cam.near_plane)) break;
+            // S5
+            const float o = __ldg(opac + s);
             r3.x = o;
+            if (!(o >= P.alpha_min)) break;
+            // S1
+            const float4 q4 = __ldg(reinterpret_cast<const float4*>(quats) + s);
+            const float qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
+            const float n2 = fa(fa(fa(fm(qw, qw), fm(qx, qx)), fm(qy, qy)), fm(qz, qz));
             if (!(n2 > 0.0f)) break;
             const float nn = fq(n2);
             const float w = fdv(qw, nn), x = fdv(qx, nn), y = fdv(qy, nn), z = fdv(qz, nn);
@@ -284,23 +305,16 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ Cams ca
             tv[0] = fm(2.0f, fs(fm(x, y), fm(w, z)));
             tv[1] = fs(1.0f, fm(2.0f, fa(fm(x, x), fm(z, z))));
             tv[2] = fm(2.0f, fa(fm(y, z), fm(w, x)));
-            // S3
-            const float su = scales[2 * s], sv = scales[2 * s + 1];
-            float e[3], au[3], av[3], pc[3];
+            // S3 (tangent columns)
+            const float2 sc2 = __ldg(reinterpret_cast<const float2*>(scales) + s);
+            const float su = sc2.x, sv = sc2.y;
+            float au[3], av[3];
             mvec(cam.R, tu, e);
 #pragma unroll
             for (int i = 0; i < 3; ++i) au[i] = fm(su, e[i]);
             mvec(cam.R, tv, e);
 #pragma unroll
             for (int i = 0; i < 3; ++i) av[i] = fm(sv, e[i]);
-            const float pm[3] = {means[3 * s], means[3 * s + 1], means[3 * s + 2]};
-            mvec(cam.R, pm, e);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) pc[i] = fa(e[i], cam.t[i]);
-            // S4, S5
-            r3.y = pc[2];
-            if (!(pc[2] > cam.near_plane)) break;
-            if (!(o >= P.alpha_min)) break;
             // S6: k^2 = 2 ln(o / alpha_min)
             const float k2 = fm(2.0f, ln32(fdv(o, P.alpha_min)));
             r3.z = k2;
@@ -345,7 +359,7 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ Cams ca
 #pragma unroll
             for (int i = 0; i < 9; ++i) m[i] = ldexpf(m[i], -ex);
             det = ldexpf(det, -ex);
-            r3.w = ldexpf(1.0f, -ex);  // the rescale, needed by the backward pass
+            r3.w = ldexpf(1.0f, -ex);
             r0 = make_float4(m[0], m[1], m[2], xc);
             r1 = make_float4(m[3], m[4], m[5], yc);
             r2 = make_float4(m[6], m[7], m[8], det);
@@ -405,57 +419,60 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ Cams ca
             float4* rr = rec + 4 * item;
             rr[0] = r0; rr[1] = r1; rr[2] = r2; rr[3] = r3;
             binrec[item] = br;
-            count[item] = 0u;
             // one gradient slot per surfel visible in any view (-1 -> -2 claims it)
-            if (atomicCAS(&splat_slot[s], -1, -2) == -1) splat_slot[s] = (int32_t)atomicAdd(&st->nslot, 1u);
+            claim = atomicCAS(&splat_slot[s], -1, -2) == -1;
+            claim_s = s;
+        }
+        if (vis) {  // per-tile pair counts (S20 intervals)
+            const Lines L = lines_of(br, P.bin_mode);
+            uint32_t cnt = 0;
+            for (int li = 0; li < L.n; ++li) {
+                const int o = L.first + li;
+                int a, b;
+                if (!line_interval(br, L, P.ts, o, a, b)) continue;
+                for (int k = a; k <= b; ++k) {
+                    const int tx = L.rows ? k : o, ty = L.rows ? o : k;
+                    atomicAdd(&tile_cnt[cam.tile_off + ty * cam.tiles_x + tx], 1u);
+                }
+                cnt += (uint32_t)(b - a + 1);
+            }
+            count[item] = cnt;
+            wide = cnt > WIDE_TILES;
         }
     }
-    // warp-aggregated append of bounded visible items (unordered)
-    const unsigned mvis = __ballot_sync(0xffffffffu, vis);
-    if (mvis) {
+    // CTA-aggregated appends (one global atomic per CTA and counter)
+    {
+        __shared__ uint32_t s_cnt[3], s_base[3];
         const int lane = threadIdx.x & 31;
-        const int leader = __ffs(mvis) - 1;
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(&st->nvis, (uint32_t)__popc(mvis));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (vis) vis_list[base + __popc(mvis & ((1u << lane) - 1u))] = (uint32_t)item;
+        const unsigned lt = (1u << lane) - 1u;
+        const bool narrow = vis && !wide, wid = vis && wide;
+        const unsigned mn = __ballot_sync(0xffffffffu, narrow), mw = __ballot_sync(0xffffffffu, wid);
+        const unsigned mc = __ballot_sync(0xffffffffu, claim);
+        if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0u;
+        __syncthreads();
+        uint32_t on = 0, ow = 0, oc = 0;
+        if (lane == 0) {
+            if (mn) on = atomicAdd(&s_cnt[0], (uint32_t)__popc(mn));
+            if (mw) ow = atomicAdd(&s_cnt[1], (uint32_t)__popc(mw));
+            if (mc) oc = atomicAdd(&s_cnt[2], (uint32_t)__popc(mc));
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_base[0] = s_cnt[0] ? atomicAdd(&st->nvis, s_cnt[0]) : 0u;
+            s_base[1] = s_cnt[1] ? atomicAdd(&st->nwide, s_cnt[1]) : 0u;
+            s_base[2] = s_cnt[2] ? atomicAdd(&st->nslot, s_cnt[2]) : 0u;
+        }
+        __syncthreads();
+        on = __shfl_sync(0xffffffffu, on, 0);
+        ow = __shfl_sync(0xffffffffu, ow, 0);
+        oc = __shfl_sync(0xffffffffu, oc, 0);
+        if (narrow) vis_list[s_base[0] + on + __popc(mn & lt)] = (uint32_t)item;
+        if (wid) wide_list[s_base[1] + ow + __popc(mw & lt)] = (uint32_t)item;
+        if (claim) splat_slot[claim_s] = (int32_t)(s_base[2] + oc + __popc(mc & lt));
     }
     if (unb) {
         const uint32_t k = atomicAdd(&st->unb_cnt[view], 1u);
         unb_list[(int64_t)view * P.N + k] = (uint32_t)item;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// k_count: one warp per bounded visible item
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_count(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
-                                               const BinRec* __restrict__ binrec, const uint32_t* __restrict__ vis_list,
-                                               uint32_t* __restrict__ count, uint32_t* __restrict__ tile_cnt,
-                                               const Status* __restrict__ st) {
-    if (st->err) return;
-    const int lane = threadIdx.x & 31;
-    const uint32_t nvis = st->nvis;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t wi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wi < nvis; wi += warps) {
-        const uint32_t item = vis_list[wi];
-        const BinRec r = binrec[item];
-        const CamDev& cam = cams.c[view_of_item(item, P.N)];
-        const Lines L = lines_of(r, P.bin_mode);
-        uint32_t cnt = 0;
-        for (int li = lane; li < L.n; li += 32) {
-            const int o = L.first + li;
-            int a, b;
-            if (!line_interval(r, L, P.ts, o, a, b)) continue;
-            for (int k = a; k <= b; ++k) {
-                const int tx = L.rows ? k : o, ty = L.rows ? o : k;
-                atomicAdd(&tile_cnt[cam.tile_off + ty * cam.tiles_x + tx], 1u);
-            }
-            cnt += (uint32_t)(b - a + 1);
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
-        if (lane == 0) count[item] = cnt;
     }
 }
 
@@ -474,21 +491,14 @@ __global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ Cams cams
     const int nt = cams.total_tiles;
     constexpr int ITEMS = 4;
     for (int base = 0; base < nt; base += 1024 * ITEMS) {
-        uint32_t v[ITEMS], bounded[ITEMS];
+        uint32_t v[ITEMS];
         uint32_t sum = 0;
 #pragma unroll
         for (int k = 0; k < ITEMS; ++k) {
             const int t = base + threadIdx.x * ITEMS + k;
-            uint32_t c = 0, b = 0;
-            if (t < nt) {
-                b = tile_cnt[t];
-                c = b + st->unb_cnt[view_of_tile(cams, t)];
-            }
-            v[k] = c;
-            bounded[k] = b;
-            sum += c;
+            v[k] = t < nt ? tile_cnt[t] + st->unb_cnt[view_of_tile(cams, t)] : 0u;
+            sum += v[k];
         }
-        // block exclusive scan of per-thread sums
         uint32_t incl = sum;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -517,7 +527,6 @@ __global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ Cams cams
                 const bool fits = run <= (uint64_t)P.pair_cap;
                 ranges[t] = make_int2(fits ? (int)s0 : 0, fits ? (int)run : 0);
                 tile_cnt[t] = fits ? (uint32_t)s0 : 0u;  // emit cursor
-                (void)bounded[k];
             }
         }
         __syncthreads();
@@ -531,19 +540,122 @@ __global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ Cams cams
 }
 
 // ---------------------------------------------------------------------------
-// k_emit: one warp per bounded visible item; the warp's lanes take the
-// flattened (line, tile) pairs so a wide item costs few rounds
+// precise render record (see record_item), written in double-float
+//
+// The ray-splat solve u ~ adj(T') (x - xc, y - yc, 1) is evaluated per pixel
+// in binary32, but the adjugate itself is computed here in double-float from
+// the binary32 inputs and rounded once: for a surfel seen nearly edge-on the
+// intersection amplifies a relative error e in T by about (depth / size) /
+// cos(view angle), so a binary32 chain (the binning mirror above) would put
+// ~1e-3 relative error into alpha.  The binning record keeps the binary32
+// values; only the render record r0..r2 and the rescale r3.w change.
+// With n2 = |q|^2, R(q/|q|) = R'(q) / n2 where R' is the homogeneous
+// (unnormalised) rotation polynomial, so n2 * T = K [r_u Rv t_u', r_v Rv t_v',
+// n2 (Rv p + t)] needs no square root; its adjugate is n2^2 adj(T).
+// ---------------------------------------------------------------------------
+__device__ void record_item(const Cams& cams, const RParams& P, const float* __restrict__ means,
+                            const float* __restrict__ scales, const float* __restrict__ quats,
+                            float4* __restrict__ rec, uint32_t item) {
+    const int view = view_of_item(item, P.N);
+    const int64_t s = (int64_t)item - (int64_t)view * P.N;
+    const CamDev& cam = cams.c[view];
+    float4* rr = rec + 4 * (size_t)item;
+    const float xc = rr[0].w, yc = rr[1].w;
+    const float4 q4 = __ldg(reinterpret_cast<const float4*>(quats) + s);
+    const float qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
+    const df ww = two_prod(qw, qw), xx = two_prod(qx, qx), yy = two_prod(qy, qy), zz = two_prod(qz, qz);
+    const df xy = two_prod(qx, qy), wz = two_prod(qw, qz), xz = two_prod(qx, qz), wy = two_prod(qw, qy);
+    const df yz = two_prod(qy, qz), wx = two_prod(qw, qx);
+    const df n2 = dadd(dadd(ww, xx), dadd(yy, zz));
+    const df tu[3] = {dsub(dadd(ww, xx), dadd(yy, zz)), dmulf(dadd(xy, wz), 2.0f), dmulf(dsub(xz, wy), 2.0f)};
+    const df tv[3] = {dmulf(dsub(xy, wz), 2.0f), dsub(dadd(ww, yy), dadd(xx, zz)), dmulf(dadd(yz, wx), 2.0f)};
+    df eu[3], ev[3], pc[3];
+    dmvec(cam.R, tu, eu);
+    dmvec(cam.R, tv, ev);
+    const df pm[3] = {dfrom(means[3 * s]), dfrom(means[3 * s + 1]), dfrom(means[3 * s + 2])};
+    dmvec(cam.R, pm, pc);
+    const float su = scales[2 * s], sv = scales[2 * s + 1];
+    df col[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        col[0][i] = dmulf(eu[i], su);
+        col[1][i] = dmulf(ev[i], sv);
+        col[2][i] = dmul(dadd(pc[i], dfrom(cam.t[i])), n2);
+    }
+    // columns of n2 * T, then shifted about (xc, yc)
+    df d[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const df cx = dadd(dmulf(col[j][0], cam.fx), dmulf(col[j][2], cam.cx));
+        const df cy = dadd(dmulf(col[j][1], cam.fy), dmulf(col[j][2], cam.cy));
+        d[j][0] = dsub(cx, dmulf(col[j][2], xc));
+        d[j][1] = dsub(cy, dmulf(col[j][2], yc));
+        d[j][2] = col[j][2];
+    }
+    df m[3][3];
+    dcross(d[1], d[2], m[0]);
+    dcross(d[2], d[0], m[1]);
+    dcross(d[0], d[1], m[2]);
+    const df det = dadd(dadd(dmul(d[0][0], m[0][0]), dmul(d[0][1], m[0][1])), dmul(d[0][2], m[0][2]));
+    float mx = 0.0f;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) mx = fmaxf(mx, fabsf(m[r][c].hi));
+    if (!(mx > 0.0f)) return;
+    int ex;
+    frexpf(mx, &ex);
+    // hit depth det(T') / c2: with M = 2^-ex n2^2 adj(T'), store 2^-ex det(n2 T') / n2
+    const float detr = ldexpf(fdv(det.hi, n2.hi), -ex);
+    rr[0] = make_float4(ldexpf(m[0][0].hi, -ex), ldexpf(m[0][1].hi, -ex), ldexpf(m[0][2].hi, -ex), xc);
+    rr[1] = make_float4(ldexpf(m[1][0].hi, -ex), ldexpf(m[1][1].hi, -ex), ldexpf(m[1][2].hi, -ex), yc);
+    rr[2] = make_float4(ldexpf(m[2][0].hi, -ex), ldexpf(m[2][1].hi, -ex), ldexpf(m[2][2].hi, -ex), detr);
+    // total scale of M relative to adj(T' of the normalised surfel)
+    rr[3].w = ldexpf(fm(n2.hi, n2.hi), -ex);
+}
+
+// ---------------------------------------------------------------------------
+// k_emit: writes every bounded visible item into one slot of each of its
+// tiles (slot order is arbitrary; the per-tile sort restores a total order)
+// and replaces the render records by their double-float versions.
+//   narrow items: one thread each, tiles in line order;
+//   wide items:   one warp each, lanes over the flattened (line, tile) pairs;
+//   records:      one thread per narrow, wide or unbounded item.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                                               const BinRec* __restrict__ binrec, const uint32_t* __restrict__ vis_list,
-                                              uint32_t* __restrict__ cursor, uint32_t* __restrict__ list,
-                                              const Status* __restrict__ st) {
+                                              const uint32_t* __restrict__ wide_list,
+                                              const uint32_t* __restrict__ unb_list, uint32_t* __restrict__ cursor,
+                                              uint32_t* __restrict__ list, const float* __restrict__ means,
+                                              const float* __restrict__ scales, const float* __restrict__ quats,
+                                              float4* __restrict__ rec, const Status* __restrict__ st) {
     if (st->err) return;
     const int lane = threadIdx.x & 31;
-    const uint32_t nvis = st->nvis;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t wi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wi < nvis; wi += warps) {
-        const uint32_t item = vis_list[wi];
+    const uint32_t nvis = st->nvis, nwide = st->nwide;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+    // narrow items
+    for (int64_t i = gtid; i < nvis; i += gstride) {
+        const uint32_t item = vis_list[i];
+        const BinRec r = binrec[item];
+        const CamDev& cam = cams.c[view_of_item(item, P.N)];
+        const Lines L = lines_of(r, P.bin_mode);
+        for (int li = 0; li < L.n; ++li) {
+            const int o = L.first + li;
+            int a, b;
+            if (!line_interval(r, L, P.ts, o, a, b)) continue;
+            for (int k = a; k <= b; ++k) {
+                const int tx = L.rows ? k : o, ty = L.rows ? o : k;
+                const uint32_t pos = atomicAdd(&cursor[cam.tile_off + ty * cam.tiles_x + tx], 1u);
+                if (pos < (uint32_t)P.pair_cap) list[pos] = item;
+            }
+        }
+        record_item(cams, P, means, scales, quats, rec, item);
+    }
+    // wide items: one warp each
+    const int64_t warps = gstride >> 5;
+    for (int64_t wi = gtid >> 5; wi < nwide; wi += warps) {
+        const uint32_t item = wide_list[wi];
         const BinRec r = binrec[item];
         const CamDev& cam = cams.c[view_of_item(item, P.N)];
         const Lines L = lines_of(r, P.bin_mode);
@@ -581,96 +693,20 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Cams cams,
             }
         }
     }
-}
-
-// ---------------------------------------------------------------------------
-// k_record: precise render record of every listed item (thread per item)
-//
-// The ray-splat solve u ~ adj(T') (x - xc, y - yc, 1) is evaluated per pixel
-// in binary32, but the adjugate itself is computed here in double-float from
-// the binary32 inputs and rounded once: for a surfel seen nearly edge-on the
-// intersection amplifies a relative error e in T by about (depth / size) /
-// cos(view angle), so a binary32 chain (the binning mirror above) would put
-// ~1e-3 relative error into alpha.  The binning record keeps the binary32
-// values; only the render record r0..r2 and the rescale r3.w change.
-// With n2 = |q|^2, R(q/|q|) = R'(q) / n2 where R' is the homogeneous
-// (unnormalised) rotation polynomial, so n2 * T = K [r_u Rv t_u', r_v Rv t_v',
-// n2 (Rv p + t)] needs no square root; its adjugate is n2^2 adj(T).
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_record(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
-                                                const float* __restrict__ means, const float* __restrict__ scales,
-                                                const float* __restrict__ quats, float4* __restrict__ rec,
-                                                const uint32_t* __restrict__ vis_list,
-                                                const uint32_t* __restrict__ unb_list, const Status* __restrict__ st) {
-    if (st->err) return;
-    const uint32_t nvis = st->nvis;
-    uint32_t total = nvis;
-    for (int v = 0; v < cams.n; ++v) total += st->unb_cnt[v];
-    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    // records of wide and unbounded items
+    uint32_t nunb = 0;
+    for (int v = 0; v < cams.n; ++v) nunb += st->unb_cnt[v];
+    for (int64_t i = gtid; i < (int64_t)nwide + nunb; i += gstride) {
         uint32_t item;
-        if (idx < nvis) {
-            item = vis_list[idx];
+        if (i < nwide) {
+            item = wide_list[i];
         } else {
-            uint32_t k = idx - nvis;
+            uint32_t k = (uint32_t)(i - nwide);
             int v = 0;
             while (k >= st->unb_cnt[v]) k -= st->unb_cnt[v++];
             item = unb_list[(int64_t)v * P.N + k];
         }
-        const int view = view_of_item(item, P.N);
-        const int64_t s = (int64_t)item - (int64_t)view * P.N;
-        const CamDev& cam = cams.c[view];
-        float4* rr = rec + 4 * (size_t)item;
-        const float xc = rr[0].w, yc = rr[1].w;
-        const float qw = quats[4 * s], qx = quats[4 * s + 1], qy = quats[4 * s + 2], qz = quats[4 * s + 3];
-        const df ww = two_prod(qw, qw), xx = two_prod(qx, qx), yy = two_prod(qy, qy), zz = two_prod(qz, qz);
-        const df xy = two_prod(qx, qy), wz = two_prod(qw, qz), xz = two_prod(qx, qz), wy = two_prod(qw, qy);
-        const df yz = two_prod(qy, qz), wx = two_prod(qw, qx);
-        const df n2 = dadd(dadd(ww, xx), dadd(yy, zz));
-        const df tu[3] = {dsub(dadd(ww, xx), dadd(yy, zz)), dmulf(dadd(xy, wz), 2.0f), dmulf(dsub(xz, wy), 2.0f)};
-        const df tv[3] = {dmulf(dsub(xy, wz), 2.0f), dsub(dadd(ww, yy), dadd(xx, zz)), dmulf(dadd(yz, wx), 2.0f)};
-        df eu[3], ev[3], pc[3];
-        dmvec(cam.R, tu, eu);
-        dmvec(cam.R, tv, ev);
-        const df pm[3] = {dfrom(means[3 * s]), dfrom(means[3 * s + 1]), dfrom(means[3 * s + 2])};
-        dmvec(cam.R, pm, pc);
-        const float su = scales[2 * s], sv = scales[2 * s + 1];
-        df col[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            col[0][i] = dmulf(eu[i], su);
-            col[1][i] = dmulf(ev[i], sv);
-            col[2][i] = dmul(dadd(pc[i], dfrom(cam.t[i])), n2);
-        }
-        // columns of n2 * T, then shifted about (xc, yc)
-        df d[3][3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const df cx = dadd(dmulf(col[j][0], cam.fx), dmulf(col[j][2], cam.cx));
-            const df cy = dadd(dmulf(col[j][1], cam.fy), dmulf(col[j][2], cam.cy));
-            d[j][0] = dsub(cx, dmulf(col[j][2], xc));
-            d[j][1] = dsub(cy, dmulf(col[j][2], yc));
-            d[j][2] = col[j][2];
-        }
-        df m[3][3];
-        dcross(d[1], d[2], m[0]);
-        dcross(d[2], d[0], m[1]);
-        dcross(d[0], d[1], m[2]);
-        const df det = dadd(dadd(dmul(d[0][0], m[0][0]), dmul(d[0][1], m[0][1])), dmul(d[0][2], m[0][2]));
-        float mx = 0.0f;
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) mx = fmaxf(mx, fabsf(m[r][c].hi));
-        if (!(mx > 0.0f)) continue;
-        int ex;
-        frexpf(mx, &ex);
-        // hit depth det(T') / c2: with M = 2^-ex n2^2 adj(T'), store 2^-ex det(n2 T') / n2
-        const float detr = ldexpf(fdv(det.hi, n2.hi), -ex);
-        rr[0] = make_float4(ldexpf(m[0][0].hi, -ex), ldexpf(m[0][1].hi, -ex), ldexpf(m[0][2].hi, -ex), xc);
-        rr[1] = make_float4(ldexpf(m[1][0].hi, -ex), ldexpf(m[1][1].hi, -ex), ldexpf(m[1][2].hi, -ex), yc);
-        rr[2] = make_float4(ldexpf(m[2][0].hi, -ex), ldexpf(m[2][1].hi, -ex), ldexpf(m[2][2].hi, -ex), detr);
-        // total scale of M relative to adj(T' of the normalised surfel)
-        rr[3].w = ldexpf(fm(n2.hi, n2.hi), -ex);
+        record_item(cams, P, means, scales, quats, rec, item);
     }
 }
 

@@ -62,28 +62,81 @@ __device__ __forceinline__ void reduce_scatter(float* v) {
     }
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// k_bwd_feat (Top-K): dots and feature gradients, grouped per tile
+// k_bwd_dots (Top-K): dots[pixel, k] = c_i . dL/dF(x) for the selected surfels
+//
+// G = (C / E) lanes per pixel (E channels per 16-byte chunk, G a power of two
+// <= 32): each lane holds one 16-byte chunk of the pixel's dL/dF row and,
+// per selected surfel, loads the same chunk of its feature row; the partial
+// dot products are summed over the G lanes with shuffles.
+// ---------------------------------------------------------------------------
+template <typename FT, int G>
+__global__ void __launch_bounds__(256) k_bwd_dots(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
+                                                  const BwdArgs a) {
+    constexpr int E = FeatVec<FT>::E;
+    if (a.st->err) return;
+    const int K = P.K, C = P.C, ts = P.ts;
+    const FT* __restrict__ feats = reinterpret_cast<const FT*>(a.feats);
+    const FT* __restrict__ dF = reinterpret_cast<const FT*>(a.d_feat);
+    const int lane = threadIdx.x & 31, sub = lane & (G - 1);
+    constexpr int GPW = 32 / G;  // pixel groups per warp
+    const int64_t groups = cams.total_pix;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // warp-uniform loop (the shuffles below need the whole warp); groups past the end idle
+    for (int64_t wb = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * GPW; wb < groups; wb += nwarps * GPW) {
+        const int64_t pix = wb + lane / G;
+        const bool live = pix < groups;
+        int view = 0;
+        if (live) {
+            int lo = 0, hi = cams.n - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (cams.c[mid].pix_off <= pix) lo = mid; else hi = mid - 1;
+            }
+            view = lo;
+        }
+        const CamDev& cam = cams.c[view];
+        const int loc = live ? (int)(pix - cam.pix_off) : 0;
+        const int py = loc / cam.W, px = loc - py * cam.W;
+        const int2 rg = live ? a.ranges[cam.tile_off + (py / ts) * cam.tiles_x + px / ts] : make_int2(0, 0);
+        const int64_t vbase = (int64_t)view * P.N;
+        float g[E];
+        if (live && sub < C / E) FeatVec<FT>::load(dF + pix * C + sub * E, g);
+        else
+#pragma unroll
+            for (int e = 0; e < E; ++e) g[e] = 0.0f;
+        for (int k = 0; k < K; ++k) {
+            const int pos = live ? a.saved_pos[pix * K + k] : -1;
+            float d = 0.0f;
+            if (pos >= 0 && sub < C / E) {
+                const int64_t sp = (int64_t)a.list[rg.x + pos] - vbase;
+                float f[E];
+                FeatVec<FT>::load(feats + sp * C + sub * E, f);
+#pragma unroll
+                for (int e = 0; e < E; ++e) d = fmaf(f[e], g[e], d);
+            }
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            if (pos >= 0 && sub == 0) a.dots[pix * K + k] = d;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_bwd_feat (Top-K): feature gradients sum_x w_i(x) dL/dF(x), grouped per tile
 //
 // Per tile (and per chunk of at most ECAP (pixel, k) entries): the tile's
-// dL/dF rows and the feature rows of the distinct selected surfels are
-// staged in shared memory (rows padded by 16 bytes so 16-byte loads from
-// different rows hit different banks); a counting sort groups the entries
-// by surfel (CSR).  Then
-//   dots   one thread per entry: c_i . dL/dF(x) -> dots[pixel, k];
-//   grads  one thread per (surfel, 4 channels): sum_x w_i(x) dL/dF(x)
-//          over the surfel's entries -> one 16-byte vector reduction.
+// dL/dF rows are staged in shared memory (rows padded by 16 bytes) and a
+// counting sort groups the entries by surfel (CSR); then one thread per
+// (surfel, 4 channels) sums its entries and issues one 16-byte vector
+// reduction.  Each thread keeps its entries' list positions and weights in
+// registers across the passes.
 // ---------------------------------------------------------------------------
 constexpr int ECAP = 2048;  // (pixel, k) entries per pass
 constexpr int PTAB = 2048;  // list positions per pass
+constexpr int EPT = ECAP / BWD_FEAT_THREADS;  // entries per thread
 
 template <typename FT>
 __device__ __forceinline__ void lds4(const FT* p, float* o);
@@ -102,165 +155,129 @@ __device__ __forceinline__ void lds4<__nv_bfloat16>(const __nv_bfloat16* p, floa
 template <int TS, typename FT>
 __global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_constant__ Cams cams,
                                                               const __grid_constant__ RParams P, const BwdArgs a,
-                                                              int pch, int ucap, int rowe) {
+                                                              int pch, int rowe) {
     constexpr int E = FeatVec<FT>::E;
     extern __shared__ __align__(16) unsigned char smem[];
     int* s_tab = reinterpret_cast<int*>(smem);  // [PTAB] position -> slot
     int* s_off = s_tab + PTAB;                  // [ECAP + 1] per-slot counts -> offsets
     int* s_cur = s_off + ECAP + 1;              // [ECAP] scatter cursors
     int* s_inv = s_cur + ECAP;                  // [ECAP] slot -> position
-    int* s_ent = s_inv + ECAP;                  // [ECAP] (slot << 16) | entry, grouped by slot
+    int* s_ent = s_inv + ECAP;                  // [ECAP] local pixel of each entry, grouped by slot
     float* s_ew = reinterpret_cast<float*>(s_ent + ECAP);  // [ECAP] weights, grouped by slot
     FT* s_df = reinterpret_cast<FT*>(smem + (((size_t)(PTAB + 5 * ECAP + 1) * 4 + 15) & ~(size_t)15));
-    FT* s_ft = s_df + (size_t)pch * rowe;
     __shared__ int s_red[33];
     __shared__ int s_max;
+    __shared__ int s_tile;
 
     if (a.st->err) return;
-    const int t = blockIdx.x;
     const int tid = threadIdx.x;
-    constexpr int ts = TS, npx = TS * TS;
+    constexpr int npx = TS * TS;
     const int K = P.K, C = P.C, nvec = C / E, nc4 = C / 4;
     const FastDiv divK(K);
     const int rv = BWD_FEAT_THREADS / nvec, r0v = tid / nvec, v0 = tid - r0v * nvec;  // row-chunk mapping
     const int rc = BWD_FEAT_THREADS / nc4, r0c = tid / nc4, c40 = tid - r0c * nc4;    // slot-channel mapping
-    const int view = view_of_tile(cams, t);
-    const CamDev& cam = cams.c[view];
-    const int lt = t - cam.tile_off;
-    const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-    const int2 rg = a.ranges[t];
-    const int64_t vbase = (int64_t)view * P.N;
-    const FT* __restrict__ feats = reinterpret_cast<const FT*>(a.feats);
-    const FT* __restrict__ dF = reinterpret_cast<const FT*>(a.d_feat);
-    auto pix_of = [&](int p, int64_t& pix) {  // tile pixel p -> global pixel; false if outside
-        const int px = tx * ts + p % ts, py = ty * ts + p / ts;
-        pix = cam.pix_off + (int64_t)py * cam.W + px;
-        return px < cam.W && py < cam.H;
-    };
+    for (int t = next_tile_q(a.persistent, &a.st->work_feat, &s_tile, true); t < cams.total_tiles;
+         t = next_tile_q(a.persistent, &a.st->work_feat, &s_tile, false)) {
+        const int view = view_of_tile(cams, t);
+        const CamDev& cam = cams.c[view];
+        const int lt = t - cam.tile_off;
+        const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
+        const int2 rg = a.ranges[t];
+        const int64_t vbase = (int64_t)view * P.N;
+        const FT* __restrict__ dF = reinterpret_cast<const FT*>(a.d_feat);
 
-    if (tid == 0) s_max = 0;
-    __syncthreads();
-    int lmax = 0;
-    for (int p = tid; p < npx; p += BWD_FEAT_THREADS) {
-        int64_t pix;
-        if (!pix_of(p, pix)) continue;
-        for (int k = K - 1; k >= 0; --k) {
-            const int pos = a.saved_pos[pix * K + k];
-            if (pos >= 0) { lmax = max(lmax, pos + 1); break; }
-        }
-    }
-    atomicMax(&s_max, lmax);
-    __syncthreads();
-    const int L = s_max;
-    if (L == 0) return;
-
-    for (int pc0 = 0; pc0 < npx; pc0 += pch) {
-        const int np = min(pch, npx - pc0);
-        const int ne = np * K;
-        // stage the chunk's dL/dF rows (zeros outside the image)
-        if (r0v < rv) {
-            for (int q = r0v; q < np; q += rv) {
-                int64_t pix;
-                uint4 val = make_uint4(0u, 0u, 0u, 0u);
-                if (pix_of(pc0 + q, pix)) val = __ldg(reinterpret_cast<const uint4*>(dF + pix * C + v0 * E));
-                *reinterpret_cast<uint4*>(s_df + (size_t)q * rowe + v0 * E) = val;
+        for (int pc0 = 0; pc0 < npx; pc0 += pch) {
+            const int np = min(pch, npx - pc0), ne = np * K;
+            // this thread's entries (e = tid + i * BLOCK): list position and weight
+            int epos[EPT], eq[EPT];
+            float ew[EPT];
+            int lmax = 0;
+#pragma unroll
+            for (int i = 0; i < EPT; ++i) {
+                const int e = tid + i * BWD_FEAT_THREADS;
+                epos[i] = -1;
+                ew[i] = 0.0f;
+                eq[i] = 0;
+                if (e < ne) {
+                    const int q = divK.div(e), k = e - q * K, p = pc0 + q;
+                    const int px = tx * TS + p % TS, py = ty * TS + p / TS;
+                    eq[i] = q;
+                    if (px < cam.W && py < cam.H) {
+                        const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
+                        epos[i] = a.saved_pos[pix * K + k];
+                        ew[i] = a.saved_w[pix * K + k];
+                        lmax = max(lmax, epos[i] + 1);
+                    }
+                }
             }
-        }
-        for (int p0 = 0; p0 < L; p0 += PTAB) {
-            for (int i = tid; i < PTAB; i += BWD_FEAT_THREADS) s_tab[i] = 0;
-            for (int i = tid; i <= ECAP; i += BWD_FEAT_THREADS) s_off[i] = 0;
-            __syncthreads();
-            // mark the selected positions of this pass
-            for (int e = tid; e < ne; e += BWD_FEAT_THREADS) {
-                const int q = divK.div(e);
-                int64_t pix;
-                if (!pix_of(pc0 + q, pix)) continue;
-                const int pos = a.saved_pos[pix * K + (e - q * K)];
-                if (pos >= p0 && pos < p0 + PTAB) s_tab[pos - p0] = 1;
-            }
-            __syncthreads();
-            const int U = block_exscan(s_tab, PTAB, s_red);  // s_tab[pos] = slot where marked
-            if (U == 0) continue;
-            for (int i = tid; i < PTAB; i += BWD_FEAT_THREADS) {
-                const int nxt = i + 1 < PTAB ? s_tab[i + 1] : U;
-                if (nxt - s_tab[i] == 1) s_inv[s_tab[i]] = i;
-            }
-            // count entries per slot, then offsets (CSR)
-            for (int e = tid; e < ne; e += BWD_FEAT_THREADS) {
-                const int q = divK.div(e);
-                int64_t pix;
-                if (!pix_of(pc0 + q, pix)) continue;
-                const int pos = a.saved_pos[pix * K + (e - q * K)];
-                if (pos >= p0 && pos < p0 + PTAB) atomicAdd(&s_off[s_tab[pos - p0]], 1);
-            }
-            __syncthreads();
-            const int nsel = block_exscan(s_off, U, s_red);
-            for (int i = tid; i < U; i += BWD_FEAT_THREADS) s_cur[i] = s_off[i];
-            if (tid == 0) s_off[U] = nsel;
-            __syncthreads();
-            for (int e = tid; e < ne; e += BWD_FEAT_THREADS) {
-                const int q = divK.div(e);
-                int64_t pix;
-                if (!pix_of(pc0 + q, pix)) continue;
-                const int pos = a.saved_pos[pix * K + (e - q * K)];
-                if (pos >= p0 && pos < p0 + PTAB) {
-                    const int slot = s_tab[pos - p0];
-                    const int at = atomicAdd(&s_cur[slot], 1);
-                    s_ent[at] = (slot << 16) | e;
-                    s_ew[at] = a.saved_w[pix * K + (e - q * K)];
+            if (tid == 0) s_max = 0;
+            // stage the chunk's dL/dF rows (zeros outside the image)
+            if (r0v < rv) {
+                for (int q = r0v; q < np; q += rv) {
+                    const int p = pc0 + q, px = tx * TS + p % TS, py = ty * TS + p / TS;
+                    uint4 val = make_uint4(0u, 0u, 0u, 0u);
+                    if (px < cam.W && py < cam.H)
+                        val = __ldg(reinterpret_cast<const uint4*>(
+                            dF + (cam.pix_off + (int64_t)py * cam.W + px) * C + v0 * E));
+                    *reinterpret_cast<uint4*>(s_df + (size_t)q * rowe + v0 * E) = val;
                 }
             }
             __syncthreads();
-            for (int u0 = 0; u0 < U; u0 += ucap) {
-                const int u1 = min(U, u0 + ucap);
-                // stage the feature rows of slots [u0, u1)
-                if (r0v < rv) {
-                    for (int sl = r0v; sl < u1 - u0; sl += rv) {
-                        const int64_t sp = (int64_t)a.list[rg.x + p0 + s_inv[u0 + sl]] - vbase;
-                        *reinterpret_cast<uint4*>(s_ft + (size_t)sl * rowe + v0 * E) =
-                            __ldg(reinterpret_cast<const uint4*>(feats + sp * C + v0 * E));
+            atomicMax(&s_max, lmax);
+            __syncthreads();
+            const int L = s_max;
+            for (int p0 = 0; p0 < L; p0 += PTAB) {
+                for (int i = tid; i < PTAB; i += BWD_FEAT_THREADS) s_tab[i] = 0;
+                for (int i = tid; i <= ECAP; i += BWD_FEAT_THREADS) s_off[i] = 0;
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < EPT; ++i)
+                    if (epos[i] >= p0 && epos[i] < p0 + PTAB) s_tab[epos[i] - p0] = 1;
+                __syncthreads();
+                const int U = block_exscan(s_tab, PTAB, s_red);  // s_tab[pos] = slot where marked
+                if (U == 0) continue;
+                for (int i = tid; i < PTAB; i += BWD_FEAT_THREADS) {
+                    const int nxt = i + 1 < PTAB ? s_tab[i + 1] : U;
+                    if (nxt - s_tab[i] == 1) s_inv[s_tab[i]] = i;
+                }
+#pragma unroll
+                for (int i = 0; i < EPT; ++i)
+                    if (epos[i] >= p0 && epos[i] < p0 + PTAB) atomicAdd(&s_off[s_tab[epos[i] - p0]], 1);
+                __syncthreads();
+                const int nsel = block_exscan(s_off, U, s_red);
+                for (int i = tid; i < U; i += BWD_FEAT_THREADS) s_cur[i] = s_off[i];
+                if (tid == 0) s_off[U] = nsel;
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < EPT; ++i) {
+                    if (epos[i] >= p0 && epos[i] < p0 + PTAB) {
+                        const int at = atomicAdd(&s_cur[s_tab[epos[i] - p0]], 1);
+                        s_ent[at] = eq[i];
+                        s_ew[at] = ew[i];
                     }
                 }
                 __syncthreads();
-                // dots: one thread per entry
-                for (int i = s_off[u0] + tid; i < s_off[u1]; i += BWD_FEAT_THREADS) {
-                    const int ent = s_ent[i], e = ent & 0xffff, sl = (ent >> 16) - u0, q = divK.div(e);
-                    const FT* fr = s_ft + (size_t)sl * rowe;
-                    const FT* gr = s_df + (size_t)q * rowe;
-                    float d0 = 0.0f, d1 = 0.0f;
-                    for (int c = 0; c < C; c += E) {
-                        float f[E], g[E];
-                        FeatVec<FT>::lds(fr + c, f);
-                        FeatVec<FT>::lds(gr + c, g);
+                // one thread per (slot, 4 channels)
+                if (r0c < rc) {
+                    for (int slot = r0c; slot < U; slot += rc) {
+                        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                        const int e1 = s_off[slot + 1];
+                        for (int i = s_off[slot]; i < e1; ++i) {
+                            const float w = s_ew[i];
+                            float gv[4];
+                            lds4<FT>(s_df + (size_t)s_ent[i] * rowe + 4 * c40, gv);
 #pragma unroll
-                        for (int k = 0; k < E; k += 2) {
-                            d0 = fmaf(f[k], g[k], d0);
-                            d1 = fmaf(f[k + 1], g[k + 1], d1);
+                            for (int k = 0; k < 4; ++k) acc[k] = fmaf(w, gv[k], acc[k]);
                         }
+                        const int64_t sp = (int64_t)a.list[rg.x + p0 + s_inv[slot]] - vbase;
+                        red_add_v4(a.feat_acc + (int64_t)a.splat_slot[sp] * C + 4 * c40, acc[0], acc[1], acc[2],
+                                   acc[3]);
                     }
-                    int64_t pix;
-                    pix_of(pc0 + q, pix);
-                    a.dots[pix * K + (e - q * K)] = d0 + d1;
-                }
-                // feature gradients: one thread per (slot, 4 channels)
-                for (int sl = r0c; r0c < rc && sl < u1 - u0; sl += rc) {
-                    const int c4 = c40, slot = u0 + sl;
-                    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-                    for (int i = s_off[slot]; i < s_off[slot + 1]; ++i) {
-                        const int q = divK.div(s_ent[i] & 0xffff);
-                        const float w = s_ew[i];
-                        float g[4];
-                        lds4<FT>(s_df + (size_t)q * rowe + 4 * c4, g);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) acc[k] = fmaf(w, g[k], acc[k]);
-                    }
-                    const int64_t sp = (int64_t)a.list[rg.x + p0 + s_inv[slot]] - vbase;
-                    red_add_v4(a.feat_acc + (int64_t)a.splat_slot[sp] * C + 4 * c4, acc[0], acc[1], acc[2], acc[3]);
                 }
                 __syncthreads();
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
@@ -282,12 +299,14 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
     float* s_f = s_g + NB * 16;    // FULL: [NB][C] features
     float* s_gf = s_f + (FULL ? NB * P.C : 0);  // FULL: [NB][C] feature gradients
     __shared__ int s_max;
+    __shared__ int s_tile;
 
     if (a.st->err) return;
-    const int t = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t wbit = 1u << (tid >> 5);
     const int C = P.C, K = P.K;
+    for (int t = next_tile_q(a.persistent, &a.st->work_geo, &s_tile, true); t < cams.total_tiles;
+         t = next_tile_q(a.persistent, &a.st->work_geo, &s_tile, false)) {
     const int view = view_of_tile(cams, t);
     const CamDev& cam = cams.c[view];
     const int lt = t - cam.tile_off;
@@ -377,7 +396,7 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
             if (pos < nstop && eval_splat(s_r0[j], s_r1[j], s_r2[j], oc.x, pxf, pyf, P.alpha_min, cam.near_plane, h)) {
                 contrib = true;
                 const float alpha = fminf(h.alpha_raw, P.alpha_max);
-                const float Tj = T / (1.0f - alpha);
+                const float Tj = T * rcp_approx(1.0f - alpha);
                 w = alpha * Tj;
                 float s = oc.y * gr + oc.z * gg + oc.w * gb;
                 if (!FULL) {
@@ -408,8 +427,7 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
                 g[11] = w * gg;
                 g[12] = w * gb;
                 if (h.alpha_raw < P.alpha_max) {
-                    const float G = h.alpha_raw / oc.x;
-                    g[9] = dal * G;
+                    g[9] = dal * h.G;
                     const float drho = -0.5f * alpha * dal;
                     const float du = 2.0f * h.u * drho, dv = 2.0f * h.v * drho;
                     const float gc0 = du * h.inv, gc1 = dv * h.inv, gc2 = -(du * h.u + dv * h.v) * h.inv;
@@ -464,6 +482,8 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
             }
         }
     }
+    __syncthreads();
+    }  // tiles
 }
 
 // ---------------------------------------------------------------------------
@@ -611,6 +631,10 @@ __global__ void __launch_bounds__(256) k_feat_out(const __grid_constant__ RParam
 // zero the gradient slots in use: grad rows (all views) and feature rows
 __global__ void __launch_bounds__(256) k_bwd_clear(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                                                    const BwdArgs a) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.st->work_feat = 0u;
+        a.st->work_geo = 0u;
+    }
     const int64_t ns = a.st->nslot;
     const int64_t g4 = ns * (GRAD_STRIDE / 4);
     const int64_t f4 = ns * (P.C / 4);
@@ -636,21 +660,53 @@ cudaError_t set_smem(const void* k, size_t smem) {
     return cudaSuccess;
 }
 
+// one resident wave: CTAs per SM times SMs, capped by the number of tiles
+cudaError_t persistent_grid(const void* k, int threads, size_t smem, int& grid) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    grid = std::max(1, std::min(grid, std::max(1, per_sm) * sms));
+    return cudaSuccess;
+}
+
 template <typename FT>
-cudaError_t launch_feat(const Cams& cams, const RParams& P, const BwdArgs& a, cudaStream_t s) {
+cudaError_t launch_feat(const Cams& cams, const RParams& P, const BwdArgs& a, int num_sms, cudaStream_t s) {
+    // dots: G lanes per pixel
+    const int nvec = P.C / FeatVec<FT>::E;
+    int G = 1;
+    while (G < nvec) G <<= 1;
+    if (G > 32) return cudaErrorInvalidValue;  // C too large for the dot kernel (checked by the ABI)
+    const int64_t groups = cams.total_pix;
+    const int blocks = (int)std::min<int64_t>((groups * G + 255) / 256, (int64_t)num_sms * 16);
+#define FSS_DOTS(GG) k_bwd_dots<FT, GG><<<std::max(1, blocks), 256, 0, s>>>(cams, P, a)
+    switch (G) {
+        case 1: FSS_DOTS(1); break;
+        case 2: FSS_DOTS(2); break;
+        case 4: FSS_DOTS(4); break;
+        case 8: FSS_DOTS(8); break;
+        case 16: FSS_DOTS(16); break;
+        default: FSS_DOTS(32); break;
+    }
+#undef FSS_DOTS
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // grouped feature gradients
     const int rowe = P.C + 16 / (int)sizeof(FT);  // padded row, elements
     const size_t rowb = (size_t)rowe * sizeof(FT);
     const size_t fixed = (((size_t)(PTAB + 5 * ECAP + 1) * 4 + 15) & ~(size_t)15);
-    const size_t budget = 112 * 1024;
     const int npx = P.ts * P.ts;
     int pch = std::min(npx, ECAP / std::max(1, P.K));
-    pch = (int)std::min<size_t>((size_t)pch, std::max<size_t>(32, (40 * 1024) / rowb));
-    const int ucap = (int)std::max<size_t>(16, std::min<size_t>(ECAP, (budget - fixed - pch * rowb) / rowb));
-    const size_t smem = fixed + (size_t)(pch + ucap) * rowb;
+    pch = (int)std::min<size_t>((size_t)pch, std::max<size_t>(32, (64 * 1024) / rowb));
+    const size_t smem = fixed + (size_t)pch * rowb;
     auto go = [&](auto kern) {
-        cudaError_t e = set_smem((const void*)kern, smem);
-        if (e != cudaSuccess) return e;
-        kern<<<cams.total_tiles, BWD_FEAT_THREADS, smem, s>>>(cams, P, a, pch, ucap, rowe);
+        cudaError_t e2 = set_smem((const void*)kern, smem);
+        if (e2 != cudaSuccess) return e2;
+        int grid = cams.total_tiles;
+        if (a.persistent && (e2 = persistent_grid((const void*)kern, BWD_FEAT_THREADS, smem, grid)) != cudaSuccess)
+            return e2;
+        kern<<<grid, BWD_FEAT_THREADS, smem, s>>>(cams, P, a, pch, rowe);
         return cudaGetLastError();
     };
     if (P.ts == 8) return go(k_bwd_feat<8, FT>);
@@ -664,7 +720,11 @@ cudaError_t launch_geo_one(const Cams& cams, const RParams& P, const BwdArgs& a,
     const size_t smem = (size_t)NB * (4 * 16 + 8) + (size_t)NB * 16 * 4 + (FULL ? (size_t)NB * P.C * 8 : 0);  // staging, masks, partials, rows
     cudaError_t e = set_smem((const void*)k_bwd_geo<TS, FULL, CMAX, FT>, smem);
     if (e != cudaSuccess) return e;
-    k_bwd_geo<TS, FULL, CMAX, FT><<<cams.total_tiles, TS * TS, smem, s>>>(cams, P, a);
+    int grid = cams.total_tiles;
+    if (a.persistent && (e = persistent_grid((const void*)k_bwd_geo<TS, FULL, CMAX, FT>, TS * TS, smem, grid)) !=
+                            cudaSuccess)
+        return e;
+    k_bwd_geo<TS, FULL, CMAX, FT><<<grid, TS * TS, smem, s>>>(cams, P, a);
     return cudaGetLastError();
 }
 
@@ -682,7 +742,7 @@ cudaError_t launch_all(const Cams& cams, const RParams& P, const BwdArgs& a, int
     k_bwd_clear<<<num_sms * 4, 256, 0, s>>>(cams, P, a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (P.K > 0) {
-        if ((e = launch_feat<FT>(cams, P, a, s)) != cudaSuccess) return e;
+        if ((e = launch_feat<FT>(cams, P, a, num_sms, s)) != cudaSuccess) return e;
     }
     if (P.ts == 8) e = launch_geo<8, FT>(cams, P, a, s);
     else if (P.ts == 16) e = launch_geo<16, FT>(cams, P, a, s);

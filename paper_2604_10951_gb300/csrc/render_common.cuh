@@ -5,6 +5,8 @@
 
 #include "fss_internal.cuh"
 
+#include <climits>
+
 namespace fss {
 
 constexpr int BATCH = 256;   // staged records per batch (Top-K kernels)
@@ -27,7 +29,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // the surfel is skipped (alpha below alpha_min, hit at or behind the near
 // plane, or a non-finite intersection).
 struct Hit {
-    float X, Y, u, v, inv, alpha_raw;
+    float X, Y, u, v, inv, G, alpha_raw;  // G = exp(-(u^2+v^2)/2), alpha_raw = o G
 };
 
 __device__ __forceinline__ bool eval_splat(const float4& A, const float4& B, const float4& Cq, float o, float pxf,
@@ -41,7 +43,8 @@ __device__ __forceinline__ bool eval_splat(const float4& A, const float4& B, con
     h.u = c0 * h.inv;
     h.v = c1 * h.inv;
     const float rho = fmaf(h.u, h.u, h.v * h.v);
-    h.alpha_raw = o * ex2_approx(NEG_HALF_LOG2E * rho);
+    h.G = ex2_approx(NEG_HALF_LOG2E * rho);
+    h.alpha_raw = o * h.G;
     return (h.alpha_raw >= alpha_min) && (Cq.w * h.inv > near_plane);
 }
 
@@ -135,6 +138,18 @@ __device__ __forceinline__ uint32_t warp_row_mask(int tile_y0, int py0, int py1)
     const int w0 = r0 / R, w1 = r1 / R;
     const uint32_t hi = (w1 >= 31) ? 0xffffffffu : ((2u << w1) - 1u);
     return (hi & ~((1u << w0) - 1u)) & (NW >= 32 ? 0xffffffffu : ((1u << NW) - 1u));
+}
+
+// Next tile of a CTA: its own index (grid schedule), or the head of a
+// device work queue (persistent schedule).  Contains __syncthreads in the
+// persistent case, so it also separates consecutive tiles' use of shared
+// memory.
+__device__ __forceinline__ int next_tile_q(int persistent, uint32_t* queue, int* s_tile, bool first) {
+    if (!persistent) return first ? (int)blockIdx.x : INT_MAX;
+    __syncthreads();
+    if (threadIdx.x == 0) *s_tile = (int)atomicAdd(queue, 1u);
+    __syncthreads();
+    return *s_tile;
 }
 
 // exclusive scan of v[0, n) in shared memory by the whole CTA (n <= 8 *

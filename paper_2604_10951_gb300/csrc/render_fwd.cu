@@ -29,13 +29,8 @@ namespace fss {
 
 namespace {
 
-// next tile of this CTA: its own index, or the head of the work queue
 __device__ __forceinline__ int next_tile(const FwdArgs& a, int* s_tile, bool first) {
-    if (!a.persistent) return first ? (int)blockIdx.x : INT_MAX;
-    __syncthreads();
-    if (threadIdx.x == 0) *s_tile = (int)atomicAdd(&a.st->work, 1u);
-    __syncthreads();
-    return *s_tile;
+    return next_tile_q(a.persistent, &a.st->work, s_tile, first);
 }
 
 }  // namespace
@@ -375,7 +370,7 @@ cudaError_t launch(KernelT kern, int threads, size_t smem, const Cams& cams, con
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
         if (e != cudaSuccess) return e;
-        grid = max(1, per_sm) * num_sms;
+        grid = std::min(cams.total_tiles, max(1, per_sm) * num_sms);
     }
     if (grid <= 0) return cudaSuccess;
     kern<<<grid, threads, smem, stream>>>(cams, P, a);

@@ -15,13 +15,15 @@ from . import _lib as L
 
 BIN_MODES = {"aabb": L.FSS_BIN_AABB, "snug": L.FSS_BIN_SNUG, "accu": L.FSS_BIN_ACCU}
 STOP_RULES = {"tmin": L.FSS_STOP_TMIN, "exact_topk": L.FSS_STOP_EXACT_TOPK}
+SCHEDULES = {"grid": L.FSS_SCHED_GRID, "persistent": L.FSS_SCHED_PERSISTENT}
 DTYPES = {torch.float32: L.FSS_F32, torch.bfloat16: L.FSS_BF16}
 TORCH_DTYPES = {L.FSS_F32: torch.float32, L.FSS_BF16: torch.bfloat16}
 
 
 def make_params(C: int, K: int = 8, tile_size: int = 16, bin_mode="accu", stop_rule="tmin",
                 alpha_min: float = 1.0 / 255.0, alpha_max: float = 0.99, T_min: float = 1e-4,
-                feat_dtype=torch.float32, out_dtype=None, bg=(0.0, 0.0, 0.0)) -> L.fss_params:
+                feat_dtype=torch.float32, out_dtype=None, bg=(0.0, 0.0, 0.0),
+                schedule="grid") -> L.fss_params:
     p = L.fss_default_params()
     p.tile_size, p.K, p.C = int(tile_size), int(K), int(C)
     p.bin_mode = BIN_MODES[bin_mode] if isinstance(bin_mode, str) else int(bin_mode)
@@ -32,6 +34,7 @@ def make_params(C: int, K: int = 8, tile_size: int = 16, bin_mode="accu", stop_r
     p.out_dtype = DTYPES[od] if isinstance(od, torch.dtype) else int(od)
     for k in range(3):
         p.bg_rgb[k] = float(bg[k])
+    p.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
     return p
 
 
