@@ -105,7 +105,10 @@ def test_graph_replay_of_batched_fwd_bwd_matches_eager():
         assert torch.equal(got[k], eager[k])
     for x, y in zip(got[4:], eager[4:]):  # gradient sums use atomics: equal up to rounding order
         scale = y.float().abs().max().item()
-        assert (x.float() - y.float()).abs().max().item() <= 1e-5 * scale + 1e-12
+        # a different summation order may round a BF16 result one BF16 ulp (2^-8 relative) apart
+        rel = 2.0 ** -7 if x.dtype == torch.bfloat16 else 1e-5
+        tol = rel * y.float().abs() + 1e-5 * scale + 1e-12
+        assert bool(((x.float() - y.float()).abs() <= tol).all())
 
 
 def test_autotuner_picks_a_valid_configuration(tmp_path):
