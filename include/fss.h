@@ -5,10 +5,12 @@
  *
  * All device memory is owned by the caller.  The library allocates nothing:
  * every entry point works inside a caller-provided `workspace` (size from
- * fss_workspace_size) and caller-provided outputs.  Every compute call is
- * asynchronous on the given CUDA stream (`fss_stream_t` is the same type as
- * cudaStream_t; NULL means the legacy default stream) and can be captured in
- * a CUDA graph.  Only fss_read_status synchronises with the host.
+ * fss_workspace_size) and caller-provided outputs.  The one exception is
+ * fss_forward_static, which uses a fixed static device array instead.  Every
+ * other compute call is asynchronous on the given CUDA stream (`fss_stream_t`
+ * is the same type as cudaStream_t; NULL means the legacy default stream) and
+ * can be captured in a CUDA graph.  Only fss_read_status and
+ * fss_forward_static synchronise with the host.
  *
  * Conventions shared by all calls:
  *   - surfel parameters are float32, row-major, N rows:
@@ -186,6 +188,56 @@ fss_status fss_read_status(const fss_params *params, const fss_camera *cams, int
 fss_status fss_loss_l2_l1(const fss_params *params, int64_t n_pix, const void *feat, const float *rgb,
                           const void *feat_target, const float *rgb_target, float w_feat, float w_rgb,
                           void *d_feat, float *d_rgb, double *loss, fss_stream_t stream);
+
+/*
+ * Size of the device scratch array behind fss_forward_static: 64 MiB per
+ * device, reserved when the library's module loads on that device.
+ */
+#define FSS_STATIC_SCRATCH_BYTES (64u << 20)
+
+/*
+ * fss_forward_static -- a forward frame that allocates nothing and needs no
+ * caller workspace.  The paper has no counterpart: this is a convenience of
+ * this library's C ABI.
+ *
+ * Who it is for: callers that cannot hand the library device memory at call
+ * time.  Examples are a plain C host program with no device allocator of its
+ * own; a real-time loop where cudaMalloc/cudaFree are not acceptable, since
+ * cudaFree waits for the whole device; and a process whose device memory is
+ * already fully reserved by another framework's pool.  Such a caller provides
+ * only the surfel inputs and the outputs.
+ *
+ * What it does: fss_project_bin, fss_sort and fss_render_forward, then
+ * fss_read_status, with the same arguments, on a workspace inside a
+ * file-scope device array of FSS_STATIC_SCRATCH_BYTES.  The outputs equal
+ * those calls' outputs on a caller workspace.  The call returns after
+ * `stream` has finished the frame.  It returns FSS_ERR_CAPACITY (with
+ * *num_pairs = pairs needed; retry with a larger pair_capacity) or FSS_OK
+ * (with *num_pairs = pairs used); num_pairs may be NULL.
+ *
+ * Limit: a frame whose fss_workspace_size(params, cams, n_cams, N,
+ * pair_capacity) exceeds FSS_STATIC_SCRATCH_BYTES is rejected with
+ * FSS_ERR_UNSUPPORTED before anything is launched.  About 64 + 80 + 20 bytes
+ * per (surfel, view), 64 per (surfel, view) and 4 C per surfel for the
+ * gradient regions, 4 K per pixel, and 20 bytes per pair must fit.
+ *
+ * Set-up: the first call on each device looks up the array's address
+ * (cudaGetSymbolAddress, with that device current) and keeps it.  Make
+ * that first call before any stream capture.
+ *
+ * Sharing: all calls on one device share the one array, so calls that
+ * overlap in time race and corrupt each other's frames.  Overlap comes from
+ * other streams or other host threads.  Serialise them, e.g. one stream
+ * and one thread.  A frame's `saved` buffer stays valid.  Running
+ * fss_render_backward on it needs the workspace, which lives in the static
+ * array and is not exposed; use a caller workspace when gradients are
+ * needed.
+ */
+fss_status fss_forward_static(const fss_params *params, const fss_camera *cams, int32_t n_cams, int64_t N,
+                              int64_t pair_capacity, const float *means, const float *scales,
+                              const float *quats, const float *opac, const float *rgb, const void *feats,
+                              void *out_feat, float *out_rgb, float *out_T, int32_t *out_topk_id, void *saved,
+                              int64_t *num_pairs, fss_stream_t stream);
 
 /* Message of the last error returned to the calling thread ("" if none). */
 const char *fss_last_error(void);

@@ -29,7 +29,8 @@ REG_SORTTMP, REG_GRAD_ITEM, REG_FEAT_ACC, REG_DOTS, REG_VIS, REG_UNB, REG_SLOT, 
 
 EXPORTS = ["fss_default_params", "fss_workspace_size", "fss_saved_size", "fss_project_bin", "fss_sort",
            "fss_render_forward", "fss_render_backward", "fss_read_status", "fss_last_error",
-           "fss_workspace_region", "fss_loss_l2_l1"]
+           "fss_workspace_region", "fss_loss_l2_l1", "fss_forward_static"]
+FSS_STATIC_SCRATCH_BYTES = 64 << 20
 
 
 class fss_camera(C.Structure):
@@ -77,6 +78,8 @@ def lib():
                 "fss_read_status": [pp, pc, i32, i64, P, i64, C.POINTER(C.c_int64), P],
                 "fss_workspace_region": [pp, pc, i32, i64, i64, i32, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)],
                 "fss_loss_l2_l1": [pp, i64, P, P, P, P, C.c_float, C.c_float, P, P, P, P],
+                "fss_forward_static": [pp, pc, i32, i64, i64, P, P, P, P, P, P, P, P, P, P, P,
+                                       C.POINTER(C.c_int64), P],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -156,4 +159,15 @@ def fss_read_status(params, cams, n_cams, N, workspace, pair_capacity, stream):
     """Returns (status, num_pairs) without raising on device-side errors."""
     n = C.c_int64()
     s = lib().fss_read_status(C.byref(params), cams, n_cams, N, workspace, pair_capacity, C.byref(n), stream)
+    return s, n.value
+
+
+def fss_forward_static(params, cams, n_cams, N, pair_capacity, means, scales, quats, opac, rgb, feats, out_feat,
+                       out_rgb, out_T, out_topk_id, saved, stream):
+    """Returns (status, num_pairs); raises only on argument or CUDA errors."""
+    n = C.c_int64()
+    s = lib().fss_forward_static(C.byref(params), cams, n_cams, N, pair_capacity, means, scales, quats, opac, rgb,
+                                 feats, out_feat, out_rgb, out_T, out_topk_id, saved, C.byref(n), stream)
+    if s not in (FSS_OK, FSS_ERR_CAPACITY):
+        check(s)
     return s, n.value

@@ -28,6 +28,7 @@ UNITS = {
     "render_fwd.cu": [],
     "render_bwd.cu": [],
     "loss.cu": [],
+    "static_scratch.cu": [],
 }
 
 

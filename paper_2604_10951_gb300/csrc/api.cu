@@ -166,6 +166,10 @@ fss_status prepare(const fss_params* params, const fss_camera* cams, int32_t n_c
 bool misaligned16(const void* p) { return p && (reinterpret_cast<uintptr_t>(p) & 15); }
 
 }  // namespace
+
+// Records `msg` as the calling thread's last error (for units outside this file).
+fss_status set_error(fss_status s, const char* msg) { return fail(s, "%s", msg); }
+
 }  // namespace fss
 
 using namespace fss;

@@ -1,0 +1,117 @@
+"""The C ABI library loads on a machine without a GPU, exports every function
+that include/fss.h declares, and its host-only calls (sizes, layout,
+argument validation) behave as documented.  No call here reaches the GPU:
+every call either needs no device or is rejected before any launch."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2604_10951_gb300 import _lib as L
+from paper_2604_10951_gb300.build import build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "fss.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return L.lib()
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:fss_status|const char \*)\s*(fss_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_binding_exports():
+    assert _declared() == sorted(L.EXPORTS)
+
+
+def test_library_exports_every_declared_function(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_header_constants_match_binding():
+    text = open(HEADER).read()
+    assert f"#define FSS_MAX_CAMS {L.FSS_MAX_CAMS}" in text
+    assert f"#define FSS_MAX_K {L.FSS_MAX_K}" in text
+    m = re.search(r"#define FSS_STATIC_SCRATCH_BYTES \((\d+)u << (\d+)\)", text)
+    assert m and int(m.group(1)) << int(m.group(2)) == L.FSS_STATIC_SCRATCH_BYTES
+
+
+def _cam(w=64, h=48):
+    c = (L.fss_camera * 1)()
+    c[0].fx = c[0].fy = 50.0
+    c[0].cx, c[0].cy = w / 2, h / 2
+    c[0].width, c[0].height = w, h
+    for k, v in enumerate([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 3]):
+        c[0].viewmat[k] = v
+    c[0].near_plane = 0.2
+    return c
+
+
+def test_default_params_and_sizes(lib):
+    p = L.fss_default_params()
+    assert (p.tile_size, p.K, p.bin_mode, p.stop_rule, p.C) == (16, 8, L.FSS_BIN_ACCU, L.FSS_STOP_TMIN, 16)
+    cams = _cam()
+    ws = L.fss_workspace_size(p, cams, 1, 1000, 5000)
+    assert ws % 256 == 0 and ws > 0
+    # every region lies inside the workspace, 256-byte aligned, without overlap
+    spans = []
+    for r in range(16):
+        off, size = L.fss_workspace_region(p, cams, 1, 1000, 5000, r)
+        assert off + size <= ws
+        if r == L.REG_COUNTERS:  # the counters sit inside the status block
+            s0, n0 = L.fss_workspace_region(p, cams, 1, 1000, 5000, L.REG_STATUS)
+            assert s0 <= off and off + size <= s0 + n0
+        elif size:
+            assert off % 256 == 0
+            spans.append((off, off + size))
+    spans.sort()
+    assert all(a[1] <= b[0] for a, b in zip(spans, spans[1:]))
+    # pairs cost 20 bytes each (list + sort scratch)
+    assert L.fss_workspace_size(p, cams, 1, 1000, 5000 + 256 * 100) - ws == 256 * 100 * 20
+    sv = L.fss_saved_size(p, cams, 1)
+    assert sv == 2 * 64 * 48 * 8 * 4 + 64 * 48 * 4
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("tile_size", 12, L.FSS_ERR_UNSUPPORTED), ("K", 33, L.FSS_ERR_UNSUPPORTED),
+    ("C", 6, L.FSS_ERR_UNSUPPORTED), ("alpha_min", 0.0, L.FSS_ERR_INVALID_ARG),
+    ("alpha_max", 1.0, L.FSS_ERR_INVALID_ARG), ("schedule", 5, L.FSS_ERR_INVALID_ARG),
+    ("bin_mode", 7, L.FSS_ERR_INVALID_ARG)])
+def test_invalid_params_are_rejected_before_any_launch(lib, field, value, status):
+    p = L.fss_default_params()
+    setattr(p, field, value)
+    out = C.c_size_t()
+    assert lib.fss_workspace_size(C.byref(p), _cam(), 1, 10, 10, C.byref(out)) == status
+    assert L.last_error()
+    # compute calls validate the same way and return before touching a device
+    assert lib.fss_project_bin(C.byref(p), _cam(), 1, 10, None, None, None, None, None, 10, None) == status
+
+
+def test_bad_camera_and_sizes_are_rejected(lib):
+    p = L.fss_default_params()
+    out = C.c_size_t()
+    cams = _cam()
+    cams[0].fx = 0.0
+    assert lib.fss_workspace_size(C.byref(p), cams, 1, 10, 10, C.byref(out)) == L.FSS_ERR_INVALID_ARG
+    assert lib.fss_workspace_size(C.byref(p), _cam(), 0, 10, 10, C.byref(out)) == L.FSS_ERR_UNSUPPORTED
+    assert lib.fss_workspace_size(C.byref(p), _cam(), 1, -1, 10, C.byref(out)) == L.FSS_ERR_UNSUPPORTED
+    assert lib.fss_workspace_size(C.byref(p), _cam(), 1, 10, 1 << 31, C.byref(out)) == L.FSS_ERR_UNSUPPORTED
+    assert lib.fss_project_bin(C.byref(L.fss_default_params()), _cam(), 1, 10, None, None, None, None, None, 10,
+                               None) == L.FSS_ERR_INVALID_ARG  # NULL workspace
+
+
+def test_static_forward_rejects_oversized_frames_on_the_host(lib):
+    p = L.fss_default_params()
+    cams = _cam()
+    big = L.FSS_STATIC_SCRATCH_BYTES // 16
+    assert L.fss_workspace_size(p, cams, 1, 1000, big) > L.FSS_STATIC_SCRATCH_BYTES
+    n = C.c_int64()
+    s = lib.fss_forward_static(C.byref(p), cams, 1, 1000, big, *([None] * 11), C.byref(n), None)
+    assert s == L.FSS_ERR_UNSUPPORTED and "FSS_STATIC_SCRATCH_BYTES" in L.last_error()
