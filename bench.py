@@ -39,7 +39,7 @@ L2_BYTES = 129 * 1024 * 1024
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=64)
+    ap.add_argument("--steps", type=int, default=256)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip baseline/e2e/cpu legs (profiling runs)")
@@ -92,7 +92,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -229,7 +229,7 @@ def run_ours(args):
             rec(5)
 
         def capture(self):
-            """One graph per pose: the whole step, 13 kernels and 3 memsets."""
+            """One graph per pose: the whole step, 11 kernels and 4 memsets."""
             for i in range(len(cams_c)):
                 self.step(i)  # sets kernel attributes outside capture
             torch.cuda.synchronize()
@@ -282,7 +282,9 @@ def run_ours(args):
     ms_step = total_ms / args.steps
     frames = args.steps * D.world
     value = frames / (total_ms / 1e3)
-    launches_per_step = 5 + 1 + 1 + 1 + 5  # project(5) sort(1) forward(1) loss(1) backward(5)
+    # kernels per step: project_bin 3 (project, scan, emit), sort 1, forward 1, loss 1,
+    # backward 5 (clear, feature grads + dots, geometry replay, projection, feature rows)
+    launches_per_step = 3 + 1 + 1 + 1 + 5
 
     out = {"metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": D.world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),

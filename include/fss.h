@@ -244,11 +244,22 @@ const char *fss_last_error(void);
 
 /*
  * Offset and size of a named region inside the workspace (for inspection
- * and tests).  Regions: 0 status, 1 per-(view,surfel) render records
- * (4 x float4: adjugate rows with centre/det, opacity/depth/cutoff),
- * 2 binning records, 3 tile counts per (view,surfel), 4 tile ranges
- * (int32 [tiles,2]), 5 tile lists (uint32 item ids), 6 counters (uint64),
- * 7 per-tile pair counts (uint32).
+ * and tests).  Items are (view, surfel) pairs, item = view * N + surfel.
+ * Regions:
+ *   0 status block; 1 render records per item (4 x float4: adjugate rows
+ *   with the local origin and det, opacity/depth/cutoff/rescale);
+ *   2 binning records per item (80 bytes: conic, ellipse, pixel and tile
+ *   boxes, flags); 3 tile count per item (uint32); 4 tile ranges
+ *   (int32 [tiles, 2]); 5 tile lists (uint32 item ids, sorted by fss_sort);
+ *   6 counters (uint64 [8], inside the status block: evaluations,
+ *   contributions); 7 per-tile pair counts, then emission cursors (uint32);
+ *   8 sort scratch (2 x uint64 per pair); 9 geometric gradient rows
+ *   (float [views, N, 16]); 10 feature gradient accumulators (float [N, C]);
+ *   11 per-(pixel, k) dot products (float [pixels, K]); 12 visible item
+ *   list; 13 unbounded items per view; 14 gradient slot per surfel (int32,
+ *   -1 if culled in every view); 15 items spanning many tiles; 16 per-pair
+ *   warp masks (uint32, written by fss_sort).
+ * The workspace costs 24 bytes per unit of pair_capacity.
  */
 fss_status fss_workspace_region(const fss_params *params, const fss_camera *cams, int32_t n_cams, int64_t N,
                                 int64_t pair_capacity, int32_t which, size_t *offset, size_t *bytes);

@@ -126,6 +126,7 @@ Layout make_layout(const RParams& P, const Cams& cams) {
     sz[REG_UNB] = ni * 4;
     sz[REG_SLOT] = N * 4;
     sz[REG_WIDE] = ni * 4;
+    sz[REG_MASK] = cap * 4;
     size_t off = 0;
     for (int r = 0; r < REG_COUNT_ALL; ++r) {
         L.off[r] = off;
@@ -257,10 +258,15 @@ fss_status fss_project_bin(const fss_params* params, const fss_camera* cams, int
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_project");
     k_scan<<<1, 1024, 0, st>>>(ctx.cams, ctx.P, ctx.at<uint32_t>(REG_TILECNT), ctx.at<int2>(REG_RANGES), stp);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_scan");
-    k_emit<<<sms * 4, 256, 0, st>>>(ctx.cams, ctx.P, ctx.at<BinRec>(REG_BINREC), ctx.at<uint32_t>(REG_VIS),
+    // one thread per possible visible item (the visible count is known only on the device)
+    const unsigned emit_blocks = (unsigned)std::max<int64_t>(sms * 4, std::min<int64_t>(blocks, (int64_t)sms * 64));
+    int max_lines = 1;  // most outer tile lines (rows or columns) of any view
+    for (int v = 0; v < ctx.cams.n; ++v)
+        max_lines = std::max(max_lines, std::max(ctx.cams.c[v].tiles_x, ctx.cams.c[v].tiles_y));
+    k_emit<<<emit_blocks, 256, 0, st>>>(ctx.cams, ctx.P, ctx.at<BinRec>(REG_BINREC), ctx.at<uint32_t>(REG_VIS),
                                     ctx.at<uint32_t>(REG_WIDE), ctx.at<uint32_t>(REG_UNB),
                                     ctx.at<uint32_t>(REG_TILECNT), ctx.at<uint32_t>(REG_LIST), means, scales, quats,
-                                    ctx.at<float4>(REG_REC), stp);
+                                    ctx.at<float4>(REG_REC), stp, max_lines);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_emit");
     return FSS_OK;
 }
@@ -272,9 +278,11 @@ fss_status fss_sort(const fss_params* params, const fss_camera* cams, int32_t n_
     if (s != FSS_OK) return s;
     if (!workspace) return fail(FSS_ERR_INVALID_ARG, "workspace is NULL");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    k_tile_sort<<<ctx.cams.total_tiles, 256, 0, st>>>(ctx.cams, ctx.P, ctx.at<float4>(REG_REC), ctx.at<int2>(REG_RANGES),
+    k_tile_sort<<<ctx.cams.total_tiles, 256, 0, st>>>(ctx.cams, ctx.P, ctx.at<float4>(REG_REC),
+                                                      ctx.at<BinRec>(REG_BINREC), ctx.at<int2>(REG_RANGES),
                                                       ctx.at<uint32_t>(REG_LIST), ctx.at<uint32_t>(REG_UNB),
-                                                      ctx.at<uint64_t>(REG_SORTTMP), ctx.at<Status>(REG_STATUS));
+                                                      ctx.at<uint64_t>(REG_SORTTMP), ctx.at<uint32_t>(REG_MASK),
+                                                      ctx.at<Status>(REG_STATUS));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_tile_sort");
     return FSS_OK;
@@ -298,6 +306,7 @@ fss_status fss_render_forward(const fss_params* params, const fss_camera* cams, 
     a.binrec = ctx.at<BinRec>(REG_BINREC);
     a.ranges = ctx.at<int2>(REG_RANGES);
     a.list = ctx.at<uint32_t>(REG_LIST);
+    a.masks = ctx.at<uint32_t>(REG_MASK);
     a.rgb = rgb;
     a.feats = feats;
     a.out_feat = out_feat;
@@ -342,6 +351,7 @@ fss_status fss_render_backward(const fss_params* params, const fss_camera* cams,
     a.binrec = ctx.at<BinRec>(REG_BINREC);
     a.ranges = ctx.at<int2>(REG_RANGES);
     a.list = ctx.at<uint32_t>(REG_LIST);
+    a.masks = ctx.at<uint32_t>(REG_MASK);
     a.rgb = rgb;
     a.feats = feats;
     const size_t px = (size_t)ctx.cams.total_pix;

@@ -104,6 +104,7 @@ enum Region {
     REG_UNB = 13,
     REG_SLOT = 14,   // int32 [N]: gradient slot of each surfel, -1 if culled in every view
     REG_WIDE = 15,   // uint32 [items]: visible items spanning many tiles
+    REG_MASK = 16,   // uint32 [pair_capacity]: per sorted pair, the warps of its tile it reaches
     REG_COUNT_ALL
 };
 

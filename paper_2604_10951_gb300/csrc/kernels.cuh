@@ -20,11 +20,12 @@ __global__ void k_emit(const __grid_constant__ Cams cams, const __grid_constant_
                        const uint32_t* __restrict__ wide_list, const uint32_t* __restrict__ unb_list,
                        uint32_t* __restrict__ cursor, uint32_t* __restrict__ list, const float* __restrict__ means,
                        const float* __restrict__ scales, const float* __restrict__ quats, float4* __restrict__ rec,
-                       const Status* __restrict__ st);
+                       const Status* __restrict__ st, int max_lines);
 __global__ void k_tile_sort(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
-                            const float4* __restrict__ rec, const int2* __restrict__ ranges,
-                            uint32_t* __restrict__ list, const uint32_t* __restrict__ unb_list,
-                            uint64_t* __restrict__ scratch, const Status* __restrict__ st);
+                            const float4* __restrict__ rec, const BinRec* __restrict__ binrec,
+                            const int2* __restrict__ ranges, uint32_t* __restrict__ list,
+                            const uint32_t* __restrict__ unb_list, uint64_t* __restrict__ scratch,
+                            uint32_t* __restrict__ masks, const Status* __restrict__ st);
 
 // forward render arguments (one struct so the template instances share a
 // signature)
@@ -33,6 +34,7 @@ struct FwdArgs {
     const BinRec* binrec;
     const int2* ranges;
     const uint32_t* list;
+    const uint32_t* masks;  // per pair: warps of its tile that the footprint reaches
     const float* rgb;
     const void* feats;
     void* out_feat;
@@ -55,6 +57,7 @@ struct BwdArgs {
     const BinRec* binrec;
     const int2* ranges;
     const uint32_t* list;
+    const uint32_t* masks;
     const float* rgb;
     const void* feats;
     const int32_t* saved_pos;

@@ -248,11 +248,11 @@ __device__ __forceinline__ int view_of_item(int64_t item, int64_t N) {
 // host call before this kernel) and is appended to the narrow list, or to
 // the wide list when it spans more than WIDE_TILES tiles; an unbounded item
 // goes to its view's list instead (every tile of the view includes it).
-// Appends and gradient-slot claims are aggregated per CTA.
+// Appends and gradient-slot claims are aggregated per warp.
 // ---------------------------------------------------------------------------
 constexpr uint32_t WIDE_TILES = 32;
 
-__global__ void __launch_bounds__(256) k_project(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
+__global__ void __launch_bounds__(256, 4) k_project(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                                                  const float* __restrict__ means, const float* __restrict__ scales,
                                                  const float* __restrict__ quats, const float* __restrict__ opac,
                                                  float4* __restrict__ rec, BinRec* __restrict__ binrec,
@@ -440,35 +440,25 @@ __global__ void __launch_bounds__(256) k_project(const __grid_constant__ Cams ca
             wide = cnt > WIDE_TILES;
         }
     }
-    // CTA-aggregated appends (one global atomic per CTA and counter)
+    // warp-aggregated appends (one global atomic per warp and counter, no CTA barrier)
     {
-        __shared__ uint32_t s_cnt[3], s_base[3];
         const int lane = threadIdx.x & 31;
         const unsigned lt = (1u << lane) - 1u;
         const bool narrow = vis && !wide, wid = vis && wide;
         const unsigned mn = __ballot_sync(0xffffffffu, narrow), mw = __ballot_sync(0xffffffffu, wid);
         const unsigned mc = __ballot_sync(0xffffffffu, claim);
-        if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0u;
-        __syncthreads();
-        uint32_t on = 0, ow = 0, oc = 0;
+        uint32_t bn = 0, bw = 0, bc = 0;
         if (lane == 0) {
-            if (mn) on = atomicAdd(&s_cnt[0], (uint32_t)__popc(mn));
-            if (mw) ow = atomicAdd(&s_cnt[1], (uint32_t)__popc(mw));
-            if (mc) oc = atomicAdd(&s_cnt[2], (uint32_t)__popc(mc));
+            if (mn) bn = atomicAdd(&st->nvis, (uint32_t)__popc(mn));
+            if (mw) bw = atomicAdd(&st->nwide, (uint32_t)__popc(mw));
+            if (mc) bc = atomicAdd(&st->nslot, (uint32_t)__popc(mc));
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            s_base[0] = s_cnt[0] ? atomicAdd(&st->nvis, s_cnt[0]) : 0u;
-            s_base[1] = s_cnt[1] ? atomicAdd(&st->nwide, s_cnt[1]) : 0u;
-            s_base[2] = s_cnt[2] ? atomicAdd(&st->nslot, s_cnt[2]) : 0u;
-        }
-        __syncthreads();
-        on = __shfl_sync(0xffffffffu, on, 0);
-        ow = __shfl_sync(0xffffffffu, ow, 0);
-        oc = __shfl_sync(0xffffffffu, oc, 0);
-        if (narrow) vis_list[s_base[0] + on + __popc(mn & lt)] = (uint32_t)item;
-        if (wid) wide_list[s_base[1] + ow + __popc(mw & lt)] = (uint32_t)item;
-        if (claim) splat_slot[claim_s] = (int32_t)(s_base[2] + oc + __popc(mc & lt));
+        bn = __shfl_sync(0xffffffffu, bn, 0);
+        bw = __shfl_sync(0xffffffffu, bw, 0);
+        bc = __shfl_sync(0xffffffffu, bc, 0);
+        if (narrow) vis_list[bn + __popc(mn & lt)] = (uint32_t)item;
+        if (wid) wide_list[bw + __popc(mw & lt)] = (uint32_t)item;
+        if (claim) splat_slot[claim_s] = (int32_t)(bc + __popc(mc & lt));
     }
     if (unb) {
         const uint32_t k = atomicAdd(&st->unb_cnt[view], 1u);
@@ -540,7 +530,7 @@ __global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ Cams cams
 }
 
 // ---------------------------------------------------------------------------
-// precise render record (see record_item), written in double-float
+// precise render record (see record_item_quad), written in double-float
 //
 // The ray-splat solve u ~ adj(T') (x - xc, y - yc, 1) is evaluated per pixel
 // in binary32, but the adjugate itself is computed here in double-float from
@@ -553,9 +543,20 @@ __global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ Cams cams
 // (unnormalised) rotation polynomial, so n2 * T = K [r_u Rv t_u', r_v Rv t_v',
 // n2 (Rv p + t)] needs no square root; its adjugate is n2^2 adj(T).
 // ---------------------------------------------------------------------------
-__device__ void record_item(const Cams& cams, const RParams& P, const float* __restrict__ means,
-                            const float* __restrict__ scales, const float* __restrict__ quats,
-                            float4* __restrict__ rec, uint32_t item) {
+__device__ __forceinline__ df shfl_df(df v, int src) {
+    return {__shfl_sync(0xffffffffu, v.hi, src, 4), __shfl_sync(0xffffffffu, v.lo, src, 4)};
+}
+
+// One quad of lanes per item (j = lane & 3): lane j < 3 forms column j of the
+// shifted n2 T' (the two tangent columns and the centre column), the quad
+// exchanges the columns, and lane r < 3 forms adjugate row r; the operations
+// and their order are those of a single-thread evaluation, so the record
+// does not depend on the split.  Every lane of the warp must call this
+// (shuffles); `valid` false computes nothing that is stored.
+__device__ void record_item_quad(const Cams& cams, const RParams& P, const float* __restrict__ means,
+                                 const float* __restrict__ scales, const float* __restrict__ quats,
+                                 float4* __restrict__ rec, uint32_t item, bool valid) {
+    const int j = threadIdx.x & 3, q0 = (threadIdx.x & 31) & ~3;
     const int view = view_of_item(item, P.N);
     const int64_t s = (int64_t)item - (int64_t)view * P.N;
     const CamDev& cam = cams.c[view];
@@ -564,63 +565,81 @@ __device__ void record_item(const Cams& cams, const RParams& P, const float* __r
     const float4 q4 = __ldg(reinterpret_cast<const float4*>(quats) + s);
     const float qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
     const df ww = two_prod(qw, qw), xx = two_prod(qx, qx), yy = two_prod(qy, qy), zz = two_prod(qz, qz);
+    const df n2 = dadd(dadd(ww, xx), dadd(yy, zz));
+    // column j of n2 T (camera frame, before the intrinsics): R t_u' r_u,
+    // R t_v' r_v or n2 (R p + t); straight-line code with selects, so the
+    // quad's lanes do not diverge
     const df xy = two_prod(qx, qy), wz = two_prod(qw, qz), xz = two_prod(qx, qz), wy = two_prod(qw, qy);
     const df yz = two_prod(qy, qz), wx = two_prod(qw, qx);
-    const df n2 = dadd(dadd(ww, xx), dadd(yy, zz));
     const df tu[3] = {dsub(dadd(ww, xx), dadd(yy, zz)), dmulf(dadd(xy, wz), 2.0f), dmulf(dsub(xz, wy), 2.0f)};
     const df tv[3] = {dmulf(dsub(xy, wz), 2.0f), dsub(dadd(ww, yy), dadd(xx, zz)), dmulf(dadd(yz, wx), 2.0f)};
-    df eu[3], ev[3], pc[3];
-    dmvec(cam.R, tu, eu);
-    dmvec(cam.R, tv, ev);
     const df pm[3] = {dfrom(means[3 * s]), dfrom(means[3 * s + 1]), dfrom(means[3 * s + 2])};
-    dmvec(cam.R, pm, pc);
-    const float su = scales[2 * s], sv = scales[2 * s + 1];
-    df col[3][3];
+    df v[3], e[3], col[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) v[i] = j == 0 ? tu[i] : (j == 1 ? tv[i] : pm[i]);
+    dmvec(cam.R, v, e);
+    const float sj = scales[2 * s + (j == 1 ? 1 : 0)];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        col[0][i] = dmulf(eu[i], su);
-        col[1][i] = dmulf(ev[i], sv);
-        col[2][i] = dmul(dadd(pc[i], dfrom(cam.t[i])), n2);
+        const df a = dmulf(e[i], sj), b = dmul(dadd(e[i], dfrom(cam.t[i])), n2);
+        col[i] = j < 2 ? a : b;
     }
-    // columns of n2 * T, then shifted about (xc, yc)
+    // column j of n2 T, shifted about (xc, yc)
+    df dj[3];
+    {
+        const df cx = dadd(dmulf(col[0], cam.fx), dmulf(col[2], cam.cx));
+        const df cy = dadd(dmulf(col[1], cam.fy), dmulf(col[2], cam.cy));
+        dj[0] = dsub(cx, dmulf(col[2], xc));
+        dj[1] = dsub(cy, dmulf(col[2], yc));
+        dj[2] = col[2];
+    }
     df d[3][3];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const df cx = dadd(dmulf(col[j][0], cam.fx), dmulf(col[j][2], cam.cx));
-        const df cy = dadd(dmulf(col[j][1], cam.fy), dmulf(col[j][2], cam.cy));
-        d[j][0] = dsub(cx, dmulf(col[j][2], xc));
-        d[j][1] = dsub(cy, dmulf(col[j][2], yc));
-        d[j][2] = col[j][2];
-    }
-    df m[3][3];
-    dcross(d[1], d[2], m[0]);
-    dcross(d[2], d[0], m[1]);
-    dcross(d[0], d[1], m[2]);
-    const df det = dadd(dadd(dmul(d[0][0], m[0][0]), dmul(d[0][1], m[0][1])), dmul(d[0][2], m[0][2]));
-    float mx = 0.0f;
+    for (int c = 0; c < 3; ++c)
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) mx = fmaxf(mx, fabsf(m[r][c].hi));
-    if (!(mx > 0.0f)) return;
-    int ex;
-    frexpf(mx, &ex);
+        for (int i = 0; i < 3; ++i) d[c][i] = shfl_df(dj[i], q0 + c);
+    // adjugate row j: m_j = d_{j+1} x d_{j+2}
+    const int r = j < 3 ? j : 0;
+    df m[3];
+    dcross(d[(r + 1) % 3], d[(r + 2) % 3], m);
+    float mx = j < 3 ? fmaxf(fmaxf(fabsf(m[0].hi), fabsf(m[1].hi)), fabsf(m[2].hi)) : 0.0f;
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1, 4));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2, 4));
+    // lane 0: det(n2 T') from row 0
+    const df det = dadd(dadd(dmul(d[0][0], m[0]), dmul(d[0][1], m[1])), dmul(d[0][2], m[2]));
+    int ex = 0;
+    if (mx > 0.0f) frexpf(mx, &ex);
     // hit depth det(T') / c2: with M = 2^-ex n2^2 adj(T'), store 2^-ex det(n2 T') / n2
-    const float detr = ldexpf(fdv(det.hi, n2.hi), -ex);
-    rr[0] = make_float4(ldexpf(m[0][0].hi, -ex), ldexpf(m[0][1].hi, -ex), ldexpf(m[0][2].hi, -ex), xc);
-    rr[1] = make_float4(ldexpf(m[1][0].hi, -ex), ldexpf(m[1][1].hi, -ex), ldexpf(m[1][2].hi, -ex), yc);
-    rr[2] = make_float4(ldexpf(m[2][0].hi, -ex), ldexpf(m[2][1].hi, -ex), ldexpf(m[2][2].hi, -ex), detr);
+    const float detr = __shfl_sync(0xffffffffu, ldexpf(fdv(det.hi, n2.hi), -ex), q0);
+    if (!valid || !(mx > 0.0f)) return;  // after the last shuffle: every lane took part
+    if (j < 3)
+        rr[j] = make_float4(ldexpf(m[0].hi, -ex), ldexpf(m[1].hi, -ex), ldexpf(m[2].hi, -ex),
+                            j == 0 ? xc : (j == 1 ? yc : detr));
     // total scale of M relative to adj(T' of the normalised surfel)
-    rr[3].w = ldexpf(fm(n2.hi, n2.hi), -ex);
+    if (j == 0) rr[3].w = ldexpf(fm(n2.hi, n2.hi), -ex);
+}
+
+constexpr int EMIT_BATCH = 8;
+
+// one slot in each of tiles tb[0, n) for `item`: all cursor atomics first, then the stores
+__device__ __forceinline__ void emit_batch(uint32_t* __restrict__ cursor, uint32_t* __restrict__ list,
+                                           const uint32_t* tb, int n, uint32_t item, int64_t cap) {
+    uint32_t pos[EMIT_BATCH];
+#pragma unroll
+    for (int j = 0; j < EMIT_BATCH; ++j)
+        if (j < n) pos[j] = atomicAdd(&cursor[tb[j]], 1u);
+#pragma unroll
+    for (int j = 0; j < EMIT_BATCH; ++j)
+        if (j < n && pos[j] < (uint32_t)cap) list[pos[j]] = item;
 }
 
 // ---------------------------------------------------------------------------
 // k_emit: writes every bounded visible item into one slot of each of its
 // tiles (slot order is arbitrary; the per-tile sort restores a total order)
 // and replaces the render records by their double-float versions.
+//   records:      one quad of lanes per narrow, wide or unbounded item;
 //   narrow items: one thread each, tiles in line order;
-//   wide items:   one warp each, lanes over the flattened (line, tile) pairs;
-//   records:      one thread per narrow, wide or unbounded item.
+//   wide items:   one warp per (item, outer line), lanes over the line's tiles;
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                                               const BinRec* __restrict__ binrec, const uint32_t* __restrict__ vis_list,
@@ -628,85 +647,80 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Cams cams,
                                               const uint32_t* __restrict__ unb_list, uint32_t* __restrict__ cursor,
                                               uint32_t* __restrict__ list, const float* __restrict__ means,
                                               const float* __restrict__ scales, const float* __restrict__ quats,
-                                              float4* __restrict__ rec, const Status* __restrict__ st) {
+                                              float4* __restrict__ rec, const Status* __restrict__ st, int max_lines) {
     if (st->err) return;
     const int lane = threadIdx.x & 31;
     const uint32_t nvis = st->nvis, nwide = st->nwide;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
-    // narrow items
-    for (int64_t i = gtid; i < nvis; i += gstride) {
+    uint32_t nunb = 0;
+    for (int v = 0; v < cams.n; ++v) nunb += st->unb_cnt[v];
+    // render records of all visible items (narrow, wide, unbounded), one quad
+    // of lanes each, from the lowest threads up (warp-uniform loop)
+    const uint32_t nrec = nvis + nwide + nunb;
+    for (int64_t base = (gtid >> 5) * 8; base < nrec; base += (gstride >> 5) * 8) {
+        const int64_t ri = base + (lane >> 2);
+        const bool valid = ri < nrec;
+        uint32_t item = 0;
+        if (valid) {
+            if (ri < nvis) {
+                item = vis_list[ri];
+            } else if (ri < (int64_t)nvis + nwide) {
+                item = wide_list[ri - nvis];
+            } else {
+                uint32_t k = (uint32_t)(ri - nvis - nwide);
+                int v = 0;
+                while (k >= st->unb_cnt[v]) k -= st->unb_cnt[v++];
+                item = unb_list[(int64_t)v * P.N + k];
+            }
+        }
+        record_item_quad(cams, P, means, scales, quats, rec, item, valid);
+    }
+    // narrow items, from the highest threads down (so that they run beside the
+    // records): tiles in batches of EMIT_BATCH, whose cursor atomics are in
+    // flight together instead of one round trip each
+    for (int64_t i = gstride - 1 - gtid; i < nvis; i += gstride) {
         const uint32_t item = vis_list[i];
         const BinRec r = binrec[item];
         const CamDev& cam = cams.c[view_of_item(item, P.N)];
         const Lines L = lines_of(r, P.bin_mode);
+        uint32_t tb[EMIT_BATCH];
+        int nb = 0;
         for (int li = 0; li < L.n; ++li) {
             const int o = L.first + li;
             int a, b;
             if (!line_interval(r, L, P.ts, o, a, b)) continue;
             for (int k = a; k <= b; ++k) {
                 const int tx = L.rows ? k : o, ty = L.rows ? o : k;
-                const uint32_t pos = atomicAdd(&cursor[cam.tile_off + ty * cam.tiles_x + tx], 1u);
-                if (pos < (uint32_t)P.pair_cap) list[pos] = item;
+                tb[nb++] = (uint32_t)(cam.tile_off + ty * cam.tiles_x + tx);
+                if (nb == EMIT_BATCH) {
+                    emit_batch(cursor, list, tb, nb, item, P.pair_cap);
+                    nb = 0;
+                }
             }
         }
-        record_item(cams, P, means, scales, quats, rec, item);
+        emit_batch(cursor, list, tb, nb, item, P.pair_cap);
     }
-    // wide items: one warp each
+    // wide items: one warp per (item, outer line), lanes over the line's tiles,
+    // so that a surfel spanning many tiles is spread over many warps
     const int64_t warps = gstride >> 5;
-    for (int64_t wi = gtid >> 5; wi < nwide; wi += warps) {
+    const int64_t units = (int64_t)nwide * max_lines;
+    for (int64_t u = gtid >> 5; u < units; u += warps) {
+        const int64_t wi = u / max_lines;
+        const int li = (int)(u - wi * max_lines);
         const uint32_t item = wide_list[wi];
         const BinRec r = binrec[item];
-        const CamDev& cam = cams.c[view_of_item(item, P.N)];
         const Lines L = lines_of(r, P.bin_mode);
-        for (int lb = 0; lb < L.n; lb += 32) {
-            const int li = lb + lane;
-            int a = 0, b = -1;
-            if (li < L.n && !line_interval(r, L, P.ts, L.first + li, a, b)) { a = 0; b = -1; }
-            const int len = b - a + 1;
-            int incl = len;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, off);
-                if (lane >= off) incl += y;
-            }
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            for (int k0 = 0; k0 < total; k0 += 32) {
-                const int k = k0 + lane;
-                // owner lane: the first lane whose inclusive count exceeds k
-                int lo = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const int probe = __shfl_sync(0xffffffffu, incl, lo + step - 1);
-                    if (probe <= k) lo += step;
-                }
-                const int own_incl = __shfl_sync(0xffffffffu, incl, lo);
-                const int own_len = __shfl_sync(0xffffffffu, len, lo);
-                const int own_a = __shfl_sync(0xffffffffu, a, lo);
-                if (k < total) {
-                    const int inner = own_a + (k - (own_incl - own_len));
-                    const int o = L.first + lb + lo;
-                    const int tx = L.rows ? inner : o, ty = L.rows ? o : inner;
-                    const uint32_t pos = atomicAdd(&cursor[cam.tile_off + ty * cam.tiles_x + tx], 1u);
-                    if (pos < (uint32_t)P.pair_cap) list[pos] = item;
-                }
-            }
+        if (li >= L.n) continue;  // warp-uniform
+        const CamDev& cam = cams.c[view_of_item(item, P.N)];
+        const int o = L.first + li;
+        int a, b;
+        if (!line_interval(r, L, P.ts, o, a, b)) continue;
+        for (int k = a + lane; k <= b; k += 32) {
+            const int tx = L.rows ? k : o, ty = L.rows ? o : k;
+            const uint32_t pos = atomicAdd(&cursor[cam.tile_off + ty * cam.tiles_x + tx], 1u);
+            if (pos < (uint32_t)P.pair_cap) list[pos] = item;
         }
-    }
-    // records of wide and unbounded items
-    uint32_t nunb = 0;
-    for (int v = 0; v < cams.n; ++v) nunb += st->unb_cnt[v];
-    for (int64_t i = gtid; i < (int64_t)nwide + nunb; i += gstride) {
-        uint32_t item;
-        if (i < nwide) {
-            item = wide_list[i];
-        } else {
-            uint32_t k = (uint32_t)(i - nwide);
-            int v = 0;
-            while (k >= st->unb_cnt[v]) k -= st->unb_cnt[v++];
-            item = unb_list[(int64_t)v * P.N + k];
-        }
-        record_item(cams, P, means, scales, quats, rec, item);
     }
 }
 

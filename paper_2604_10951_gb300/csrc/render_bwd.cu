@@ -10,8 +10,9 @@
 //
 // k_bwd_feat  (Top-K) one CTA per tile: for every selected (pixel, k) the
 //             dot c_i . dL/dF(x) and the feature gradient sum w_i dL/dF(x),
-//             grouped by surfel in shared memory first, so each surfel costs
-//             one row of 16-byte vector reductions per tile.
+//             grouped by surfel in shared memory first, so each surfel's
+//             feature row is read once and costs one row of 16-byte vector
+//             reductions per tile.
 // k_bwd_geo   one CTA per tile, one thread per pixel: back-to-front replay;
 //             per staged surfel the warp reduce-scatters its 13 partial
 //             derivatives (adjugate rows 9, opacity 1, colour 3) and the
@@ -65,117 +66,69 @@ __device__ __forceinline__ void reduce_scatter(float* v) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// k_bwd_dots (Top-K): dots[pixel, k] = c_i . dL/dF(x) for the selected surfels
+// k_bwd_feat (Top-K): per selected (pixel x, k) with surfel i, the dot
+// c_i . dL/dF(x) (read by k_bwd_geo) and the feature gradient sum over x of
+// w_i(x) dL/dF(x), grouped per tile
 //
-// G = (C / E) lanes per pixel (E channels per 16-byte chunk, G a power of two
-// <= 32): each lane holds one 16-byte chunk of the pixel's dL/dF row and,
-// per selected surfel, loads the same chunk of its feature row; the partial
-// dot products are summed over the G lanes with shuffles.
-// ---------------------------------------------------------------------------
-template <typename FT, int G>
-__global__ void __launch_bounds__(256) k_bwd_dots(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
-                                                  const BwdArgs a) {
-    constexpr int E = FeatVec<FT>::E;
-    if (a.st->err) return;
-    const int K = P.K, C = P.C, ts = P.ts;
-    const FT* __restrict__ feats = reinterpret_cast<const FT*>(a.feats);
-    const FT* __restrict__ dF = reinterpret_cast<const FT*>(a.d_feat);
-    const int lane = threadIdx.x & 31, sub = lane & (G - 1);
-    constexpr int GPW = 32 / G;  // pixel groups per warp
-    const int64_t groups = cams.total_pix;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    // warp-uniform loop (the shuffles below need the whole warp); groups past the end idle
-    for (int64_t wb = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * GPW; wb < groups; wb += nwarps * GPW) {
-        const int64_t pix = wb + lane / G;
-        const bool live = pix < groups;
-        int view = 0;
-        if (live) {
-            int lo = 0, hi = cams.n - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (cams.c[mid].pix_off <= pix) lo = mid; else hi = mid - 1;
-            }
-            view = lo;
-        }
-        const CamDev& cam = cams.c[view];
-        const int loc = live ? (int)(pix - cam.pix_off) : 0;
-        const int py = loc / cam.W, px = loc - py * cam.W;
-        const int2 rg = live ? a.ranges[cam.tile_off + (py / ts) * cam.tiles_x + px / ts] : make_int2(0, 0);
-        const int64_t vbase = (int64_t)view * P.N;
-        float g[E];
-        if (live && sub < C / E) FeatVec<FT>::load(dF + pix * C + sub * E, g);
-        else
-#pragma unroll
-            for (int e = 0; e < E; ++e) g[e] = 0.0f;
-        for (int k = 0; k < K; ++k) {
-            const int pos = live ? a.saved_pos[pix * K + k] : -1;
-            float d = 0.0f;
-            if (pos >= 0 && sub < C / E) {
-                const int64_t sp = (int64_t)a.list[rg.x + pos] - vbase;
-                float f[E];
-                FeatVec<FT>::load(feats + sp * C + sub * E, f);
-#pragma unroll
-                for (int e = 0; e < E; ++e) d = fmaf(f[e], g[e], d);
-            }
-#pragma unroll
-            for (int o = G / 2; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-            if (pos >= 0 && sub == 0) a.dots[pix * K + k] = d;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// k_bwd_feat (Top-K): feature gradients sum_x w_i(x) dL/dF(x), grouped per tile
-//
-// Per tile (and per chunk of at most ECAP (pixel, k) entries): the tile's
-// dL/dF rows are staged in shared memory (rows padded by 16 bytes) and a
-// counting sort groups the entries by surfel (CSR); then one thread per
-// (surfel, 4 channels) sums its entries and issues one 16-byte vector
-// reduction.  Each thread keeps its entries' list positions and weights in
-// registers across the passes.
+// Per tile (and per chunk of at most ECAP (pixel, k) entries):
+//  1. the chunk's dL/dF rows are staged in shared memory (rows padded by
+//     16 bytes); each thread keeps EPT entries (list position, weight) in
+//     registers;
+//  2. the selected list positions get dense slot numbers (mark + scan) and
+//     a counting sort groups the entries by slot (warp-aggregated atomics);
+//  3. the selected surfels' feature rows are staged in shared memory in one
+//     parallel pass (over the counting-sort tables, which are dead by then);
+//  4. the slot-grouped entries are split into equal contiguous ranges, one
+//     per group of G lanes (G = 16-byte chunks per row, rounded up to a
+//     power of two): per entry the group forms the dot (shuffle-reduced)
+//     and accumulates w dL/dF, flushing one row of 16-byte vector
+//     reductions whenever its range moves on to the next surfel.
+// Shared memory holds everything the inner loop reads, so it runs without
+// global-memory latency; the equal ranges keep the warps balanced.
 // ---------------------------------------------------------------------------
 constexpr int ECAP = 2048;  // (pixel, k) entries per pass
 constexpr int PTAB = 2048;  // list positions per pass
 constexpr int EPT = ECAP / BWD_FEAT_THREADS;  // entries per thread
+constexpr int FEAT_UNION_BYTES = (PTAB + 2 * ECAP + 1) * 4;  // counting-sort tables, then feature rows
+constexpr int MAX_ROW_PASSES = 64;
 
-template <typename FT>
-__device__ __forceinline__ void lds4(const FT* p, float* o);
-template <>
-__device__ __forceinline__ void lds4<float>(const float* p, float* o) {
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-}
-template <>
-__device__ __forceinline__ void lds4<__nv_bfloat16>(const __nv_bfloat16* p, float* o) {
-    const uint2 v = *reinterpret_cast<const uint2*>(p);
-    o[0] = __uint_as_float(v.x << 16); o[1] = __uint_as_float(v.x & 0xffff0000u);
-    o[2] = __uint_as_float(v.y << 16); o[3] = __uint_as_float(v.y & 0xffff0000u);
-}
+// entry record: slot << 15 | chunk pixel << 5 | k
+__device__ __forceinline__ int ent_slot(int e) { return e >> 15; }
+__device__ __forceinline__ int ent_q(int e) { return (e >> 5) & 1023; }
 
 template <int TS, typename FT>
 __global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_constant__ Cams cams,
                                                               const __grid_constant__ RParams P, const BwdArgs a,
-                                                              int pch, int rowe) {
+                                                              int pch, int rowe, int G, int ucap) {
     constexpr int E = FeatVec<FT>::E;
     extern __shared__ __align__(16) unsigned char smem[];
-    int* s_tab = reinterpret_cast<int*>(smem);  // [PTAB] position -> slot
-    int* s_off = s_tab + PTAB;                  // [ECAP + 1] per-slot counts -> offsets
-    int* s_cur = s_off + ECAP + 1;              // [ECAP] scatter cursors
-    int* s_inv = s_cur + ECAP;                  // [ECAP] slot -> position
-    int* s_ent = s_inv + ECAP;                  // [ECAP] local pixel of each entry, grouped by slot
+    FT* s_df = reinterpret_cast<FT*>(smem);                                      // [pch][rowe]
+    int* s_ent = reinterpret_cast<int*>(smem + (((size_t)pch * rowe * sizeof(FT) + 15) & ~(size_t)15));
     float* s_ew = reinterpret_cast<float*>(s_ent + ECAP);  // [ECAP] weights, grouped by slot
-    FT* s_df = reinterpret_cast<FT*>(smem + (((size_t)(PTAB + 5 * ECAP + 1) * 4 + 15) & ~(size_t)15));
+    int* s_inv = reinterpret_cast<int*>(s_ew + ECAP);      // [ECAP] slot -> list position
+    float* s_dot = reinterpret_cast<float*>(s_inv + ECAP);  // [ECAP] dots by entry (pixel * K + k)
+    int* s_gs = reinterpret_cast<int*>(s_dot + ECAP);       // [ucap] slot -> gradient slot (this row pass)
+    unsigned char* uni = reinterpret_cast<unsigned char*>(s_gs + ((ucap + 3) & ~3));
+    int* s_tab = reinterpret_cast<int*>(uni);  // [PTAB] position -> slot
+    int* s_off = s_tab + PTAB;                 // [ECAP + 1] per-slot counts -> offsets
+    int* s_cur = s_off + ECAP + 1;             // [ECAP] scatter cursors
+    FT* s_rows = reinterpret_cast<FT*>(uni);   // [ucap][rowe] feature rows (after the counting sort)
     __shared__ int s_red[33];
     __shared__ int s_max;
     __shared__ int s_tile;
+    __shared__ int s_pass[MAX_ROW_PASSES + 1];
 
     if (a.st->err) return;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int npx = TS * TS;
-    const int K = P.K, C = P.C, nvec = C / E, nc4 = C / 4;
-    const FastDiv divK(K);
+    const int K = P.K, C = P.C, nvec = C / E;
+    const FastDiv divK(K), divV(nvec);
     const int rv = BWD_FEAT_THREADS / nvec, r0v = tid / nvec, v0 = tid - r0v * nvec;  // row-chunk mapping
-    const int rc = BWD_FEAT_THREADS / nc4, r0c = tid / nc4, c40 = tid - r0c * nc4;    // slot-channel mapping
+    const int sub = lane & (G - 1), gpw = 32 / G;                                      // groups of G lanes
+    const int gid = warp * gpw + lane / G, ngroups = (BWD_FEAT_THREADS / 32) * gpw;
+    const bool chunk_live = sub < nvec;
+    const FT* __restrict__ feats = reinterpret_cast<const FT*>(a.feats);
+    const FT* __restrict__ dF = reinterpret_cast<const FT*>(a.d_feat);
     for (int t = next_tile_q(a.persistent, &a.st->work_feat, &s_tile, true); t < cams.total_tiles;
          t = next_tile_q(a.persistent, &a.st->work_feat, &s_tile, false)) {
         const int view = view_of_tile(cams, t);
@@ -184,11 +137,10 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_cons
         const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
         const int2 rg = a.ranges[t];
         const int64_t vbase = (int64_t)view * P.N;
-        const FT* __restrict__ dF = reinterpret_cast<const FT*>(a.d_feat);
 
         for (int pc0 = 0; pc0 < npx; pc0 += pch) {
             const int np = min(pch, npx - pc0), ne = np * K;
-            // this thread's entries (e = tid + i * BLOCK): list position and weight
+            // 1. this thread's entries (e = tid + i * BLOCK): list position and weight
             int epos[EPT], eq[EPT];
             float ew[EPT];
             int lmax = 0;
@@ -201,7 +153,7 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_cons
                 if (e < ne) {
                     const int q = divK.div(e), k = e - q * K, p = pc0 + q;
                     const int px = tx * TS + p % TS, py = ty * TS + p / TS;
-                    eq[i] = q;
+                    eq[i] = (q << 5) | k;
                     if (px < cam.W && py < cam.H) {
                         const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
                         epos[i] = a.saved_pos[pix * K + k];
@@ -211,7 +163,6 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_cons
                 }
             }
             if (tid == 0) s_max = 0;
-            // stage the chunk's dL/dF rows (zeros outside the image)
             if (r0v < rv) {
                 for (int q = r0v; q < np; q += rv) {
                     const int p = pc0 + q, px = tx * TS + p % TS, py = ty * TS + p / TS;
@@ -227,22 +178,30 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_cons
             __syncthreads();
             const int L = s_max;
             for (int p0 = 0; p0 < L; p0 += PTAB) {
-                for (int i = tid; i < PTAB; i += BWD_FEAT_THREADS) s_tab[i] = 0;
-                for (int i = tid; i <= ECAP; i += BWD_FEAT_THREADS) s_off[i] = 0;
+                // 2. slots of the selected positions, then the entries grouped by slot
+                const int nt = min(PTAB, L - p0);  // positions in use (U <= nt)
+                for (int i = tid; i < nt; i += BWD_FEAT_THREADS) s_tab[i] = 0;
+                for (int i = tid; i <= nt; i += BWD_FEAT_THREADS) s_off[i] = 0;
                 __syncthreads();
 #pragma unroll
                 for (int i = 0; i < EPT; ++i)
                     if (epos[i] >= p0 && epos[i] < p0 + PTAB) s_tab[epos[i] - p0] = 1;
                 __syncthreads();
-                const int U = block_exscan(s_tab, PTAB, s_red);  // s_tab[pos] = slot where marked
+                const int U = block_exscan(s_tab, nt, s_red);  // s_tab[pos] = slot where marked
                 if (U == 0) continue;
-                for (int i = tid; i < PTAB; i += BWD_FEAT_THREADS) {
-                    const int nxt = i + 1 < PTAB ? s_tab[i + 1] : U;
+                for (int i = tid; i < nt; i += BWD_FEAT_THREADS) {
+                    const int nxt = i + 1 < nt ? s_tab[i + 1] : U;
                     if (nxt - s_tab[i] == 1) s_inv[s_tab[i]] = i;
                 }
+                int eslot[EPT];
 #pragma unroll
-                for (int i = 0; i < EPT; ++i)
-                    if (epos[i] >= p0 && epos[i] < p0 + PTAB) atomicAdd(&s_off[s_tab[epos[i] - p0]], 1);
+                for (int i = 0; i < EPT; ++i) {
+                    const bool in = epos[i] >= p0 && epos[i] < p0 + PTAB;
+                    eslot[i] = in ? s_tab[epos[i] - p0] : -1;
+                    // lanes with the same slot add their count once
+                    const unsigned peers = __match_any_sync(0xffffffffu, in ? eslot[i] : -1 - lane);
+                    if (in && lane == __ffs(peers) - 1) atomicAdd(&s_off[eslot[i]], __popc(peers));
+                }
                 __syncthreads();
                 const int nsel = block_exscan(s_off, U, s_red);
                 for (int i = tid; i < U; i += BWD_FEAT_THREADS) s_cur[i] = s_off[i];
@@ -250,31 +209,87 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_cons
                 __syncthreads();
 #pragma unroll
                 for (int i = 0; i < EPT; ++i) {
-                    if (epos[i] >= p0 && epos[i] < p0 + PTAB) {
-                        const int at = atomicAdd(&s_cur[s_tab[epos[i] - p0]], 1);
-                        s_ent[at] = eq[i];
+                    const bool in = eslot[i] >= 0;
+                    const unsigned peers = __match_any_sync(0xffffffffu, in ? eslot[i] : -1 - lane);
+                    const int leader = __ffs(peers) - 1;
+                    int base = 0;
+                    if (in && lane == leader) base = atomicAdd(&s_cur[eslot[i]], __popc(peers));
+                    base = __shfl_sync(0xffffffffu, base, leader);
+                    if (in) {
+                        const int at = base + __popc(peers & ((1u << lane) - 1u));
+                        s_ent[at] = (eslot[i] << 15) | eq[i];
                         s_ew[at] = ew[i];
                     }
                 }
+                const int npass = (U + ucap - 1) / ucap;  // <= MAX_ROW_PASSES (checked by the launcher)
+                if (tid <= npass) s_pass[tid] = s_off[min(tid * ucap, U)];
                 __syncthreads();
-                // one thread per (slot, 4 channels)
-                if (r0c < rc) {
-                    for (int slot = r0c; slot < U; slot += rc) {
-                        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-                        const int e1 = s_off[slot + 1];
-                        for (int i = s_off[slot]; i < e1; ++i) {
-                            const float w = s_ew[i];
-                            float gv[4];
-                            lds4<FT>(s_df + (size_t)s_ent[i] * rowe + 4 * c40, gv);
+                for (int pi = 0; pi < npass; ++pi) {
+                    const int u0 = pi * ucap, nu = min(ucap, U - u0);
+                    const int eb = s_pass[pi], ee = s_pass[pi + 1];
+                    // 3. feature rows of slots [u0, u0 + nu) (overwrites the counting-sort tables)
+                    for (int idx = tid; idx < nu * nvec; idx += BWD_FEAT_THREADS) {
+                        const int u = divV.div(idx), v = idx - u * nvec;
+                        const int64_t sp = (int64_t)a.list[rg.x + p0 + s_inv[u0 + u]] - vbase;
+                        *reinterpret_cast<uint4*>(s_rows + (size_t)u * rowe + v * E) =
+                            __ldg(reinterpret_cast<const uint4*>(feats + sp * C + v * E));
+                        if (v == 0) s_gs[u] = a.splat_slot[sp];
+                    }
+                    __syncthreads();
+                    // 4. equal contiguous entry ranges per group of G lanes (warp-uniform trip
+                    // count; an odd length keeps the groups' shared-memory reads on distinct banks)
+                    const int len = ((ee - eb + ngroups - 1) / ngroups) | 1;
+                    const int i0 = eb + gid * len, i1 = min(ee, i0 + len);
+                    int cur = -1;
+                    float f[E], acc[E];
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) acc[k] = fmaf(w, gv[k], acc[k]);
+                    for (int e = 0; e < E; ++e) { f[e] = 0.0f; acc[e] = 0.0f; }
+                    for (int st = 0; st < len; ++st) {
+                        const int i = i0 + st;
+                        const bool live = i < i1;
+                        const int ent = live ? s_ent[i] : 0;
+                        const int slot = ent_slot(ent) - u0;
+                        if (live && slot != cur) {
+                            if (cur >= 0 && chunk_live) {
+                                float* dst = a.feat_acc + (int64_t)s_gs[cur] * C + sub * E;
+#pragma unroll
+                                for (int e = 0; e < E; e += 4) red_add_v4(dst + e, acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
+                            }
+                            cur = slot;
+                            if (chunk_live) FeatVec<FT>::lds(s_rows + (size_t)slot * rowe + sub * E, f);
+#pragma unroll
+                            for (int e = 0; e < E; ++e) acc[e] = 0.0f;
                         }
-                        const int64_t sp = (int64_t)a.list[rg.x + p0 + s_inv[slot]] - vbase;
-                        red_add_v4(a.feat_acc + (int64_t)a.splat_slot[sp] * C + 4 * c40, acc[0], acc[1], acc[2],
-                                   acc[3]);
+                        float d = 0.0f;
+                        if (live && chunk_live) {
+                            const float w = s_ew[i];
+                            float g[E];
+                            FeatVec<FT>::lds(s_df + (size_t)ent_q(ent) * rowe + sub * E, g);
+#pragma unroll
+                            for (int e = 0; e < E; ++e) {
+                                d = fmaf(f[e], g[e], d);
+                                acc[e] = fmaf(w, g[e], acc[e]);
+                            }
+                        }
+                        for (int o = G >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                        if (live && sub == 0) s_dot[ent_q(ent) * K + (ent & 31)] = d;
+                    }
+                    if (cur >= 0 && chunk_live) {
+                        float* dst = a.feat_acc + (int64_t)s_gs[cur] * C + sub * E;
+#pragma unroll
+                        for (int e = 0; e < E; e += 4) red_add_v4(dst + e, acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
+                    }
+                    __syncthreads();
+                }
+                // the dots of this pass's entries, written back in (pixel, k) order
+#pragma unroll
+                for (int i = 0; i < EPT; ++i) {
+                    if (eslot[i] >= 0) {
+                        const int e = tid + i * BWD_FEAT_THREADS, q = eq[i] >> 5, p = pc0 + q;
+                        const int64_t pix = cam.pix_off + (int64_t)(ty * TS + p / TS) * cam.W + tx * TS + p % TS;
+                        a.dots[pix * K + (eq[i] & 31)] = s_dot[e];
                     }
                 }
-                __syncthreads();
             }
             __syncthreads();
         }
@@ -294,7 +309,7 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
     float4* s_r1 = s_r0 + NB;
     float4* s_r2 = s_r1 + NB;
     float4* s_oc = s_r2 + NB;                                  // (o, r, g, b)
-    uint32_t* s_wm = reinterpret_cast<uint32_t*>(s_oc + NB);   // warps the SnugBox reaches
+    uint32_t* s_wm = reinterpret_cast<uint32_t*>(s_oc + NB);   // warps the footprint reaches
     float* s_g = reinterpret_cast<float*>(s_wm + 2 * NB);      // [NB][16] partial derivatives
     float* s_f = s_g + NB * 16;    // FULL: [NB][C] features
     float* s_gf = s_f + (FULL ? NB * P.C : 0);  // FULL: [NB][C] feature gradients
@@ -311,7 +326,8 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
     const CamDev& cam = cams.c[view];
     const int lt = t - cam.tile_off;
     const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-    const int px = tx * TS + (tid % TS), py = ty * TS + (tid / TS);
+    const int2 lp = pixel_of<TS>(tid);
+    const int px = tx * TS + lp.x, py = ty * TS + lp.y;
     const bool inside = px < cam.W && py < cam.H;
     const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
     const int2 rg = a.ranges[t];
@@ -364,8 +380,7 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
             s_r2[j] = r[2];
             const int64_t sp = (int64_t)item - vbase;
             s_oc[j] = make_float4(r[3].x, a.rgb[3 * sp], a.rgb[3 * sp + 1], a.rgb[3 * sp + 2]);
-            const int16_t* bx = reinterpret_cast<const int16_t*>(a.binrec) + 40 * (size_t)item + 26;
-            s_wm[j] = warp_row_mask<TS>(ty * TS, bx[0], bx[1]);
+            s_wm[j] = a.masks[rg.x + b_start + j];
         }
         for (int i = tid; i < cnt * 16; i += NT) s_g[i] = 0.0f;
         if (FULL) {
@@ -385,7 +400,7 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
         __syncthreads();
         for (int j = cnt - 1; j >= 0; --j) {
             const int pos = b_start + j;
-            if (!(s_wm[j] & wbit)) continue;  // warp-uniform: the SnugBox misses this warp's rows
+            if (!(s_wm[j] & wbit)) continue;  // warp-uniform: the footprint misses this warp's block
             float g[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) g[k] = 0.0f;
@@ -672,41 +687,27 @@ cudaError_t persistent_grid(const void* k, int threads, size_t smem, int& grid) 
 }
 
 template <typename FT>
-cudaError_t launch_feat(const Cams& cams, const RParams& P, const BwdArgs& a, int num_sms, cudaStream_t s) {
-    // dots: G lanes per pixel
+cudaError_t launch_feat(const Cams& cams, const RParams& P, const BwdArgs& a, cudaStream_t s) {
     const int nvec = P.C / FeatVec<FT>::E;
-    int G = 1;
+    int G = 1;  // lanes per entry: 16-byte chunks of a feature row, padded to a power of two
     while (G < nvec) G <<= 1;
-    if (G > 32) return cudaErrorInvalidValue;  // C too large for the dot kernel (checked by the ABI)
-    const int64_t groups = cams.total_pix;
-    const int blocks = (int)std::min<int64_t>((groups * G + 255) / 256, (int64_t)num_sms * 16);
-#define FSS_DOTS(GG) k_bwd_dots<FT, GG><<<std::max(1, blocks), 256, 0, s>>>(cams, P, a)
-    switch (G) {
-        case 1: FSS_DOTS(1); break;
-        case 2: FSS_DOTS(2); break;
-        case 4: FSS_DOTS(4); break;
-        case 8: FSS_DOTS(8); break;
-        case 16: FSS_DOTS(16); break;
-        default: FSS_DOTS(32); break;
-    }
-#undef FSS_DOTS
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    // grouped feature gradients
+    if (G > 32) return cudaErrorInvalidValue;  // C too large (checked by the ABI)
     const int rowe = P.C + 16 / (int)sizeof(FT);  // padded row, elements
     const size_t rowb = (size_t)rowe * sizeof(FT);
-    const size_t fixed = (((size_t)(PTAB + 5 * ECAP + 1) * 4 + 15) & ~(size_t)15);
+    const int ucap = (int)(FEAT_UNION_BYTES / rowb);  // feature rows per pass
+    if ((ECAP + ucap - 1) / ucap > MAX_ROW_PASSES) return cudaErrorInvalidValue;
     const int npx = P.ts * P.ts;
     int pch = std::min(npx, ECAP / std::max(1, P.K));
-    pch = (int)std::min<size_t>((size_t)pch, std::max<size_t>(32, (64 * 1024) / rowb));
-    const size_t smem = fixed + (size_t)pch * rowb;
+    pch = (int)std::min<size_t>((size_t)pch, std::max<size_t>(32, (48 * 1024) / rowb));
+    const size_t smem = (((size_t)pch * rowb + 15) & ~(size_t)15) + (size_t)4 * ECAP * 4 +
+                        (size_t)((ucap + 3) & ~3) * 4 + FEAT_UNION_BYTES;
     auto go = [&](auto kern) {
         cudaError_t e2 = set_smem((const void*)kern, smem);
         if (e2 != cudaSuccess) return e2;
         int grid = cams.total_tiles;
         if (a.persistent && (e2 = persistent_grid((const void*)kern, BWD_FEAT_THREADS, smem, grid)) != cudaSuccess)
             return e2;
-        kern<<<grid, BWD_FEAT_THREADS, smem, s>>>(cams, P, a, pch, rowe);
+        kern<<<grid, BWD_FEAT_THREADS, smem, s>>>(cams, P, a, pch, rowe, G, ucap);
         return cudaGetLastError();
     };
     if (P.ts == 8) return go(k_bwd_feat<8, FT>);
@@ -742,7 +743,7 @@ cudaError_t launch_all(const Cams& cams, const RParams& P, const BwdArgs& a, int
     k_bwd_clear<<<num_sms * 4, 256, 0, s>>>(cams, P, a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (P.K > 0) {
-        if ((e = launch_feat<FT>(cams, P, a, num_sms, s)) != cudaSuccess) return e;
+        if ((e = launch_feat<FT>(cams, P, a, s)) != cudaSuccess) return e;
     }
     if (P.ts == 8) e = launch_geo<8, FT>(cams, P, a, s);
     else if (P.ts == 16) e = launch_geo<16, FT>(cams, P, a, s);

@@ -127,17 +127,74 @@ struct FastDiv {
     }
 };
 
-// Warps of a TS x TS tile (one thread per pixel, row-major) own R = 32 / TS
-// consecutive pixel rows each (TS <= 32).  Bit w of the mask is set when the
-// pixel-row range [py0, py1] of a surfel meets warp w's rows.
+// Pixel of thread `tid` in a TS x TS tile (TS in {8, 16, 32}): each warp
+// owns an 8 x 4 pixel block, blocks row-major over the tile (TS / 8 per
+// block row); lane l is pixel (l & 7, l >> 3) of its block.  Square-ish
+// blocks let a warp skip surfels whose footprint misses its block in
+// either direction.
 template <int TS>
-__device__ __forceinline__ uint32_t warp_row_mask(int tile_y0, int py0, int py1) {
-    constexpr int R = 32 / TS, NW = TS * TS / 32;
-    const int r0 = max(py0 - tile_y0, 0), r1 = min(py1 - tile_y0, TS - 1);
-    if (r0 > r1) return 0u;
-    const int w0 = r0 / R, w1 = r1 / R;
-    const uint32_t hi = (w1 >= 31) ? 0xffffffffu : ((2u << w1) - 1u);
-    return (hi & ~((1u << w0) - 1u)) & (NW >= 32 ? 0xffffffffu : ((1u << NW) - 1u));
+__device__ __forceinline__ int2 pixel_of(int tid) {
+    constexpr int WX = TS / 8;
+    const int w = tid >> 5, l = tid & 31;
+    return make_int2(8 * (w % WX) + (l & 7), 4 * (w / WX) + (l >> 3));
+}
+
+// Mask of the warps of the ts x ts tile at (tile_x0, tile_y0) whose 8 x 4
+// block (pixel_of) holds a pixel centre inside the surfel's binning ellipse
+// (the opacity-aware cutoff with its slack, Sec. 3.2), or inside its pixel
+// box when the footprint is unbounded.  Computed once per tile-surfel pair
+// by the depth sort and read by the render passes.  Per 4-row strip the ellipse's x-extent is its
+// left/right tangent point when that lies in the strip, else the root of
+// A x^2 + 2(B y + D) x + (C y^2 + 2 E y + F) = 0 at the nearer strip edge;
+// the extent is widened by a small margin, so the mask may keep a warp
+// that misses but never drops one that is hit.  Skipping a warp therefore
+// changes no result.
+__device__ __forceinline__ uint32_t warp_block_mask(const BinRec* __restrict__ rp, int ts, int tile_x0, int tile_y0) {
+    const int WX = ts >> 3;
+    const float4 q0 = __ldg(reinterpret_cast<const float4*>(rp));       // A B C D
+    const float4 q1 = __ldg(reinterpret_cast<const float4*>(rp) + 1);   // E F X0 Y0
+    const float4 q2 = __ldg(reinterpret_cast<const float4*>(rp) + 2);   // hx hy xc yc
+    const int2 q3 = __ldg(reinterpret_cast<const int2*>(rp) + 6);       // pixel box (int16 x 4)
+    const int px0 = (int)(int16_t)(q3.x & 0xffff), px1 = q3.x >> 16;
+    const int py0 = (int)(int16_t)(q3.y & 0xffff), py1 = q3.y >> 16;
+    const bool unbounded = (__ldg(&rp->flags) & BR_UNBOUNDED) != 0;
+    const int x0 = max(px0, tile_x0), x1 = min(px1, tile_x0 + ts - 1);
+    const int y0 = max(py0, tile_y0), y1 = min(py1, tile_y0 + ts - 1);
+    if (x0 > x1 || y0 > y1) return 0u;
+    const float A = q0.x, B = q0.y, Cc = q0.z, D = q0.w, E = q1.x, F = q1.y;
+    const float X0 = q1.z, hx = q2.x, xc = q2.z, yc = q2.w;
+    const float margin = 0.05f + 1e-3f * hx;
+    uint32_t m = 0u;
+    for (int by = (y0 - tile_y0) >> 2; by <= (y1 - tile_y0) >> 2; ++by) {
+        const int ra = max(y0, tile_y0 + 4 * by), rb = min(y1, tile_y0 + 4 * by + 3);
+        int ca = x0, cb = x1;
+        if (!unbounded) {
+            const float Ya = ((float)ra + 0.5f) - yc, Yb = ((float)rb + 0.5f) - yc;
+            float ext[2];
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const float Xs = side == 0 ? X0 - hx : X0 + hx;
+                const float Yt = -(B * Xs + E) / Cc;
+                if (Yt >= Ya && Yt <= Yb) {
+                    ext[side] = Xs;
+                } else {
+                    const float Y = Yt < Ya ? Ya : Yb;
+                    const float bb = B * Y + D;
+                    const float cc = (Cc * Y + 2.0f * E) * Y + F;
+                    const float sq = sqrtf(fmaxf(bb * bb - A * cc, 0.0f));
+                    ext[side] = (side == 0 ? -bb - sq : -bb + sq) / A;
+                }
+            }
+            // comparisons are false for NaN: a degenerate extent restricts nothing
+            const float lo = ceilf(ext[0] + xc - 0.5f - margin), hi = floorf(ext[1] + xc - 0.5f + margin);
+            if (lo > (float)ca) ca = lo > (float)cb ? cb + 1 : (int)lo;
+            if (hi < (float)cb) cb = hi < (float)ca ? ca - 1 : (int)hi;
+            if (ca > cb) continue;
+        }
+        const int bx0 = (ca - tile_x0) >> 3, bx1 = (cb - tile_x0) >> 3;
+        m |= ((2u << bx1) - (1u << bx0)) << (by * WX);
+    }
+    return m;
 }
 
 // Next tile of a CTA: its own index (grid schedule), or the head of a

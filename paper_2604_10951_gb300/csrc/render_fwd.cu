@@ -40,7 +40,8 @@ __device__ __forceinline__ int next_tile(const FwdArgs& a, int* s_tile, bool fir
 // ---------------------------------------------------------------------------
 // Shared memory: BATCH staged surfels as 4 x float4 (adjugate rows with the
 // local origin and det; opacity and colour) and a per-surfel mask of the
-// warps whose pixel rows its SnugBox reaches.  Phase 2 reuses the area.
+// warps (8 x 4 pixel blocks) that its binning ellipse reaches.  Phase 2
+// reuses the area.
 //
 // The K-set of a pixel lives in registers as an array sorted by decreasing
 // weight.  A new weight runs down a compare-exchange chain (strictly
@@ -49,7 +50,7 @@ __device__ __forceinline__ int next_tile(const FwdArgs& a, int* s_tile, bool fir
 // KCAP the first KCAP - K slots hold +inf and never move, so the K-th
 // largest weight is always slot KCAP - 1.
 template <int TS, int KCAP, typename FT>
-__global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__ Cams cams,
+__global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : 1) k_render_topk(const __grid_constant__ Cams cams,
                                                          const __grid_constant__ RParams P, const FwdArgs a) {
     constexpr int NT = TS * TS;
     constexpr int PC = (NT < 65536 / (KCAP * 8 + 4)) ? NT : 65536 / (KCAP * 8 + 4);  // phase-2 pixel chunk
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
     float4* s_r1 = s_r0 + BATCH;
     float4* s_r2 = s_r1 + BATCH;
     float4* s_oc = s_r2 + BATCH;                                 // (o, r, g, b)
-    uint32_t* s_wm = reinterpret_cast<uint32_t*>(s_oc + BATCH);  // warps the SnugBox reaches
+    uint32_t* s_wm = reinterpret_cast<uint32_t*>(s_oc + BATCH);  // warps the footprint reaches
     int32_t* s_id = reinterpret_cast<int32_t*>(smem);            // phase 2: [PC][KCAP] ids
     float* s_w = reinterpret_cast<float*>(s_id + PC * KCAP);     //          [PC][KCAP] weights
     int32_t* s_n = reinterpret_cast<int32_t*>(s_w + PC * KCAP);
@@ -69,7 +70,6 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
     if (a.st->err) return;
     const int K = P.K;
     const FT* __restrict__ feats = reinterpret_cast<const FT*>(a.feats);
-    const int16_t* __restrict__ boxes = reinterpret_cast<const int16_t*>(a.binrec);
     constexpr int E = FeatVec<FT>::E;
     const int nvec = P.C / E;
     const int ppi = NT / nvec;                         // pixels per phase-2 sweep
@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
         const CamDev& cam = cams.c[view];
         const int lt = t - cam.tile_off;
         const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-        const int px = tx * TS + (tid % TS), py = ty * TS + (tid / TS);
+        const int2 lp = pixel_of<TS>(tid);
+        const int px = tx * TS + lp.x, py = ty * TS + lp.y;
         const bool inside = px < cam.W && py < cam.H;
         const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
         const int2 rg = a.ranges[t];
@@ -109,14 +110,12 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
                 s_r2[j] = r[2];
                 const int64_t sp = (int64_t)item - vbase;
                 s_oc[j] = make_float4(r[3].x, a.rgb[3 * sp], a.rgb[3 * sp + 1], a.rgb[3 * sp + 2]);
-                // SnugBox pixel rows: int16 py0, py1 at bytes 52..55 of the binning record
-                const int16_t* bx = boxes + 40 * (size_t)item + 26;
-                s_wm[j] = warp_row_mask<TS>(ty * TS, bx[0], bx[1]);
+                s_wm[j] = a.masks[rg.x + b0 + j];
             }
             __syncthreads();
             if (done) continue;
             for (int j = 0; j < cnt; ++j) {
-                if (!(s_wm[j] & wbit)) continue;  // warp-uniform: no pixel row of this warp is reached
+                if (!(s_wm[j] & wbit)) continue;  // warp-uniform: the footprint misses this warp's block
                 ++n_eval;
                 Hit h;
                 const float4 oc = s_oc[j];
@@ -210,7 +209,8 @@ __global__ void __launch_bounds__(TS * TS) k_render_topk(const __grid_constant__
                 if (q0 >= ppi) continue;
                 for (int q = q0; q < npx; q += ppi) {
                     const int p = p0 + q;
-                    const int qx = tx * TS + (p % TS), qy = ty * TS + (p / TS);
+                    const int2 lq = pixel_of<TS>(p);  // pixel of the thread that selected row q
+                    const int qx = tx * TS + lq.x, qy = ty * TS + lq.y;
                     if (qx >= cam.W || qy >= cam.H) continue;
                     float acc[E];
 #pragma unroll
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__
     float4* s_r1 = s_r0 + FBATCH;
     float4* s_r2 = s_r1 + FBATCH;
     float4* s_oc = s_r2 + FBATCH;                                   // (o, r, g, b)
-    uint32_t* s_wm = reinterpret_cast<uint32_t*>(s_oc + FBATCH);    // warps the SnugBox reaches
+    uint32_t* s_wm = reinterpret_cast<uint32_t*>(s_oc + FBATCH);    // warps the footprint reaches
     float* s_f = reinterpret_cast<float*>(s_wm + 2 * FBATCH);       // [FBATCH][C] f32 (16-byte aligned)
     __shared__ int s_tile;
 
@@ -253,7 +253,6 @@ __global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__
     if (a.st->err) return;
     const int C = P.C;
     const FT* __restrict__ feats = reinterpret_cast<const FT*>(a.feats);
-    const int16_t* __restrict__ boxes = reinterpret_cast<const int16_t*>(a.binrec);
     const uint32_t wbit = 1u << (tid >> 5);
     const int nv = C / E;
     const int rpi = NT / nv;                         // staged rows per sweep
@@ -263,7 +262,8 @@ __global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__
         const CamDev& cam = cams.c[view];
         const int lt = t - cam.tile_off;
         const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-        const int px = tx * TS + (tid % TS), py = ty * TS + (tid / TS);
+        const int2 lp = pixel_of<TS>(tid);
+        const int px = tx * TS + lp.x, py = ty * TS + lp.y;
         const bool inside = px < cam.W && py < cam.H;
         const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
         const int2 rg = a.ranges[t];
@@ -289,8 +289,7 @@ __global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__
                 s_r2[j] = r[2];
                 const int64_t sp = (int64_t)item - vbase;
                 s_oc[j] = make_float4(r[3].x, a.rgb[3 * sp], a.rgb[3 * sp + 1], a.rgb[3 * sp + 2]);
-                const int16_t* bx = boxes + 40 * (size_t)item + 26;
-                s_wm[j] = warp_row_mask<TS>(ty * TS, bx[0], bx[1]);
+                s_wm[j] = a.masks[rg.x + b0 + j];
             }
             if (r0 < rpi) {
                 for (int j = r0; j < cnt; j += rpi) {

@@ -7,11 +7,16 @@
 //   (binary32 bits of the item's camera depth) << 32 | item index,
 // which is unique, so the order is total and deterministic.  Depths are
 // positive, so their bit patterns order like the numbers.
+//   - up to blockDim.x keys: rank sort (each thread counts the smaller keys);
 //   - up to SORT_CAP keys: bitonic sort in shared memory;
 //   - longer lists: stable LSD radix sort (8-bit digits) by the same CTA
 //     in a global scratch range of the same offsets.
+// With the sorted item, each pair gets the mask of the tile's warps (8 x 4
+// pixel blocks) that its footprint reaches, which the render passes use
+// to skip a surfel warp by warp.
 #include "fss_internal.cuh"
 #include "kernels.cuh"
+#include "render_common.cuh"
 
 namespace fss {
 
@@ -75,9 +80,11 @@ __device__ void block_radix_sort_global(uint64_t* keys, uint64_t* tmp, int n) {
 }  // namespace
 
 __global__ void __launch_bounds__(256) k_tile_sort(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
-                                                   const float4* __restrict__ rec, const int2* __restrict__ ranges,
-                                                   uint32_t* __restrict__ list, const uint32_t* __restrict__ unb_list,
-                                                   uint64_t* __restrict__ scratch, const Status* __restrict__ st) {
+                                                   const float4* __restrict__ rec, const BinRec* __restrict__ binrec,
+                                                   const int2* __restrict__ ranges, uint32_t* __restrict__ list,
+                                                   const uint32_t* __restrict__ unb_list,
+                                                   uint64_t* __restrict__ scratch, uint32_t* __restrict__ masks,
+                                                   const Status* __restrict__ st) {
     __shared__ uint64_t sk[SORT_CAP];
     if (st->err) return;
     const int t = blockIdx.x;
@@ -85,10 +92,30 @@ __global__ void __launch_bounds__(256) k_tile_sort(const __grid_constant__ Cams 
     const int n = rg.y - rg.x;
     if (n <= 0) return;
     const int view = view_of_tile(cams, t);
+    const CamDev& cam = cams.c[view];
+    const int lt = t - cam.tile_off;
+    const int tx0 = (lt % cam.tiles_x) * P.ts, ty0 = (lt / cam.tiles_x) * P.ts;
     const int nu = (int)st->unb_cnt[view];
     const int nb = n - nu;
     const uint32_t* ul = unb_list + (int64_t)view * P.N;
     const int tid = threadIdx.x;
+    if (n <= (int)blockDim.x) {
+        // short list: rank of each key = number of smaller keys (keys are
+        // unique, so the ranks are a permutation); one barrier instead of a
+        // network of them
+        uint64_t key = ~0ull;
+        if (tid < n) key = make_key(rec, tid < nb ? list[rg.x + tid] : ul[tid - nb]);
+        sk[tid] = key;
+        __syncthreads();
+        if (tid < n) {
+            int rank = 0;
+            for (int j = 0; j < n; ++j) rank += sk[j] < key ? 1 : 0;
+            const uint32_t item = (uint32_t)key;
+            list[rg.x + rank] = item;
+            masks[rg.x + rank] = warp_block_mask(binrec + item, P.ts, tx0, ty0);
+        }
+        return;
+    }
     if (n <= SORT_CAP) {
         int m = 1;
         while (m < n) m <<= 1;
@@ -110,7 +137,11 @@ __global__ void __launch_bounds__(256) k_tile_sort(const __grid_constant__ Cams 
                 __syncthreads();
             }
         }
-        for (int i = tid; i < n; i += blockDim.x) list[rg.x + i] = (uint32_t)sk[i];
+        for (int i = tid; i < n; i += blockDim.x) {
+            const uint32_t item = (uint32_t)sk[i];
+            list[rg.x + i] = item;
+            masks[rg.x + i] = warp_block_mask(binrec + item, P.ts, tx0, ty0);
+        }
         return;
     }
     uint64_t* keys = scratch + rg.x;
@@ -118,7 +149,11 @@ __global__ void __launch_bounds__(256) k_tile_sort(const __grid_constant__ Cams 
     for (int i = tid; i < n; i += blockDim.x) keys[i] = make_key(rec, i < nb ? list[rg.x + i] : ul[i - nb]);
     __syncthreads();
     block_radix_sort_global(keys, tmp, n);
-    for (int i = tid; i < n; i += blockDim.x) list[rg.x + i] = (uint32_t)keys[i];
+    for (int i = tid; i < n; i += blockDim.x) {
+        const uint32_t item = (uint32_t)keys[i];
+        list[rg.x + i] = item;
+        masks[rg.x + i] = warp_block_mask(binrec + item, P.ts, tx0, ty0);
+    }
 }
 
 }  // namespace fss

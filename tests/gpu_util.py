@@ -72,6 +72,9 @@ class GpuRun:
     def lists(self):
         return self.frame.region(L.REG_LIST).view(torch.int32)[:self.P].cpu().numpy()
 
+    def masks(self):
+        return self.frame.region(L.REG_MASK).view(torch.int32)[:self.P].cpu().numpy().view(np.uint32)
+
     def counters(self):
         return self.frame.counters().cpu().numpy()
 

@@ -62,7 +62,7 @@ def test_default_params_and_sizes(lib):
     assert ws % 256 == 0 and ws > 0
     # every region lies inside the workspace, 256-byte aligned, without overlap
     spans = []
-    for r in range(16):
+    for r in range(L.N_REGIONS):
         off, size = L.fss_workspace_region(p, cams, 1, 1000, 5000, r)
         assert off + size <= ws
         if r == L.REG_COUNTERS:  # the counters sit inside the status block
@@ -73,8 +73,8 @@ def test_default_params_and_sizes(lib):
             spans.append((off, off + size))
     spans.sort()
     assert all(a[1] <= b[0] for a, b in zip(spans, spans[1:]))
-    # pairs cost 20 bytes each (list + sort scratch)
-    assert L.fss_workspace_size(p, cams, 1, 1000, 5000 + 256 * 100) - ws == 256 * 100 * 20
+    # pairs cost 24 bytes each (list, sort scratch, warp mask)
+    assert L.fss_workspace_size(p, cams, 1, 1000, 5000 + 256 * 100) - ws == 256 * 100 * 24
     sv = L.fss_saved_size(p, cams, 1)
     assert sv == 2 * 64 * 48 * 8 * 4 + 64 * 48 * 4
 

@@ -105,9 +105,13 @@ def test_graph_replay_of_batched_fwd_bwd_matches_eager():
         assert torch.equal(got[k], eager[k])
     for x, y in zip(got[4:], eager[4:]):  # gradient sums use atomics: equal up to rounding order
         scale = y.float().abs().max().item()
-        # a different summation order may round a BF16 result one BF16 ulp (2^-8 relative) apart
-        rel = 2.0 ** -7 if x.dtype == torch.bfloat16 else 1e-5
-        tol = rel * y.float().abs() + 1e-5 * scale + 1e-12
+        # A gradient entry sums up to (pixels x views) terms of both signs in an
+        # order the atomics decide; reordering a binary32 sum of n terms moves it
+        # by up to ~n 2^-24 times the sum of the terms' magnitudes, which under
+        # cancellation is a few 1e-4 of the tensor's largest entry.  A BF16
+        # result may in addition round one BF16 ulp (2^-8 relative) apart.
+        rel = 2.0 ** -7 if x.dtype == torch.bfloat16 else 0.0
+        tol = rel * y.float().abs() + 2e-3 * scale + 1e-12
         assert bool(((x.float() - y.float()).abs() <= tol).all())
 
 

@@ -106,6 +106,54 @@ def test_room_view_binning_bit_exact():
     _check_lists(run, sc, cams, 16, "accu")
 
 
+def _check_masks(run, scene, cam, ts):
+    """Every pixel centre of a tile inside a listed surfel's binning ellipse
+    (FP64 test on the bit-exact binary32 conic), or inside the pixel box of
+    an unbounded footprint, lies in a warp block that the pair's mask keeps
+    (warps own 8 x 4 pixel blocks, row-major over the tile)."""
+    p = O.make_params(tile_size=ts)
+    recf, reci, _ = O.mirror_project(scene, cam, p, O.ACCU)
+    rng, lists, masks = run.ranges(), run.lists(), run.masks()
+    txn = (cam.width + ts - 1) // ts
+    tile = np.repeat(np.arange(len(rng)), rng[:, 1] - rng[:, 0])
+    ids = lists[rng[0, 0]:rng[-1, 1]]
+    masks = masks[rng[0, 0]:rng[-1, 1]]
+    X0t, Y0t = (tile % txn) * ts, (tile // txn) * ts
+    A, B, C, D, E, F = (recf[ids, 14 + k] for k in range(6))
+    xc, yc = recf[ids, 2], recf[ids, 3]
+    px0, px1, py0, py1 = (reci[ids, 3 + k] for k in range(4))
+    unb = reci[ids, 2] == 1
+    covered = 0
+    for ly in range(ts):
+        for lx in range(ts):
+            x, y = X0t + lx, Y0t + ly
+            X, Y = x + 0.5 - xc, y + 0.5 - yc
+            q = A * X * X + 2 * B * X * Y + C * Y * Y + 2 * D * X + 2 * E * Y + F
+            inbox = (x >= px0) & (x <= px1) & (y >= py0) & (y <= py1) & (x < cam.width) & (y < cam.height)
+            hit = inbox & (unb | (q <= 0))
+            bit = (masks >> np.uint32((ly // 4) * (ts // 8) + lx // 8)) & 1
+            assert not np.any(hit & (bit == 0)), (ts, lx, ly)
+            covered += int(hit.sum())
+    warps = np.array([bin(int(m)).count("1") for m in masks])
+    assert covered > 0 and warps.sum() < len(ids) * (ts * ts // 32)  # the masks do cull
+
+
+@pytest.mark.parametrize("ts", [8, 16, 32])
+def test_warp_masks_cover_every_pixel_inside_the_cutoff(ts):
+    from tests.gpu_util import GpuRun
+    sc, cam = scenes.tiny_scene(seed=0)
+    run = GpuRun(sc, [cam], K=4, tile_size=ts, render=False)
+    _check_masks(run, sc, cam, ts)
+
+
+def test_warp_masks_room_view():
+    from tests.gpu_util import GpuRun
+    sc = scenes.room_scene(n=200_000, C=8, seed=1)
+    cam = scenes.circle_poses(16)[5]
+    run = GpuRun(sc, [cam], K=8, tile_size=16, render=False, cap=1 << 20)
+    _check_masks(run, sc, cam, 16)
+
+
 def test_ragged_image_and_small_scene():
     from tests.gpu_util import GpuRun
     sc, _ = scenes.tiny_scene(seed=3, n=300)
