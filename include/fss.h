@@ -258,7 +258,8 @@ const char *fss_last_error(void);
  *   11 per-(pixel, k) dot products (float [pixels, K]); 12 visible item
  *   list; 13 unbounded items per view; 14 gradient slot per surfel (int32,
  *   -1 if culled in every view); 15 items spanning many tiles; 16 per-pair
- *   warp masks (uint32, written by fss_sort).
+ *   warp masks (uint32, written by fss_sort); 17 surfel of each gradient
+ *   slot (int32).
  * The workspace costs 24 bytes per unit of pair_capacity.
  */
 fss_status fss_workspace_region(const fss_params *params, const fss_camera *cams, int32_t n_cams, int64_t N,

@@ -188,6 +188,17 @@ static int ray_splat64(const double T[3][3], double x, double y, double near,
  *      av = sv*(Rv tv); pc = (Rv p)_r + t_r
  *  S4  z = pc2; cull unless z > near
  *  S5  cull unless o >= alpha_min
+ *  S5b conservative frustum test (a geometric cull like S17, placed
+ *      anywhere after S5): kk = (2 * ln32(o / alpha_min)) * 1.0009765625f;
+ *      rho = ((sqrt(max(kk, 0)) * max(su, sv)) * 1.001f) + 1e-6f;
+ *      zlo = pc2 - rho; zhi = pc2 + rho; if zlo > 0: xa = pc0 - rho,
+ *      xb = pc0 + rho (same for y); ux_max = xb / (xb >= 0 ? zlo : zhi),
+ *      ux_min = xa / (xa >= 0 ? zhi : zlo) (same for y);
+ *      px_max = fx*ux_max + cx, px_min = fx*ux_min + cx (same for y);
+ *      cull if px_max < -0.5 or px_min > W + 0.5 or py_max < -0.5 or
+ *      py_min > H + 0.5.  The sphere of radius rho about the centre holds
+ *      the binning disk, so in exact arithmetic this culls only surfels
+ *      whose footprint misses every pixel centre by more than a pixel.
  *  S6  k2 = 2 ln(o / alpha_min) by the binary32 procedure ln32 below:
  *      x = o / alpha_min; (m, e) = frexp(x); if m < 0.70710677f
  *      { m = m * 2; e = e - 1 }; s = (m - 1) / (m + 1); s2 = s * s;
@@ -409,6 +420,24 @@ static void mirror_project(const float *mean, const float *scale, const float *q
     for (int i = 0; i < 9; ++i) r->m[i] = ldexpf(r->m[i], -ex);
     r->det = ldexpf(det, -ex);
     r->culled_by_rule = 0;
+    /* S5b */
+    {
+        float kk = o / p->alpha_min;
+        kk = ln32(kk); kk = 2.0f * kk; kk = kk * 1.0009765625f;
+        float rho = sqrtf(fmaxf(kk, 0.0f));
+        rho = rho * fmaxf(scale[0], scale[1]); rho = rho * 1.001f; rho = rho + 1e-6f;
+        const float zlo = pc[2] - rho, zhi = pc[2] + rho;
+        if (zlo > 0.0f) {
+            const float xa = pc[0] - rho, xb = pc[0] + rho, ya = pc[1] - rho, yb = pc[1] + rho;
+            const float uxmax = xb / (xb >= 0.0f ? zlo : zhi), uxmin = xa / (xa >= 0.0f ? zhi : zlo);
+            const float uymax = yb / (yb >= 0.0f ? zlo : zhi), uymin = ya / (ya >= 0.0f ? zhi : zlo);
+            a = cam->fx * uxmax; const float pxmax = a + cam->cx;
+            a = cam->fx * uxmin; const float pxmin = a + cam->cx;
+            a = cam->fy * uymax; const float pymax = a + cam->cy;
+            a = cam->fy * uymin; const float pymin = a + cam->cy;
+            if (pxmax < -0.5f || pxmin > (float)W + 0.5f || pymax < -0.5f || pymin > (float)H + 0.5f) return;
+        }
+    }
     /* S14 */
     float kb = r->k2 * 1.0009765625f;
     float q[6];

@@ -127,6 +127,7 @@ Layout make_layout(const RParams& P, const Cams& cams) {
     sz[REG_SLOT] = N * 4;
     sz[REG_WIDE] = ni * 4;
     sz[REG_MASK] = cap * 4;
+    sz[REG_SLOT_SURF] = N * 4;
     size_t off = 0;
     for (int r = 0; r < REG_COUNT_ALL; ++r) {
         L.off[r] = off;
@@ -249,17 +250,21 @@ fss_status fss_project_bin(const fss_params* params, const fss_camera* cams, int
     const int sms = num_sms_current();
     Status* stp = ctx.at<Status>(REG_STATUS);
     const int64_t items = ctx.P.n_items;
-    const int64_t blocks = std::max<int64_t>(1, (items + 255) / 256);
+    const int64_t blocks = std::max<int64_t>(1, (items + 1023) / 1024);  // PROJ_ITEMS items per CTA
     k_project<<<(unsigned)blocks, 256, 0, st>>>(ctx.cams, ctx.P, means, scales, quats, opac, ctx.at<float4>(REG_REC),
                                                ctx.at<BinRec>(REG_BINREC), ctx.at<uint32_t>(REG_COUNT),
                                                ctx.at<uint32_t>(REG_TILECNT), ctx.at<uint32_t>(REG_VIS),
                                                ctx.at<uint32_t>(REG_WIDE), ctx.at<uint32_t>(REG_UNB),
-                                               ctx.at<int32_t>(REG_SLOT), stp);
+                                               ctx.at<int32_t>(REG_SLOT), ctx.at<int32_t>(REG_SLOT_SURF), stp);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_project");
     k_scan<<<1, 1024, 0, st>>>(ctx.cams, ctx.P, ctx.at<uint32_t>(REG_TILECNT), ctx.at<int2>(REG_RANGES), stp);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_scan");
-    // one thread per possible visible item (the visible count is known only on the device)
-    const unsigned emit_blocks = (unsigned)std::max<int64_t>(sms * 4, std::min<int64_t>(blocks, (int64_t)sms * 64));
+    // one resident wave: records run from the lowest threads up, tile emission
+    // from the highest down, so both start at once
+    int emit_per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&emit_per_sm, k_emit, 256, 0)) != cudaSuccess)
+        return cuda_fail(e, "occupancy k_emit");
+    const unsigned emit_blocks = (unsigned)(std::max(1, emit_per_sm) * sms);
     int max_lines = 1;  // most outer tile lines (rows or columns) of any view
     for (int v = 0; v < ctx.cams.n; ++v)
         max_lines = std::max(max_lines, std::max(ctx.cams.c[v].tiles_x, ctx.cams.c[v].tiles_y));
@@ -367,6 +372,7 @@ fss_status fss_render_backward(const fss_params* params, const fss_camera* cams,
     a.grad_item = ctx.at<float>(REG_GRAD_ITEM);
     a.feat_acc = ctx.at<float>(REG_FEAT_ACC);
     a.splat_slot = ctx.at<int32_t>(REG_SLOT);
+    a.slot_surf = ctx.at<int32_t>(REG_SLOT_SURF);
     a.means = means; a.scales = scales; a.quats = quats; a.opac = opac;
     a.g_means = g_means; a.g_scales = g_scales; a.g_quats = g_quats; a.g_opac = g_opac; a.g_rgb = g_rgb;
     a.g_feat = g_feat;

@@ -105,6 +105,7 @@ enum Region {
     REG_SLOT = 14,   // int32 [N]: gradient slot of each surfel, -1 if culled in every view
     REG_WIDE = 15,   // uint32 [items]: visible items spanning many tiles
     REG_MASK = 16,   // uint32 [pair_capacity]: per sorted pair, the warps of its tile it reaches
+    REG_SLOT_SURF = 17,  // int32 [N]: surfel of each gradient slot
     REG_COUNT_ALL
 };
 

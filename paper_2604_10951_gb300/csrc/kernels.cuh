@@ -12,7 +12,8 @@ __global__ void k_project(const __grid_constant__ Cams cams, const __grid_consta
                           const float* __restrict__ quats, const float* __restrict__ opac, float4* __restrict__ rec,
                           BinRec* __restrict__ binrec, uint32_t* __restrict__ count, uint32_t* __restrict__ tile_cnt,
                           uint32_t* __restrict__ vis_list, uint32_t* __restrict__ wide_list,
-                          uint32_t* __restrict__ unb_list, int32_t* __restrict__ splat_slot, Status* __restrict__ st);
+                          uint32_t* __restrict__ unb_list, int32_t* __restrict__ splat_slot,
+                          int32_t* __restrict__ slot_surf, Status* __restrict__ st);
 __global__ void k_scan(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                        uint32_t* __restrict__ tile_cnt, int2* __restrict__ ranges, Status* __restrict__ st);
 __global__ void k_emit(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
@@ -71,6 +72,7 @@ struct BwdArgs {
     float* grad_item;   // [n_cams * N, GRAD_STRIDE] per (view, slot)
     float* feat_acc;    // [N, C] f32 accumulation per slot
     const int32_t* splat_slot;  // [N]
+    const int32_t* slot_surf;   // [N] surfel of each slot
     const float* means;
     const float* scales;
     const float* quats;

@@ -239,11 +239,53 @@ __device__ __forceinline__ int view_of_item(int64_t item, int64_t N) {
 
 }  // namespace
 
+// S3 (centre), S4 (near plane), S5 (opacity) and S5b (conservative frustum
+// test): the cheap culls, which remove most surfels of a view before the
+// rest of the chain.  Returns false when the item is culled; pc and o as
+// computed (o = 0 if the depth test failed first).
+__device__ __forceinline__ bool early_culls(const CamDev& cam, const RParams& P, const float* __restrict__ means,
+                                            const float* __restrict__ scales, const float* __restrict__ opac,
+                                            int64_t s, float pc[3], float& o) {
+    float e[3];
+    const float pm[3] = {__ldg(means + 3 * s), __ldg(means + 3 * s + 1), __ldg(means + 3 * s + 2)};
+    mvec(cam.R, pm, e);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) pc[i] = fa(e[i], cam.t[i]);
+    o = 0.0f;
+    if (!(pc[2] > cam.near_plane)) return false;
+    // S5
+    o = __ldg(opac + s);
+    if (!(o >= P.alpha_min)) return false;
+    // S5b: the binning disk lies in the sphere of radius
+    // rho = sqrt(k^2 (1 + 2^-10)) max(r_u, r_v) about the centre; if that
+    // sphere is in front of the camera and its projection's bounding box
+    // misses every pixel centre by more than a pixel, no pixel can be reached.
+    const float2 scp = __ldg(reinterpret_cast<const float2*>(scales) + s);
+    const float kk = fm(fm(2.0f, ln32(fdv(o, P.alpha_min))), 1.0009765625f);
+    const float rho = fa(fm(fm(fq(fmaxf(kk, 0.0f)), fmaxf(scp.x, scp.y)), 1.001f), 1e-6f);
+    const float zlo = fs(pc[2], rho), zhi = fa(pc[2], rho);
+    if (zlo > 0.0f) {
+        const float xa = fs(pc[0], rho), xb = fa(pc[0], rho), ya = fs(pc[1], rho), yb = fa(pc[1], rho);
+        // extremes of x/z and y/z over the box [xa, xb] x [ya, yb] x [zlo, zhi]
+        const float uxmax = fdv(xb, xb >= 0.0f ? zlo : zhi), uxmin = fdv(xa, xa >= 0.0f ? zhi : zlo);
+        const float uymax = fdv(yb, yb >= 0.0f ? zlo : zhi), uymin = fdv(ya, ya >= 0.0f ? zhi : zlo);
+        const float pxmax = fa(fm(cam.fx, uxmax), cam.cx), pxmin = fa(fm(cam.fx, uxmin), cam.cx);
+        const float pymax = fa(fm(cam.fy, uymax), cam.cy), pymin = fa(fm(cam.fy, uymin), cam.cy);
+        if (pxmax < -0.5f || pxmin > (float)cam.W + 0.5f || pymax < -0.5f || pymin > (float)cam.H + 0.5f)
+            return false;
+    }
+    return true;
+}
+
+constexpr int PROJ_ITEMS = 1024;  // items per CTA of k_project
+
 // ---------------------------------------------------------------------------
-// k_project: one thread per (view, surfel) item
+// k_project: (view, surfel) items, PROJ_ITEMS per CTA
 //
-// Culls on depth first (the camera-space centre needs only the mean), then
-// loads the rest of the surfel.  A visible item with a bounded conic counts
+// Stage A runs the cheap culls (depth, opacity, frustum) one thread per item
+// and queues the survivors in shared memory; stage B runs the rest of the
+// chain one thread per survivor, so the few visible surfels of a view fill
+// whole warps instead of one lane in each.  A visible item with a bounded conic counts
 // its tiles (fire-and-forget adds into the per-tile counters, cleared by the
 // host call before this kernel) and is appended to the narrow list, or to
 // the wide list when it spans more than WIDE_TILES tiles; an unbounded item
@@ -259,9 +301,35 @@ __global__ void __launch_bounds__(256, 4) k_project(const __grid_constant__ Cams
                                                  uint32_t* __restrict__ count, uint32_t* __restrict__ tile_cnt,
                                                  uint32_t* __restrict__ vis_list, uint32_t* __restrict__ wide_list,
                                                  uint32_t* __restrict__ unb_list, int32_t* __restrict__ splat_slot,
-                                                 Status* __restrict__ st) {
-    const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                                                 int32_t* __restrict__ slot_surf, Status* __restrict__ st) {
+    __shared__ uint32_t s_q[PROJ_ITEMS];
+    __shared__ int s_nq;
     if (st->err) return;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) s_nq = 0;
+    __syncthreads();
+    // stage A: the cheap culls for PROJ_ITEMS items; survivors queued in shared memory
+    const int64_t base = (int64_t)blockIdx.x * PROJ_ITEMS;
+    for (int k = threadIdx.x; k < PROJ_ITEMS; k += blockDim.x) {
+        const int64_t it = base + k;
+        bool keep = false;
+        if (it < P.n_items) {
+            const int v = view_of_item(it, P.N);
+            float pc[3], o;
+            keep = early_culls(cams.c[v], P, means, scales, opac, it - (int64_t)v * P.N, pc, o);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        int b = 0;
+        if (lane == 0 && m) b = atomicAdd(&s_nq, __popc(m));
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (keep) s_q[b + __popc(m & ((1u << lane) - 1u))] = (uint32_t)k;
+    }
+    __syncthreads();
+    const int nq = s_nq;
+    // stage B: the whole chain for the survivors, packed densely into warps
+    // (warp-uniform loop: the appends below use whole-warp ballots)
+    for (int q0 = threadIdx.x & ~31; q0 < nq; q0 += blockDim.x) {
+    const int64_t item = q0 + lane < nq ? base + s_q[q0 + lane] : P.n_items;
     bool vis = false, wide = false, unb = false, claim = false;
     int64_t claim_s = 0;
     int view = 0;
@@ -278,18 +346,12 @@ __global__ void __launch_bounds__(256, 4) k_project(const __grid_constant__ Cams
         br.pad[0] = br.pad[1] = br.pad[2] = 0;
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
         do {
-            // S3 (centre) and S4 first: the order of the cull tests does not change the result
-            float e[3], pc[3];
-            const float pm[3] = {__ldg(means + 3 * s), __ldg(means + 3 * s + 1), __ldg(means + 3 * s + 2)};
-            mvec(cam.R, pm, e);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) pc[i] = fa(e[i], cam.t[i]);
+            // S3 (centre), S4, S5, S5b first: the order of the cull tests does not change the result
+            float pc[3], o;
+            const bool pass = early_culls(cam, P, means, scales, opac, s, pc, o);
             r3.y = pc[2];
-            if (!(pc[2] > cam.near_plane)) break;
-            // S5
-            const float o = __ldg(opac + s);
             r3.x = o;
-            if (!(o >= P.alpha_min)) break;
+            if (!pass) break;
             // S1
             const float4 q4 = __ldg(reinterpret_cast<const float4*>(quats) + s);
             const float qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
@@ -308,7 +370,7 @@ __global__ void __launch_bounds__(256, 4) k_project(const __grid_constant__ Cams
             // S3 (tangent columns)
             const float2 sc2 = __ldg(reinterpret_cast<const float2*>(scales) + s);
             const float su = sc2.x, sv = sc2.y;
-            float au[3], av[3];
+            float au[3], av[3], e[3];
             mvec(cam.R, tu, e);
 #pragma unroll
             for (int i = 0; i < 3; ++i) au[i] = fm(su, e[i]);
@@ -458,12 +520,17 @@ __global__ void __launch_bounds__(256, 4) k_project(const __grid_constant__ Cams
         bc = __shfl_sync(0xffffffffu, bc, 0);
         if (narrow) vis_list[bn + __popc(mn & lt)] = (uint32_t)item;
         if (wid) wide_list[bw + __popc(mw & lt)] = (uint32_t)item;
-        if (claim) splat_slot[claim_s] = (int32_t)(bc + __popc(mc & lt));
+        if (claim) {
+            const int32_t sl = (int32_t)(bc + __popc(mc & lt));
+            splat_slot[claim_s] = sl;
+            slot_surf[sl] = (int32_t)claim_s;
+        }
     }
     if (unb) {
         const uint32_t k = atomicAdd(&st->unb_cnt[view], 1u);
         unb_list[(int64_t)view * P.N + k] = (uint32_t)item;
     }
+    }  // survivors
 }
 
 // ---------------------------------------------------------------------------

@@ -80,32 +80,34 @@ __device__ __forceinline__ void reduce_scatter(float* v) {
 //     parallel pass (over the counting-sort tables, which are dead by then);
 //  4. the slot-grouped entries are split into equal contiguous ranges, one
 //     per group of G lanes (G = 16-byte chunks per row, rounded up to a
-//     power of two): per entry the group forms the dot (shuffle-reduced)
-//     and accumulates w dL/dF, flushing one row of 16-byte vector
-//     reductions whenever its range moves on to the next surfel.
+//     power of two, so a group reads whole rows without bank conflicts):
+//     two entries per step, the group forms each dot (shuffle-reduced) and
+//     accumulates w dL/dF, flushing one row of 16-byte vector reductions
+//     whenever its range moves on to the next surfel.
 // Shared memory holds everything the inner loop reads, so it runs without
 // global-memory latency; the equal ranges keep the warps balanced.
 // ---------------------------------------------------------------------------
-constexpr int ECAP = 2048;  // (pixel, k) entries per pass
+constexpr int ECAP = 1024;  // (pixel, k) entries per pass
 constexpr int PTAB = 2048;  // list positions per pass
 constexpr int EPT = ECAP / BWD_FEAT_THREADS;  // entries per thread
 constexpr int FEAT_UNION_BYTES = (PTAB + 2 * ECAP + 1) * 4;  // counting-sort tables, then feature rows
 constexpr int MAX_ROW_PASSES = 64;
+constexpr int STAGE_UNROLL = 4;  // global loads in flight per thread while staging
 
 // entry record: slot << 15 | chunk pixel << 5 | k
 __device__ __forceinline__ int ent_slot(int e) { return e >> 15; }
 __device__ __forceinline__ int ent_q(int e) { return (e >> 5) & 1023; }
 
 template <int TS, typename FT>
-__global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_constant__ Cams cams,
+__global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_constant__ Cams cams,
                                                               const __grid_constant__ RParams P, const BwdArgs a,
                                                               int pch, int rowe, int G, int ucap) {
     constexpr int E = FeatVec<FT>::E;
     extern __shared__ __align__(16) unsigned char smem[];
     FT* s_df = reinterpret_cast<FT*>(smem);                                      // [pch][rowe]
     int* s_ent = reinterpret_cast<int*>(smem + (((size_t)pch * rowe * sizeof(FT) + 15) & ~(size_t)15));
-    float* s_ew = reinterpret_cast<float*>(s_ent + ECAP);  // [ECAP] weights, grouped by slot
-    int* s_inv = reinterpret_cast<int*>(s_ew + ECAP);      // [ECAP] slot -> list position
+    float* s_ew = reinterpret_cast<float*>(s_ent + ECAP);   // [ECAP] weights, grouped by slot
+    int* s_inv = reinterpret_cast<int*>(s_ew + ECAP);       // [ECAP] slot -> list position
     float* s_dot = reinterpret_cast<float*>(s_inv + ECAP);  // [ECAP] dots by entry (pixel * K + k)
     int* s_gs = reinterpret_cast<int*>(s_dot + ECAP);       // [ucap] slot -> gradient slot (this row pass)
     unsigned char* uni = reinterpret_cast<unsigned char*>(s_gs + ((ucap + 3) & ~3));
@@ -163,14 +165,24 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_cons
                 }
             }
             if (tid == 0) s_max = 0;
+            // the chunk's dL/dF rows (zeros outside the image), STAGE_UNROLL loads in
+            // flight per thread before their shared-memory stores
             if (r0v < rv) {
-                for (int q = r0v; q < np; q += rv) {
-                    const int p = pc0 + q, px = tx * TS + p % TS, py = ty * TS + p / TS;
-                    uint4 val = make_uint4(0u, 0u, 0u, 0u);
-                    if (px < cam.W && py < cam.H)
-                        val = __ldg(reinterpret_cast<const uint4*>(
-                            dF + (cam.pix_off + (int64_t)py * cam.W + px) * C + v0 * E));
-                    *reinterpret_cast<uint4*>(s_df + (size_t)q * rowe + v0 * E) = val;
+                for (int qb = r0v; qb < np; qb += STAGE_UNROLL * rv) {
+                    uint4 val[STAGE_UNROLL];
+#pragma unroll
+                    for (int u = 0; u < STAGE_UNROLL; ++u) {
+                        const int q = qb + u * rv, p = pc0 + q, px = tx * TS + p % TS, py = ty * TS + p / TS;
+                        val[u] = make_uint4(0u, 0u, 0u, 0u);
+                        if (q < np && px < cam.W && py < cam.H)
+                            val[u] = __ldg(reinterpret_cast<const uint4*>(
+                                dF + (cam.pix_off + (int64_t)py * cam.W + px) * C + v0 * E));
+                    }
+#pragma unroll
+                    for (int u = 0; u < STAGE_UNROLL; ++u) {
+                        const int q = qb + u * rv;
+                        if (q < np) *reinterpret_cast<uint4*>(s_df + (size_t)q * rowe + v0 * E) = val[u];
+                    }
                 }
             }
             __syncthreads();
@@ -227,52 +239,86 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS) k_bwd_feat(const __grid_cons
                 for (int pi = 0; pi < npass; ++pi) {
                     const int u0 = pi * ucap, nu = min(ucap, U - u0);
                     const int eb = s_pass[pi], ee = s_pass[pi + 1];
-                    // 3. feature rows of slots [u0, u0 + nu) (overwrites the counting-sort tables)
-                    for (int idx = tid; idx < nu * nvec; idx += BWD_FEAT_THREADS) {
-                        const int u = divV.div(idx), v = idx - u * nvec;
-                        const int64_t sp = (int64_t)a.list[rg.x + p0 + s_inv[u0 + u]] - vbase;
-                        *reinterpret_cast<uint4*>(s_rows + (size_t)u * rowe + v * E) =
-                            __ldg(reinterpret_cast<const uint4*>(feats + sp * C + v * E));
-                        if (v == 0) s_gs[u] = a.splat_slot[sp];
+                    // 3. feature rows of slots [u0, u0 + nu) (over the counting-sort tables)
+                    for (int ib = tid; ib < nu * nvec; ib += 2 * BWD_FEAT_THREADS) {
+                        uint4 val[2];
+                        int64_t sp[2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int idx = ib + h * BWD_FEAT_THREADS;
+                            const int u = divV.div(idx);
+                            sp[h] = idx < nu * nvec ? (int64_t)a.list[rg.x + p0 + s_inv[u0 + u]] - vbase : -1;
+                        }
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int idx = ib + h * BWD_FEAT_THREADS, u = divV.div(idx), v = idx - u * nvec;
+                            if (sp[h] >= 0) val[h] = __ldg(reinterpret_cast<const uint4*>(feats + sp[h] * C + v * E));
+                        }
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int idx = ib + h * BWD_FEAT_THREADS, u = divV.div(idx), v = idx - u * nvec;
+                            if (sp[h] >= 0) {
+                                *reinterpret_cast<uint4*>(s_rows + (size_t)u * rowe + v * E) = val[h];
+                                if (v == 0) s_gs[u] = a.splat_slot[sp[h]];
+                            }
+                        }
                     }
                     __syncthreads();
-                    // 4. equal contiguous entry ranges per group of G lanes (warp-uniform trip
-                    // count; an odd length keeps the groups' shared-memory reads on distinct banks)
-                    const int len = ((ee - eb + ngroups - 1) / ngroups) | 1;
+                    // 4. equal contiguous entry ranges per group of G lanes, two entries per
+                    // step (warp-uniform trip count; a range length of 2 mod 4 keeps the
+                    // groups' shared-memory reads on distinct banks)
+                    int len = (ee - eb + ngroups - 1) / ngroups;
+                    len = ((len + 1) & ~3) + 2;
                     const int i0 = eb + gid * len, i1 = min(ee, i0 + len);
                     int cur = -1;
                     float f[E], acc[E];
 #pragma unroll
                     for (int e = 0; e < E; ++e) { f[e] = 0.0f; acc[e] = 0.0f; }
-                    for (int st = 0; st < len; ++st) {
-                        const int i = i0 + st;
-                        const bool live = i < i1;
-                        const int ent = live ? s_ent[i] : 0;
-                        const int slot = ent_slot(ent) - u0;
-                        if (live && slot != cur) {
-                            if (cur >= 0 && chunk_live) {
-                                float* dst = a.feat_acc + (int64_t)s_gs[cur] * C + sub * E;
+                    for (int st = 0; st < len; st += 2) {
+                        float dd[2];
+                        int en[2];
 #pragma unroll
-                                for (int e = 0; e < E; e += 4) red_add_v4(dst + e, acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
+                        for (int h = 0; h < 2; ++h) {
+                            const int i = i0 + st + h;
+                            const bool live = i < i1;
+                            const int ent = live ? s_ent[i] : -1;
+                            en[h] = ent;
+                            const int slot = ent_slot(ent) - u0;
+                            if (live && slot != cur) {
+                                if (cur >= 0 && chunk_live) {
+                                    float* dst = a.feat_acc + (int64_t)s_gs[cur] * C + sub * E;
+#pragma unroll
+                                    for (int e = 0; e < E; e += 4) red_add_v4(dst + e, acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
+                                }
+                                cur = slot;
+                                if (chunk_live) FeatVec<FT>::lds(s_rows + (size_t)slot * rowe + sub * E, f);
+#pragma unroll
+                                for (int e = 0; e < E; ++e) acc[e] = 0.0f;
                             }
-                            cur = slot;
-                            if (chunk_live) FeatVec<FT>::lds(s_rows + (size_t)slot * rowe + sub * E, f);
+                            float d0 = 0.0f, d1 = 0.0f;
+                            if (live && chunk_live) {
+                                const float w = s_ew[i];
+                                float g[E];
+                                FeatVec<FT>::lds(s_df + (size_t)ent_q(ent) * rowe + sub * E, g);
 #pragma unroll
-                            for (int e = 0; e < E; ++e) acc[e] = 0.0f;
-                        }
-                        float d = 0.0f;
-                        if (live && chunk_live) {
-                            const float w = s_ew[i];
-                            float g[E];
-                            FeatVec<FT>::lds(s_df + (size_t)ent_q(ent) * rowe + sub * E, g);
-#pragma unroll
-                            for (int e = 0; e < E; ++e) {
-                                d = fmaf(f[e], g[e], d);
-                                acc[e] = fmaf(w, g[e], acc[e]);
+                                for (int e = 0; e < E; e += 2) {
+                                    d0 = fmaf(f[e], g[e], d0);
+                                    d1 = fmaf(f[e + 1], g[e + 1], d1);
+                                    acc[e] = fmaf(w, g[e], acc[e]);
+                                    acc[e + 1] = fmaf(w, g[e + 1], acc[e + 1]);
+                                }
                             }
+                            dd[h] = d0 + d1;
                         }
-                        for (int o = G >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                        if (live && sub == 0) s_dot[ent_q(ent) * K + (ent & 31)] = d;
+                        for (int o = G >> 1; o > 0; o >>= 1) {
+                            dd[0] += __shfl_xor_sync(0xffffffffu, dd[0], o);
+                            dd[1] += __shfl_xor_sync(0xffffffffu, dd[1], o);
+                        }
+                        if (sub == 0) {
+#pragma unroll
+                            for (int h = 0; h < 2; ++h)
+                                if (en[h] >= 0) s_dot[ent_q(en[h]) * K + (en[h] & 31)] = dd[h];
+                        }
                     }
                     if (cur >= 0 && chunk_live) {
                         float* dst = a.feat_acc + (int64_t)s_gs[cur] * C + sub * E;
@@ -504,12 +550,9 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
 // ---------------------------------------------------------------------------
 // k_bwd_project: per surfel, d(adjugate rows) -> d(means, scales, quats)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_bwd_project(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
-                                                     const BwdArgs a) {
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= P.N) return;
+// gradients of surfel s from its slot's per-view rows (slot < 0: zeros)
+__device__ __forceinline__ void project_grad(const Cams& cams, const RParams& P, const BwdArgs& a, int64_t s, int slot) {
     float gm[3] = {0, 0, 0}, gs[2] = {0, 0}, gq[4] = {0, 0, 0, 0}, go = 0.0f, gc[3] = {0, 0, 0};
-    const int slot = a.st->err ? -1 : a.splat_slot[s];
     if (slot >= 0) {
         const float q0 = a.quats[4 * s], q1 = a.quats[4 * s + 1], q2 = a.quats[4 * s + 2], q3 = a.quats[4 * s + 3];
         const float qn = sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
@@ -615,6 +658,21 @@ __global__ void __launch_bounds__(256) k_bwd_project(const __grid_constant__ Cam
     if (a.g_rgb) { a.g_rgb[3 * s] = gc[0]; a.g_rgb[3 * s + 1] = gc[1]; a.g_rgb[3 * s + 2] = gc[2]; }
 }
 
+// Zeros for surfels culled in every view (one thread each), then the chain
+// rule for the surfels that have a slot, densely over the slots (a few
+// percent of the surfels are visible, so a thread per surfel would leave
+// most lanes of a warp idle through the long path).
+__global__ void __launch_bounds__(256) k_bwd_project(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
+                                                     const BwdArgs a) {
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+    const bool err = a.st->err != 0;
+    for (int64_t s = gtid; s < P.N; s += gstride)
+        if (err || a.splat_slot[s] < 0) project_grad(cams, P, a, s, -1);
+    const int64_t ns = err ? 0 : (int64_t)a.st->nslot;
+    for (int64_t sl = gtid; sl < ns; sl += gstride) project_grad(cams, P, a, a.slot_surf[sl], (int)sl);
+}
+
 // ---------------------------------------------------------------------------
 // k_feat_out: g_feat[s] = slot >= 0 ? feat_acc[slot] : 0 (16-byte chunks)
 // ---------------------------------------------------------------------------
@@ -695,10 +753,10 @@ cudaError_t launch_feat(const Cams& cams, const RParams& P, const BwdArgs& a, cu
     const int rowe = P.C + 16 / (int)sizeof(FT);  // padded row, elements
     const size_t rowb = (size_t)rowe * sizeof(FT);
     const int ucap = (int)(FEAT_UNION_BYTES / rowb);  // feature rows per pass
-    if ((ECAP + ucap - 1) / ucap > MAX_ROW_PASSES) return cudaErrorInvalidValue;
+    if (ucap < 1 || (PTAB + ucap - 1) / ucap > MAX_ROW_PASSES) return cudaErrorInvalidValue;
     const int npx = P.ts * P.ts;
     int pch = std::min(npx, ECAP / std::max(1, P.K));
-    pch = (int)std::min<size_t>((size_t)pch, std::max<size_t>(32, (48 * 1024) / rowb));
+    pch = (int)std::min<size_t>((size_t)pch, std::max<size_t>(32, (24 * 1024) / rowb));
     const size_t smem = (((size_t)pch * rowb + 15) & ~(size_t)15) + (size_t)4 * ECAP * 4 +
                         (size_t)((ucap + 3) & ~3) * 4 + FEAT_UNION_BYTES;
     auto go = [&](auto kern) {
