@@ -313,7 +313,7 @@ def run_ours(args):
         if calls:
             fwd_ms = calls["project_bin"] + calls["sort"] + calls["render_forward"]
             out["forward_only"] = {"ms": round(fwd_ms, 4), "frames_per_s": round(1e3 / fwd_ms, 2)}
-            out["roofline"] = roofline(ours, calls, torch)
+            out["roofline"], out["roofline_kernels"], out["kernel_us"] = roofline(ours, torch, L, flush)
         out["e2e"] = e2e(ours, torch, dev, ptr, L, args)
         del base
     if D.rank == 0 and not args.no_extras:
@@ -323,31 +323,102 @@ def run_ours(args):
     D.close()
 
 
-def roofline(path, calls, torch):
-    """Forward render kernel: algorithmic bytes per launch / its event time."""
-    peak, src = measured_peaks()
+KERNELS = ["k_project", "k_scan", "k_emit", "k_tile_sort", "k_render_topk", "k_loss", "k_bwd_clear", "k_bwd_feat",
+           "k_bwd_geo", "k_bwd_project", "k_feat_out"]
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch (camera pose 1) from the
+# ncu capture summarised in profiles/<kernel>_room500k_640x480_c64_k8.md; to be set
+# to None whenever the kernel changes after that capture
+NCU_TRAFFIC = {"k_render_topk": 27166208, "k_bwd_feat": 70297600, "k_bwd_geo": 37996032}
+
+
+def kernel_times(path, torch, L, flush, rounds=4):
+    """Per-kernel durations (ms) over the 16 poses, from events that the library
+    records after each of its launches (fss_set_kernel_events), captured into
+    one graph per pose; L2 flushed before every replay."""
+    graphs, evs = [], []
+    for i in range(16):
+        # the first event is recorded by torch inside the capture (an external event
+        # becomes a graph node); the others by the library after each launch
+        ev = [torch.cuda.Event(enable_timing=True, external=True)] + \
+             [torch.cuda.Event(enable_timing=True) for _ in range(len(KERNELS))]
+        for e in ev:  # creates the CUDA events
+            e.record()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            ev[0].record()
+            L.fss_set_kernel_events(ev[1:])
+            path.step(i)
+            L.fss_set_kernel_events([])
+        graphs.append(g)
+        evs.append(ev)
+    sums = np.zeros(len(KERNELS))
+    n = 0
+    nbytes, sizes = {}, {}
+    for r in range(rounds):
+        for i, (g, ev) in enumerate(zip(graphs, evs)):
+            flush.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            sums += [ev[k].elapsed_time(ev[k + 1]) for k in range(len(KERNELS))]
+            n += 1
+            if r == 0:  # the pose's algorithmic bytes, averaged over the 16 poses
+                b, z = algorithmic_bytes(path, torch, L)
+                for k in b:
+                    nbytes[k] = nbytes.get(k, 0.0) + b[k] / len(graphs)
+                for k in z:
+                    sizes[k] = sizes.get(k, 0.0) + z[k] / len(graphs)
+    return dict(zip(KERNELS, (sums / n).tolist())), nbytes, {k: int(round(v)) for k, v in sizes.items()}
+
+
+def algorithmic_bytes(path, torch, L):
+    """Unique bytes each of the three render kernels must move per launch for
+    the frame last rendered by `path`: reads of their inputs and writes of
+    their outputs once, nothing re-read."""
     fr = path.frame
-    fr.cams = fr.cams  # last pose rendered; recount on pose 0 for the byte model
-    ids = path.ids.cpu().numpy()
-    ranges = fr.region(3 + 1).view(torch.int32).view(-1, 2).cpu().numpy()
+    ranges = fr.region(L.REG_RANGES).view(torch.int32).view(-1, 2).cpu().numpy()
     P = int((ranges[:, 1] - ranges[:, 0]).sum())
     tiles = ranges.shape[0]
-    H, W = 480, 640
-    ts = 16
-    idv = ids.reshape(H, W, -1)
+    nslot = int(fr.region(L.REG_STATUS).view(torch.int32)[22].item())
+    H, W, ts = fr.sizes[0][0], fr.sizes[0][1], 16
+    ids = path.ids.cpu().numpy().reshape(H, W, -1)
     U = 0
     for ty in range(0, H, ts):
         for tx in range(0, W, ts):
-            blk = idv[ty:ty + ts, tx:tx + ts].reshape(-1)
+            blk = ids[ty:ty + ts, tx:tx + ts].reshape(-1)
             U += np.unique(blk[blk >= 0]).size
-    s, K, Cc = 2, K_TOP, C_FEAT
-    npx = H * W
-    bytes_ = tiles * 8 + P * (4 + 48 + 4 + 12) + U * Cc * s + npx * (Cc * s + 12 + 4 + 4 * K + 4 * K + 4 * K + 4)
-    t = calls["render_forward"] * 1e-3
-    ach = bytes_ / t / 1e9
-    return {"kernel": "k_render_topk (fss_render_forward)", "bound": "hbm", "achieved": round(ach, 1),
-            "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": None,
-            "peak_source": src, "algorithmic_bytes": int(bytes_), "pairs": P, "unique_rows": int(U)}
+    s, K, Cc, npx = 2, K_TOP, C_FEAT, H * W
+    return {
+        # ranges; per pair: list id, warp mask, adjugate rows, opacity, colour;
+        # selected rows once per tile; per pixel: features, rgb, T, ids, saved pos/w, nstop
+        "k_render_topk": tiles * 8 + P * (4 + 4 + 48 + 4 + 12) + U * Cc * s
+        + npx * (Cc * s + 12 + 4 + 4 * K * 3 + 4),
+        # per pixel: saved pos/w, dL/dF, dots written; selected rows (+ list id, slot) once
+        # per tile; the FP32 feature-gradient accumulators written once
+        "k_bwd_feat": tiles * 8 + npx * (8 * K + Cc * s + 4 * K) + U * (Cc * s + 8) + nslot * Cc * 4,
+        # per pixel: nstop, T, dL/drgb, saved pos, dots; per pair: list id, mask, record
+        # rows, colour; the per-(view, slot) gradient rows written once
+        "k_bwd_geo": tiles * 8 + npx * (4 + 4 + 12 + 8 * K) + P * (4 + 4 + 64 + 12) + nslot * 64,
+    }, {"pairs": P, "unique_rows": U, "slots": nslot}
+
+
+def roofline(path, torch, L, flush):
+    """Roofline of the dominant kernel (largest average duration): algorithmic
+    bytes per launch / its event-timed duration (both averaged over the 16
+    poses), against the measured HBM copy bandwidth; the other render kernels
+    alongside."""
+    peak, src = measured_peaks()
+    kt, nbytes, sizes = kernel_times(path, torch, L, flush)
+    rows = {}
+    for k, b in nbytes.items():
+        ach = b / (kt[k] * 1e-3) / 1e9
+        rows[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                   "traffic": NCU_TRAFFIC.get(k), "algorithmic_bytes": int(b), "ms": round(kt[k], 5)}
+    dom = max(kt, key=kt.get)
+    main = dict(rows.get(dom, {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
+                               "traffic": None}), kernel=dom, peak_source=f"{src} (MEASURED_PEAKS.json hbm_gbs)")
+    main.update(sizes)
+    return main, rows, {k: round(v * 1e3, 2) for k, v in kt.items()}
 
 
 def e2e(path, torch, dev, ptr, L, args):

@@ -239,6 +239,21 @@ fss_status fss_forward_static(const fss_params *params, const fss_camera *cams, 
                               void *out_feat, float *out_rgb, float *out_T, int32_t *out_topk_id, void *saved,
                               int64_t *num_pairs, fss_stream_t stream);
 
+/*
+ * Measurement hook (the paper has no counterpart): after this call, the
+ * next n_events kernels that this library launches from the calling thread
+ * each record one of `events` (cudaEvent_t handles created by the caller,
+ * in order) on their stream right after the launch, as external events, so
+ * that they also become nodes of a captured CUDA graph.  The elapsed time
+ * between consecutive events is then one kernel's duration.  n_events = 0
+ * switches the hook off.  The array must stay valid while the hook is on.
+ * Kernels per call: fss_project_bin 3 (project, scan, emit), fss_sort 1,
+ * fss_render_forward 1, fss_loss_l2_l1 1, fss_render_backward 4 for Top-K
+ * (clear, feature gradients, geometry replay, projection) or 3 for K = 0,
+ * plus 1 when g_feat is given (feature rows).
+ */
+fss_status fss_set_kernel_events(void *const *events, int32_t n_events);
+
 /* Message of the last error returned to the calling thread ("" if none). */
 const char *fss_last_error(void);
 

@@ -32,7 +32,7 @@ N_REGIONS = 18
 
 EXPORTS = ["fss_default_params", "fss_workspace_size", "fss_saved_size", "fss_project_bin", "fss_sort",
            "fss_render_forward", "fss_render_backward", "fss_read_status", "fss_last_error",
-           "fss_workspace_region", "fss_loss_l2_l1", "fss_forward_static"]
+           "fss_workspace_region", "fss_loss_l2_l1", "fss_forward_static", "fss_set_kernel_events"]
 FSS_STATIC_SCRATCH_BYTES = 64 << 20
 
 
@@ -83,6 +83,7 @@ def lib():
                 "fss_loss_l2_l1": [pp, i64, P, P, P, P, C.c_float, C.c_float, P, P, P, P],
                 "fss_forward_static": [pp, pc, i32, i64, i64, P, P, P, P, P, P, P, P, P, P, P,
                                        C.POINTER(C.c_int64), P],
+                "fss_set_kernel_events": [C.POINTER(C.c_void_p), i32],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -174,3 +175,15 @@ def fss_forward_static(params, cams, n_cams, N, pair_capacity, means, scales, qu
     if s not in (FSS_OK, FSS_ERR_CAPACITY):
         check(s)
     return s, n.value
+
+
+_events_keepalive = None
+
+
+def fss_set_kernel_events(events):
+    """events: sequence of torch.cuda.Event (timing enabled) or raw handles; [] switches the hook off."""
+    global _events_keepalive
+    handles = [e.cuda_event if hasattr(e, "cuda_event") else int(e) for e in events]
+    arr = (C.c_void_p * max(1, len(handles)))(*handles)
+    check(lib().fss_set_kernel_events(arr, len(handles)))
+    _events_keepalive = arr if handles else None

@@ -172,6 +172,29 @@ bool misaligned16(const void* p) { return p && (reinterpret_cast<uintptr_t>(p) &
 // Records `msg` as the calling thread's last error (for units outside this file).
 fss_status set_error(fss_status s, const char* msg) { return fail(s, "%s", msg); }
 
+namespace {
+thread_local cudaEvent_t* g_mark_ev = nullptr;
+thread_local int g_mark_n = 0, g_mark_k = 0;
+}  // namespace
+
+void kernel_mark(cudaStream_t s) {
+    if (g_mark_k >= g_mark_n) return;
+    // an external record becomes a node of a graph being captured; outside a
+    // capture the plain record is the valid form
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e == cudaSuccess)
+        e = cs == cudaStreamCaptureStatusActive
+                ? cudaEventRecordWithFlags(g_mark_ev[g_mark_k], s, cudaEventRecordExternal)
+                : cudaEventRecord(g_mark_ev[g_mark_k], s);
+    ++g_mark_k;
+    if (e != cudaSuccess) {  // timing must never fail a compute call: drop the hook
+        (void)cudaGetLastError();
+        g_mark_n = g_mark_k = 0;
+        g_mark_ev = nullptr;
+    }
+}
+
 }  // namespace fss
 
 using namespace fss;
@@ -257,8 +280,10 @@ fss_status fss_project_bin(const fss_params* params, const fss_camera* cams, int
                                                ctx.at<uint32_t>(REG_WIDE), ctx.at<uint32_t>(REG_UNB),
                                                ctx.at<int32_t>(REG_SLOT), ctx.at<int32_t>(REG_SLOT_SURF), stp);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_project");
+    kernel_mark(st);
     k_scan<<<1, 1024, 0, st>>>(ctx.cams, ctx.P, ctx.at<uint32_t>(REG_TILECNT), ctx.at<int2>(REG_RANGES), stp);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_scan");
+    kernel_mark(st);
     // one resident wave: records run from the lowest threads up, tile emission
     // from the highest down, so both start at once
     int emit_per_sm = 0;
@@ -273,6 +298,7 @@ fss_status fss_project_bin(const fss_params* params, const fss_camera* cams, int
                                     ctx.at<uint32_t>(REG_TILECNT), ctx.at<uint32_t>(REG_LIST), means, scales, quats,
                                     ctx.at<float4>(REG_REC), stp, max_lines);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_emit");
+    kernel_mark(st);
     return FSS_OK;
 }
 
@@ -290,6 +316,7 @@ fss_status fss_sort(const fss_params* params, const fss_camera* cams, int32_t n_
                                                       ctx.at<Status>(REG_STATUS));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_tile_sort");
+    kernel_mark(st);
     return FSS_OK;
 }
 
@@ -425,5 +452,15 @@ fss_status fss_loss_l2_l1(const fss_params* params, int64_t n_pix, const void* f
 }
 
 const char* fss_last_error(void) { return g_err.c_str(); }
+
+fss_status fss_set_kernel_events(void* const* events, int32_t n_events) {
+    if (n_events < 0 || (n_events > 0 && !events)) return fail(FSS_ERR_INVALID_ARG, "events is NULL or n_events < 0");
+    for (int32_t k = 0; k < n_events; ++k)
+        if (!events[k]) return fail(FSS_ERR_INVALID_ARG, "event %d is NULL", k);
+    g_mark_ev = n_events ? reinterpret_cast<cudaEvent_t*>(const_cast<void**>(events)) : nullptr;
+    g_mark_n = n_events;
+    g_mark_k = 0;
+    return FSS_OK;
+}
 
 }  // extern "C"

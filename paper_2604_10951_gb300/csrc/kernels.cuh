@@ -7,6 +7,11 @@ namespace fss {
 
 constexpr int SORT_CAP = 4096;  // longest tile list sorted in shared memory
 
+// Measurement hook (fss_set_kernel_events): called right after every kernel
+// launch; records the calling thread's next caller-supplied event, if any,
+// on the launch stream.
+void kernel_mark(cudaStream_t s);
+
 __global__ void k_project(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                           const float* __restrict__ means, const float* __restrict__ scales,
                           const float* __restrict__ quats, const float* __restrict__ opac, float4* __restrict__ rec,

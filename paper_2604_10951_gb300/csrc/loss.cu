@@ -63,7 +63,9 @@ cudaError_t launch_loss(int64_t n_pix, int C, int dtype, const void* F, const fl
     else
         k_loss<float><<<num_sms * 4, 256, 0, s>>>(n_pix, C, (const float*)F, rgb, (const float*)Ft, rgbt, wf, wc,
                                                   (float*)dF, drgb, loss);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess) kernel_mark(s);
+    return e;
 }
 
 }  // namespace fss

@@ -766,7 +766,9 @@ cudaError_t launch_feat(const Cams& cams, const RParams& P, const BwdArgs& a, cu
         if (a.persistent && (e2 = persistent_grid((const void*)kern, BWD_FEAT_THREADS, smem, grid)) != cudaSuccess)
             return e2;
         kern<<<grid, BWD_FEAT_THREADS, smem, s>>>(cams, P, a, pch, rowe, G, ucap);
-        return cudaGetLastError();
+        e2 = cudaGetLastError();
+        if (e2 == cudaSuccess) kernel_mark(s);
+        return e2;
     };
     if (P.ts == 8) return go(k_bwd_feat<8, FT>);
     if (P.ts == 16) return go(k_bwd_feat<16, FT>);
@@ -784,7 +786,9 @@ cudaError_t launch_geo_one(const Cams& cams, const RParams& P, const BwdArgs& a,
                             cudaSuccess)
         return e;
     k_bwd_geo<TS, FULL, CMAX, FT><<<grid, TS * TS, smem, s>>>(cams, P, a);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess) kernel_mark(s);
+    return e;
 }
 
 template <int TS, typename FT>
@@ -800,6 +804,7 @@ cudaError_t launch_all(const Cams& cams, const RParams& P, const BwdArgs& a, int
     cudaError_t e;
     k_bwd_clear<<<num_sms * 4, 256, 0, s>>>(cams, P, a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    kernel_mark(s);
     if (P.K > 0) {
         if ((e = launch_feat<FT>(cams, P, a, s)) != cudaSuccess) return e;
     }
@@ -810,9 +815,11 @@ cudaError_t launch_all(const Cams& cams, const RParams& P, const BwdArgs& a, int
     const int64_t nb = (P.N + 255) / 256;
     k_bwd_project<<<(unsigned)std::max<int64_t>(1, nb), 256, 0, s>>>(cams, P, a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    kernel_mark(s);
     if (a.g_feat) {
         k_feat_out<FT><<<num_sms * 8, 256, 0, s>>>(P, a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        kernel_mark(s);
     }
     return cudaSuccess;
 }

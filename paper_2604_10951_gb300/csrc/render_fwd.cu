@@ -373,7 +373,9 @@ cudaError_t launch(KernelT kern, int threads, size_t smem, const Cams& cams, con
     }
     if (grid <= 0) return cudaSuccess;
     kern<<<grid, threads, smem, stream>>>(cams, P, a);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess) kernel_mark(stream);
+    return e;
 }
 
 template <int TS, typename FT>

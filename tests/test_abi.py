@@ -115,3 +115,11 @@ def test_static_forward_rejects_oversized_frames_on_the_host(lib):
     n = C.c_int64()
     s = lib.fss_forward_static(C.byref(p), cams, 1, 1000, big, *([None] * 11), C.byref(n), None)
     assert s == L.FSS_ERR_UNSUPPORTED and "FSS_STATIC_SCRATCH_BYTES" in L.last_error()
+
+
+def test_kernel_event_hook_arguments(lib):
+    assert lib.fss_set_kernel_events(None, 0) == L.FSS_OK
+    assert lib.fss_set_kernel_events(None, 2) == L.FSS_ERR_INVALID_ARG
+    arr = (C.c_void_p * 2)(None, None)
+    assert lib.fss_set_kernel_events(arr, 2) == L.FSS_ERR_INVALID_ARG
+    assert lib.fss_set_kernel_events(arr, -1) == L.FSS_ERR_INVALID_ARG
