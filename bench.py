@@ -316,6 +316,8 @@ def run_ours(args):
             out["roofline"], out["roofline_kernels"], out["kernel_us"] = roofline(ours, torch, L, flush)
         out["e2e"] = e2e(ours, torch, dev, ptr, L, args)
         del base
+        out["ablation_fwd"] = ablation(torch, L, dev, means, scales, quats, opac, rgb, feats[torch.float32], poses,
+                                       flush)
     if D.rank == 0 and not args.no_extras:
         out["cpu_baseline"] = cpu_baseline(sc, poses, sample_frames=1)
     if D.rank == 0:
@@ -419,6 +421,44 @@ def roofline(path, torch, L, flush):
                                "traffic": None}), kernel=dom, peak_source=f"{src} (MEASURED_PEAKS.json hbm_gbs)")
     main.update(sizes)
     return main, rows, {k: round(v * 1e3, 2) for k, v in kt.items()}
+
+
+def ablation(torch, L, dev, means, scales, quats, opac, rgb, feats, poses, flush, reps=3):
+    """Forward-only ablation in the layout of the paper's Table 2 on the same
+    frames, FP32 features: (A) square box + full accumulation, (B) AccuTile +
+    full, (C) square box + Top-K (K=8), (D) AccuTile + Top-K.  Per row: mean
+    over the 16 poses of the binning + sort + render time (CUDA events, L2
+    flushed before each frame), tile-surfel pairs per frame (the paper's
+    RN-Total) and pairs per tile."""
+    from paper_2604_10951_gb300.raster import Frame, make_cams, make_params
+
+    rows = {}
+    for name, mode, K in (("A", "aabb", 0), ("B", "accu", 0), ("C", "aabb", K_TOP), ("D", "accu", K_TOP)):
+        p = make_params(C=C_FEAT, K=K, tile_size=16, bin_mode=mode, stop_rule="exact_topk" if K else "tmin")
+        fr = Frame([poses[0]], N_SPLATS, p, pair_capacity=1 << 21, device=dev)
+        F, rgb_o, T, ids = fr.new_outputs()
+        ms, pairs = [], []
+        for cam in poses:
+            fr.cams = make_cams([cam])
+            fr.bin_and_sort(means, scales, quats, opac)
+            pairs.append(fr.num_pairs)
+            for _ in range(reps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fr.project_bin(means, scales, quats, opac)
+                fr.sort()
+                fr.render_forward(rgb, feats, F, rgb_o, T, ids)
+                b.record()
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+        s, n = fr.read_status()
+        tiles = fr.region(L.REG_RANGES).shape[0] // 8
+        rows[name] = {"bin_mode": mode, "K": K, "fwd_ms": round(float(np.mean(ms)), 4),
+                      "fps": round(1e3 / float(np.mean(ms)), 1), "pairs_per_frame": int(np.mean(pairs)),
+                      "pairs_per_tile": round(float(np.mean(pairs)) / tiles, 1), "status": int(s)}
+        del fr
+    return rows
 
 
 def e2e(path, torch, dev, ptr, L, args):

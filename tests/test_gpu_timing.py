@@ -69,6 +69,7 @@ def test_one_event_per_kernel_in_order(graph):
     assert all(x >= 0.0 for x in t)
     total = ev[0].elapsed_time(end)
     assert sum(t) <= total + 1e-3 and sum(t) >= 0.5 * total
-    # with the hook off no further event is recorded: the spare events keep their time
-    spare = ev[N_KERNELS + 1].elapsed_time(ev[N_KERNELS + 2])
-    assert abs(spare) < 1e-2
+    # no event beyond the n given is recorded: the spare ones keep their time from
+    # before the step, so they lie at least the whole step before its end
+    for k in (N_KERNELS + 1, N_KERNELS + 2):
+        assert ev[k].elapsed_time(end) >= total - 1e-3
