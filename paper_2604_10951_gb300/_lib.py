@@ -181,7 +181,8 @@ _events_keepalive = None
 
 
 def fss_set_kernel_events(events):
-    """events: sequence of torch.cuda.Event (timing enabled) or raw handles; [] switches the hook off."""
+    """events: sequence of torch.cuda.Event (timing enabled) or raw handles; [] switches the hook off.
+    torch creates an event's CUDA handle at its first record, so record each one once beforehand."""
     global _events_keepalive
     handles = [e.cuda_event if hasattr(e, "cuda_event") else int(e) for e in events]
     arr = (C.c_void_p * max(1, len(handles)))(*handles)
