@@ -27,6 +27,7 @@ _lock = threading.Lock()
 AABB, SNUG, ACCU = 0, 1, 2
 TMIN, EXACT_TOPK = 0, 1
 FLAG_ALPHA, FLAG_TMIN, FLAG_TIE, FLAG_EXACT, FLAG_NEAR, FLAG_CLAMP, FLAG_GRAZE = 1, 2, 4, 8, 16, 32, 64
+FLAG_MEDIAN = 128
 
 
 class OrcCam(C.Structure):
@@ -71,10 +72,10 @@ def _load():
             lib.orc_ranges.argtypes = [i64, P, C.c_int32, P]
             lib.orc_ranges.restype = None
             lib.orc_render.argtypes = [i64, P, P, P, P, P, P, C.POINTER(OrcCam), C.POINTER(OrcParams), P, P, P, P,
-                                       P, P, P, P, P, P, P, P, P, P, C.c_int]
+                                       P, P, P, P, P, P, P, P, P, P, C.c_int, P, P, P]
             lib.orc_render.restype = None
             lib.orc_render_backward.argtypes = [i64, P, P, P, P, P, P, C.POINTER(OrcCam), C.POINTER(OrcParams),
-                                                P, P, P, P, P, P, P, P, P, P, P, P, P, P]
+                                                P, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
             lib.orc_render_backward.restype = None
             lib.orc_geometry.argtypes = [i64, P, P, P, P, C.POINTER(OrcCam), C.POINTER(OrcParams), P, P, P, P]
             lib.orc_geometry.restype = None
@@ -232,7 +233,8 @@ def render(scene, cam, params, feats=None, binned=None, brute=False, visible=Non
         binned = binning(scene, cam, params)
     out = dict(F=np.zeros((H, W, Cc)), rgb=np.zeros((H, W, 3)), T=np.zeros((H, W)),
                nstop=np.zeros((H, W), np.int32), ncontrib=np.zeros((H, W), np.int32),
-               flags=np.zeros((H, W), np.int32), counters=np.zeros(2, np.int64))
+               flags=np.zeros((H, W), np.int32), counters=np.zeros(2, np.int64),
+               depth=np.zeros((H, W)), depth_med=np.zeros((H, W)), normal=np.zeros((H, W, 3)))
     Kc = max(K, 1)
     out.update(ids=np.full((H, W, Kc), -1, np.int32), w=np.zeros((H, W, Kc)), pos=np.full((H, W, Kc), -1, np.int32))
     rng = None if brute else _i32(binned["ranges"])
@@ -243,7 +245,8 @@ def render(scene, cam, params, feats=None, binned=None, brute=False, visible=Non
                    C.byref(params), _ptr(rng), _ptr(sid), _ptr(vis), _ptr(zk),
                    _ptr(out["F"]), _ptr(out["rgb"]), _ptr(out["T"]),
                    _ptr(out["ids"]) if K else None, _ptr(out["w"]) if K else None, _ptr(out["pos"]) if K else None,
-                   _ptr(out["nstop"]), _ptr(out["ncontrib"]), _ptr(out["flags"]), _ptr(out["counters"]), int(threads))
+                   _ptr(out["nstop"]), _ptr(out["ncontrib"]), _ptr(out["flags"]), _ptr(out["counters"]), int(threads),
+                   _ptr(out["depth"]), _ptr(out["depth_med"]), _ptr(out["normal"]))
     if not K:
         for k in ("ids", "w", "pos"):
             out.pop(k)
@@ -253,7 +256,10 @@ def render(scene, cam, params, feats=None, binned=None, brute=False, visible=Non
 
 def render_backward(scene, cam, params, gF, grgb, gT=None, feats=None, binned=None, brute=False,
                     visible=None, zkey=None):
-    """Analytic FP64 gradients of sum(gF*F) + sum(grgb*rgb) + sum(gT*T)."""
+    """Analytic FP64 gradients of sum(gF*F) + sum(grgb*rgb) + sum(gT*T), and
+    under "abs" [N, 10] the same chain over magnitudes (means, scales, quats,
+    opacity): a bound on the sum of |terms| that each geometric gradient
+    entry adds up."""
     lib = _load()
     m, s, q, o = _scene_arrays64(scene)
     rgb = _f64(scene.rgb)
@@ -263,7 +269,7 @@ def render_backward(scene, cam, params, gF, grgb, gT=None, feats=None, binned=No
     if not brute and binned is None:
         binned = binning(scene, cam, params)
     g = dict(means=np.zeros((N, 3)), scales=np.zeros((N, 2)), quats=np.zeros((N, 4)), opac=np.zeros(N),
-             rgb=np.zeros((N, 3)), feat=np.zeros((N, Cc)), Tmat=np.zeros((N, 9)))
+             rgb=np.zeros((N, 3)), feat=np.zeros((N, Cc)), Tmat=np.zeros((N, 9)), abs=np.zeros((N, 10)))
     rng = None if brute else _i32(binned["ranges"])
     sid = None if brute else _i32(binned["ids"])
     vis = None if visible is None else _i32(visible)
@@ -275,7 +281,7 @@ def render_backward(scene, cam, params, gF, grgb, gT=None, feats=None, binned=No
                             C.byref(params), _ptr(rng), _ptr(sid), _ptr(vis), _ptr(zk),
                             _ptr(gF), _ptr(grgb), _ptr(gT),
                             _ptr(g["means"]), _ptr(g["scales"]), _ptr(g["quats"]), _ptr(g["opac"]),
-                            _ptr(g["rgb"]), _ptr(g["feat"]), _ptr(g["Tmat"]))
+                            _ptr(g["rgb"]), _ptr(g["feat"]), _ptr(g["Tmat"]), _ptr(g["abs"]))
     return g
 
 

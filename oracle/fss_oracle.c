@@ -46,7 +46,9 @@
  *   - k^2 = 2 ln(o / alpha_min): the cutoff where o f(u) reaches alpha_min;
  *   - stop rules: TMIN stops before a surfel that would take T below T_min;
  *     EXACT_TOPK additionally stops once the K-set is full and no later
- *     surfel can enter it (alpha_max * T <= smallest selected weight).
+ *     surfel can enter it (alpha_max * T <= smallest selected weight); with
+ *     the first-K selection (select = 1, the other reading of Eq. 7) it
+ *     stops once K surfels contributed.
  */
 #include <math.h>
 #include <stdint.h>
@@ -88,7 +90,8 @@ enum {
     FLAG_EXACT = 8,  /* EXACT_TOPK stop within 1e-6 of its bound  */
     FLAG_NEAR = 16,  /* some |z_hit - near| < 1e-5                */
     FLAG_CLAMP = 32, /* some |o f(u) - alpha_max| < 1e-6          */
-    FLAG_GRAZE = 64  /* contributor seen nearly edge-on           */
+    FLAG_GRAZE = 64, /* contributor seen nearly edge-on           */
+    FLAG_MEDIAN = 128 /* some |T (1 - alpha) - 1/2| < 1e-6 (median depth) */
 };
 
 #define DEG_EPS 1e-3 /* edge-on cull: |n . p_c| <= DEG_EPS |p_c| */
@@ -119,6 +122,7 @@ typedef struct {
     double pc[3];    /* surfel centre in camera space */
     double z;        /* = pc[2] */
     double cosang;   /* n.p_c / |p_c| */
+    double nf[3];    /* camera-space unit normal, turned to face the camera (n.p_c <= 0) */
     int ok;          /* passes the FP64 cull rules */
 } geo64;
 
@@ -149,6 +153,8 @@ static void geometry64(const double *mean, const double *scale, const double *qu
     g->z = g->pc[2];
     double pn = sqrt(g->pc[0] * g->pc[0] + g->pc[1] * g->pc[1] + g->pc[2] * g->pc[2]);
     g->cosang = (nc[0] * g->pc[0] + nc[1] * g->pc[1] + nc[2] * g->pc[2]) / pn;
+    const double sgn = g->cosang > 0.0 ? -1.0 : 1.0;
+    for (int k = 0; k < 3; ++k) g->nf[k] = sgn * nc[k];
     g->ok = (g->z > cam->near_plane) && (opac >= p->alpha_min) && (fabs(g->cosang) > DEG_EPS);
 }
 
@@ -696,6 +702,7 @@ typedef struct {
     int32_t id;     /* surfel index */
     double alpha, T, w;
     double u, v, oG; /* for gradients */
+    double zh;       /* camera depth of the ray-surfel hit */
     double hx[3], hy[3], c[3];
 } contrib_t;
 
@@ -735,6 +742,8 @@ static void composite_pixel(const geo64 *geo, const double *opac, const double *
             if (fabs(amax * T - wmin) <= 1e-6) flags |= FLAG_EXACT;
             if (amax * T <= wmin) break;
         }
+        /* first-K selection: the set is final once K surfels contributed */
+        if (K > 0 && p->stop_rule == ORC_EXACT && p->select == 1 && n == K) break;
         const int32_t id = cand[j];
         const geo64 *g = &geo[id];
         double u, v, zh, hx[3], hy[3], c[3];
@@ -750,10 +759,11 @@ static void composite_pixel(const geo64 *geo, const double *opac, const double *
         if (alpha < amin) continue;
         double Tn = T * (1.0 - alpha);
         if (fabs(Tn - tmin) < 1e-8) flags |= FLAG_TMIN;
+        if (fabs(Tn - 0.5) < 1e-6) flags |= FLAG_MEDIAN;
         if (Tn < tmin) break;
         contrib_t *e = &cb[n++];
         e->pos = j; e->id = id; e->alpha = alpha; e->T = T; e->w = alpha * T;
-        e->u = u; e->v = v; e->oG = oG;
+        e->u = u; e->v = v; e->oG = oG; e->zh = zh;
         memcpy(e->hx, hx, sizeof hx); memcpy(e->hy, hy, sizeof hy); memcpy(e->c, c, sizeof c);
         if (fabs(g->cosang) < 2e-3) flags |= FLAG_GRAZE;
         for (int k = 0; k < 3; ++k) rgbacc[k] += e->w * rgb[3 * id + k];
@@ -858,7 +868,8 @@ void orc_render(int64_t N, const double *means, const double *scales, const doub
                 const orc_params *p, const int32_t *ranges, const int32_t *sorted_ids,
                 const int32_t *visible, const float *zkey,
                 double *F, double *out_rgb, double *out_T, int32_t *ids, double *wout, int32_t *pos,
-                int32_t *nstop, int32_t *ncontrib, int32_t *flags, int64_t *counters, int n_threads)
+                int32_t *nstop, int32_t *ncontrib, int32_t *flags, int64_t *counters, int n_threads,
+                double *depth, double *depth_med, double *normal)
 {
     const int W = cam->width, H = cam->height, ts = p->tile_size, C = p->C, K = p->K;
     const int tiles_x = (W + ts - 1) / ts;
@@ -901,6 +912,22 @@ void orc_render(int64_t N, const double *means, const double *scales, const doub
             if (nstop) nstop[pix] = o.n_stop;
             if (ncontrib) ncontrib[pix] = o.n_contrib;
             if (flags) flags[pix] = o.flags;
+            /* sensor outputs over the traversed contributors, like RGB: expected
+             * depth sum w z_hit, median depth (the hit where T first drops below
+             * 1/2, else 0) and normal sum w n (camera space, facing the camera) */
+            if (depth || depth_med || normal) {
+                double dz = 0.0, zm = 0.0, nn[3] = {0.0, 0.0, 0.0};
+                int found = 0;
+                for (int i = 0; i < o.n_contrib; ++i) {
+                    const contrib_t *e = &cb[i];
+                    dz += e->w * e->zh;
+                    for (int k = 0; k < 3; ++k) nn[k] += e->w * sp.geo[e->id].nf[k];
+                    if (!found && e->T * (1.0 - e->alpha) < 0.5) { zm = e->zh; found = 1; }
+                }
+                if (depth) depth[pix] = dz;
+                if (depth_med) depth_med[pix] = zm;
+                if (normal) for (int k = 0; k < 3; ++k) normal[3 * pix + k] = nn[k];
+            }
             if (F) {
                 double *f = F + pix * C;
                 for (int ch = 0; ch < C; ++ch) f[ch] = 0.0;
@@ -954,6 +981,14 @@ static void dframe(const double q[4], double dtu[4][3], double dtv[4][3])
  * Outputs (accumulated, caller zeroes): g_means[N*3], g_scales[N*2],
  * g_quats[N*4], g_opac[N], g_rgb[N*3], g_feat[N*C], and optionally the
  * per-surfel derivative w.r.t. the rows of T, g_T[N*9].
+ * g_abs[N*10] (optional, accumulated): the same chain evaluated over
+ * magnitudes, per surfel (means 3, scales 2, quats 4, opacity 1): every
+ * sum and product of the chain, from the upstream gradients through
+ * dL/dalpha, the ray-splat quotients, the cross products and the T-row
+ * sums to the parameters, is taken over the absolute values of its
+ * operands.  This is the scale of the rounding error of a finite-precision
+ * evaluation of the same chain under cancellation (forward error
+ * analysis), used for test tolerances; it is >= |gradient| entry by entry.
  */
 void orc_render_backward(int64_t N, const double *means, const double *scales, const double *quats,
                          const double *opac, const double *rgb, const double *feats, const orc_cam *cam,
@@ -961,13 +996,14 @@ void orc_render_backward(int64_t N, const double *means, const double *scales, c
                          const int32_t *visible, const float *zkey,
                          const double *gF, const double *grgb, const double *gT,
                          double *g_means, double *g_scales, double *g_quats, double *g_opac,
-                         double *g_rgb, double *g_feat, double *g_Tmat)
+                         double *g_rgb, double *g_feat, double *g_Tmat, double *g_abs)
 {
     const int W = cam->width, H = cam->height, ts = p->tile_size, C = p->C, K = p->K;
     const int tiles_x = (W + ts - 1) / ts;
     scene_prep sp;
     prepare(N, means, scales, quats, opac, cam, p, visible, zkey, ranges == NULL, &sp);
     double *dT = (double *)calloc((size_t)(N > 0 ? N : 1) * 9, sizeof(double));
+    double *dTa = g_abs ? (double *)calloc((size_t)(N > 0 ? N : 1) * 9, sizeof(double)) : NULL;
     int64_t cap = ranges ? 0 : sp.n_order;
     if (ranges) {
         int nt = tiles_x * ((H + ts - 1) / ts);
@@ -978,6 +1014,7 @@ void orc_render_backward(int64_t N, const double *means, const double *scales, c
     }
     contrib_t *cb = (contrib_t *)malloc(sizeof(contrib_t) * (size_t)(cap > 0 ? cap : 1));
     double *s = (double *)malloc(sizeof(double) * (size_t)(cap > 0 ? cap : 1));
+    double *sa = (double *)malloc(sizeof(double) * (size_t)(cap > 0 ? cap : 1));
     char *insel = (char *)malloc((size_t)(cap > 0 ? cap : 1));
     for (int py = 0; py < H; ++py) {
         for (int px = 0; px < W; ++px) {
@@ -1004,27 +1041,34 @@ void orc_render_backward(int64_t N, const double *means, const double *scales, c
             /* s_i: what each blending weight multiplies */
             for (int i = 0; i < n; ++i) {
                 const int id = cb[i].id;
-                double v = 0.0;
+                double v = 0.0, va = 0.0;
                 for (int k = 0; k < 3; ++k) v += rgb[3 * id + k] * gc[k];
+                for (int k = 0; k < 3; ++k) va += fabs(rgb[3 * id + k] * gc[k]);
                 if (insel[i] && gf) {
                     const double *c = feats + (int64_t)id * C;
                     for (int ch = 0; ch < C; ++ch) v += c[ch] * gf[ch];
+                    for (int ch = 0; ch < C; ++ch) va += fabs(c[ch] * gf[ch]);
                 }
                 s[i] = v;
+                sa[i] = va;
                 for (int k = 0; k < 3; ++k) g_rgb[3 * id + k] += cb[i].w * gc[k];
                 if (insel[i] && gf)
                     for (int ch = 0; ch < C; ++ch) g_feat[(int64_t)id * C + ch] += cb[i].w * gf[ch];
             }
             /* dL/dalpha_j = T_j s_j - (sum_{i>j} w_i s_i + T_final (bg.grgb + gT)) / (1 - alpha_j) */
             double tail = o.T * (p->bg[0] * gc[0] + p->bg[1] * gc[1] + p->bg[2] * gc[2] + gt);
+            double taila = o.T * (fabs(p->bg[0] * gc[0]) + fabs(p->bg[1] * gc[1]) + fabs(p->bg[2] * gc[2]) + fabs(gt));
             for (int j = n - 1; j >= 0; --j) {
                 const contrib_t *e = &cb[j];
                 const int id = e->id;
                 double dal = e->T * s[j] - tail / (1.0 - e->alpha);
+                const double dala = e->T * sa[j] + taila / (1.0 - e->alpha);
                 tail += e->w * s[j];
+                taila += e->w * sa[j];
                 if (!(e->oG < p->alpha_max)) continue; /* clamped: flat */
                 double G = e->oG / opac[id];
                 g_opac[id] += dal * G;
+                if (g_abs) g_abs[10 * (int64_t)id + 9] += dala * G;
                 double drho = dal * (-0.5 * e->oG);
                 double du = 2.0 * e->u * drho, dv = 2.0 * e->v * drho;
                 double gcv[3] = {du / e->c[2], dv / e->c[2], -(du * e->u + dv * e->v) / e->c[2]};
@@ -1036,6 +1080,24 @@ void orc_render_backward(int64_t N, const double *means, const double *scales, c
                     d[k] += dhx[k];
                     d[3 + k] += dhy[k];
                     d[6 + k] += -x * dhx[k] - y * dhy[k];
+                }
+                if (dTa) { /* the same steps over magnitudes */
+                    const double dra = dala * 0.5 * e->oG;
+                    const double dua = 2.0 * fabs(e->u) * dra, dva = 2.0 * fabs(e->v) * dra;
+                    const double ic = 1.0 / fabs(e->c[2]);
+                    const double ga[3] = {dua * ic, dva * ic, (dua * fabs(e->u) + dva * fabs(e->v)) * ic};
+                    const double ax[3] = {fabs(e->hx[0]), fabs(e->hx[1]), fabs(e->hx[2])};
+                    const double ay[3] = {fabs(e->hy[0]), fabs(e->hy[1]), fabs(e->hy[2])};
+                    const double ahx[3] = {ay[1] * ga[2] + ay[2] * ga[1], ay[2] * ga[0] + ay[0] * ga[2],
+                                           ay[0] * ga[1] + ay[1] * ga[0]};
+                    const double ahy[3] = {ga[1] * ax[2] + ga[2] * ax[1], ga[2] * ax[0] + ga[0] * ax[2],
+                                           ga[0] * ax[1] + ga[1] * ax[0]};
+                    double *da = dTa + 9 * (int64_t)id;
+                    for (int k = 0; k < 3; ++k) {
+                        da[k] += ahx[k];
+                        da[3 + k] += ahy[k];
+                        da[6 + k] += x * ahx[k] + y * ahy[k];
+                    }
                 }
             }
         }
@@ -1078,8 +1140,31 @@ void orc_render_backward(int64_t N, const double *means, const double *scales, c
                      Jv[a][0] * dtv[0] + Jv[a][1] * dtv[1] + Jv[a][2] * dtv[2];
         double dot = dqh[0] * qh[0] + dqh[1] * qh[1] + dqh[2] * qh[2] + dqh[3] * qh[3];
         for (int a = 0; a < 4; ++a) g_quats[4 * i + a] += (dqh[a] - dot * qh[a]) / qn;
+        if (dTa) { /* the same chain over magnitudes */
+            const double *da = dTa + 9 * i;
+            double acol[3][3], au[3], av[3], aqh[4], adot = 0.0;
+            double *ga = g_abs + 10 * i;
+            for (int c = 0; c < 3; ++c) {
+                acol[c][0] = cam->fx * da[c];
+                acol[c][1] = cam->fy * da[3 + c];
+                acol[c][2] = fabs(cam->cx) * da[c] + fabs(cam->cy) * da[3 + c] + da[6 + c];
+            }
+            for (int k = 0; k < 3; ++k) {
+                ga[k] += fabs(R[k]) * acol[2][0] + fabs(R[3 + k]) * acol[2][1] + fabs(R[6 + k]) * acol[2][2];
+                au[k] = scales[2 * i] * (fabs(R[k]) * acol[0][0] + fabs(R[3 + k]) * acol[0][1] + fabs(R[6 + k]) * acol[0][2]);
+                av[k] = scales[2 * i + 1] * (fabs(R[k]) * acol[1][0] + fabs(R[3 + k]) * acol[1][1] + fabs(R[6 + k]) * acol[1][2]);
+            }
+            ga[3] += fabs(Rtu[0]) * acol[0][0] + fabs(Rtu[1]) * acol[0][1] + fabs(Rtu[2]) * acol[0][2];
+            ga[4] += fabs(Rtv[0]) * acol[1][0] + fabs(Rtv[1]) * acol[1][1] + fabs(Rtv[2]) * acol[1][2];
+            for (int a = 0; a < 4; ++a) {
+                aqh[a] = 0.0;
+                for (int k = 0; k < 3; ++k) aqh[a] += fabs(Ju[a][k]) * au[k] + fabs(Jv[a][k]) * av[k];
+                adot += aqh[a] * fabs(qh[a]);
+            }
+            for (int a = 0; a < 4; ++a) ga[5 + a] += (aqh[a] + adot * fabs(qh[a])) / qn;
+        }
     }
-    free(dT); free(cb); free(s); free(insel);
+    free(dT); free(dTa); free(cb); free(s); free(sa); free(insel);
     release(&sp);
 }
 

@@ -173,3 +173,14 @@ def test_front_k_selection_variant_takes_the_first_contributors():
             w = full["F"][py, px]
             first = [i for i in order if w[i] > 0][:3]
             assert [i for i in front["ids"][py, px] if i >= 0] == first
+
+
+def test_front_k_exact_stop_keeps_features_and_stops_after_k_contributors():
+    sc, cam = scenes.tiny_scene(seed=13, n=1500)
+    a = O.render(sc, cam, O.make_params(K=3, select=1, stop_rule=O.TMIN))
+    b = O.render(sc, cam, O.make_params(K=3, select=1, stop_rule=O.EXACT_TOPK))
+    np.testing.assert_allclose(a["F"], b["F"], atol=1e-13)
+    np.testing.assert_array_equal(a["ids"], b["ids"])
+    # the traversal ends at the third contributor: exactly min(3, n) of them
+    np.testing.assert_array_equal(b["ncontrib"], np.minimum(a["ncontrib"], 3))
+    assert b["counters"][0] < a["counters"][0]
