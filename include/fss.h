@@ -87,11 +87,15 @@ typedef struct {
     int32_t schedule;   /* FSS_SCHED_GRID: one CTA per tile; FSS_SCHED_PERSISTENT:
                            one wave of CTAs pulling tiles from a device work
                            queue (balances views of mixed size) */
+    int32_t select;     /* K > 0: FSS_SELECT_TOPW, the K largest blending weights
+                           (Eq. 7); FSS_SELECT_FRONT, the first K contributors
+                           in depth order (the other reading of the selection set) */
 } fss_params;
 
 enum { FSS_SCHED_GRID = 0, FSS_SCHED_PERSISTENT = 1 };
+enum { FSS_SELECT_TOPW = 0, FSS_SELECT_FRONT = 1 };
 
-/* Fills the defaults listed above (tile 16, K 8, ACCU, TMIN, F32, C 16, grid). */
+/* Fills the defaults listed above (tile 16, K 8, ACCU, TMIN, F32, C 16, grid, TOPW). */
 fss_status fss_default_params(fss_params *params);
 
 /* Bytes of device workspace needed for these cameras, N surfels and at most
@@ -136,7 +140,10 @@ fss_status fss_sort(const fss_params *params, const fss_camera *cams, int32_t n_
  * (u,v), alpha = min(alpha_max, o exp(-(u^2+v^2)/2)), skip if
  * alpha < alpha_min, stop by params->stop_rule, w = alpha T, T *= 1 - alpha.
  * K = 0: F = sum_i w_i c_i over all contributors.  K > 0: F = sum over the K
- * largest w_i (ties: earlier wins), no renormalisation.
+ * largest w_i (ties: earlier wins; FSS_SELECT_FRONT: over the first K
+ * contributors), no renormalisation.  FSS_STOP_EXACT_TOPK stops once no
+ * later surfel can enter the set (TOPW: alpha_max T <= smallest selected
+ * weight; FRONT: K contributors found).
  * Device inputs: rgb [N,3] f32, feats [N,C] (feat_dtype).
  * Device outputs (any may be NULL except as noted; per view concatenated):
  *   out_feat [pix, C] in out_dtype; out_rgb [pix, 3] = sum w rgb + T bg;
@@ -148,6 +155,32 @@ fss_status fss_render_forward(const fss_params *params, const fss_camera *cams, 
                               void *workspace, int64_t pair_capacity, const float *rgb, const void *feats,
                               void *out_feat, float *out_rgb, float *out_T, int32_t *out_topk_id,
                               void *saved, fss_stream_t stream);
+
+/*
+ * Sensor outputs of the forward render: depth images by the same alpha
+ * blending as the colour (Sec. 3.5 with Eq. 2; the simulator's depth images,
+ * Sec. 4.4) and normals from the tangent vectors (Sec. 3.1), each
+ * [pix] or [pix, 3] float32 on the device, NULL to skip, summed over the
+ * same traversed contributors as out_rgb and not renormalised:
+ *   depth        sum_i w_i z_i, z_i the camera depth of the ray-surfel hit;
+ *   depth_median z_i of the first contributor after which T < 1/2, else 0;
+ *   normal       sum_i w_i n_i, n_i the surfel's camera-space unit normal
+ *                turned to face the camera.
+ * The backward pass does not differentiate them.
+ */
+typedef struct {
+    float *depth;
+    float *depth_median;
+    float *normal;
+} fss_aux_outputs;
+
+/* fss_render_forward plus the sensor outputs in `aux` (may be NULL); the
+ * same arguments, ownership and errors.  Either call may run more than once
+ * on one binning (the persistent schedule resets its tile queue first). */
+fss_status fss_render_forward_aux(const fss_params *params, const fss_camera *cams, int32_t n_cams, int64_t N,
+                                  void *workspace, int64_t pair_capacity, const float *rgb, const void *feats,
+                                  void *out_feat, float *out_rgb, float *out_T, int32_t *out_topk_id,
+                                  void *saved, const fss_aux_outputs *aux, fss_stream_t stream);
 
 /*
  * Backward render: vector-Jacobian product of fss_render_forward for the

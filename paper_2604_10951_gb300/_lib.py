@@ -18,6 +18,7 @@ FSS_BIN_AABB, FSS_BIN_SNUG, FSS_BIN_ACCU = 0, 1, 2
 FSS_STOP_TMIN, FSS_STOP_EXACT_TOPK = 0, 1
 FSS_F32, FSS_BF16 = 0, 1
 FSS_SCHED_GRID, FSS_SCHED_PERSISTENT = 0, 1
+FSS_SELECT_TOPW, FSS_SELECT_FRONT = 0, 1
 FSS_MAX_CAMS = 64
 FSS_MAX_K = 32
 STATUS_NAMES = {0: "FSS_OK", 1: "FSS_ERR_INVALID_ARG", 2: "FSS_ERR_UNSUPPORTED", 3: "FSS_ERR_CAPACITY",
@@ -32,7 +33,8 @@ N_REGIONS = 18
 
 EXPORTS = ["fss_default_params", "fss_workspace_size", "fss_saved_size", "fss_project_bin", "fss_sort",
            "fss_render_forward", "fss_render_backward", "fss_read_status", "fss_last_error",
-           "fss_workspace_region", "fss_loss_l2_l1", "fss_forward_static", "fss_set_kernel_events"]
+           "fss_workspace_region", "fss_loss_l2_l1", "fss_forward_static", "fss_set_kernel_events",
+           "fss_render_forward_aux"]
 FSS_STATIC_SCRATCH_BYTES = 64 << 20
 
 
@@ -46,7 +48,11 @@ class fss_params(C.Structure):
     _fields_ = [("tile_size", C.c_int32), ("K", C.c_int32), ("bin_mode", C.c_int32), ("stop_rule", C.c_int32),
                 ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("T_min", C.c_float),
                 ("feat_dtype", C.c_int32), ("out_dtype", C.c_int32), ("C", C.c_int32),
-                ("bg_rgb", C.c_float * 3), ("schedule", C.c_int32)]
+                ("bg_rgb", C.c_float * 3), ("schedule", C.c_int32), ("select", C.c_int32)]
+
+
+class fss_aux_outputs(C.Structure):
+    _fields_ = [("depth", C.c_void_p), ("depth_median", C.c_void_p), ("normal", C.c_void_p)]
 
 
 class FssError(RuntimeError):
@@ -84,6 +90,8 @@ def lib():
                 "fss_forward_static": [pp, pc, i32, i64, i64, P, P, P, P, P, P, P, P, P, P, P,
                                        C.POINTER(C.c_int64), P],
                 "fss_set_kernel_events": [C.POINTER(C.c_void_p), i32],
+                "fss_render_forward_aux": [pp, pc, i32, i64, P, i64, P, P, P, P, P, P, P,
+                                           C.POINTER(fss_aux_outputs), P],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -188,3 +196,10 @@ def fss_set_kernel_events(events):
     arr = (C.c_void_p * max(1, len(handles)))(*handles)
     check(lib().fss_set_kernel_events(arr, len(handles)))
     _events_keepalive = arr if handles else None
+
+
+def fss_render_forward_aux(params, cams, n_cams, N, workspace, pair_capacity, rgb, feats, out_feat, out_rgb, out_T,
+                           out_topk_id, saved, depth, depth_median, normal, stream):
+    aux = fss_aux_outputs(depth, depth_median, normal)
+    return check(lib().fss_render_forward_aux(C.byref(params), cams, n_cams, N, workspace, pair_capacity, rgb, feats,
+                                              out_feat, out_rgb, out_T, out_topk_id, saved, C.byref(aux), stream))

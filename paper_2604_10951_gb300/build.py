@@ -26,6 +26,9 @@ UNITS = {
     "project.cu": ["-fmad=false"],
     "sort.cu": [],
     "render_fwd.cu": [],
+    "render_topk_f32.cu": [],
+    "render_topk_bf16.cu": [],
+    "render_full.cu": [],
     "render_bwd.cu": [],
     "loss.cu": [],
     "static_scratch.cu": [],

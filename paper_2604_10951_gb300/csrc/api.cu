@@ -58,6 +58,8 @@ fss_status check_params(const fss_params* p) {
     if (!(p->T_min >= 0.0f) || !(p->T_min < 1.0f)) return fail(FSS_ERR_INVALID_ARG, "need 0 <= T_min < 1");
     if (p->schedule != FSS_SCHED_GRID && p->schedule != FSS_SCHED_PERSISTENT)
         return fail(FSS_ERR_INVALID_ARG, "schedule %d", p->schedule);
+    if (p->select != FSS_SELECT_TOPW && p->select != FSS_SELECT_FRONT)
+        return fail(FSS_ERR_INVALID_ARG, "select %d", p->select);
     return FSS_OK;
 }
 
@@ -99,6 +101,7 @@ RParams make_rparams(const fss_params* p, const Cams& cams, int64_t N, int64_t c
     r.ts = p->tile_size; r.K = p->K; r.bin_mode = p->bin_mode; r.stop_rule = p->stop_rule;
     r.alpha_min = p->alpha_min; r.alpha_max = p->alpha_max; r.T_min = p->T_min;
     r.feat_dtype = p->feat_dtype; r.out_dtype = p->out_dtype; r.C = p->C;
+    r.select = p->select;
     for (int k = 0; k < 3; ++k) r.bg[k] = p->bg_rgb[k];
     r.N = N;
     r.n_items = N * cams.n;
@@ -324,6 +327,14 @@ fss_status fss_render_forward(const fss_params* params, const fss_camera* cams, 
                               void* workspace, int64_t pair_capacity, const float* rgb, const void* feats,
                               void* out_feat, float* out_rgb, float* out_T, int32_t* out_topk_id, void* saved,
                               fss_stream_t stream) {
+    return fss_render_forward_aux(params, cams, n_cams, N, workspace, pair_capacity, rgb, feats, out_feat, out_rgb,
+                                  out_T, out_topk_id, saved, nullptr, stream);
+}
+
+fss_status fss_render_forward_aux(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N,
+                                  void* workspace, int64_t pair_capacity, const float* rgb, const void* feats,
+                                  void* out_feat, float* out_rgb, float* out_T, int32_t* out_topk_id, void* saved,
+                                  const fss_aux_outputs* aux, fss_stream_t stream) {
     Ctx ctx;
     fss_status s = prepare(params, cams, n_cams, N, pair_capacity, workspace, ctx);
     if (s != FSS_OK) return s;
@@ -352,9 +363,16 @@ fss_status fss_render_forward(const fss_params* params, const fss_camera* cams, 
         a.saved_w = params->K > 0 ? reinterpret_cast<float*>(sv + align256(px * params->K * 4)) : nullptr;
         a.saved_nstop = reinterpret_cast<int32_t*>(sv + 2 * align256(px * params->K * 4));
     }
+    AuxOut x{nullptr, nullptr, nullptr};
+    if (aux) x = AuxOut{aux->depth, aux->depth_median, aux->normal};
     a.st = ctx.at<Status>(REG_STATUS);
     a.persistent = params->schedule == FSS_SCHED_PERSISTENT;
-    cudaError_t e = launch_render_forward(ctx.cams, ctx.P, a, num_sms_current(), reinterpret_cast<cudaStream_t>(stream));
+    if (a.persistent) {  // the queue head, so that a frame's forward may run more than once
+        cudaError_t e = cudaMemsetAsync(ctx.ws + ctx.L.off[REG_STATUS] + offsetof(Status, work), 0, sizeof(uint32_t),
+                                        reinterpret_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) return cuda_fail(e, "memset work queue");
+    }
+    cudaError_t e = launch_render_forward(ctx.cams, ctx.P, a, x, num_sms_current(), reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "render_forward");
     return FSS_OK;
 }

@@ -37,6 +37,7 @@ struct RParams {
     int32_t ts, K, bin_mode, stop_rule;
     float alpha_min, alpha_max, T_min;
     int32_t feat_dtype, out_dtype, C;
+    int32_t select;  // FSS_SELECT_TOPW | FSS_SELECT_FRONT
     float bg[3];
     int64_t N;
     int64_t n_items;

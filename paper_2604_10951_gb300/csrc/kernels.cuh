@@ -54,9 +54,26 @@ struct FwdArgs {
     int persistent;
 };
 
+// sensor outputs of the forward render, each may be NULL.  A kernel parameter
+// of its own: a larger FwdArgs costs the main Top-K instance register spills.
+struct AuxOut {
+    float* depth;      // [pix] sum w z_hit
+    float* depth_med;  // [pix] z_hit where T first drops below 1/2, else 0
+    float* normal;     // [pix, 3] sum w n, camera-space normals facing the camera
+    __host__ __device__ bool any() const { return depth || depth_med || normal; }
+};
+
 // launchers (defined in render_fwd.cu / render_bwd.cu); return a cudaError_t
-cudaError_t launch_render_forward(const Cams& cams, const RParams& P, const FwdArgs& a, int num_sms,
+cudaError_t launch_render_forward(const Cams& cams, const RParams& P, const FwdArgs& a, const AuxOut& x, int num_sms,
                                   cudaStream_t stream);
+// the full-accumulation kernel (K = 0), in render_full.cu, and the Top-K kernel
+// per feature type, in render_topk_f32.cu / render_topk_bf16.cu
+cudaError_t launch_render_full(const Cams& cams, const RParams& P, const FwdArgs& a, const AuxOut& x, int num_sms,
+                               cudaStream_t stream);
+cudaError_t launch_render_topk_f32(const Cams& cams, const RParams& P, const FwdArgs& a, const AuxOut& x, int num_sms,
+                                   cudaStream_t stream);
+cudaError_t launch_render_topk_bf16(const Cams& cams, const RParams& P, const FwdArgs& a, const AuxOut& x, int num_sms,
+                                    cudaStream_t stream);
 
 struct BwdArgs {
     const float4* rec;

@@ -4,6 +4,7 @@
 #pragma once
 
 #include "fss_internal.cuh"
+#include "kernels.cuh"
 
 #include <climits>
 
@@ -45,7 +46,22 @@ __device__ __forceinline__ bool eval_splat(const float4& A, const float4& B, con
     const float rho = fmaf(h.u, h.u, h.v * h.v);
     h.G = ex2_approx(NEG_HALF_LOG2E * rho);
     h.alpha_raw = o * h.G;
-    return (h.alpha_raw >= alpha_min) && (Cq.w * h.inv > near_plane);
+    return (h.alpha_raw >= alpha_min) && (Cq.w * h.inv > near_plane);  // hit depth det / c2
+}
+
+// Camera-space unit normal of a surfel from its render record, turned to face
+// the camera.  The third adjugate row m2 about the projected centre (xc, yc)
+// is (S K)^-T (r_u r_v R_v n) up to a positive factor, with K the intrinsics
+// and S the shift to the centre, so R_v n is along K^T S^T m2; it faces the
+// camera when its dot product with the centre's ray (xc - cx)/fx,
+// (yc - cy)/fy, 1 is not positive.
+__device__ __forceinline__ float4 facing_normal(const float4& m2, float xc, float yc, const CamDev& cam) {
+    const float nx = cam.fx * m2.x, ny = cam.fy * m2.y;
+    const float nz = fmaf(cam.cx - xc, m2.x, fmaf(cam.cy - yc, m2.y, m2.z));
+    const float dx = (xc - cam.cx) / cam.fx, dy = (yc - cam.cy) / cam.fy;
+    const float inv = rsqrtf(fmaf(nx, nx, fmaf(ny, ny, nz * nz)));
+    const float sg = fmaf(nx, dx, fmaf(ny, dy, nz)) > 0.0f ? -inv : inv;
+    return make_float4(nx * sg, ny * sg, nz * sg, 0.0f);
 }
 
 template <typename FT>
@@ -264,5 +280,30 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
                  : "memory");
 }
+
+// Launch of a render kernel over the tiles (one CTA per tile, or one resident
+// wave for the persistent schedule), recording the measurement hook after it.
+template <typename KernelT>
+inline cudaError_t launch_tiles(KernelT kern, int threads, size_t smem, const Cams& cams, const RParams& P, const FwdArgs& a,
+                               const AuxOut& x, int num_sms, cudaStream_t stream) {
+    cudaError_t e = cudaSuccess;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int grid = cams.total_tiles;
+    if (a.persistent) {
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+        if (e != cudaSuccess) return e;
+        grid = std::min(cams.total_tiles, max(1, per_sm) * num_sms);
+    }
+    if (grid <= 0) return cudaSuccess;
+    kern<<<grid, threads, smem, stream>>>(cams, P, a, x);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) kernel_mark(stream);
+    return e;
+}
+
 
 }  // namespace fss

@@ -1,0 +1,11 @@
+// Top-K forward render instances for BF16 feature rows.
+#include "render_topk.cuh"
+
+namespace fss {
+
+cudaError_t launch_render_topk_bf16(const Cams& cams, const RParams& P, const FwdArgs& a, const AuxOut& x, int num_sms,
+                                   cudaStream_t stream) {
+    return launch_topk_dtype<__nv_bfloat16>(cams, P, a, x, num_sms, stream);
+}
+
+}  // namespace fss

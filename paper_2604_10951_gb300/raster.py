@@ -16,6 +16,7 @@ from . import _lib as L
 BIN_MODES = {"aabb": L.FSS_BIN_AABB, "snug": L.FSS_BIN_SNUG, "accu": L.FSS_BIN_ACCU}
 STOP_RULES = {"tmin": L.FSS_STOP_TMIN, "exact_topk": L.FSS_STOP_EXACT_TOPK}
 SCHEDULES = {"grid": L.FSS_SCHED_GRID, "persistent": L.FSS_SCHED_PERSISTENT}
+SELECTS = {"topw": L.FSS_SELECT_TOPW, "front": L.FSS_SELECT_FRONT}
 DTYPES = {torch.float32: L.FSS_F32, torch.bfloat16: L.FSS_BF16}
 TORCH_DTYPES = {L.FSS_F32: torch.float32, L.FSS_BF16: torch.bfloat16}
 
@@ -23,7 +24,7 @@ TORCH_DTYPES = {L.FSS_F32: torch.float32, L.FSS_BF16: torch.bfloat16}
 def make_params(C: int, K: int = 8, tile_size: int = 16, bin_mode="accu", stop_rule="tmin",
                 alpha_min: float = 1.0 / 255.0, alpha_max: float = 0.99, T_min: float = 1e-4,
                 feat_dtype=torch.float32, out_dtype=None, bg=(0.0, 0.0, 0.0),
-                schedule="grid") -> L.fss_params:
+                schedule="grid", select="topw") -> L.fss_params:
     p = L.fss_default_params()
     p.tile_size, p.K, p.C = int(tile_size), int(K), int(C)
     p.bin_mode = BIN_MODES[bin_mode] if isinstance(bin_mode, str) else int(bin_mode)
@@ -35,6 +36,7 @@ def make_params(C: int, K: int = 8, tile_size: int = 16, bin_mode="accu", stop_r
     for k in range(3):
         p.bg_rgb[k] = float(bg[k])
     p.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
+    p.select = SELECTS[select] if isinstance(select, str) else int(select)
     return p
 
 
@@ -110,6 +112,14 @@ class Frame:
     def render_forward(self, rgb, feats, out_feat=None, out_rgb=None, out_T=None, out_ids=None, stream=None):
         L.fss_render_forward(*self.args(), _ptr(self.ws), self.cap, _ptr(rgb), _ptr(feats), _ptr(out_feat),
                              _ptr(out_rgb), _ptr(out_T), _ptr(out_ids), _ptr(self.saved), _stream(stream))
+
+    def render_forward_aux(self, rgb, feats, out_feat=None, out_rgb=None, out_T=None, out_ids=None, depth=None,
+                           depth_median=None, normal=None, stream=None):
+        """render_forward plus the sensor outputs (expected depth [pix], median depth [pix],
+        facing normal [pix, 3]; float32 tensors or None)."""
+        L.fss_render_forward_aux(*self.args(), _ptr(self.ws), self.cap, _ptr(rgb), _ptr(feats), _ptr(out_feat),
+                                 _ptr(out_rgb), _ptr(out_T), _ptr(out_ids), _ptr(self.saved), _ptr(depth),
+                                 _ptr(depth_median), _ptr(normal), _stream(stream))
 
     def render_backward(self, means, scales, quats, opac, rgb, feats, out_T, d_feat, d_rgb, d_T, g_means, g_scales,
                         g_quats, g_opac, g_rgb, g_feat, stream=None):

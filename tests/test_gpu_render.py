@@ -137,3 +137,15 @@ def test_counters_match_oracle_contributions():
     ref, _ = _oracle(sc, cam, 0)
     ctr = run.counters()
     assert abs(int(ctr[1]) - int(ref["counters"][1])) <= 0.001 * int(ref["counters"][1])
+
+
+@pytest.mark.parametrize("K,stop", [(1, "tmin"), (4, "tmin"), (4, "exact_topk"), (12, "exact_topk")])
+def test_front_k_selection(K, stop):
+    """The first K contributors in depth order (the other reading of Eq. 7)."""
+    sc, cam = scenes.tiny_scene(seed=4)
+    run = GpuRun(sc, [cam], K=K, stop_rule=stop, select="front")
+    p = O.make_params(K=K, stop_rule=O.EXACT_TOPK if stop == "exact_topk" else O.TMIN, select=1)
+    b = O.binning(sc, cam, p)
+    ref = O.render(sc, cam, p, binned=b)
+    S = tol_scale(O, sc, cam, p, b)
+    _compare(run.view(0), ref, S, 1e-4, K)
