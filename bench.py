@@ -297,6 +297,7 @@ def run_ours(args):
                       "global_batch": D.world, "seq_len": npx, "parallelism": f"views sharded x{D.world}",
                       "l2": "flushed between timed steps (512 MB write)"},
            "gpu_launches": launches_per_step * args.steps,
+           "step_ms": {q: round(float(np.percentile(step_ms, v)), 4) for q, v in (("p10", 10), ("p50", 50), ("p90", 90))},
            "calls_ms": {k: round(v, 4) for k, v in calls.items()},
            "pairs_per_frame_max": ours.max_pairs}
     clocks = clk.summary()
@@ -313,7 +314,8 @@ def run_ours(args):
         if calls:
             fwd_ms = calls["project_bin"] + calls["sort"] + calls["render_forward"]
             out["forward_only"] = {"ms": round(fwd_ms, 4), "frames_per_s": round(1e3 / fwd_ms, 2)}
-            out["roofline"], out["roofline_kernels"], out["kernel_us"] = roofline(ours, torch, L, flush)
+            out["roofline"], out["roofline_kernels"], out["kernel_us"], out["roofline_frame"] = \
+                roofline(ours, torch, L, flush)
         out["e2e"] = e2e(ours, torch, dev, ptr, L, args)
         del base
         out["ablation_fwd"] = ablation(torch, L, dev, means, scales, quats, opac, rgb, feats[torch.float32], poses,
@@ -331,6 +333,9 @@ KERNELS = ["k_project", "k_scan", "k_emit", "k_tile_sort", "k_render_topk", "k_l
 # ncu capture summarised in profiles/<kernel>_room500k_640x480_c64_k8.md; to be set
 # to None whenever the kernel changes after that capture
 NCU_TRAFFIC = {"k_render_topk": 27166208, "k_bwd_feat": 70297600, "k_bwd_geo": 37996032}
+# (smsp__inst_executed.sum, gpu__time_duration.sum in us) of the same captures
+NCU_ISSUE = {"k_render_topk": (84202380, 108.288), "k_bwd_feat": (110324067, 126.496),
+             "k_bwd_geo": (88788804, 130.208)}
 
 
 def kernel_times(path, torch, L, flush, rounds=4):
@@ -366,6 +371,7 @@ def kernel_times(path, torch, L, flush, rounds=4):
             n += 1
             if r == 0:  # the pose's algorithmic bytes, averaged over the 16 poses
                 b, z = algorithmic_bytes(path, torch, L)
+                b.update(z.pop("rest"))
                 for k in b:
                     nbytes[k] = nbytes.get(k, 0.0) + b[k] / len(graphs)
                 for k in z:
@@ -381,7 +387,11 @@ def algorithmic_bytes(path, torch, L):
     ranges = fr.region(L.REG_RANGES).view(torch.int32).view(-1, 2).cpu().numpy()
     P = int((ranges[:, 1] - ranges[:, 0]).sum())
     tiles = ranges.shape[0]
-    nslot = int(fr.region(L.REG_STATUS).view(torch.int32)[22].item())
+    st = fr.region(L.REG_STATUS).view(torch.int32)[:28].cpu().numpy()
+    cnt = fr.region(L.REG_STATUS).view(torch.int64)[2:10].cpu().numpy()
+    nslot = int(st[22])
+    nvis = int(st[20]) + int(st[25])  # bounded visible items (narrow + wide)
+    n_eval, n_contrib = int(cnt[0]), int(cnt[1])
     H, W, ts = fr.sizes[0][0], fr.sizes[0][1], 16
     ids = path.ids.cpu().numpy().reshape(H, W, -1)
     U = 0
@@ -390,6 +400,22 @@ def algorithmic_bytes(path, torch, L):
             blk = ids[ty:ty + ts, tx:tx + ts].reshape(-1)
             U += np.unique(blk[blk >= 0]).size
     s, K, Cc, npx = 2, K_TOP, C_FEAT, H * W
+    N = N_SPLATS
+    # the other kernels of the step, for the per-frame total
+    rest = {
+        "k_project": N * 16 + nvis * (24 + 64 + 80 + 8),  # centres and opacities of all, the rest of the visible
+        "k_scan": tiles * 12,
+        "k_emit": nvis * (80 + 64 + 4) + P * 4,
+        "k_tile_sort": P * (4 + 4 + 64 + 4 + 4),
+        "k_loss": npx * (2 * Cc * s + 24) + npx * (Cc * s + 12),
+        "k_bwd_clear": nslot * (64 + 4 * Cc),
+        "k_bwd_project": N * 52 + nslot * (64 + 48 + 40),
+        "k_feat_out": N * Cc * s + nslot * 4 * Cc,
+    }
+    # FP32 operations of the forward: ~20 per evaluation (ray-splat solve,
+    # density, opacity, depth test) + ~10 per contribution (compositing, K-set
+    # test) + 2 C per selected row (feature accumulation); two MUFU ops per evaluation
+    flops_fwd = 20 * n_eval + 10 * n_contrib + 2 * Cc * min(K, 8) * npx
     return {
         # ranges; per pair: list id, warp mask, adjugate rows, opacity, colour;
         # selected rows once per tile; per pixel: features, rgb, T, ids, saved pos/w, nstop
@@ -401,7 +427,8 @@ def algorithmic_bytes(path, torch, L):
         # per pixel: nstop, T, dL/drgb, saved pos, dots; per pair: list id, mask, record
         # rows, colour; the per-(view, slot) gradient rows written once
         "k_bwd_geo": tiles * 8 + npx * (4 + 4 + 12 + 8 * K) + P * (4 + 4 + 64 + 12) + nslot * 64,
-    }, {"pairs": P, "unique_rows": U, "slots": nslot}
+    }, {"pairs": P, "unique_rows": U, "slots": nslot, "evaluations": n_eval, "contributions": n_contrib,
+        "flops_fwd": flops_fwd, "rest": rest}
 
 
 def roofline(path, torch, L, flush):
@@ -413,14 +440,32 @@ def roofline(path, torch, L, flush):
     kt, nbytes, sizes = kernel_times(path, torch, L, flush)
     rows = {}
     for k, b in nbytes.items():
+        if k not in ("k_render_topk", "k_bwd_feat", "k_bwd_geo"):
+            continue
         ach = b / (kt[k] * 1e-3) / 1e9
         rows[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
                    "traffic": NCU_TRAFFIC.get(k), "algorithmic_bytes": int(b), "ms": round(kt[k], 5)}
+    # the forward's arithmetic against the FP32 peak: 152 SMs x 128 lanes x 2 flops x 2.07 GHz
+    fp32_peak = 152 * 128 * 2 * 2.07e9
+    rows["k_render_topk"]["alu"] = {"flops": int(sizes["flops_fwd"]),
+                                    "achieved_tflops": round(sizes["flops_fwd"] / (kt["k_render_topk"] * 1e-3) / 1e12, 2),
+                                    "peak_tflops": round(fp32_peak / 1e12, 1),
+                                    "frac": round(sizes["flops_fwd"] / (kt["k_render_topk"] * 1e-3) / fp32_peak, 4)}
+    # warp-instruction issue of the ncu captures against 152 SMs x 4 schedulers x 2.07 GHz
+    for k, v in NCU_ISSUE.items():
+        if k in rows and v is not None:
+            rows[k]["issue_frac_ncu"] = round(v[0] / (v[1] * 1e-6) / (152 * 4 * 2.07e9), 3)
     dom = max(kt, key=kt.get)
     main = dict(rows.get(dom, {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
                                "traffic": None}), kernel=dom, peak_source=f"{src} (MEASURED_PEAKS.json hbm_gbs)")
-    main.update(sizes)
-    return main, rows, {k: round(v * 1e3, 2) for k, v in kt.items()}
+    main.update({k: v for k, v in sizes.items() if k != "flops_fwd"})
+    # per frame: all kernels' algorithmic bytes over the summed kernel times
+    tot_b = sum(nbytes.get(k, 0.0) for k in KERNELS)
+    tot_t = sum(kt.values()) * 1e-3
+    frame = {"algorithmic_bytes": int(tot_b), "kernel_ms": round(tot_t * 1e3, 4),
+             "achieved": round(tot_b / tot_t / 1e9, 1), "peak": peak, "unit": "GB/s",
+             "frac": round(tot_b / tot_t / 1e9 / peak, 4)}
+    return main, rows, {k: round(v * 1e3, 2) for k, v in kt.items()}, frame
 
 
 def ablation(torch, L, dev, means, scales, quats, opac, rgb, feats, poses, flush, reps=3):
