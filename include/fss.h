@@ -90,12 +90,16 @@ typedef struct {
     int32_t select;     /* K > 0: FSS_SELECT_TOPW, the K largest blending weights
                            (Eq. 7); FSS_SELECT_FRONT, the first K contributors
                            in depth order (the other reading of the selection set) */
+    int32_t renorm;     /* K > 0: 0 = Eq. 7 as printed (no normalisation); 1 = divide
+                           the Top-K feature sum by the selected weights' sum, so the
+                           selected surfels' weights add up to 1 (a variant; K = 0
+                           rejects it) */
 } fss_params;
 
 enum { FSS_SCHED_GRID = 0, FSS_SCHED_PERSISTENT = 1 };
 enum { FSS_SELECT_TOPW = 0, FSS_SELECT_FRONT = 1 };
 
-/* Fills the defaults listed above (tile 16, K 8, ACCU, TMIN, F32, C 16, grid, TOPW). */
+/* Fills the defaults listed above (tile 16, K 8, ACCU, TMIN, F32, C 16, grid, TOPW, no renormalisation). */
 fss_status fss_default_params(fss_params *params);
 
 /* Bytes of device workspace needed for these cameras, N surfels and at most
@@ -141,7 +145,8 @@ fss_status fss_sort(const fss_params *params, const fss_camera *cams, int32_t n_
  * alpha < alpha_min, stop by params->stop_rule, w = alpha T, T *= 1 - alpha.
  * K = 0: F = sum_i w_i c_i over all contributors.  K > 0: F = sum over the K
  * largest w_i (ties: earlier wins; FSS_SELECT_FRONT: over the first K
- * contributors), no renormalisation.  FSS_STOP_EXACT_TOPK stops once no
+ * contributors), no renormalisation unless params->renorm (then divided by
+ * the sum of the selected w_i; saved weights stay unnormalised).  FSS_STOP_EXACT_TOPK stops once no
  * later surfel can enter the set (TOPW: alpha_max T <= smallest selected
  * weight; FRONT: K contributors found).
  * Device inputs: rgb [N,3] f32, feats [N,C] (feat_dtype).

@@ -48,7 +48,11 @@
  *     EXACT_TOPK additionally stops once the K-set is full and no later
  *     surfel can enter it (alpha_max * T <= smallest selected weight); with
  *     the first-K selection (select = 1, the other reading of Eq. 7) it
- *     stops once K surfels contributed.
+ *     stops once K surfels contributed;
+ *   - Eq. 7 sums the selected w_i c_i without normalising; the variant
+ *     renorm = 1 divides that sum by the selected weights' sum W_K (the
+ *     selected surfels' share of the pixel becomes 1), which the paper does
+ *     not use and the GPU path offers as an option.
  */
 #include <math.h>
 #include <stdint.h>
@@ -77,6 +81,7 @@ typedef struct {
     float bg[3];
     int32_t C;
     int32_t select;    /* 0: K largest weights (Eq. 7); 1: first K in depth order */
+    int32_t renorm;    /* K > 0: 1 divides the Top-K sum by the selected weights' sum */
 } orc_params;
 
 enum { ORC_AABB = 0, ORC_SNUG = 1, ORC_ACCU = 2 };
@@ -937,11 +942,15 @@ void orc_render(int64_t N, const double *means, const double *scales, const doub
                         for (int ch = 0; ch < C; ++ch) f[ch] += cb[i].w * c[ch];
                     }
                 } else {
+                    double Wk = 0.0;
                     for (int a = 0; a < o.nsel; ++a) {
                         const contrib_t *e = &cb[o.sel[a]];
                         const double *c = feats + (int64_t)e->id * C;
                         for (int ch = 0; ch < C; ++ch) f[ch] += e->w * c[ch];
+                        Wk += e->w;
                     }
+                    if (p->renorm && o.nsel > 0)
+                        for (int ch = 0; ch < C; ++ch) f[ch] /= Wk;
                 }
             }
             if (K > 0) {
@@ -1038,6 +1047,23 @@ void orc_render_backward(int64_t N, const double *means, const double *scales, c
             const int n = o.n_contrib;
             memset(insel, K == 0 ? 1 : 0, (size_t)(n > 0 ? n : 1));
             if (K > 0) for (int a = 0; a < o.nsel; ++a) insel[o.sel[a]] = 1;
+            /* renormalised Top-K, F = sum_K w c / W: dL/dw_i = (c_i.gF - Fg) / W
+             * with Fg = F.gF, and dL/dc_i = (w_i / W) gF */
+            double Wk = 1.0, Fg = 0.0, Fga = 0.0;
+            const int renorm = K > 0 && p->renorm && o.nsel > 0 && gf;
+            if (renorm) {
+                Wk = 0.0;
+                for (int a = 0; a < o.nsel; ++a) Wk += cb[o.sel[a]].w;
+                for (int a = 0; a < o.nsel; ++a) {
+                    const contrib_t *e = &cb[o.sel[a]];
+                    const double *c = feats + (int64_t)e->id * C;
+                    double d = 0.0, da = 0.0;
+                    for (int ch = 0; ch < C; ++ch) d += c[ch] * gf[ch];
+                    for (int ch = 0; ch < C; ++ch) da += fabs(c[ch] * gf[ch]);
+                    Fg += e->w / Wk * d;
+                    Fga += e->w / Wk * da;
+                }
+            }
             /* s_i: what each blending weight multiplies */
             for (int i = 0; i < n; ++i) {
                 const int id = cb[i].id;
@@ -1046,14 +1072,17 @@ void orc_render_backward(int64_t N, const double *means, const double *scales, c
                 for (int k = 0; k < 3; ++k) va += fabs(rgb[3 * id + k] * gc[k]);
                 if (insel[i] && gf) {
                     const double *c = feats + (int64_t)id * C;
-                    for (int ch = 0; ch < C; ++ch) v += c[ch] * gf[ch];
-                    for (int ch = 0; ch < C; ++ch) va += fabs(c[ch] * gf[ch]);
+                    double d = 0.0, da = 0.0;
+                    for (int ch = 0; ch < C; ++ch) d += c[ch] * gf[ch];
+                    for (int ch = 0; ch < C; ++ch) da += fabs(c[ch] * gf[ch]);
+                    v += renorm ? (d - Fg) / Wk : d;
+                    va += renorm ? (da + Fga) / Wk : da;
                 }
                 s[i] = v;
                 sa[i] = va;
                 for (int k = 0; k < 3; ++k) g_rgb[3 * id + k] += cb[i].w * gc[k];
                 if (insel[i] && gf)
-                    for (int ch = 0; ch < C; ++ch) g_feat[(int64_t)id * C + ch] += cb[i].w * gf[ch];
+                    for (int ch = 0; ch < C; ++ch) g_feat[(int64_t)id * C + ch] += cb[i].w / Wk * gf[ch];
             }
             /* dL/dalpha_j = T_j s_j - (sum_{i>j} w_i s_i + T_final (bg.grgb + gT)) / (1 - alpha_j) */
             double tail = o.T * (p->bg[0] * gc[0] + p->bg[1] * gc[1] + p->bg[2] * gc[2] + gt);

@@ -60,6 +60,8 @@ fss_status check_params(const fss_params* p) {
         return fail(FSS_ERR_INVALID_ARG, "schedule %d", p->schedule);
     if (p->select != FSS_SELECT_TOPW && p->select != FSS_SELECT_FRONT)
         return fail(FSS_ERR_INVALID_ARG, "select %d", p->select);
+    if (p->renorm != 0 && p->renorm != 1) return fail(FSS_ERR_INVALID_ARG, "renorm %d", p->renorm);
+    if (p->renorm && p->K == 0) return fail(FSS_ERR_INVALID_ARG, "renorm needs K > 0");
     return FSS_OK;
 }
 
@@ -102,6 +104,7 @@ RParams make_rparams(const fss_params* p, const Cams& cams, int64_t N, int64_t c
     r.alpha_min = p->alpha_min; r.alpha_max = p->alpha_max; r.T_min = p->T_min;
     r.feat_dtype = p->feat_dtype; r.out_dtype = p->out_dtype; r.C = p->C;
     r.select = p->select;
+    r.renorm = p->renorm;
     for (int k = 0; k < 3; ++k) r.bg[k] = p->bg_rgb[k];
     r.N = N;
     r.n_items = N * cams.n;

@@ -38,6 +38,7 @@ struct RParams {
     float alpha_min, alpha_max, T_min;
     int32_t feat_dtype, out_dtype, C;
     int32_t select;  // FSS_SELECT_TOPW | FSS_SELECT_FRONT
+    int32_t renorm;  // Top-K features divided by the selected weights' sum
     float bg[3];
     int64_t N;
     int64_t n_items;

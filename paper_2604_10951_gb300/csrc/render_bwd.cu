@@ -160,6 +160,11 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                         const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
                         epos[i] = a.saved_pos[pix * K + k];
                         ew[i] = a.saved_w[pix * K + k];
+                        if (P.renorm) {  // dL/dc = (w / W) dL/dF, W the selected weights' sum
+                            float ws = 0.0f;
+                            for (int k2 = 0; k2 < K; ++k2) ws += a.saved_w[pix * K + k2];
+                            ew[i] = ws > 0.0f ? ew[i] / ws : 0.0f;
+                        }
                         lmax = max(lmax, epos[i] + 1);
                     }
                 }
@@ -385,6 +390,9 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
     float T = 1.0f, gr = 0.0f, gg = 0.0f, gb = 0.0f, Sh = 0.0f;
     int kk = -1, next_pos = -1;
     float next_dot = 0.0f;
+    // a selected surfel adds rn_a * dot + rn_b to what its weight multiplies:
+    // the dot itself, or (dot - F.dL/dF) / W for the renormalised variant
+    float rn_a = 1.0f, rn_b = 0.0f;
     float dfr[FULL ? CMAX : 1];
 #pragma unroll
     for (int c = 0; c < (FULL ? CMAX : 1); ++c) dfr[c] = 0.0f;
@@ -401,6 +409,16 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
             if (kk >= 0) {
                 next_pos = a.saved_pos[pix * K + kk];
                 next_dot = a.dots[pix * K + kk];
+            }
+            if (P.renorm) {  // entries 0..kk are the selected ones, front to back
+                float ws = 0.0f, wd = 0.0f;
+                for (int k2 = 0; k2 <= kk; ++k2) {
+                    const float wv = a.saved_w[pix * K + k2];
+                    ws += wv;
+                    wd = fmaf(wv, a.dots[pix * K + k2], wd);
+                }
+                rn_a = ws > 0.0f ? 1.0f / ws : 0.0f;
+                rn_b = -wd * rn_a * rn_a;
             }
         } else {
             const FT* dF = reinterpret_cast<const FT*>(a.d_feat) + pix * C;
@@ -462,7 +480,7 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
                 float s = oc.y * gr + oc.z * gg + oc.w * gb;
                 if (!FULL) {
                     if (pos == next_pos) {
-                        s += next_dot;
+                        s += fmaf(next_dot, rn_a, rn_b);
                         --kk;
                         next_pos = kk >= 0 ? a.saved_pos[pix * K + kk] : -1;
                         next_dot = kk >= 0 ? a.dots[pix * K + kk] : 0.0f;

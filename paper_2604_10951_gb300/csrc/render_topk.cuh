@@ -241,11 +241,18 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : 1) k_r
                 if (tid >= p0 && tid < p0 + PC) {
                     const int q = tid - p0;
                     s_n[q] = inside ? hc : 0;
+                    float wsc = 1.0f;  // renormalised variant: 1 / (sum of the selected weights)
+                    if (P.renorm) {
+                        float ws = 0.0f;
+#pragma unroll
+                        for (int k = 0; k < KCAP; ++k) ws += hp[k] >= 0 ? hw[k] : 0.0f;
+                        wsc = ws > 0.0f ? __frcp_rn(ws) : 0.0f;
+                    }
 #pragma unroll
                     for (int k = 0; k < KCAP; ++k) {
                         if (hp[k] >= 0) {
                             s_id[q * KCAP + rank[k]] = hid[k];
-                            s_w[q * KCAP + rank[k]] = hw[k];
+                            s_w[q * KCAP + rank[k]] = hw[k] * wsc;
                         }
                     }
                 }

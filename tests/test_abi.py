@@ -83,7 +83,8 @@ def test_default_params_and_sizes(lib):
     ("tile_size", 12, L.FSS_ERR_UNSUPPORTED), ("K", 33, L.FSS_ERR_UNSUPPORTED),
     ("C", 6, L.FSS_ERR_UNSUPPORTED), ("alpha_min", 0.0, L.FSS_ERR_INVALID_ARG),
     ("alpha_max", 1.0, L.FSS_ERR_INVALID_ARG), ("schedule", 5, L.FSS_ERR_INVALID_ARG),
-    ("bin_mode", 7, L.FSS_ERR_INVALID_ARG)])
+    ("bin_mode", 7, L.FSS_ERR_INVALID_ARG), ("select", 2, L.FSS_ERR_INVALID_ARG),
+    ("renorm", 2, L.FSS_ERR_INVALID_ARG)])
 def test_invalid_params_are_rejected_before_any_launch(lib, field, value, status):
     p = L.fss_default_params()
     setattr(p, field, value)
@@ -92,6 +93,16 @@ def test_invalid_params_are_rejected_before_any_launch(lib, field, value, status
     assert L.last_error()
     # compute calls validate the same way and return before touching a device
     assert lib.fss_project_bin(C.byref(p), _cam(), 1, 10, None, None, None, None, None, 10, None) == status
+
+
+def test_renormalisation_needs_top_k(lib):
+    p = L.fss_default_params()
+    p.K, p.renorm = 0, 1
+    out = C.c_size_t()
+    assert lib.fss_workspace_size(C.byref(p), _cam(), 1, 10, 10, C.byref(out)) == L.FSS_ERR_INVALID_ARG
+    assert "renorm" in L.last_error()
+    p.K = 4
+    assert lib.fss_workspace_size(C.byref(p), _cam(), 1, 10, 10, C.byref(out)) == L.FSS_OK
 
 
 def test_bad_camera_and_sizes_are_rejected(lib):

@@ -161,3 +161,16 @@ def test_backward_front_k_selection():
     g_ref = O.render_backward(sc, cam, p, gF, grgb, gT, binned=b)
     g = _gpu_backward(run, gF, grgb, gT)
     _assert_close(g, g_ref)
+
+
+@pytest.mark.parametrize("select", ["topw", "front"])
+def test_backward_renormalised_topk(select):
+    sc, cam = scenes.tiny_scene(seed=6, n=1500)
+    run = GpuRun(sc, [cam], K=4, select=select, renorm=True)
+    p = O.make_params(K=4, select=1 if select == "front" else 0, renorm=1)
+    b = O.binning(sc, cam, p)
+    ref = O.render(sc, cam, p, binned=b)
+    gF, grgb, gT = _upstream(ref, sc.C, seed=6)
+    g_ref = O.render_backward(sc, cam, p, gF, grgb, gT, binned=b)
+    g = _gpu_backward(run, gF, grgb, gT)
+    _assert_close(g, g_ref)

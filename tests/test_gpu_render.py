@@ -149,3 +149,22 @@ def test_front_k_selection(K, stop):
     ref = O.render(sc, cam, p, binned=b)
     S = tol_scale(O, sc, cam, p, b)
     _compare(run.view(0), ref, S, 1e-4, K)
+
+
+@pytest.mark.parametrize("K,select,feat_dtype", [(4, "topw", torch.float32), (8, "topw", torch.bfloat16),
+                                                 (4, "front", torch.float32)])
+def test_renormalised_topk(K, select, feat_dtype):
+    """The Top-K feature sum divided by the selected weights' sum (a variant of
+    Eq. 7); colour, transmittance and ids are those of the plain Top-K call."""
+    sc, cam = scenes.tiny_scene(seed=9, C=32)
+    run = GpuRun(sc, [cam], K=K, select=select, renorm=True, feat_dtype=feat_dtype)
+    feats = torch.as_tensor(sc.feats).to(feat_dtype).double().numpy()
+    p = O.make_params(K=K, select=1 if select == "front" else 0, renorm=1)
+    b = O.binning(sc, cam, p)
+    ref = O.render(sc, cam, p, feats=feats, binned=b)
+    S = tol_scale(O, _with_feats(sc, feats), cam, p, b)
+    _compare(run.view(0), ref, S, 1e-4 if feat_dtype == torch.float32 else 2e-2, K)
+    plain = GpuRun(sc, [cam], K=K, select=select, feat_dtype=feat_dtype).view(0)
+    g = run.view(0)
+    for k in ("rgb", "T", "ids", "w"):
+        np.testing.assert_array_equal(g[k], plain[k])

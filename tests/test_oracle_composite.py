@@ -184,3 +184,35 @@ def test_front_k_exact_stop_keeps_features_and_stops_after_k_contributors():
     # the traversal ends at the third contributor: exactly min(3, n) of them
     np.testing.assert_array_equal(b["ncontrib"], np.minimum(a["ncontrib"], 3))
     assert b["counters"][0] < a["counters"][0]
+
+
+def test_renormalised_topk_constant_and_one_hot_features():
+    # the renormalised variant divides the Top-K sum by the selected weights'
+    # sum: constant features give exactly 1 wherever a surfel is selected, and
+    # one-hot features give the selected weights over their sum
+    sc, cam = scenes.tiny_scene(seed=14, n=120)
+    n = sc.n
+    one = make_scene(sc.means, sc.scales, sc.quats, sc.opacities, sc.rgb, np.ones((n, 3), np.float32))
+    hot = make_scene(sc.means, sc.scales, sc.quats, sc.opacities, sc.rgb, np.eye(n, dtype=np.float32))
+    for K, sel in ((1, 0), (4, 0), (4, 1)):
+        c = O.render(one, cam, O.make_params(K=K, select=sel, renorm=1))
+        has = c["ids"][..., 0] >= 0
+        assert has.mean() > 0.3
+        np.testing.assert_allclose(c["F"][has], 1.0, atol=1e-14)
+        assert (c["F"][~has] == 0).all()
+        h = O.render(hot, cam, O.make_params(K=K, select=sel, renorm=1))
+        plain = O.render(hot, cam, O.make_params(K=K, select=sel))
+        Wk = plain["w"].sum(-1)
+        np.testing.assert_allclose(h["F"][has], plain["F"][has] / Wk[has, None], atol=1e-14)
+        np.testing.assert_array_equal(h["ids"], plain["ids"])
+
+
+def test_renormalised_topk_with_large_K_is_the_full_blend_over_its_coverage():
+    # K >= every pixel's contributor count: W_K = 1 - T, so the renormalised
+    # features are the full blend divided by the covered fraction
+    sc, cam = scenes.tiny_scene(seed=6, n=800)
+    full = O.render(sc, cam, O.make_params(K=0))
+    rn = O.render(sc, cam, O.make_params(K=32, renorm=1))
+    ok = (full["ncontrib"] <= 32) & (full["T"] < 1.0)
+    assert ok.mean() > 0.5
+    np.testing.assert_allclose(rn["F"][ok], full["F"][ok] / (1.0 - full["T"][ok, None]), rtol=1e-11, atol=1e-12)

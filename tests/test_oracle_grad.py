@@ -31,10 +31,10 @@ def _loss(s64, cam, p, gF, grgb, gT):
     return L, struct
 
 
-@pytest.mark.parametrize("K", [0, 4])
-def test_analytic_gradients_match_central_differences(K):
+@pytest.mark.parametrize("K,renorm", [(0, 0), (4, 0), (4, 1)])
+def test_analytic_gradients_match_central_differences(K, renorm):
     sc, cam = scenes.fd_subscene(seed=5)
-    p = O.make_params(K=K, alpha_min=1e-8, T_min=0.0, bg=(0.2, 0.3, 0.1))
+    p = O.make_params(K=K, alpha_min=1e-8, T_min=0.0, bg=(0.2, 0.3, 0.1), renorm=renorm)
     rng = np.random.default_rng(1)
     H, W, Cc = cam.height, cam.width, sc.C
     gF = rng.normal(size=(H, W, Cc)); grgb = rng.normal(size=(H, W, 3)); gT = rng.normal(size=(H, W))
