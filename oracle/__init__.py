@@ -84,6 +84,8 @@ def _load():
             lib.orc_ray_splat.restype = None
             lib.orc_check_conservative.argtypes = [i64, P, P, P, P, C.POINTER(OrcCam), C.POINTER(OrcParams), C.c_int, P]
             lib.orc_check_conservative.restype = i64
+            lib.orc_query_labels.argtypes = [i64, C.c_int32, C.c_int32, P, P, P, P, P, P]
+            lib.orc_query_labels.restype = None
             lib.orc_num_threads.argtypes = []
             lib.orc_num_threads.restype = C.c_int
             _lib = lib
@@ -284,6 +286,20 @@ def render_backward(scene, cam, params, gF, grgb, gT=None, feats=None, binned=No
                             _ptr(g["means"]), _ptr(g["scales"]), _ptr(g["quats"]), _ptr(g["opac"]),
                             _ptr(g["rgb"]), _ptr(g["feat"]), _ptr(g["Tmat"]), _ptr(g["abs"]))
     return g
+
+
+def query_labels(f_ins, means, f_q, p_q, prec):
+    """Instance label distributions l_ins [N, nq] of Sec. 3.3 in FP64:
+    softmax over queries of sigmoid(f_q . f_ins) exp(-1/2 d^T prec d),
+    d = p_g - p_q, prec [nq, 6] = (xx, yy, zz, xy, xz, yz) of Sigma_q^-1."""
+    lib = _load()
+    f_ins, means, f_q, p_q, prec = (_f64(a) for a in (f_ins, means, f_q, p_q, prec))
+    N, dim = f_ins.shape
+    nq = f_q.shape[0]
+    assert f_q.shape[1] == dim and means.shape == (N, 3) and p_q.shape == (nq, 3) and prec.shape == (nq, 6)
+    out = np.zeros((N, nq))
+    lib.orc_query_labels(N, nq, dim, _ptr(f_ins), _ptr(means), _ptr(f_q), _ptr(p_q), _ptr(prec), _ptr(out))
+    return out
 
 
 def check_conservative(scene, cam, params, mode=None):

@@ -1296,6 +1296,52 @@ int64_t orc_check_conservative(int64_t N, const float *means, const float *scale
     return bad;
 }
 
+/* ================================================================== */
+/* 6. query-guided instance labels (Sec. 3.3)                           */
+/* ================================================================== */
+
+/*
+ * Instance label distribution of every scene Gaussian g over the nq
+ * instance queries, following the paper's steps in order:
+ *   S(q, g) = sigmoid(f_q . f_ins(g))                 (feature similarity)
+ *   D(q, g) = phi_q(p_g) / phi_q(p_q)                 (spatial proximity)
+ *           = exp(-1/2 (p_g - p_q)^T Sigma_q^-1 (p_g - p_q)),
+ *     phi_q the density of the query's Gaussian N(p_q, Sigma_q); the
+ *     normalising constant cancels in the ratio;
+ *   A(q, g) = S(q, g) D(q, g)                         (attention)
+ *   l_ins(g) = softmax over q of A(q, g).
+ * Scene Gaussians enter as points (their centres), as the paper states.
+ * Inputs: f_ins [N, dim], means [N, 3], f_q [nq, dim], p_q [nq, 3],
+ * prec [nq, 6] = Sigma_q^-1 entries (xx, yy, zz, xy, xz, yz).
+ * Output: labels [N, nq].
+ */
+void orc_query_labels(int64_t N, int32_t nq, int32_t dim, const double *f_ins, const double *means,
+                      const double *f_q, const double *p_q, const double *prec, double *labels)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t g = 0; g < N; ++g) {
+        double *l = labels + g * nq;
+        double sum = 0.0;
+        for (int q = 0; q < nq; ++q) {
+            double dot = 0.0;
+            for (int k = 0; k < dim; ++k) dot += f_q[(int64_t)q * dim + k] * f_ins[g * dim + k];
+            const double S = 1.0 / (1.0 + exp(-dot));
+            const double d[3] = {means[3 * g] - p_q[3 * q], means[3 * g + 1] - p_q[3 * q + 1],
+                                 means[3 * g + 2] - p_q[3 * q + 2]};
+            const double *P = prec + 6 * (int64_t)q;
+            const double Pm[3][3] = {{P[0], P[3], P[4]}, {P[3], P[1], P[5]}, {P[4], P[5], P[2]}};
+            double quad = 0.0;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) quad += d[a] * Pm[a][b] * d[b];
+            const double D = exp(-0.5 * quad);
+            const double A = S * D;
+            l[q] = exp(A);
+            sum += l[q];
+        }
+        for (int q = 0; q < nq; ++q) l[q] /= sum;
+    }
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

@@ -252,6 +252,36 @@ def room_scene(n: int = 500_000, C: int = 64, seed: int = 1, n_blobs: int = 40,
     return Scene(means[perm], log_scales[perm], quats[perm], logits[perm], rgb[perm], feats[perm])
 
 
+def room_queries(means: np.ndarray, n_queries: int = 32, dim: int = 32, seed: int = 0):
+    """Inputs of the query-guided instance labels (Sec. 3.3) for Gaussians at
+    ``means``: ``n_queries`` instance queries with centres uniform in the
+    room (0.5 m from the walls), Gaussian extents with per-axis standard
+    deviations U[0.4, 1.2] m under a uniform random rotation (given as the
+    precision matrix entries xx, yy, zz, xy, xz, yz), and ``dim``-d query
+    features 3 c_q with c_q ~ N(0, 1/dim); each scene Gaussian takes the
+    nearest query centre as its instance, and its instance feature is that
+    query's feature plus N(0, 0.3^2 / dim) noise.  Returns float32 arrays
+    (f_ins [N, dim], f_q [nq, dim], p_q [nq, 3], prec [nq, 6])."""
+    rng = np.random.default_rng(seed)
+    p_q = rng.uniform(-ROOM_HALF + 0.5, ROOM_HALF - 0.5, (n_queries, 3))
+    sig = rng.uniform(0.4, 1.2, (n_queries, 3))
+    q = _random_unit_quats(rng, n_queries)
+    w, x, y, z = q.T
+    R = np.stack([np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
+                  np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
+                  np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], 1)
+    Pm = np.einsum("qab,qb,qcb->qac", R, 1.0 / sig ** 2, R)
+    prec = np.stack([Pm[:, 0, 0], Pm[:, 1, 1], Pm[:, 2, 2], Pm[:, 0, 1], Pm[:, 0, 2], Pm[:, 1, 2]], -1)
+    f_q = 3.0 * rng.normal(0.0, 1.0 / math.sqrt(dim), (n_queries, dim))
+    m = np.asarray(means, np.float64)
+    inst = np.empty(m.shape[0], np.int64)
+    for a in range(0, m.shape[0], 65536):
+        d2 = ((m[a:a + 65536, None, :] - p_q[None]) ** 2).sum(-1)
+        inst[a:a + 65536] = d2.argmin(1)
+    f_ins = f_q[inst] + rng.normal(0.0, 0.3 / math.sqrt(dim), (m.shape[0], dim))
+    return (f_ins.astype(np.float32), f_q.astype(np.float32), p_q.astype(np.float32), prec.astype(np.float32))
+
+
 def circle_poses(n_poses: int = 16, width: int = 640, height: int = 480, f: float = 525.0,
                  radius: float = CAM_CIRCLE_R, yaw_offset_deg: float = 30.0,
                  pitch_deg: float = 10.0) -> List[Camera]:
