@@ -177,6 +177,10 @@ typedef struct {
     float *depth;
     float *depth_median;
     float *normal;
+    int32_t *label;     /* [pix] argmax over the C channels of the rendered features
+                           (lowest channel on ties; -1 where no surfel is blended):
+                           the instance mask when the features are the query labels
+                           of fss_query_labels; needs no out_feat */
 } fss_aux_outputs;
 
 /* fss_render_forward plus the sensor outputs in `aux` (may be NULL); the
@@ -186,6 +190,32 @@ fss_status fss_render_forward_aux(const fss_params *params, const fss_camera *ca
                                   void *workspace, int64_t pair_capacity, const float *rgb, const void *feats,
                                   void *out_feat, float *out_rgb, float *out_T, int32_t *out_topk_id,
                                   void *saved, const fss_aux_outputs *aux, fss_stream_t stream);
+
+/*
+ * Query-guided instance labels (Sec. 3.3): for every scene Gaussian g and
+ * instance query q, S = sigmoid(f_q . f_ins(g)), D = phi_q(p_g) / phi_q(p_q)
+ * = exp(-1/2 d^T Sigma_q^-1 d) with d = p_g - p_q (the query's Gaussian
+ * density ratio; scene Gaussians enter as points), A = S D, and
+ * labels[g, :] = softmax over q of A(q, g).  The result is the per-Gaussian
+ * label distribution that the render calls blend like any C = n_queries
+ * feature (the paper's instance-label blending), and whose per-pixel argmax
+ * fss_render_forward_aux returns as the instance mask.
+ * Device inputs: f_ins [N, dim] BF16, means [N, 3] f32, f_q [n_queries, dim]
+ * BF16, p_q [n_queries, 3] f32, prec_q [n_queries, 6] f32 = the entries
+ * (xx, yy, zz, xy, xz, yz) of Sigma_q^-1 (symmetric positive definite).
+ * Device output: labels [N, n_queries] in out_dtype (FSS_F32 | FSS_BF16).
+ * n_queries: multiple of 16 in [16, 256]; dim: multiple of 16 in [16, 128];
+ * f_ins, f_q and labels 16-byte aligned.  The similarity logits run on the
+ * tensor cores (BF16 products, FP32 sums); the rest in FP32.
+ * err: device int32 that the kernel sets to 1 if a bounded wait on the
+ * tensor cores expired (the caller clears and reads it; never expected).
+ * Asynchronous on `stream`; the caller owns every buffer.  Errors:
+ * FSS_ERR_UNSUPPORTED for sizes out of range, FSS_ERR_INVALID_ARG for NULL
+ * or misaligned pointers and bad dtypes, FSS_ERR_CUDA for launch failures.
+ */
+fss_status fss_query_labels(int64_t N, int32_t n_queries, int32_t dim, const void *f_ins, const float *means,
+                            const void *f_q, const float *p_q, const float *prec_q, void *labels, int32_t out_dtype,
+                            int32_t *err, fss_stream_t stream);
 
 /*
  * Backward render: vector-Jacobian product of fss_render_forward for the

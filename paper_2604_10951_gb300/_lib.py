@@ -34,7 +34,7 @@ N_REGIONS = 18
 EXPORTS = ["fss_default_params", "fss_workspace_size", "fss_saved_size", "fss_project_bin", "fss_sort",
            "fss_render_forward", "fss_render_backward", "fss_read_status", "fss_last_error",
            "fss_workspace_region", "fss_loss_l2_l1", "fss_forward_static", "fss_set_kernel_events",
-           "fss_render_forward_aux"]
+           "fss_render_forward_aux", "fss_query_labels"]
 FSS_STATIC_SCRATCH_BYTES = 64 << 20
 
 
@@ -53,7 +53,7 @@ class fss_params(C.Structure):
 
 
 class fss_aux_outputs(C.Structure):
-    _fields_ = [("depth", C.c_void_p), ("depth_median", C.c_void_p), ("normal", C.c_void_p)]
+    _fields_ = [("depth", C.c_void_p), ("depth_median", C.c_void_p), ("normal", C.c_void_p), ("label", C.c_void_p)]
 
 
 class FssError(RuntimeError):
@@ -93,6 +93,7 @@ def lib():
                 "fss_set_kernel_events": [C.POINTER(C.c_void_p), i32],
                 "fss_render_forward_aux": [pp, pc, i32, i64, P, i64, P, P, P, P, P, P, P,
                                            C.POINTER(fss_aux_outputs), P],
+                "fss_query_labels": [i64, i32, i32, P, P, P, P, P, P, i32, P, P],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -168,6 +169,11 @@ def fss_loss_l2_l1(params, n_pix, feat, rgb, feat_target, rgb_target, w_feat, w_
                                       float(w_rgb), d_feat, d_rgb, loss, stream))
 
 
+def fss_query_labels(N, n_queries, dim, f_ins, means, f_q, p_q, prec_q, labels, out_dtype, err, stream):
+    return check(lib().fss_query_labels(N, n_queries, dim, f_ins, means, f_q, p_q, prec_q, labels, out_dtype, err,
+                                        stream))
+
+
 def fss_read_status(params, cams, n_cams, N, workspace, pair_capacity, stream):
     """Returns (status, num_pairs) without raising on device-side errors."""
     n = C.c_int64()
@@ -200,7 +206,7 @@ def fss_set_kernel_events(events):
 
 
 def fss_render_forward_aux(params, cams, n_cams, N, workspace, pair_capacity, rgb, feats, out_feat, out_rgb, out_T,
-                           out_topk_id, saved, depth, depth_median, normal, stream):
-    aux = fss_aux_outputs(depth, depth_median, normal)
+                           out_topk_id, saved, depth, depth_median, normal, stream, label=None):
+    aux = fss_aux_outputs(depth, depth_median, normal, label)
     return check(lib().fss_render_forward_aux(C.byref(params), cams, n_cams, N, workspace, pair_capacity, rgb, feats,
                                               out_feat, out_rgb, out_T, out_topk_id, saved, C.byref(aux), stream))

@@ -32,6 +32,7 @@ UNITS = {
     "render_bwd.cu": [],
     "loss.cu": [],
     "static_scratch.cu": [],
+    "query.cu": [],
 }
 
 

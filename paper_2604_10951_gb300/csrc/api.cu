@@ -366,8 +366,8 @@ fss_status fss_render_forward_aux(const fss_params* params, const fss_camera* ca
         a.saved_w = params->K > 0 ? reinterpret_cast<float*>(sv + align256(px * params->K * 4)) : nullptr;
         a.saved_nstop = reinterpret_cast<int32_t*>(sv + 2 * align256(px * params->K * 4));
     }
-    AuxOut x{nullptr, nullptr, nullptr};
-    if (aux) x = AuxOut{aux->depth, aux->depth_median, aux->normal};
+    AuxOut x{nullptr, nullptr, nullptr, nullptr};
+    if (aux) x = AuxOut{aux->depth, aux->depth_median, aux->normal, aux->label};
     a.st = ctx.at<Status>(REG_STATUS);
     a.persistent = params->schedule == FSS_SCHED_PERSISTENT;
     if (a.persistent) {  // the queue head, so that a frame's forward may run more than once
@@ -469,6 +469,26 @@ fss_status fss_loss_l2_l1(const fss_params* params, int64_t n_pix, const void* f
     cudaError_t e = launch_loss(n_pix, params->C, params->out_dtype, feat, rgb, feat_target, rgb_target, w_feat, w_rgb,
                                 d_feat, d_rgb, loss, num_sms_current(), reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "loss");
+    return FSS_OK;
+}
+
+fss_status fss_query_labels(int64_t N, int32_t n_queries, int32_t dim, const void* f_ins, const float* means,
+                            const void* f_q, const float* p_q, const float* prec_q, void* labels, int32_t out_dtype,
+                            int32_t* err, fss_stream_t stream) {
+    if (N < 0 || N > (int64_t)INT32_MAX * 128) return fail(FSS_ERR_UNSUPPORTED, "N %lld out of range", (long long)N);
+    if (n_queries < 16 || n_queries > 256 || n_queries % 16)
+        return fail(FSS_ERR_UNSUPPORTED, "n_queries %d must be a multiple of 16 in [16,256]", n_queries);
+    if (dim < 16 || dim > 128 || dim % 16)
+        return fail(FSS_ERR_UNSUPPORTED, "dim %d must be a multiple of 16 in [16,128]", dim);
+    if (out_dtype != FSS_F32 && out_dtype != FSS_BF16) return fail(FSS_ERR_INVALID_ARG, "out_dtype %d", out_dtype);
+    if (!err || !f_q || !p_q || !prec_q) return fail(FSS_ERR_INVALID_ARG, "NULL query argument or err");
+    if (N > 0 && (!f_ins || !means || !labels)) return fail(FSS_ERR_INVALID_ARG, "NULL Gaussian argument");
+    if (misaligned16(f_ins) || misaligned16(f_q) || misaligned16(labels))
+        return fail(FSS_ERR_INVALID_ARG, "f_ins, f_q and labels must be 16-byte aligned");
+    cudaError_t e = launch_query_labels(N, n_queries, dim, f_ins, means, f_q, p_q, prec_q, labels,
+                                        out_dtype == FSS_BF16, err, num_sms_current(),
+                                        reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "query_labels");
     return FSS_OK;
 }
 

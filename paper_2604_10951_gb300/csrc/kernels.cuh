@@ -60,7 +60,8 @@ struct AuxOut {
     float* depth;      // [pix] sum w z_hit
     float* depth_med;  // [pix] z_hit where T first drops below 1/2, else 0
     float* normal;     // [pix, 3] sum w n, camera-space normals facing the camera
-    __host__ __device__ bool any() const { return depth || depth_med || normal; }
+    int32_t* label;    // [pix] argmax over the channels of the rendered features, -1 if none blended
+    __host__ __device__ bool any() const { return depth || depth_med || normal || label; }
 };
 
 // launchers (defined in render_fwd.cu / render_bwd.cu); return a cudaError_t
@@ -111,6 +112,14 @@ struct BwdArgs {
 
 cudaError_t launch_render_backward(const Cams& cams, const RParams& P, const BwdArgs& a, int num_sms,
                                    cudaStream_t stream);
+
+// query-guided instance labels (query.cu): l_ins [N, nq] (F32 or BF16) from
+// BF16 f_ins [N, dim] and f_q [nq, dim]; nq in {16, 32, ..., 256}, dim in
+// {16, 32, ..., 128}; *err set to 1 if a bounded wait on the tensor cores expired
+size_t query_labels_smem(int nq, int dim);
+cudaError_t launch_query_labels(int64_t N, int nq, int dim, const void* f_ins, const float* means, const void* f_q,
+                                const float* p_q, const float* prec, void* out, int out_bf16, int32_t* err,
+                                int num_sms, cudaStream_t stream);
 
 cudaError_t launch_loss(int64_t n_pix, int C, int dtype, const void* F, const float* rgb, const void* Ft,
                         const float* rgbt, float wf, float wc, void* dF, float* drgb, double* loss, int num_sms,

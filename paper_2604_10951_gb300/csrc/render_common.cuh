@@ -281,6 +281,17 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
                  : "memory");
 }
 
+// Order-preserving 64-bit key of (value, channel) for an argmax by integer
+// maximum: larger values first, then smaller channel indices.
+__device__ __forceinline__ unsigned long long argmax_key(float v, int c) {
+    const uint32_t b = __float_as_uint(v);
+    const uint32_t o = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+    return ((unsigned long long)o << 32) | (0xFFFFFFFFu - (uint32_t)c);
+}
+__device__ __forceinline__ int argmax_channel(unsigned long long key) {
+    return (int)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFull));
+}
+
 // Launch of a render kernel over the tiles (one CTA per tile, or one resident
 // wave for the persistent schedule), recording the measurement hook after it.
 template <typename KernelT>

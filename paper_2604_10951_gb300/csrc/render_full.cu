@@ -149,6 +149,17 @@ __global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__
                     x.normal[3 * pix + 1] = ny;
                     x.normal[3 * pix + 2] = nz;
                 }
+                if (x.label) {  // argmax over the channels, lowest index on ties
+                    int cb = 0;
+                    float bv = acc[0];
+#pragma unroll
+                    for (int c = 1; c < CMAX; ++c) {
+                        const bool gt = c < C && acc[c] > bv;
+                        cb = gt ? c : cb;
+                        bv = gt ? acc[c] : bv;
+                    }
+                    x.label[pix] = n_contrib > 0 ? cb : -1;
+                }
             }
             if (a.out_feat) {
 #pragma unroll

@@ -72,6 +72,8 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : 1) k_r
     int32_t* s_id = reinterpret_cast<int32_t*>(smem);            // phase 2: [PC][KCAP] ids
     float* s_w = reinterpret_cast<float*>(s_id + PC * KCAP);     //          [PC][KCAP] weights
     int32_t* s_n = reinterpret_cast<int32_t*>(s_w + PC * KCAP);
+    unsigned long long* s_lab =  // AUX: per-pixel argmax keys
+        reinterpret_cast<unsigned long long*>(smem + (((size_t)PC * KCAP * 8 + PC * 4 + 7) & ~(size_t)7));
     __shared__ int s_tile;
 
     const int tid = threadIdx.x;
@@ -234,13 +236,14 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : 1) k_r
         warp_count(&a.st->counters[0], n_eval);
         warp_count(&a.st->counters[1], n_contrib);
 
-        // phase 2: gather-accumulate the selected feature rows
-        if (a.out_feat) {
+        // phase 2: gather-accumulate the selected feature rows (AUX: and their argmax)
+        if (a.out_feat || (AUX && x.label)) {
             for (int p0 = 0; p0 < NT; p0 += PC) {
                 __syncthreads();
                 if (tid >= p0 && tid < p0 + PC) {
                     const int q = tid - p0;
                     s_n[q] = inside ? hc : 0;
+                    if (AUX) s_lab[q] = 0ull;
                     float wsc = 1.0f;  // renormalised variant: 1 / (sum of the selected weights)
                     if (P.renorm) {
                         float ws = 0.0f;
@@ -258,8 +261,7 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : 1) k_r
                 }
                 __syncthreads();
                 const int npx = min(PC, NT - p0);
-                if (q0 >= ppi) continue;
-                for (int q = q0; q < npx; q += ppi) {
+                for (int q = q0; q0 < ppi && q < npx; q += ppi) {
                     const int p = p0 + q;
                     const int2 lq = pixel_of<TS>(p);  // pixel of the thread that selected row q
                     const int qx = tx * TS + lq.x, qy = ty * TS + lq.y;
@@ -277,7 +279,27 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : 1) k_r
                         for (int e = 0; e < E; ++e) acc[e] = fmaf(w, f[e], acc[e]);
                     }
                     const int64_t qpix = cam.pix_off + (int64_t)qy * cam.W + qx;
-                    store_vec<E>(a.out_feat, qpix * P.C + vv * E, acc, P.out_dtype);
+                    if (a.out_feat) store_vec<E>(a.out_feat, qpix * P.C + vv * E, acc, P.out_dtype);
+                    if (AUX && x.label) {
+                        int eb = 0;
+                        float bv = acc[0];
+#pragma unroll
+                        for (int e = 1; e < E; ++e) {
+                            eb = acc[e] > bv ? e : eb;
+                            bv = acc[e] > bv ? acc[e] : bv;
+                        }
+                        atomicMax(&s_lab[q], argmax_key(bv, vv * E + eb));
+                    }
+                }
+                if (AUX && x.label) {
+                    __syncthreads();
+                    if (tid < npx) {
+                        const int2 lq = pixel_of<TS>(p0 + tid);
+                        const int qx = tx * TS + lq.x, qy = ty * TS + lq.y;
+                        if (qx < cam.W && qy < cam.H)
+                            x.label[cam.pix_off + (int64_t)qy * cam.W + qx] =
+                                s_n[tid] > 0 ? argmax_channel(s_lab[tid]) : -1;
+                    }
                 }
             }
         }
@@ -292,7 +314,7 @@ cudaError_t launch_topk(const Cams& cams, const RParams& P, const FwdArgs& a, co
     auto smem = [aux](int kcap) {
         const size_t p1 = (size_t)BATCH * (4 * 16 + 4) + (aux ? (size_t)BATCH * 16 : 0);  // staging (+ normals)
         const int pc = (NT < 65536 / (kcap * 8 + 4)) ? NT : 65536 / (kcap * 8 + 4);
-        return std::max(p1, (size_t)pc * (kcap * 8 + 4));
+        return std::max(p1, (size_t)pc * (kcap * 8 + 4) + (aux ? (size_t)pc * 8 + 8 : 0));  // (+ argmax keys)
     };
     // variants (first-K selection, sensor outputs) need unsorted or few slots: two capacities
     if (P.select == FSS_SELECT_FRONT) {

@@ -115,12 +115,13 @@ class Frame:
                              _ptr(out_rgb), _ptr(out_T), _ptr(out_ids), _ptr(self.saved), _stream(stream))
 
     def render_forward_aux(self, rgb, feats, out_feat=None, out_rgb=None, out_T=None, out_ids=None, depth=None,
-                           depth_median=None, normal=None, stream=None):
+                           depth_median=None, normal=None, stream=None, label=None):
         """render_forward plus the sensor outputs (expected depth [pix], median depth [pix],
-        facing normal [pix, 3]; float32 tensors or None)."""
+        facing normal [pix, 3]; float32 tensors or None) and the per-pixel argmax over the
+        rendered channels (label [pix] int32 or None)."""
         L.fss_render_forward_aux(*self.args(), _ptr(self.ws), self.cap, _ptr(rgb), _ptr(feats), _ptr(out_feat),
                                  _ptr(out_rgb), _ptr(out_T), _ptr(out_ids), _ptr(self.saved), _ptr(depth),
-                                 _ptr(depth_median), _ptr(normal), _stream(stream))
+                                 _ptr(depth_median), _ptr(normal), _stream(stream), label=_ptr(label))
 
     def render_backward(self, means, scales, quats, opac, rgb, feats, out_T, d_feat, d_rgb, d_T, g_means, g_scales,
                         g_quats, g_opac, g_rgb, g_feat, stream=None):
@@ -194,6 +195,24 @@ class _RenderFn(torch.autograd.Function):
         frame.render_backward(means, scales, quats, opac, rgb, feats, T, dF.to(feats.dtype), drgb, dT, g_means,
                               g_scales, g_quats, g_opac, g_rgb, g_feat)
         return g_means, g_scales, g_quats, g_opac, g_rgb, g_feat, None
+
+
+def query_labels(f_ins, means, f_q, p_q, prec_q, out_dtype=torch.float32, err=None, stream=None):
+    """Per-Gaussian instance label distributions [N, n_queries] (fss_query_labels):
+    f_ins [N, dim] and f_q [n_queries, dim] BF16, means [N, 3], p_q [n_queries, 3],
+    prec_q [n_queries, 6] float32 on the device.  `err` (int32 [1], zeroed) receives
+    the kernel's wait-expiry flag; by default a fresh one is checked after the call."""
+    N, dim = f_ins.shape
+    nq = f_q.shape[0]
+    out = torch.empty(N, nq, dtype=out_dtype, device=f_ins.device)
+    own = err is None
+    if own:
+        err = torch.zeros(1, dtype=torch.int32, device=f_ins.device)
+    L.fss_query_labels(N, nq, dim, _ptr(f_ins), _ptr(means), _ptr(f_q), _ptr(p_q), _ptr(prec_q), _ptr(out),
+                       DTYPES[out_dtype], _ptr(err), _stream(stream))
+    if own and int(err.item()) != 0:
+        raise RuntimeError("query_labels: a wait on the tensor cores expired")
+    return out
 
 
 def render(means, scales, quats, opacities, rgb, feats, frame: Frame):

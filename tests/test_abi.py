@@ -134,3 +134,16 @@ def test_kernel_event_hook_arguments(lib):
     arr = (C.c_void_p * 2)(None, None)
     assert lib.fss_set_kernel_events(arr, 2) == L.FSS_ERR_INVALID_ARG
     assert lib.fss_set_kernel_events(arr, -1) == L.FSS_ERR_INVALID_ARG
+
+
+def test_query_label_arguments_are_checked_on_the_host(lib):
+    z = C.c_void_p(16)  # never dereferenced: every call below is rejected first
+    assert lib.fss_query_labels(10, 24, 32, z, z, z, z, z, z, L.FSS_F32, z, None) == L.FSS_ERR_UNSUPPORTED
+    assert lib.fss_query_labels(10, 32, 40, z, z, z, z, z, z, L.FSS_F32, z, None) == L.FSS_ERR_UNSUPPORTED
+    assert lib.fss_query_labels(10, 512, 32, z, z, z, z, z, z, L.FSS_F32, z, None) == L.FSS_ERR_UNSUPPORTED
+    assert lib.fss_query_labels(-1, 32, 32, z, z, z, z, z, z, L.FSS_F32, z, None) == L.FSS_ERR_UNSUPPORTED
+    assert lib.fss_query_labels(10, 32, 32, z, z, z, z, z, z, 7, z, None) == L.FSS_ERR_INVALID_ARG
+    assert lib.fss_query_labels(10, 32, 32, None, z, z, z, z, z, L.FSS_F32, z, None) == L.FSS_ERR_INVALID_ARG
+    assert lib.fss_query_labels(10, 32, 32, z, z, z, z, z, z, L.FSS_F32, None, None) == L.FSS_ERR_INVALID_ARG
+    assert lib.fss_query_labels(10, 32, 32, C.c_void_p(24), z, z, z, z, z, L.FSS_F32, z, None) == L.FSS_ERR_INVALID_ARG
+    assert "aligned" in L.last_error()
