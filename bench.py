@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip baseline/e2e/cpu legs (profiling runs)")
+    ap.add_argument("--queries-only", action="store_true",
+                    help="only the query-guided instance-label measurement (profiling runs)")
     return ap.parse_args()
 
 
@@ -141,6 +143,15 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def measured_bf16_tflops():
+    """Burst cuBLAS bf16 TFLOP/s (a kernel timed alone), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
 # ---------------------------------------------------------------------------
 # our implementation
 # ---------------------------------------------------------------------------
@@ -170,6 +181,12 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    if args.queries_only:
+        if D.rank == 0:
+            print(json.dumps({"query_labels": queries(torch, dev, sc, means, scales, quats, opac, rgb, poses, flush)}))
+        D.close()
+        return
 
     names = ["project_bin", "sort", "render_forward", "loss", "render_backward"]
 
@@ -320,6 +337,9 @@ def run_ours(args):
         del base
         out["ablation_fwd"] = ablation(torch, L, dev, means, scales, quats, opac, rgb, feats[torch.float32], poses,
                                        flush)
+        out["variants_render_ms"] = variants(torch, dev, means, scales, quats, opac, rgb, feats[torch.bfloat16],
+                                             poses, flush)
+        out["query_labels"] = queries(torch, dev, sc, means, scales, quats, opac, rgb, poses, flush)
     if D.rank == 0 and not args.no_extras:
         out["cpu_baseline"] = cpu_baseline(sc, poses, sample_frames=1)
     if D.rank == 0:
@@ -332,10 +352,12 @@ KERNELS = ["k_project", "k_scan", "k_emit", "k_tile_sort", "k_render_topk", "k_l
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch (camera pose 1) from the
 # ncu capture summarised in profiles/<kernel>_room500k_640x480_c64_k8.md; to be set
 # to None whenever the kernel changes after that capture
-NCU_TRAFFIC = {"k_render_topk": 27166208, "k_bwd_feat": 70297600, "k_bwd_geo": 37996032}
+NCU_TRAFFIC = {"k_render_topk": 26669824, "k_bwd_feat": 70577152, "k_bwd_geo": 37997056}
 # (smsp__inst_executed.sum, gpu__time_duration.sum in us) of the same captures
-NCU_ISSUE = {"k_render_topk": (84202380, 108.288), "k_bwd_feat": (110324067, 126.496),
-             "k_bwd_geo": (88788804, 130.208)}
+NCU_ISSUE = {"k_render_topk": (84912865, 110.24), "k_bwd_feat": (110458467, 124.736),
+             "k_bwd_geo": (88779420, 125.792)}
+# the query-label kernel's capture (profiles/k_query_labels_room500k_nq32_dim32.md): DRAM read + write
+NCU_QUERY_TRAFFIC = {"nq32_dim32_f32": 47276544}
 
 
 def kernel_times(path, torch, L, flush, rounds=4):
@@ -503,6 +525,108 @@ def ablation(torch, L, dev, means, scales, quats, opac, rgb, feats, poses, flush
                       "fps": round(1e3 / float(np.mean(ms)), 1), "pairs_per_frame": int(np.mean(pairs)),
                       "pairs_per_tile": round(float(np.mean(pairs)) / tiles, 1), "status": int(s)}
         del fr
+    return rows
+
+
+def variants(torch, dev, means, scales, quats, opac, rgb, feats, poses, flush, reps=3):
+    """Render-call time (mean over the 16 poses, L2 flushed, CUDA events) of
+    the bench's forward configuration and of its variants on the same binned
+    frames: the sensor outputs (expected and median depth, normal), the
+    first-K selection and the renormalised Top-K."""
+    from paper_2604_10951_gb300.raster import Frame, make_cams, make_params
+
+    rows = {}
+    for name, sel, rn, aux in (("topw", "topw", False, False), ("topw_sensors", "topw", False, True),
+                               ("front", "front", False, False), ("renorm", "topw", True, False)):
+        p = make_params(C=C_FEAT, K=K_TOP, feat_dtype=torch.bfloat16, stop_rule="exact_topk", select=sel, renorm=rn)
+        fr = Frame([poses[0]], N_SPLATS, p, pair_capacity=1 << 21, device=dev)
+        F, rgb_o, T, ids = fr.new_outputs()
+        depth = torch.empty(fr.total_pix, device=dev) if aux else None
+        med = torch.empty(fr.total_pix, device=dev) if aux else None
+        nrm = torch.empty(fr.total_pix, 3, device=dev) if aux else None
+        ms = []
+        for cam in poses:
+            fr.cams = make_cams([cam])
+            fr.bin_and_sort(means, scales, quats, opac)
+            for _ in range(reps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fr.render_forward_aux(rgb, feats, F, rgb_o, T, ids, depth, med, nrm)
+                b.record()
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+        rows[name] = round(float(np.mean(ms)), 4)
+        del fr
+    return rows
+
+
+def queries(torch, dev, sc, means, scales, quats, opac, rgb, poses, flush, reps=20):
+    """Query-guided instance labels (Sec. 3.3) on the bench's 500k Gaussians:
+    the tensor-core label kernel (32 queries and 32-d instance features as in
+    the paper, plus 128 queries) timed alone with CUDA events, L2 flushed
+    before each launch, against the HBM roofline of its algorithmic bytes
+    (instance features, centres, labels out) and the bf16 tensor peak of its
+    2 N nq dim flops; and the instance-mask render (the labels blended by the
+    K = 8 Top-K renderer with the per-pixel argmax output, C = 32 BF16) over
+    the 16 poses."""
+    from paper_2604_10951_gb300 import scenes
+    from paper_2604_10951_gb300.raster import Frame, make_cams, make_params, query_labels
+
+    peak, src = measured_peaks()
+    tpeak, tsrc = measured_bf16_tflops()
+    N = sc.n
+    rows = {}
+    for nq, dim, od in ((32, 32, torch.float32), (32, 32, torch.bfloat16), (128, 32, torch.bfloat16)):
+        f_ins, f_q, p_q, prec = scenes.room_queries(sc.means, nq, dim, seed=0)
+        fi = torch.as_tensor(f_ins).to(dev, torch.bfloat16)
+        fq = torch.as_tensor(f_q).to(dev, torch.bfloat16)
+        pq, pr = torch.as_tensor(p_q).to(dev), torch.as_tensor(prec).to(dev)
+        err = torch.zeros(1, dtype=torch.int32, device=dev)
+        lab = query_labels(fi, means, fq, pq, pr, out_dtype=od, err=err)
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            lab = query_labels(fi, means, fq, pq, pr, out_dtype=od, err=err)
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        if int(err.item()):
+            raise RuntimeError("query_labels: a tensor-core wait expired")
+        t = float(np.median(ms)) * 1e-3
+        sz = 2 if od == torch.bfloat16 else 4
+        nbytes = N * dim * 2 + N * 12 + N * nq * sz + nq * (dim * 2 + 36)
+        flops = 2.0 * N * nq * dim
+        key = f"nq{nq}_dim{dim}_{'bf16' if sz == 2 else 'f32'}"
+        rows[key] = {"us": round(t * 1e6, 2), "bound": "hbm", "algorithmic_bytes": int(nbytes),
+                     "achieved_gbs": round(nbytes / t / 1e9, 1), "peak_gbs": peak,
+                     "frac": round(nbytes / t / 1e9 / peak, 4), "tensor_tflops": round(flops / t / 1e12, 2),
+                     "tensor_frac": round(flops / t / 1e12 / tpeak, 5), "traffic": NCU_QUERY_TRAFFIC.get(key)}
+        if key == "nq32_dim32_bf16":
+            mask_lab = lab
+    rows["peaks"] = {"hbm": src, "bf16_tflops": tpeak, "bf16_source": tsrc}
+    # the instance mask: labels blended by the Top-K renderer, argmax per pixel
+    p = make_params(C=32, K=K_TOP, feat_dtype=torch.bfloat16, stop_rule="exact_topk")
+    fr = Frame([poses[0]], N_SPLATS, p, pair_capacity=1 << 21, device=dev)
+    label = torch.empty(fr.total_pix, dtype=torch.int32, device=dev)
+    F = torch.empty(fr.total_pix, 32, dtype=torch.bfloat16, device=dev)
+    ms = []
+    for cam in poses:
+        fr.cams = make_cams([cam])
+        fr.bin_and_sort(means, scales, quats, opac)
+        for _ in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fr.render_forward_aux(rgb, mask_lab, F, None, None, None, label=label)
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+    rows["mask_render_ms"] = round(float(np.mean(ms)), 4)
+    rows["mask_covered"] = round(float((label >= 0).float().mean().item()), 4)
+    del fr
     return rows
 
 

@@ -23,6 +23,7 @@
 // returns.
 #include "fss_internal.cuh"
 #include "kernels.cuh"
+#include "render_common.cuh"
 
 #include <cuda_bf16.h>
 
@@ -35,6 +36,7 @@ namespace {
 constexpr int QM = 128;        // Gaussians per tile (MMA M)
 constexpr int QTHREADS = 128;  // warp w reads TMEM lanes 32 w .. 32 w + 31
 constexpr int QWAIT = 1 << 22; // try_wait rounds before giving up
+constexpr float QLOG2E = 1.4426950408889634f;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -94,30 +96,62 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
         : "memory");
 }
 
-// copy rows [r0, r0 + nrows) of a row-major [*, dim] BF16 matrix into the
-// core-matrix layout at dst (rows past `valid` are zero)
+// Operand staging in the core-matrix layout.  Chunk j of a tile (16 bytes,
+// 8 BF16) goes to row r = 8 (j / (8 KC)) + j % 8 and K-chunk c = (j / 8) % KC:
+// the 8 threads of a shared-memory store phase write the 8 rows of one core
+// matrix (128 consecutive bytes, no bank conflict), and a warp still reads
+// 8 whole consecutive rows of global memory.
+template <int KC>
+__device__ __forceinline__ int stage_row(int j) { return ((j / (8 * KC)) << 3) | (j & 7); }
+template <int KC>
+__device__ __forceinline__ int stage_col(int j) { return (j >> 3) % KC; }
+template <int KC>
+__device__ __forceinline__ uint32_t stage_off(int j) {
+    const int r = stage_row<KC>(j), c = stage_col<KC>(j);
+    return ((uint32_t)((r >> 3) * KC + c) << 7) + ((uint32_t)(r & 7) << 4);
+}
+
+// rows [r0, r0 + nrows) of a row-major [*, 8 KC] BF16 matrix (rows past
+// `valid` are zero) into the core-matrix layout at dst
+template <int KC>
 __device__ __forceinline__ void stage_rows(unsigned char* dst, const __nv_bfloat16* __restrict__ src, int64_t r0,
-                                           int nrows, int64_t valid, int dim) {
-    const int kc = dim >> 3;  // 16-byte chunks per row
-    for (int j = threadIdx.x; j < nrows * kc; j += blockDim.x) {
-        const int r = j / kc, c = j - r * kc;
+                                           int nrows, int64_t valid) {
+    for (int j = threadIdx.x; j < nrows * KC; j += blockDim.x) {
+        const int r = stage_row<KC>(j), c = stage_col<KC>(j);
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (r0 + r < valid) v = __ldg(reinterpret_cast<const uint4*>(src + (r0 + r) * dim) + c);
-        *reinterpret_cast<uint4*>(dst + ((size_t)((r >> 3) * kc + c) << 7) + ((r & 7) << 4)) = v;
+        if (r0 + r < valid) v = __ldg(reinterpret_cast<const uint4*>(src + (r0 + r) * (8 * KC)) + c);
+        *reinterpret_cast<uint4*>(dst + stage_off<KC>(j)) = v;
     }
 }
 
-__global__ void __launch_bounds__(QTHREADS) k_query_labels(int64_t N, int nq, int dim, int ncols,
+// this thread's KC chunks of a 128-row tile (chunk j = tid + i * 128), into registers
+template <int KC>
+__device__ __forceinline__ void load_tile(uint4 (&v)[KC], const __nv_bfloat16* __restrict__ src, int64_t r0,
+                                          int64_t valid) {
+#pragma unroll
+    for (int i = 0; i < KC; ++i) {
+        const int j = threadIdx.x + i * QTHREADS;
+        const int r = stage_row<KC>(j), c = stage_col<KC>(j);
+        v[i] = make_uint4(0u, 0u, 0u, 0u);
+        if (r0 + r < valid) v[i] = __ldg(reinterpret_cast<const uint4*>(src + (r0 + r) * (8 * KC)) + c);
+    }
+}
+
+template <int KC>
+__global__ void __launch_bounds__(QTHREADS, KC <= 4 ? 8 : 1) k_query_labels(int64_t N, int nq, int ncols,
                                                            const __nv_bfloat16* __restrict__ f_ins,
                                                            const float* __restrict__ means,
                                                            const __nv_bfloat16* __restrict__ f_q,
                                                            const float* __restrict__ p_q,
                                                            const float* __restrict__ prec, void* __restrict__ out,
                                                            int out_bf16, int32_t* __restrict__ err) {
+    constexpr int dim = 8 * KC;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;                                  // [128 x dim] core matrices
     unsigned char* sB = sA + (size_t)QM * dim * 2;             // [nq x dim] core matrices
-    float* s_qp = reinterpret_cast<float*>(sB + (size_t)nq * dim * 2);  // [nq][12]: p_q, Sigma^-1, pad
+    // [nq][3] float4: (p_q, -log2(e)/2 xx), (-log2(e)/2 yy, zz; -log2(e) xy, xz), (-log2(e) yz, 0, 0, 0),
+    // so that D = 2^(quadratic form in d)
+    float4* s_qp = reinterpret_cast<float4*>(sB + (size_t)nq * dim * 2);
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
@@ -126,12 +160,13 @@ __global__ void __launch_bounds__(QTHREADS) k_query_labels(int64_t N, int nq, in
     const int64_t ntiles = (N + QM - 1) / QM;
 
     // queries: operand B and the per-query proximity parameters, once per CTA
-    stage_rows(sB, f_q, 0, nq, nq, dim);
+    stage_rows<KC>(sB, f_q, 0, nq, nq);
     for (int q = tid; q < nq; q += blockDim.x) {
-        float* d = s_qp + 12 * q;
-        d[0] = p_q[3 * q]; d[1] = p_q[3 * q + 1]; d[2] = p_q[3 * q + 2];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) d[3 + k] = prec[6 * q + k];
+        const float h = -0.5f * QLOG2E, f = -QLOG2E;
+        const float* P = prec + 6 * q;
+        s_qp[3 * q] = make_float4(p_q[3 * q], p_q[3 * q + 1], p_q[3 * q + 2], h * P[0]);
+        s_qp[3 * q + 1] = make_float4(h * P[1], h * P[2], f * P[3], f * P[4]);
+        s_qp[3 * q + 2] = make_float4(f * P[5], 0.0f, 0.0f, 0.0f);
     }
     if (tid == 0) {
         s_abort = 0;
@@ -150,20 +185,31 @@ __global__ void __launch_bounds__(QTHREADS) k_query_labels(int64_t N, int nq, in
     const uint32_t tmem = s_tmem;
     const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's lanes, column 0
     const uint32_t bar = smem_u32(&s_bar);
-    const uint32_t kc = (uint32_t)dim >> 3;
     const uint32_t idesc = mma_idesc(nq);
     uint32_t phase = 0;
 
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // the next tile's operand rows and Gaussian centre, loaded while the
+    // current tile is in the tensor core and the epilogue
+    uint4 pre[KC];
+    float npx = 0.0f, npy = 0.0f, npz = 0.0f;
+    int64_t tile = blockIdx.x;
+    if (tile < ntiles) {
+        load_tile<KC>(pre, f_ins, tile * QM, N);
+        const int64_t g = tile * QM + tid;
+        if (g < N) { npx = means[3 * g]; npy = means[3 * g + 1]; npz = means[3 * g + 2]; }
+    }
+    for (; tile < ntiles; tile += gridDim.x) {
         const int64_t g0 = tile * QM;
-        stage_rows(sA, f_ins, g0, QM, N, dim);
+#pragma unroll
+        for (int i = 0; i < KC; ++i) *reinterpret_cast<uint4*>(sA + stage_off<KC>(tid + i * QTHREADS)) = pre[i];
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic stores -> tensor core reads
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            for (int s = 0; s < (dim >> 4); ++s) {  // K = 16 per MMA: two 16-byte chunks
-                const uint64_t da = smem_desc(smem_u32(sA) + 256u * s, 128u, kc * 128u);
-                const uint64_t db = smem_desc(smem_u32(sB) + 256u * s, 128u, kc * 128u);
+#pragma unroll
+            for (int s = 0; s < KC / 2; ++s) {  // K = 16 per MMA: two 16-byte chunks
+                const uint64_t da = smem_desc(smem_u32(sA) + 256u * s, 128u, KC * 128u);
+                const uint64_t db = smem_desc(smem_u32(sB) + 256u * s, 128u, KC * 128u);
                 asm volatile(
                     "{\n\t.reg .pred p;\n\t"
                     "setp.ne.b32 p, %4, 0;\n\t"
@@ -174,29 +220,36 @@ __global__ void __launch_bounds__(QTHREADS) k_query_labels(int64_t N, int nq, in
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                          : "memory");
         }
+        // this tile's centre (the thread's TMEM lane is tid), then the next tile's loads
+        const float px = npx, py = npy, pz = npz;
+        const int64_t nt = tile + gridDim.x;
+        if (nt < ntiles) {
+            load_tile<KC>(pre, f_ins, nt * QM, N);
+            const int64_t gn = nt * QM + tid;
+            if (gn < N) { npx = means[3 * gn]; npy = means[3 * gn + 1]; npz = means[3 * gn + 2]; }
+        }
         if (!mbar_wait(bar, phase)) s_abort = 1;
         phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         __syncthreads();
         if (s_abort) break;
 
-        // epilogue: this thread's Gaussian is TMEM lane 32 warp + lane
-        const int64_t g = g0 + warp * 32 + lane;
+        // epilogue: this thread's Gaussian is TMEM lane 32 warp + lane = tid
+        const int64_t g = g0 + tid;
         const bool live = g < N;
-        float px = 0.0f, py = 0.0f, pz = 0.0f;
-        if (live) { px = means[3 * g]; py = means[3 * g + 1]; pz = means[3 * g + 2]; }
         float sum = 0.0f;
         for (int c0 = 0; c0 < nq; c0 += 16) {
             float v[16];
             tmem_ld16(tlane + c0, v);
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                const float* qp = s_qp + 12 * (c0 + i);
-                const float S = 1.0f / (1.0f + __expf(-v[i]));
-                const float dx = px - qp[0], dy = py - qp[1], dz = pz - qp[2];
-                float quad = fmaf(qp[3] * dx, dx, fmaf(qp[4] * dy, dy, qp[5] * dz * dz));
-                quad = fmaf(2.0f * qp[6] * dx, dy, fmaf(2.0f * qp[7] * dx, dz, fmaf(2.0f * qp[8] * dy, dz, quad)));
-                const float e = __expf(S * __expf(-0.5f * quad));
+                const float4 a = s_qp[3 * (c0 + i)], b = s_qp[3 * (c0 + i) + 1], c = s_qp[3 * (c0 + i) + 2];
+                const float S = rcp_approx(1.0f + ex2_approx(-QLOG2E * v[i]));  // sigmoid
+                const float dx = px - a.x, dy = py - a.y, dz = pz - a.z;
+                // log2 D = -log2(e)/2 d^T Sigma^-1 d
+                const float l2d = fmaf(fmaf(a.w, dx, fmaf(b.z, dy, b.w * dz)), dx,
+                                       fmaf(fmaf(b.x, dy, c.x * dz), dy, b.y * dz * dz));
+                const float e = ex2_approx(QLOG2E * S * ex2_approx(l2d));  // exp(A), A = S D
                 v[i] = e;
                 sum += e;
             }
@@ -213,8 +266,8 @@ __global__ void __launch_bounds__(QTHREADS) k_query_labels(int64_t N, int nq, in
                 uint32_t* h = reinterpret_cast<uint32_t*>(w);
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * i] * inv, v[2 * i + 1] * inv);
-                    h[i] = *reinterpret_cast<const uint32_t*>(&b);
+                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * i] * inv, v[2 * i + 1] * inv);
+                    h[i] = *reinterpret_cast<const uint32_t*>(&b2);
                 }
                 uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out) + g * nq + c0);
                 o[0] = w[0];
@@ -238,6 +291,41 @@ __global__ void __launch_bounds__(QTHREADS) k_query_labels(int64_t N, int nq, in
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
+template <int KC>
+cudaError_t launch_kc(int64_t N, int nq, const void* f_ins, const float* means, const void* f_q, const float* p_q,
+                      const float* prec, void* out, int out_bf16, int32_t* err, int num_sms, cudaStream_t stream) {
+    int ncols = 32;
+    while (ncols < nq) ncols <<= 1;
+    const size_t smem = query_labels_smem(nq, 8 * KC);
+    auto kern = k_query_labels<KC>;
+    cudaError_t e = cudaSuccess;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    // resident CTAs per SM from the kernel's registers and shared memory (the
+    // occupancy query answers 1 for this tensor-memory kernel), at most the
+    // number whose tensor-memory columns fit the SM's 512 together
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    int dev = 0, smem_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e != cudaSuccess) return e;
+    const int regs = ((std::max(fa.numRegs, 1) + 7) & ~7) * QTHREADS;
+    int per_sm = std::min({2048 / QTHREADS, 65536 / regs, smem_sm / (int)(smem + fa.sharedSizeBytes + 1024),
+                           512 / ncols});
+    per_sm = std::max(1, per_sm);
+    const int64_t ntiles = (N + QM - 1) / QM;
+    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)per_sm * num_sms);
+    kern<<<grid, QTHREADS, smem, stream>>>(N, nq, ncols, static_cast<const __nv_bfloat16*>(f_ins), means,
+                                           static_cast<const __nv_bfloat16*>(f_q), p_q, prec, out, out_bf16, err);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) kernel_mark(stream);
+    return e;
+}
+
 }  // namespace
 
 size_t query_labels_smem(int nq, int dim) { return (size_t)QM * dim * 2 + (size_t)nq * dim * 2 + (size_t)nq * 48; }
@@ -246,26 +334,16 @@ cudaError_t launch_query_labels(int64_t N, int nq, int dim, const void* f_ins, c
                                 const float* p_q, const float* prec, void* out, int out_bf16, int32_t* err,
                                 int num_sms, cudaStream_t stream) {
     if (N <= 0) return cudaSuccess;
-    int ncols = 32;
-    while (ncols < nq) ncols <<= 1;
-    const size_t smem = query_labels_smem(nq, dim);
-    cudaError_t e = cudaSuccess;
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_query_labels, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+    switch (dim) {
+        case 16: return launch_kc<2>(N, nq, f_ins, means, f_q, p_q, prec, out, out_bf16, err, num_sms, stream);
+        case 32: return launch_kc<4>(N, nq, f_ins, means, f_q, p_q, prec, out, out_bf16, err, num_sms, stream);
+        case 48: return launch_kc<6>(N, nq, f_ins, means, f_q, p_q, prec, out, out_bf16, err, num_sms, stream);
+        case 64: return launch_kc<8>(N, nq, f_ins, means, f_q, p_q, prec, out, out_bf16, err, num_sms, stream);
+        case 80: return launch_kc<10>(N, nq, f_ins, means, f_q, p_q, prec, out, out_bf16, err, num_sms, stream);
+        case 96: return launch_kc<12>(N, nq, f_ins, means, f_q, p_q, prec, out, out_bf16, err, num_sms, stream);
+        case 112: return launch_kc<14>(N, nq, f_ins, means, f_q, p_q, prec, out, out_bf16, err, num_sms, stream);
+        default: return launch_kc<16>(N, nq, f_ins, means, f_q, p_q, prec, out, out_bf16, err, num_sms, stream);
     }
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_query_labels, QTHREADS, smem);
-    if (e != cudaSuccess) return e;
-    per_sm = std::max(1, std::min(per_sm, 512 / ncols));  // resident CTAs never wait for tensor memory
-    const int64_t ntiles = (N + QM - 1) / QM;
-    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)per_sm * num_sms);
-    k_query_labels<<<grid, QTHREADS, smem, stream>>>(N, nq, dim, ncols, static_cast<const __nv_bfloat16*>(f_ins),
-                                                     means, static_cast<const __nv_bfloat16*>(f_q), p_q, prec, out,
-                                                     out_bf16, err);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) kernel_mark(stream);
-    return e;
 }
 
 }  // namespace fss

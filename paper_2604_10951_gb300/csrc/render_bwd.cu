@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
 // ---------------------------------------------------------------------------
 // k_bwd_geo: back-to-front replay (Top-K and full accumulation)
 // ---------------------------------------------------------------------------
-template <int TS, bool FULL, int CMAX, typename FT>
+template <int TS, bool FULL, int CMAX, typename FT, bool RN>
 __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cams cams,
                                                      const __grid_constant__ RParams P, const BwdArgs a) {
     constexpr int NT = TS * TS;
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
                 next_pos = a.saved_pos[pix * K + kk];
                 next_dot = a.dots[pix * K + kk];
             }
-            if (P.renorm) {  // entries 0..kk are the selected ones, front to back
+            if (RN) {  // entries 0..kk are the selected ones, front to back
                 float ws = 0.0f, wd = 0.0f;
                 for (int k2 = 0; k2 <= kk; ++k2) {
                     const float wv = a.saved_w[pix * K + k2];
@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
                 float s = oc.y * gr + oc.z * gg + oc.w * gb;
                 if (!FULL) {
                     if (pos == next_pos) {
-                        s += fmaf(next_dot, rn_a, rn_b);
+                        s += RN ? fmaf(next_dot, rn_a, rn_b) : next_dot;
                         --kk;
                         next_pos = kk >= 0 ? a.saved_pos[pix * K + kk] : -1;
                         next_dot = kk >= 0 ? a.dots[pix * K + kk] : 0.0f;
@@ -793,17 +793,17 @@ cudaError_t launch_feat(const Cams& cams, const RParams& P, const BwdArgs& a, cu
     return go(k_bwd_feat<32, FT>);
 }
 
-template <int TS, bool FULL, int CMAX, typename FT>
+template <int TS, bool FULL, int CMAX, typename FT, bool RN = false>
 cudaError_t launch_geo_one(const Cams& cams, const RParams& P, const BwdArgs& a, cudaStream_t s) {
     constexpr int NB = FULL ? FBATCH : BB;
     const size_t smem = (size_t)NB * (4 * 16 + 8) + (size_t)NB * 16 * 4 + (FULL ? (size_t)NB * P.C * 8 : 0);  // staging, masks, partials, rows
-    cudaError_t e = set_smem((const void*)k_bwd_geo<TS, FULL, CMAX, FT>, smem);
+    cudaError_t e = set_smem((const void*)k_bwd_geo<TS, FULL, CMAX, FT, RN>, smem);
     if (e != cudaSuccess) return e;
     int grid = cams.total_tiles;
-    if (a.persistent && (e = persistent_grid((const void*)k_bwd_geo<TS, FULL, CMAX, FT>, TS * TS, smem, grid)) !=
+    if (a.persistent && (e = persistent_grid((const void*)k_bwd_geo<TS, FULL, CMAX, FT, RN>, TS * TS, smem, grid)) !=
                             cudaSuccess)
         return e;
-    k_bwd_geo<TS, FULL, CMAX, FT><<<grid, TS * TS, smem, s>>>(cams, P, a);
+    k_bwd_geo<TS, FULL, CMAX, FT, RN><<<grid, TS * TS, smem, s>>>(cams, P, a);
     e = cudaGetLastError();
     if (e == cudaSuccess) kernel_mark(s);
     return e;
@@ -811,7 +811,8 @@ cudaError_t launch_geo_one(const Cams& cams, const RParams& P, const BwdArgs& a,
 
 template <int TS, typename FT>
 cudaError_t launch_geo(const Cams& cams, const RParams& P, const BwdArgs& a, cudaStream_t s) {
-    if (P.K > 0) return launch_geo_one<TS, false, 4, FT>(cams, P, a, s);
+    if (P.K > 0)  // the renormalised variant has its own instance: no cost on the plain path
+        return P.renorm ? launch_geo_one<TS, false, 4, FT, true>(cams, P, a, s) : launch_geo_one<TS, false, 4, FT>(cams, P, a, s);
     if (P.C <= 32) return launch_geo_one<TS, true, 32, FT>(cams, P, a, s);
     if (P.C <= 64) return launch_geo_one<TS, true, 64, FT>(cams, P, a, s);
     return launch_geo_one<TS, true, 128, FT>(cams, P, a, s);
