@@ -86,6 +86,12 @@ def _load():
             lib.orc_check_conservative.restype = i64
             lib.orc_query_labels.argtypes = [i64, C.c_int32, C.c_int32, P, P, P, P, P, P]
             lib.orc_query_labels.restype = None
+            lib.orc_sh_basis.argtypes = [C.c_int, P, P, P]
+            lib.orc_sh_basis.restype = None
+            lib.orc_sh_colors.argtypes = [i64, C.c_int, P, P, C.POINTER(OrcCam), P]
+            lib.orc_sh_colors.restype = None
+            lib.orc_sh_backward.argtypes = [i64, C.c_int, P, P, C.POINTER(OrcCam), P, P, P, P]
+            lib.orc_sh_backward.restype = None
             lib.orc_num_threads.argtypes = []
             lib.orc_num_threads.restype = C.c_int
             _lib = lib
@@ -222,12 +228,14 @@ def binning(scene, cam, params, mode=None):
     return dict(recf=recf, reci=reci, count=cnt, tiles=st, ids=si, ranges=rng, P=int(st.shape[0]))
 
 
-def render(scene, cam, params, feats=None, binned=None, brute=False, visible=None, zkey=None, threads=0):
+def render(scene, cam, params, feats=None, binned=None, brute=False, visible=None, zkey=None, threads=0, sh=None):
     """FP64 render.  Tiled over ``binned`` lists (computed if None) unless
-    ``brute``; returns a dict of per-pixel outputs."""
+    ``brute``; returns a dict of per-pixel outputs.  ``sh`` [N, B, 3]:
+    view-dependent colours from spherical-harmonic coefficients instead of
+    ``scene.rgb``."""
     lib = _load()
     m, s, q, o = _scene_arrays64(scene)
-    rgb = _f64(scene.rgb)
+    rgb = _f64(scene.rgb) if sh is None else sh_colors(sh, scene.means, cam)
     feats = _f64(scene.feats if feats is None else feats)
     N, Cc = m.shape[0], feats.shape[1]
     params.C = Cc
@@ -258,14 +266,16 @@ def render(scene, cam, params, feats=None, binned=None, brute=False, visible=Non
 
 
 def render_backward(scene, cam, params, gF, grgb, gT=None, feats=None, binned=None, brute=False,
-                    visible=None, zkey=None):
+                    visible=None, zkey=None, sh=None):
     """Analytic FP64 gradients of sum(gF*F) + sum(grgb*rgb) + sum(gT*T), and
     under "abs" [N, 10] the same chain over magnitudes (means, scales, quats,
     opacity): a bound on the sum of |terms| that each geometric gradient
-    entry adds up."""
+    entry adds up.  With ``sh`` [N, B, 3] the colours are view dependent: "sh"
+    holds dL/dcoefficients, "rgb" the gradient of this view's colours, and
+    the direction term joins "means" (and its magnitude "abs")."""
     lib = _load()
     m, s, q, o = _scene_arrays64(scene)
-    rgb = _f64(scene.rgb)
+    rgb = _f64(scene.rgb) if sh is None else sh_colors(sh, scene.means, cam)
     feats = _f64(scene.feats if feats is None else feats)
     N, Cc = m.shape[0], feats.shape[1]
     params.C = Cc
@@ -285,7 +295,40 @@ def render_backward(scene, cam, params, gF, grgb, gT=None, feats=None, binned=No
                             _ptr(gF), _ptr(grgb), _ptr(gT),
                             _ptr(g["means"]), _ptr(g["scales"]), _ptr(g["quats"]), _ptr(g["opac"]),
                             _ptr(g["rgb"]), _ptr(g["feat"]), _ptr(g["Tmat"]), _ptr(g["abs"]))
+    if sh is not None:
+        shc = _f64(sh)
+        g["sh"] = np.zeros_like(shc)
+        lib.orc_sh_backward(N, _sh_degree(shc), _ptr(shc), _ptr(m), C.byref(make_cam(cam)), _ptr(g["rgb"]),
+                            _ptr(g["sh"]), _ptr(g["means"]), _ptr(g["abs"]))
     return g
+
+
+def _sh_degree(sh):
+    nb = sh.shape[1]
+    deg = int(round(nb ** 0.5)) - 1
+    assert (deg + 1) ** 2 == nb and 0 <= deg <= 3 and sh.shape[2] == 3, sh.shape
+    return deg
+
+
+def sh_basis(deg, dirs):
+    """Real spherical harmonics of degree <= deg at unit directions [M, 3]:
+    (Y [M, B], dY/d(x, y, z) [M, B, 3]) of the Cartesian polynomials."""
+    lib = _load()
+    dirs = _f64(dirs).reshape(-1, 3)
+    nb = (deg + 1) ** 2
+    Y, G = np.zeros((len(dirs), 16)), np.zeros((len(dirs), 16, 3))
+    for i, d in enumerate(dirs):
+        lib.orc_sh_basis(deg, _ptr(np.ascontiguousarray(d)), _ptr(Y[i]), _ptr(G[i]))
+    return Y[:, :nb], G[:, :nb]
+
+
+def sh_colors(sh, means, cam):
+    """Per-surfel colours [N, 3] seen from ``cam``: max(0, sum_b sh[:, b] Y_b(d) + 1/2)."""
+    lib = _load()
+    shc, m = _f64(sh), _f64(means)
+    out = np.zeros((m.shape[0], 3))
+    lib.orc_sh_colors(m.shape[0], _sh_degree(shc), _ptr(shc), _ptr(m), C.byref(make_cam(cam)), _ptr(out))
+    return out
 
 
 def query_labels(f_ins, means, f_q, p_q, prec):

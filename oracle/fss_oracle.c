@@ -54,6 +54,7 @@
  *     selected surfels' share of the pixel becomes 1), which the paper does
  *     not use and the GPU path offers as an option.
  */
+#define _GNU_SOURCE
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -1339,6 +1340,152 @@ void orc_query_labels(int64_t N, int32_t nq, int32_t dim, const double *f_ins, c
             sum += l[q];
         }
         for (int q = 0; q < nq; ++q) l[q] /= sum;
+    }
+}
+
+/* ================================================================== */
+/* 7. view-dependent colour: real spherical harmonics (Sec. 3.1)        */
+/* ================================================================== */
+
+/*
+ * The surfel colour c_i is view dependent (Sec. 3.1).  Reading: as in the
+ * 2DGS/3DGS base models, real spherical harmonics of degree <= 3 of the
+ * unit direction d from the camera centre to the surfel centre, plus 1/2,
+ * clamped at 0 per channel:  c = max(0, sum_b k_b Y_b(d) + 1/2).
+ * Basis index b = l^2 + l + m.  Real harmonics without the Condon-Shortley
+ * sign, written in Cartesian form on the unit sphere from the textbook
+ * definition: with A_m + i B_m = (x + i y)^m and L_l^m = d^m P_l / dz^m
+ * (P_l the Legendre polynomial),
+ *   Y_l0  = n_l0 P_l(z),
+ *   Y_lm  = sqrt(2) n_lm L_l^m(z) A_m(x, y),   m > 0,
+ *   Y_l-m = sqrt(2) n_lm L_l^m(z) B_m(x, y),   m > 0,
+ * n_lm = sqrt((2l + 1) / (4 pi) (l - m)! / (l + m)!).
+ * grad[b][3] (optional) = the partial derivatives of that polynomial in
+ * (x, y, z), for the chain rule through the direction.
+ */
+static void legendre_poly(int l, double c[4])  /* coefficients of P_l, ascending powers */
+{
+    double p0[4] = {1, 0, 0, 0}, p1[4] = {0, 1, 0, 0};
+    if (l == 0) { memcpy(c, p0, sizeof p0); return; }
+    for (int k = 1; k < l; ++k) { /* (k+1) P_{k+1} = (2k+1) z P_k - k P_{k-1} */
+        double p2[4] = {0, 0, 0, 0};
+        for (int j = 0; j < 3; ++j) p2[j + 1] += (2 * k + 1) * p1[j];
+        for (int j = 0; j < 4; ++j) p2[j] = (p2[j] - k * p0[j]) / (k + 1);
+        memcpy(p0, p1, sizeof p1);
+        memcpy(p1, p2, sizeof p2);
+    }
+    memcpy(c, p1, sizeof p1);
+}
+
+static double poly_deriv_eval(const double c[4], int m, double z)  /* d^m/dz^m of the polynomial at z */
+{
+    double d[4];
+    memcpy(d, c, sizeof d);
+    for (int k = 0; k < m; ++k) {
+        for (int j = 0; j < 3; ++j) d[j] = (j + 1) * d[j + 1];
+        d[3] = 0.0;
+    }
+    return ((d[3] * z + d[2]) * z + d[1]) * z + d[0];
+}
+
+static double factorial(int n) { double f = 1.0; for (int k = 2; k <= n; ++k) f *= k; return f; }
+
+void orc_sh_basis(int deg, const double dir[3], double *Y, double *grad)
+{
+    const double x = dir[0], y = dir[1], z = dir[2];
+    double A[5], B[5]; /* (x + i y)^m */
+    A[0] = 1.0; B[0] = 0.0;
+    for (int m = 1; m <= 4; ++m) { A[m] = x * A[m - 1] - y * B[m - 1]; B[m] = x * B[m - 1] + y * A[m - 1]; }
+    for (int l = 0; l <= deg; ++l) {
+        double P[4];
+        legendre_poly(l, P);
+        for (int m = -l; m <= l; ++m) {
+            const int am = m < 0 ? -m : m, b = l * l + l + m;
+            const double n = sqrt((2 * l + 1) / (4.0 * M_PI) * factorial(l - am) / factorial(l + am)) *
+                             (am ? sqrt(2.0) : 1.0);
+            const double L = poly_deriv_eval(P, am, z), Lz = poly_deriv_eval(P, am + 1, z);
+            const double T = m > 0 ? A[am] : (m < 0 ? B[am] : 1.0);
+            /* d A_m / dx = m A_{m-1}, d A_m / dy = -m B_{m-1}; d B_m / dx = m B_{m-1}, d B_m / dy = m A_{m-1} */
+            double Tx = 0.0, Ty = 0.0;
+            if (m > 0) { Tx = am * A[am - 1]; Ty = -am * B[am - 1]; }
+            if (m < 0) { Tx = am * B[am - 1]; Ty = am * A[am - 1]; }
+            Y[b] = n * L * T;
+            if (grad) { grad[3 * b] = n * L * Tx; grad[3 * b + 1] = n * L * Ty; grad[3 * b + 2] = n * Lz * T; }
+        }
+    }
+}
+
+/* camera centre of a world-to-camera [R | t]: -R^T t */
+static void cam_centre(const orc_cam *cam, double C[3])
+{
+    for (int k = 0; k < 3; ++k)
+        C[k] = -(cam->viewmat[k] * cam->viewmat[3] + cam->viewmat[4 + k] * cam->viewmat[7] +
+                 cam->viewmat[8 + k] * cam->viewmat[11]);
+}
+
+/*
+ * Per-surfel colours for one camera: rgb[N, 3] = max(0, sum_b coef[N, B, 3]
+ * Y_b(d) + 1/2), d = (p - C) / |p - C|, B = (deg + 1)^2.
+ */
+void orc_sh_colors(int64_t N, int deg, const double *coef, const double *means, const orc_cam *cam, double *rgb)
+{
+    const int nb = (deg + 1) * (deg + 1);
+    double C[3];
+    cam_centre(cam, C);
+    for (int64_t i = 0; i < N; ++i) {
+        double v[3] = {means[3 * i] - C[0], means[3 * i + 1] - C[1], means[3 * i + 2] - C[2]};
+        const double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        const double d[3] = {v[0] / r, v[1] / r, v[2] / r};
+        double Y[16];
+        orc_sh_basis(deg, d, Y, NULL);
+        for (int ch = 0; ch < 3; ++ch) {
+            double c = 0.5;
+            for (int b = 0; b < nb; ++b) c += coef[(i * nb + b) * 3 + ch] * Y[b];
+            rgb[3 * i + ch] = c > 0.0 ? c : 0.0;
+        }
+    }
+}
+
+/*
+ * Chain rule of orc_sh_colors for upstream colour gradients g_rgb[N, 3] of
+ * one camera: adds dL/dcoef to g_coef[N, B, 3] and the direction term to
+ * g_means[N, 3] (d = v / |v| gives dd/dv = (I - d d^T) / |v|); a clamped
+ * channel passes nothing.  g_abs (optional, [N, 10] as in the render
+ * backward) gets the magnitude of the direction term's chain in its means
+ * columns.
+ */
+void orc_sh_backward(int64_t N, int deg, const double *coef, const double *means, const orc_cam *cam,
+                     const double *g_rgb, double *g_coef, double *g_means, double *g_abs)
+{
+    const int nb = (deg + 1) * (deg + 1);
+    double C[3];
+    cam_centre(cam, C);
+    for (int64_t i = 0; i < N; ++i) {
+        double v[3] = {means[3 * i] - C[0], means[3 * i + 1] - C[1], means[3 * i + 2] - C[2]};
+        const double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        const double d[3] = {v[0] / r, v[1] / r, v[2] / r};
+        double Y[16], G[48];
+        orc_sh_basis(deg, d, Y, G);
+        double gd[3] = {0, 0, 0}, gda[3] = {0, 0, 0};
+        for (int ch = 0; ch < 3; ++ch) {
+            double c = 0.5;
+            for (int b = 0; b < nb; ++b) c += coef[(i * nb + b) * 3 + ch] * Y[b];
+            if (!(c > 0.0)) continue;
+            const double g = g_rgb[3 * i + ch];
+            for (int b = 0; b < nb; ++b) {
+                g_coef[(i * nb + b) * 3 + ch] += Y[b] * g;
+                for (int k = 0; k < 3; ++k) {
+                    gd[k] += g * coef[(i * nb + b) * 3 + ch] * G[3 * b + k];
+                    gda[k] += fabs(g * coef[(i * nb + b) * 3 + ch] * G[3 * b + k]);
+                }
+            }
+        }
+        const double dot = d[0] * gd[0] + d[1] * gd[1] + d[2] * gd[2];
+        const double dota = fabs(d[0]) * gda[0] + fabs(d[1]) * gda[1] + fabs(d[2]) * gda[2];
+        for (int k = 0; k < 3; ++k) {
+            g_means[3 * i + k] += (gd[k] - d[k] * dot) / r;
+            if (g_abs) g_abs[10 * i + k] += (gda[k] + fabs(d[k]) * dota) / r;
+        }
     }
 }
 
