@@ -94,10 +94,21 @@ typedef struct {
                            the Top-K feature sum by the selected weights' sum, so the
                            selected surfels' weights add up to 1 (a variant; K = 0
                            rejects it) */
+    int32_t color_mode; /* FSS_COLOR_RGB: the rgb argument of the render calls is a
+                           per-surfel colour [N, 3]; FSS_COLOR_SH: it holds
+                           view-dependent colour coefficients [N, (sh_degree+1)^2, 3]
+                           of real spherical harmonics (Sec. 3.1's view-dependent
+                           colour): c = max(0, sum_b k_b Y_b(d) + 1/2), d the unit
+                           direction from the camera centre to the surfel centre,
+                           Y_b without the Condon-Shortley sign, b = l^2 + l + m;
+                           the backward's g_rgb then has the coefficients' shape and
+                           g_means gains the direction term */
+    int32_t sh_degree;  /* 0..3 (FSS_COLOR_SH) */
 } fss_params;
 
 enum { FSS_SCHED_GRID = 0, FSS_SCHED_PERSISTENT = 1 };
 enum { FSS_SELECT_TOPW = 0, FSS_SELECT_FRONT = 1 };
+enum { FSS_COLOR_RGB = 0, FSS_COLOR_SH = 1 };
 
 /* Fills the defaults listed above (tile 16, K 8, ACCU, TMIN, F32, C 16, grid, TOPW, no renormalisation). */
 fss_status fss_default_params(fss_params *params);

@@ -18,6 +18,7 @@ FSS_BIN_AABB, FSS_BIN_SNUG, FSS_BIN_ACCU = 0, 1, 2
 FSS_STOP_TMIN, FSS_STOP_EXACT_TOPK = 0, 1
 FSS_F32, FSS_BF16 = 0, 1
 FSS_SCHED_GRID, FSS_SCHED_PERSISTENT = 0, 1
+FSS_COLOR_RGB, FSS_COLOR_SH = 0, 1
 FSS_SELECT_TOPW, FSS_SELECT_FRONT = 0, 1
 FSS_MAX_CAMS = 64
 FSS_MAX_K = 32
@@ -29,7 +30,9 @@ REG_STATUS, REG_REC, REG_BINREC, REG_COUNT, REG_RANGES, REG_LIST, REG_COUNTERS, 
 REG_SORTTMP, REG_GRAD_ITEM, REG_FEAT_ACC, REG_DOTS, REG_VIS, REG_UNB, REG_SLOT, REG_WIDE = range(8, 16)
 REG_MASK = 16
 REG_SLOT_SURF = 17
-N_REGIONS = 18
+REG_DIR = 18
+REG_COLOR = 19
+N_REGIONS = 20
 
 EXPORTS = ["fss_default_params", "fss_workspace_size", "fss_saved_size", "fss_project_bin", "fss_sort",
            "fss_render_forward", "fss_render_backward", "fss_read_status", "fss_last_error",
@@ -49,7 +52,7 @@ class fss_params(C.Structure):
                 ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("T_min", C.c_float),
                 ("feat_dtype", C.c_int32), ("out_dtype", C.c_int32), ("C", C.c_int32),
                 ("bg_rgb", C.c_float * 3), ("schedule", C.c_int32), ("select", C.c_int32),
-                ("renorm", C.c_int32)]
+                ("renorm", C.c_int32), ("color_mode", C.c_int32), ("sh_degree", C.c_int32)]
 
 
 class fss_aux_outputs(C.Structure):

@@ -33,6 +33,7 @@ UNITS = {
     "loss.cu": [],
     "static_scratch.cu": [],
     "query.cu": [],
+    "color.cu": [],
 }
 
 

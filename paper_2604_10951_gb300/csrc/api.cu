@@ -62,6 +62,10 @@ fss_status check_params(const fss_params* p) {
         return fail(FSS_ERR_INVALID_ARG, "select %d", p->select);
     if (p->renorm != 0 && p->renorm != 1) return fail(FSS_ERR_INVALID_ARG, "renorm %d", p->renorm);
     if (p->renorm && p->K == 0) return fail(FSS_ERR_INVALID_ARG, "renorm needs K > 0");
+    if (p->color_mode != FSS_COLOR_RGB && p->color_mode != FSS_COLOR_SH)
+        return fail(FSS_ERR_INVALID_ARG, "color_mode %d", p->color_mode);
+    if (p->color_mode == FSS_COLOR_SH && (p->sh_degree < 0 || p->sh_degree > 3))
+        return fail(FSS_ERR_UNSUPPORTED, "sh_degree %d not in [0,3]", p->sh_degree);
     return FSS_OK;
 }
 
@@ -105,6 +109,8 @@ RParams make_rparams(const fss_params* p, const Cams& cams, int64_t N, int64_t c
     r.feat_dtype = p->feat_dtype; r.out_dtype = p->out_dtype; r.C = p->C;
     r.select = p->select;
     r.renorm = p->renorm;
+    r.color_sh = p->color_mode == FSS_COLOR_SH;
+    r.sh_deg = r.color_sh ? p->sh_degree : 0;
     for (int k = 0; k < 3; ++k) r.bg[k] = p->bg_rgb[k];
     r.N = N;
     r.n_items = N * cams.n;
@@ -134,6 +140,8 @@ Layout make_layout(const RParams& P, const Cams& cams) {
     sz[REG_WIDE] = ni * 4;
     sz[REG_MASK] = cap * 4;
     sz[REG_SLOT_SURF] = N * 4;
+    sz[REG_DIR] = P.color_sh ? ni * 16 : 0;
+    sz[REG_COLOR] = P.color_sh ? ni * 12 : 0;
     size_t off = 0;
     for (int r = 0; r < REG_COUNT_ALL; ++r) {
         L.off[r] = off;
@@ -305,6 +313,11 @@ fss_status fss_project_bin(const fss_params* params, const fss_camera* cams, int
                                     ctx.at<float4>(REG_REC), stp, max_lines);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_emit");
     kernel_mark(st);
+    if (ctx.P.color_sh) {
+        e = launch_sh_dir(ctx.cams, ctx.P, ctx.at<uint32_t>(REG_VIS), ctx.at<uint32_t>(REG_WIDE),
+                          ctx.at<uint32_t>(REG_UNB), means, ctx.at<float4>(REG_DIR), stp, sms, st);
+        if (e != cudaSuccess) return cuda_fail(e, "k_sh_dir");
+    }
     return FSS_OK;
 }
 
@@ -353,7 +366,7 @@ fss_status fss_render_forward_aux(const fss_params* params, const fss_camera* ca
     a.ranges = ctx.at<int2>(REG_RANGES);
     a.list = ctx.at<uint32_t>(REG_LIST);
     a.masks = ctx.at<uint32_t>(REG_MASK);
-    a.rgb = rgb;
+    a.rgb = params->color_mode == FSS_COLOR_SH ? ctx.at<float>(REG_COLOR) : rgb;
     a.feats = feats;
     a.out_feat = out_feat;
     a.out_rgb = out_rgb;
@@ -374,6 +387,13 @@ fss_status fss_render_forward_aux(const fss_params* params, const fss_camera* ca
         cudaError_t e = cudaMemsetAsync(ctx.ws + ctx.L.off[REG_STATUS] + offsetof(Status, work), 0, sizeof(uint32_t),
                                         reinterpret_cast<cudaStream_t>(stream));
         if (e != cudaSuccess) return cuda_fail(e, "memset work queue");
+    }
+    if (ctx.P.color_sh && N > 0) {  // this frame's item colours from the coefficients
+        cudaError_t ec = launch_sh_color(ctx.cams, ctx.P, ctx.at<uint32_t>(REG_VIS), ctx.at<uint32_t>(REG_WIDE),
+                                         ctx.at<uint32_t>(REG_UNB), ctx.at<float4>(REG_DIR), rgb,
+                                         ctx.at<float>(REG_COLOR), a.st, num_sms_current(),
+                                         reinterpret_cast<cudaStream_t>(stream));
+        if (ec != cudaSuccess) return cuda_fail(ec, "k_sh_color");
     }
     cudaError_t e = launch_render_forward(ctx.cams, ctx.P, a, x, num_sms_current(), reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "render_forward");
@@ -405,7 +425,7 @@ fss_status fss_render_backward(const fss_params* params, const fss_camera* cams,
     a.ranges = ctx.at<int2>(REG_RANGES);
     a.list = ctx.at<uint32_t>(REG_LIST);
     a.masks = ctx.at<uint32_t>(REG_MASK);
-    a.rgb = rgb;
+    a.rgb = params->color_mode == FSS_COLOR_SH ? ctx.at<float>(REG_COLOR) : rgb;  // the forward's item colours
     a.feats = feats;
     const size_t px = (size_t)ctx.cams.total_pix;
     const unsigned char* sv = reinterpret_cast<const unsigned char*>(saved);
@@ -427,7 +447,8 @@ fss_status fss_render_backward(const fss_params* params, const fss_camera* cams,
     a.st = ctx.at<Status>(REG_STATUS);
     a.persistent = params->schedule == FSS_SCHED_PERSISTENT;
     if (N == 0) return FSS_OK;
-    cudaError_t e = launch_render_backward(ctx.cams, ctx.P, a, num_sms_current(), reinterpret_cast<cudaStream_t>(stream));
+    cudaError_t e = launch_render_backward(ctx.cams, ctx.P, a, params->color_mode == FSS_COLOR_SH ? rgb : nullptr,
+                                           num_sms_current(), reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "render_backward");
     return FSS_OK;
 }

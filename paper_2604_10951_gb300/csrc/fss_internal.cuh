@@ -39,6 +39,8 @@ struct RParams {
     int32_t feat_dtype, out_dtype, C;
     int32_t select;  // FSS_SELECT_TOPW | FSS_SELECT_FRONT
     int32_t renorm;  // Top-K features divided by the selected weights' sum
+    int32_t color_sh;  // colours per (view, surfel) item from spherical harmonics
+    int32_t sh_deg;
     float bg[3];
     int64_t N;
     int64_t n_items;
@@ -108,6 +110,8 @@ enum Region {
     REG_WIDE = 15,   // uint32 [items]: visible items spanning many tiles
     REG_MASK = 16,   // uint32 [pair_capacity]: per sorted pair, the warps of its tile it reaches
     REG_SLOT_SURF = 17,  // int32 [N]: surfel of each gradient slot
+    REG_DIR = 18,    // float4 [items] (spherical-harmonic colours only): unit direction from the camera, 1/distance
+    REG_COLOR = 19,  // float [items, 3] (spherical-harmonic colours only): each visible item's colour
     REG_COUNT_ALL
 };
 

@@ -110,7 +110,9 @@ struct BwdArgs {
     Status* st;
 };
 
-cudaError_t launch_render_backward(const Cams& cams, const RParams& P, const BwdArgs& a, int num_sms,
+// sh: spherical-harmonic colour coefficients [N, B, 3] (colour mode SH; a.rgb
+// then points at the forward's item colours), else NULL
+cudaError_t launch_render_backward(const Cams& cams, const RParams& P, const BwdArgs& a, const float* sh, int num_sms,
                                    cudaStream_t stream);
 
 // query-guided instance labels (query.cu): l_ins [N, nq] (F32 or BF16) from
@@ -120,6 +122,15 @@ size_t query_labels_smem(int nq, int dim);
 cudaError_t launch_query_labels(int64_t N, int nq, int dim, const void* f_ins, const float* means, const void* f_q,
                                 const float* p_q, const float* prec, void* out, int out_bf16, int32_t* err,
                                 int num_sms, cudaStream_t stream);
+
+// view-dependent colours (color.cu): item directions at binning, item colours
+// before the forward render
+cudaError_t launch_sh_dir(const Cams& cams, const RParams& P, const uint32_t* vis_list, const uint32_t* wide_list,
+                          const uint32_t* unb_list, const float* means, float4* dir, const Status* st, int num_sms,
+                          cudaStream_t stream);
+cudaError_t launch_sh_color(const Cams& cams, const RParams& P, const uint32_t* vis_list, const uint32_t* wide_list,
+                            const uint32_t* unb_list, const float4* dir, const float* coef, float* color,
+                            const Status* st, int num_sms, cudaStream_t stream);
 
 cudaError_t launch_loss(int64_t n_pix, int C, int dtype, const void* F, const float* rgb, const void* Ft,
                         const float* rgbt, float wf, float wc, void* dF, float* drgb, double* loss, int num_sms,

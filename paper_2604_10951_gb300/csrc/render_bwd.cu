@@ -23,6 +23,7 @@
 //             columns -> means, scales, quaternions; sums the views.
 // k_feat_out  writes every row of the feature gradient (zeros for surfels
 //             culled in every view).
+#include "color.cuh"
 #include "fss_internal.cuh"
 #include "kernels.cuh"
 #include "render_common.cuh"
@@ -350,7 +351,7 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
 // ---------------------------------------------------------------------------
 // k_bwd_geo: back-to-front replay (Top-K and full accumulation)
 // ---------------------------------------------------------------------------
-template <int TS, bool FULL, int CMAX, typename FT, bool RN>
+template <int TS, bool FULL, int CMAX, typename FT, bool RN, bool SH>
 __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cams cams,
                                                      const __grid_constant__ RParams P, const BwdArgs a) {
     constexpr int NT = TS * TS;
@@ -383,6 +384,9 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
     const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
     const int2 rg = a.ranges[t];
     const int64_t vbase = (int64_t)view * P.N;
+    // SH: the forward's item colours (a compile-time switch on the Top-K path,
+    // which keeps the plain instance's code as it is)
+    const float* __restrict__ rgbv = a.rgb + ((FULL ? P.color_sh : SH) ? 3 * vbase : 0);
     const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
     const FT* __restrict__ feats = reinterpret_cast<const FT*>(a.feats);
 
@@ -443,7 +447,7 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
             s_r1[j] = r[1];
             s_r2[j] = r[2];
             const int64_t sp = (int64_t)item - vbase;
-            s_oc[j] = make_float4(r[3].x, a.rgb[3 * sp], a.rgb[3 * sp + 1], a.rgb[3 * sp + 2]);
+            s_oc[j] = make_float4(r[3].x, rgbv[3 * sp], rgbv[3 * sp + 1], rgbv[3 * sp + 2]);
             s_wm[j] = a.masks[rg.x + b_start + j];
         }
         for (int i = tid; i < cnt * 16; i += NT) s_g[i] = 0.0f;
@@ -568,9 +572,19 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
 // ---------------------------------------------------------------------------
 // k_bwd_project: per surfel, d(adjugate rows) -> d(means, scales, quats)
 // ---------------------------------------------------------------------------
-// gradients of surfel s from its slot's per-view rows (slot < 0: zeros)
-__device__ __forceinline__ void project_grad(const Cams& cams, const RParams& P, const BwdArgs& a, int64_t s, int slot) {
+// gradients of surfel s from its slot's per-view rows (slot < 0: zeros).
+// SH: the colour gradient of each view goes to the spherical-harmonic
+// coefficients (g_rgb [N, B, 3], accumulated in place by the surfel's own
+// thread) and, through the view direction d = (p - o) / |p - o|, to the
+// means: dd/dp = (I - d d^T) / |p - o|; a clamped channel passes nothing.
+template <bool SH>
+__device__ __forceinline__ void project_grad(const Cams& cams, const RParams& P, const BwdArgs& a, const float* sh,
+                                             int64_t s, int slot) {
     float gm[3] = {0, 0, 0}, gs[2] = {0, 0}, gq[4] = {0, 0, 0, 0}, go = 0.0f, gc[3] = {0, 0, 0};
+    const int nb = (P.sh_deg + 1) * (P.sh_deg + 1);
+    float* gsh = SH && a.g_rgb ? a.g_rgb + s * nb * 3 : nullptr;
+    if (gsh)
+        for (int i = 0; i < nb * 3; ++i) gsh[i] = 0.0f;
     if (slot >= 0) {
         const float q0 = a.quats[4 * s], q1 = a.quats[4 * s + 1], q2 = a.quats[4 * s + 2], q3 = a.quats[4 * s + 3];
         const float qn = sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
@@ -588,6 +602,34 @@ __device__ __forceinline__ void project_grad(const Cams& cams, const RParams& P,
             const float g12 = gv[12];
             go += g2.y;
             gc[0] += g2.z; gc[1] += g2.w; gc[2] += g12;
+            if (SH && (g2.z != 0.f || g2.w != 0.f || g12 != 0.f)) {
+                float ox, oy, oz;
+                cam_centre(cams.c[v], ox, oy, oz);
+                const float vx = a.means[3 * s] - ox, vy = a.means[3 * s + 1] - oy, vz = a.means[3 * s + 2] - oz;
+                const float ir = rsqrtf(vx * vx + vy * vy + vz * vz);
+                const float dx = vx * ir, dy = vy * ir, dz = vz * ir;
+                float Y[16];
+                sh_basis(P.sh_deg, dx, dy, dz, Y);
+                const float* k = sh + s * nb * 3;
+                float gd[3] = {0.f, 0.f, 0.f};
+                for (int ch = 0; ch < 3; ++ch) {
+                    const float g = ch == 0 ? g2.z : (ch == 1 ? g2.w : g12);
+                    float c = 0.5f;
+                    for (int b = 0; b < nb; ++b) c = fmaf(k[3 * b + ch], Y[b], c);
+                    if (!(c > 0.0f) || g == 0.0f) continue;
+                    if (gsh)
+                        for (int b = 0; b < nb; ++b) gsh[3 * b + ch] = fmaf(Y[b], g, gsh[3 * b + ch]);
+                    float gx, gy, gz;
+                    sh_grad_dot(P.sh_deg, dx, dy, dz, k + ch, 3, gx, gy, gz);
+                    gd[0] = fmaf(g, gx, gd[0]);
+                    gd[1] = fmaf(g, gy, gd[1]);
+                    gd[2] = fmaf(g, gz, gd[2]);
+                }
+                const float dd = dx * gd[0] + dy * gd[1] + dz * gd[2];
+                gm[0] += (gd[0] - dx * dd) * ir;
+                gm[1] += (gd[1] - dy * dd) * ir;
+                gm[2] += (gd[2] - dz * dd) * ir;
+            }
             if (g0.x == 0.f && g0.y == 0.f && g0.z == 0.f && g0.w == 0.f && g1.x == 0.f && g1.y == 0.f &&
                 g1.z == 0.f && g1.w == 0.f && g2.x == 0.f)
                 continue;
@@ -673,22 +715,23 @@ __device__ __forceinline__ void project_grad(const Cams& cams, const RParams& P,
     if (a.g_scales) { a.g_scales[2 * s] = gs[0]; a.g_scales[2 * s + 1] = gs[1]; }
     if (a.g_quats) for (int k = 0; k < 4; ++k) a.g_quats[4 * s + k] = gq[k];
     if (a.g_opac) a.g_opac[s] = go;
-    if (a.g_rgb) { a.g_rgb[3 * s] = gc[0]; a.g_rgb[3 * s + 1] = gc[1]; a.g_rgb[3 * s + 2] = gc[2]; }
+    if (!SH && a.g_rgb) { a.g_rgb[3 * s] = gc[0]; a.g_rgb[3 * s + 1] = gc[1]; a.g_rgb[3 * s + 2] = gc[2]; }
 }
 
 // Zeros for surfels culled in every view (one thread each), then the chain
 // rule for the surfels that have a slot, densely over the slots (a few
 // percent of the surfels are visible, so a thread per surfel would leave
 // most lanes of a warp idle through the long path).
+template <bool SH>
 __global__ void __launch_bounds__(256) k_bwd_project(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
-                                                     const BwdArgs a) {
+                                                     const BwdArgs a, const float* __restrict__ sh) {
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
     const bool err = a.st->err != 0;
     for (int64_t s = gtid; s < P.N; s += gstride)
-        if (err || a.splat_slot[s] < 0) project_grad(cams, P, a, s, -1);
+        if (err || a.splat_slot[s] < 0) project_grad<SH>(cams, P, a, sh, s, -1);
     const int64_t ns = err ? 0 : (int64_t)a.st->nslot;
-    for (int64_t sl = gtid; sl < ns; sl += gstride) project_grad(cams, P, a, a.slot_surf[sl], (int)sl);
+    for (int64_t sl = gtid; sl < ns; sl += gstride) project_grad<SH>(cams, P, a, sh, a.slot_surf[sl], (int)sl);
 }
 
 // ---------------------------------------------------------------------------
@@ -793,17 +836,17 @@ cudaError_t launch_feat(const Cams& cams, const RParams& P, const BwdArgs& a, cu
     return go(k_bwd_feat<32, FT>);
 }
 
-template <int TS, bool FULL, int CMAX, typename FT, bool RN = false>
+template <int TS, bool FULL, int CMAX, typename FT, bool RN = false, bool SH = false>
 cudaError_t launch_geo_one(const Cams& cams, const RParams& P, const BwdArgs& a, cudaStream_t s) {
     constexpr int NB = FULL ? FBATCH : BB;
     const size_t smem = (size_t)NB * (4 * 16 + 8) + (size_t)NB * 16 * 4 + (FULL ? (size_t)NB * P.C * 8 : 0);  // staging, masks, partials, rows
-    cudaError_t e = set_smem((const void*)k_bwd_geo<TS, FULL, CMAX, FT, RN>, smem);
+    cudaError_t e = set_smem((const void*)k_bwd_geo<TS, FULL, CMAX, FT, RN, SH>, smem);
     if (e != cudaSuccess) return e;
     int grid = cams.total_tiles;
-    if (a.persistent && (e = persistent_grid((const void*)k_bwd_geo<TS, FULL, CMAX, FT, RN>, TS * TS, smem, grid)) !=
+    if (a.persistent && (e = persistent_grid((const void*)k_bwd_geo<TS, FULL, CMAX, FT, RN, SH>, TS * TS, smem, grid)) !=
                             cudaSuccess)
         return e;
-    k_bwd_geo<TS, FULL, CMAX, FT, RN><<<grid, TS * TS, smem, s>>>(cams, P, a);
+    k_bwd_geo<TS, FULL, CMAX, FT, RN, SH><<<grid, TS * TS, smem, s>>>(cams, P, a);
     e = cudaGetLastError();
     if (e == cudaSuccess) kernel_mark(s);
     return e;
@@ -811,15 +854,20 @@ cudaError_t launch_geo_one(const Cams& cams, const RParams& P, const BwdArgs& a,
 
 template <int TS, typename FT>
 cudaError_t launch_geo(const Cams& cams, const RParams& P, const BwdArgs& a, cudaStream_t s) {
-    if (P.K > 0)  // the renormalised variant has its own instance: no cost on the plain path
+    if (P.K > 0) {  // the renormalised and view-dependent-colour variants have their own instances
+        if (P.color_sh)
+            return P.renorm ? launch_geo_one<TS, false, 4, FT, true, true>(cams, P, a, s)
+                            : launch_geo_one<TS, false, 4, FT, false, true>(cams, P, a, s);
         return P.renorm ? launch_geo_one<TS, false, 4, FT, true>(cams, P, a, s) : launch_geo_one<TS, false, 4, FT>(cams, P, a, s);
+    }
     if (P.C <= 32) return launch_geo_one<TS, true, 32, FT>(cams, P, a, s);
     if (P.C <= 64) return launch_geo_one<TS, true, 64, FT>(cams, P, a, s);
     return launch_geo_one<TS, true, 128, FT>(cams, P, a, s);
 }
 
 template <typename FT>
-cudaError_t launch_all(const Cams& cams, const RParams& P, const BwdArgs& a, int num_sms, cudaStream_t s) {
+cudaError_t launch_all(const Cams& cams, const RParams& P, const BwdArgs& a, const float* sh, int num_sms,
+                       cudaStream_t s) {
     cudaError_t e;
     k_bwd_clear<<<num_sms * 4, 256, 0, s>>>(cams, P, a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -832,7 +880,10 @@ cudaError_t launch_all(const Cams& cams, const RParams& P, const BwdArgs& a, int
     else e = launch_geo<32, FT>(cams, P, a, s);
     if (e != cudaSuccess) return e;
     const int64_t nb = (P.N + 255) / 256;
-    k_bwd_project<<<(unsigned)std::max<int64_t>(1, nb), 256, 0, s>>>(cams, P, a);
+    if (P.color_sh)
+        k_bwd_project<true><<<(unsigned)std::max<int64_t>(1, nb), 256, 0, s>>>(cams, P, a, sh);
+    else
+        k_bwd_project<false><<<(unsigned)std::max<int64_t>(1, nb), 256, 0, s>>>(cams, P, a, nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     kernel_mark(s);
     if (a.g_feat) {
@@ -845,10 +896,10 @@ cudaError_t launch_all(const Cams& cams, const RParams& P, const BwdArgs& a, int
 
 }  // namespace
 
-cudaError_t launch_render_backward(const Cams& cams, const RParams& P, const BwdArgs& a, int num_sms,
+cudaError_t launch_render_backward(const Cams& cams, const RParams& P, const BwdArgs& a, const float* sh, int num_sms,
                                    cudaStream_t stream) {
-    if (P.feat_dtype == FSS_BF16) return launch_all<__nv_bfloat16>(cams, P, a, num_sms, stream);
-    return launch_all<float>(cams, P, a, num_sms, stream);
+    if (P.feat_dtype == FSS_BF16) return launch_all<__nv_bfloat16>(cams, P, a, sh, num_sms, stream);
+    return launch_all<float>(cams, P, a, sh, num_sms, stream);
 }
 
 }  // namespace fss

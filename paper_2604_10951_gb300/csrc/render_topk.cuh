@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : 1) k_r
         const int2 rg = a.ranges[t];
         const int n = rg.y - rg.x;
         const int64_t vbase = (int64_t)view * P.N;
+        const float* __restrict__ rgbv = a.rgb + (P.color_sh ? 3 * vbase : 0);  // SH: item colours
 
         float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
         bool done = !inside;
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : 1) k_r
                 s_r1[j] = r[1];
                 s_r2[j] = r[2];
                 const int64_t sp = (int64_t)item - vbase;
-                s_oc[j] = make_float4(r[3].x, a.rgb[3 * sp], a.rgb[3 * sp + 1], a.rgb[3 * sp + 2]);
+                s_oc[j] = make_float4(r[3].x, rgbv[3 * sp], rgbv[3 * sp + 1], rgbv[3 * sp + 2]);
                 s_wm[j] = a.masks[rg.x + b0 + j];
                 if (AUX) s_nrm[j] = facing_normal(r[2], r[0].w, r[1].w, cam);
             }

@@ -147,3 +147,20 @@ def test_query_label_arguments_are_checked_on_the_host(lib):
     assert lib.fss_query_labels(10, 32, 32, z, z, z, z, z, z, L.FSS_F32, None, None) == L.FSS_ERR_INVALID_ARG
     assert lib.fss_query_labels(10, 32, 32, C.c_void_p(24), z, z, z, z, z, L.FSS_F32, z, None) == L.FSS_ERR_INVALID_ARG
     assert "aligned" in L.last_error()
+
+
+def test_colour_mode_arguments(lib):
+    out = C.c_size_t()
+    p = L.fss_default_params()
+    assert (p.color_mode, p.sh_degree) == (L.FSS_COLOR_RGB, 0)
+    p.color_mode = 2
+    assert lib.fss_workspace_size(C.byref(p), _cam(), 1, 10, 10, C.byref(out)) == L.FSS_ERR_INVALID_ARG
+    p.color_mode, p.sh_degree = L.FSS_COLOR_SH, 4
+    assert lib.fss_workspace_size(C.byref(p), _cam(), 1, 10, 10, C.byref(out)) == L.FSS_ERR_UNSUPPORTED
+    p.sh_degree = 3
+    assert lib.fss_workspace_size(C.byref(p), _cam(), 1, 1000, 10, C.byref(out)) == L.FSS_OK
+    ws_sh = out.value
+    p.color_mode = L.FSS_COLOR_RGB
+    lib.fss_workspace_size(C.byref(p), _cam(), 1, 1000, 10, C.byref(out))
+    # the colour mode adds a direction (16 B) and a colour (12 B) per item
+    assert ws_sh - out.value >= 1000 * 28
