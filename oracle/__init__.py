@@ -28,6 +28,7 @@ AABB, SNUG, ACCU = 0, 1, 2
 TMIN, EXACT_TOPK = 0, 1
 FLAG_ALPHA, FLAG_TMIN, FLAG_TIE, FLAG_EXACT, FLAG_NEAR, FLAG_CLAMP, FLAG_GRAZE = 1, 2, 4, 8, 16, 32, 64
 FLAG_MEDIAN = 128
+FLAG_LOWPASS = 256
 
 
 class OrcCam(C.Structure):
@@ -40,7 +41,7 @@ class OrcParams(C.Structure):
     _fields_ = [("tile_size", C.c_int32), ("K", C.c_int32), ("bin_mode", C.c_int32),
                 ("stop_rule", C.c_int32), ("alpha_min", C.c_float), ("alpha_max", C.c_float),
                 ("T_min", C.c_float), ("bg", C.c_float * 3), ("C", C.c_int32), ("select", C.c_int32),
-                ("renorm", C.c_int32)]
+                ("renorm", C.c_int32), ("lowpass", C.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -127,13 +128,13 @@ def make_cam(cam) -> OrcCam:
 
 
 def make_params(tile_size=16, K=0, bin_mode=ACCU, stop_rule=TMIN, alpha_min=1.0 / 255.0,
-                alpha_max=0.99, T_min=1e-4, bg=(0.0, 0.0, 0.0), C=0, select=0, renorm=0) -> OrcParams:
+                alpha_max=0.99, T_min=1e-4, bg=(0.0, 0.0, 0.0), C=0, select=0, renorm=0, lowpass=0) -> OrcParams:
     p = OrcParams()
     p.tile_size, p.K, p.bin_mode, p.stop_rule = int(tile_size), int(K), int(bin_mode), int(stop_rule)
     p.alpha_min, p.alpha_max, p.T_min = float(np.float32(alpha_min)), float(alpha_max), float(T_min)
     for k in range(3):
         p.bg[k] = float(bg[k])
-    p.C, p.select, p.renorm = int(C), int(select), int(renorm)
+    p.C, p.select, p.renorm, p.lowpass = int(C), int(select), int(renorm), int(lowpass)
     return p
 
 

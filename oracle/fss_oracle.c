@@ -83,6 +83,7 @@ typedef struct {
     int32_t C;
     int32_t select;    /* 0: K largest weights (Eq. 7); 1: first K in depth order */
     int32_t renorm;    /* K > 0: 1 divides the Top-K sum by the selected weights' sum */
+    int32_t lowpass;   /* 1: the 2DGS screen-space low-pass filter (see below) */
 } orc_params;
 
 enum { ORC_AABB = 0, ORC_SNUG = 1, ORC_ACCU = 2 };
@@ -97,7 +98,8 @@ enum {
     FLAG_NEAR = 16,  /* some |z_hit - near| < 1e-5                */
     FLAG_CLAMP = 32, /* some |o f(u) - alpha_max| < 1e-6          */
     FLAG_GRAZE = 64, /* contributor seen nearly edge-on           */
-    FLAG_MEDIAN = 128 /* some |T (1 - alpha) - 1/2| < 1e-6 (median depth) */
+    FLAG_MEDIAN = 128, /* some |T (1 - alpha) - 1/2| < 1e-6 (median depth) */
+    FLAG_LOWPASS = 256 /* low-pass: some |rho_obj - rho_screen| < 1e-6 (the derivative switches) */
 };
 
 #define DEG_EPS 1e-3 /* edge-on cull: |n . p_c| <= DEG_EPS |p_c| */
@@ -129,6 +131,7 @@ typedef struct {
     double z;        /* = pc[2] */
     double cosang;   /* n.p_c / |p_c| */
     double nf[3];    /* camera-space unit normal, turned to face the camera (n.p_c <= 0) */
+    double cxp, cyp; /* projected centre T (0, 0, 1) in pixels */
     int ok;          /* passes the FP64 cull rules */
 } geo64;
 
@@ -157,6 +160,8 @@ static void geometry64(const double *mean, const double *scale, const double *qu
         g->T[2][c] = cols[c][2];
     }
     g->z = g->pc[2];
+    g->cxp = g->T[0][2] / g->T[2][2];
+    g->cyp = g->T[1][2] / g->T[2][2];
     double pn = sqrt(g->pc[0] * g->pc[0] + g->pc[1] * g->pc[1] + g->pc[2] * g->pc[2]);
     g->cosang = (nc[0] * g->pc[0] + nc[1] * g->pc[1] + nc[2] * g->pc[2]) / pn;
     const double sgn = g->cosang > 0.0 ? -1.0 : 1.0;
@@ -248,6 +253,18 @@ static int ray_splat64(const double T[3][3], double x, double y, double near,
  *      b = B*Y + D; c = ((C*Y)*Y + (2E)*Y) + F; disc = max(b*b - A*c, 0);
  *      x = ((-b) -/+ sqrt(disc))/A; pixel columns
  *      [ceil((x_min + xc) - 0.5), floor((x_max + xc) - 0.5)] clipped to S17.
+ * Low-pass filter (lowpass = 1): the footprint also holds the screen disc
+ * 2 |x - c|^2 <= k^2 about the projected centre c = (xc, yc):
+ *  S5b' the S5b margins 0.5 become mg = 0.5 + sqrt(max(kk, 0) * 0.5)
+ *  S17b rd2 = kb * 0.5; rd = sqrt(rd2); disc pixel range
+ *      [ceil((xc - rd) - 0.5), floor((xc + rd) - 0.5)] (same for y), clamped
+ *      to the image; the S17 range becomes the union of the ellipse's (when
+ *      S16 keeps it and its range is not empty) and the disc's; cull only if
+ *      both are empty
+ *  S20b per strip [Ya, Yb] (local): Yn = Ya if Ya > 0, Yb if Yb < 0, else 0;
+ *      if Yn*Yn <= rd2: hw = sqrt(rd2 - Yn*Yn), pixel columns
+ *      [ceil(((-hw) + xc) - 0.5), floor((hw + xc) - 0.5)]; the strip's
+ *      interval is the hull of the ellipse's and the disc's (columns alike).
  * k^2 only has to be identical on both sides (binning adds a 2^-10 slack);
  * the series is accurate to a few ulp, far inside that slack.
  */
@@ -261,6 +278,9 @@ typedef struct {
     float X0, Y0, hx, hy;
     int px0, px1, py0, py1;
     int tx0, tx1, ty0, ty1;
+    int ell;         /* the ellipse range is not empty (always, without the low-pass filter) */
+    int lowpass;
+    float rd2;       /* low-pass screen disc radius^2 (pixels) */
 } mirror_rec;
 
 /* natural logarithm of x > 0 in binary32 (S6): ln x = e ln 2 + 2 atanh(s) */
@@ -447,7 +467,11 @@ static void mirror_project(const float *mean, const float *scale, const float *q
             a = cam->fx * uxmin; const float pxmin = a + cam->cx;
             a = cam->fy * uymax; const float pymax = a + cam->cy;
             a = cam->fy * uymin; const float pymin = a + cam->cy;
-            if (pxmax < -0.5f || pxmin > (float)W + 0.5f || pymax < -0.5f || pymin > (float)H + 0.5f) return;
+            float mg = 0.5f;
+            if (p->lowpass) { /* S5b' */
+                float rk = fmaxf(kk, 0.0f); rk = rk * 0.5f; rk = sqrtf(rk); mg = mg + rk;
+            }
+            if (pxmax < -mg || pxmin > (float)W + mg || pymax < -mg || pymin > (float)H + mg) return;
         }
     }
     /* S14 */
@@ -457,20 +481,42 @@ static void mirror_project(const float *mean, const float *scale, const float *q
     r->A = q[0]; r->B = q[1]; r->C = q[2]; r->D = q[3]; r->E = q[4]; r->F = q[5];
     /* S15 */
     a = q[0] * q[2]; b = q[1] * q[1]; a = a - b;
+    r->lowpass = p->lowpass;
     if (!(q[0] > 0.0f && a > 0.0f)) {
         r->unbounded = 1;
         r->px0 = 0; r->px1 = W - 1; r->py0 = 0; r->py1 = H - 1;
     } else {
-        /* S16 */
-        if (!ellipse_f(q, &r->X0, &r->Y0, &r->hx, &r->hy)) return;
-        /* S17 */
-        float lo, hi;
-        lo = r->X0 - r->hx; lo = lo + r->xc; lo = lo - 0.5f;
-        hi = r->X0 + r->hx; hi = hi + r->xc; hi = hi - 0.5f;
-        if (!pix_range(lo, hi, W, &r->px0, &r->px1)) return;
-        lo = r->Y0 - r->hy; lo = lo + r->yc; lo = lo - 0.5f;
-        hi = r->Y0 + r->hy; hi = hi + r->yc; hi = hi - 0.5f;
-        if (!pix_range(lo, hi, H, &r->py0, &r->py1)) return;
+        /* S16, S17 */
+        int e0 = 0, e1 = 0, f0 = 0, f1 = 0;
+        r->ell = ellipse_f(q, &r->X0, &r->Y0, &r->hx, &r->hy);
+        if (r->ell) {
+            float lo, hi;
+            lo = r->X0 - r->hx; lo = lo + r->xc; lo = lo - 0.5f;
+            hi = r->X0 + r->hx; hi = hi + r->xc; hi = hi - 0.5f;
+            r->ell = pix_range(lo, hi, W, &e0, &e1);
+            lo = r->Y0 - r->hy; lo = lo + r->yc; lo = lo - 0.5f;
+            hi = r->Y0 + r->hy; hi = hi + r->yc; hi = hi - 0.5f;
+            r->ell = r->ell && pix_range(lo, hi, H, &f0, &f1);
+        }
+        int disc = 0, g0 = 0, g1 = 0, h0 = 0, h1 = 0;
+        if (p->lowpass) { /* S17b */
+            r->rd2 = kb * 0.5f;
+            const float rd = sqrtf(r->rd2);
+            float lo, hi;
+            lo = r->xc - rd; lo = lo - 0.5f; hi = r->xc + rd; hi = hi - 0.5f;
+            disc = pix_range(lo, hi, W, &g0, &g1);
+            lo = r->yc - rd; lo = lo - 0.5f; hi = r->yc + rd; hi = hi - 0.5f;
+            disc = disc && pix_range(lo, hi, H, &h0, &h1);
+        }
+        if (!r->ell && !disc) return;
+        if (r->ell && disc) {
+            r->px0 = e0 < g0 ? e0 : g0; r->px1 = e1 > g1 ? e1 : g1;
+            r->py0 = f0 < h0 ? f0 : h0; r->py1 = f1 > h1 ? f1 : h1;
+        } else if (r->ell) {
+            r->px0 = e0; r->px1 = e1; r->py0 = f0; r->py1 = f1;
+        } else {
+            r->px0 = g0; r->px1 = g1; r->py0 = h0; r->py1 = h1;
+        }
     }
     r->visible = 1;
     /* S18 */
@@ -500,6 +546,25 @@ static void mirror_project(const float *mean, const float *scale, const float *q
     }
 }
 
+/* S20b: pixel interval [*a, *b] (clipped to [lo_clip, hi_clip]) of the
+ * screen disc of radius^2 rd2 about the local origin on the strip [Sa, Sb]
+ * of the other coordinate; *a > *b when it misses the strip */
+static void disc_strip(float rd2, float Sa, float Sb, float origin, int lo_clip, int hi_clip, int *a, int *b)
+{
+    *a = 1; *b = 0;
+    float Sn = Sa > 0.0f ? Sa : (Sb < 0.0f ? Sb : 0.0f);
+    float s2 = Sn * Sn;
+    if (!(s2 <= rd2)) return;
+    float t = rd2 - s2;
+    float hw = sqrtf(t);
+    float lo = -hw; lo = lo + origin; lo = lo - 0.5f;
+    float hi = hw + origin; hi = hi - 0.5f;
+    float fl = ceilf(lo), fh = floorf(hi);
+    if (!(fl <= fh) || fh < (float)lo_clip || fl > (float)hi_clip) return;
+    *a = fl < (float)lo_clip ? lo_clip : (int)fl;
+    *b = fh > (float)hi_clip ? hi_clip : (int)fh;
+}
+
 /* S20, outer loop over tile rows: tile-column interval of row ty */
 static int accu_row(const mirror_rec *r, int ts, int ty, int *ta, int *tb)
 {
@@ -509,6 +574,13 @@ static int accu_row(const mirror_rec *r, int ts, int ty, int *ta, int *tb)
     const float A = r->A, B = r->B, C = r->C, D = r->D, E = r->E, F = r->F;
     float Ya = (float)ra + 0.5f; Ya = Ya - r->yc;
     float Yb = (float)rb + 0.5f; Yb = Yb - r->yc;
+    int da = 0, db = -1; /* S20b: the disc's pixel columns on this strip */
+    if (r->lowpass) disc_strip(r->rd2, Ya, Yb, r->xc, r->px0, r->px1, &da, &db);
+    if (!r->ell) {
+        if (da > db) return 0;
+        *ta = da / ts; *tb = db / ts;
+        return 1;
+    }
     float ext[2];
     for (int side = 0; side < 2; ++side) {
         float Xs = side == 0 ? r->X0 - r->hx : r->X0 + r->hx;
@@ -528,10 +600,16 @@ static int accu_row(const mirror_rec *r, int ts, int ty, int *ta, int *tb)
     float lo = ext[0] + r->xc; lo = lo - 0.5f;
     float hi = ext[1] + r->xc; hi = hi - 0.5f;
     float fl = ceilf(lo), fh = floorf(hi);
-    if (!(fl <= fh)) return 0;
-    if (fh < (float)r->px0 || fl > (float)r->px1) return 0;
-    int a = fl < (float)r->px0 ? r->px0 : (int)fl;
-    int b = fh > (float)r->px1 ? r->px1 : (int)fh;
+    int a = 1, b = 0;
+    if (fl <= fh && !(fh < (float)r->px0 || fl > (float)r->px1)) {
+        a = fl < (float)r->px0 ? r->px0 : (int)fl;
+        b = fh > (float)r->px1 ? r->px1 : (int)fh;
+    }
+    if (da <= db) {
+        if (a > b) { a = da; b = db; }
+        else { a = a < da ? a : da; b = b > db ? b : db; }
+    }
+    if (a > b) return 0;
     *ta = a / ts; *tb = b / ts;
     return 1;
 }
@@ -545,6 +623,13 @@ static int accu_col(const mirror_rec *r, int ts, int tx, int *ta, int *tb)
     const float A = r->A, B = r->B, C = r->C, D = r->D, E = r->E, F = r->F;
     float Xa = (float)ca + 0.5f; Xa = Xa - r->xc;
     float Xb = (float)cb + 0.5f; Xb = Xb - r->xc;
+    int da = 0, db = -1; /* S20b: the disc's pixel rows on this strip */
+    if (r->lowpass) disc_strip(r->rd2, Xa, Xb, r->yc, r->py0, r->py1, &da, &db);
+    if (!r->ell) {
+        if (da > db) return 0;
+        *ta = da / ts; *tb = db / ts;
+        return 1;
+    }
     float ext[2];
     for (int side = 0; side < 2; ++side) {
         float Ys = side == 0 ? r->Y0 - r->hy : r->Y0 + r->hy;
@@ -564,10 +649,16 @@ static int accu_col(const mirror_rec *r, int ts, int tx, int *ta, int *tb)
     float lo = ext[0] + r->yc; lo = lo - 0.5f;
     float hi = ext[1] + r->yc; hi = hi - 0.5f;
     float fl = ceilf(lo), fh = floorf(hi);
-    if (!(fl <= fh)) return 0;
-    if (fh < (float)r->py0 || fl > (float)r->py1) return 0;
-    int a = fl < (float)r->py0 ? r->py0 : (int)fl;
-    int b = fh > (float)r->py1 ? r->py1 : (int)fh;
+    int a = 1, b = 0;
+    if (fl <= fh && !(fh < (float)r->py0 || fl > (float)r->py1)) {
+        a = fl < (float)r->py0 ? r->py0 : (int)fl;
+        b = fh > (float)r->py1 ? r->py1 : (int)fh;
+    }
+    if (da <= db) {
+        if (a > b) { a = da; b = db; }
+        else { a = a < da ? a : da; b = b > db ? b : db; }
+    }
+    if (a > b) return 0;
     *ta = a / ts; *tb = b / ts;
     return 1;
 }
@@ -708,8 +799,10 @@ typedef struct {
     int32_t id;     /* surfel index */
     double alpha, T, w;
     double u, v, oG; /* for gradients */
-    double zh;       /* camera depth of the ray-surfel hit */
+    double zh;       /* camera depth of the ray-surfel hit (low-pass screen term: of the centre) */
     double hx[3], hy[3], c[3];
+    int scr;         /* low-pass: the screen-space term gave alpha */
+    double sx, sy;   /* pixel point minus the projected centre */
 } contrib_t;
 
 typedef struct {
@@ -752,12 +845,25 @@ static void composite_pixel(const geo64 *geo, const double *opac, const double *
         if (K > 0 && p->stop_rule == ORC_EXACT && p->select == 1 && n == K) break;
         const int32_t id = cand[j];
         const geo64 *g = &geo[id];
-        double u, v, zh, hx[3], hy[3], c[3];
+        double u = 0.0, v = 0.0, zh = 0.0, hx[3], hy[3], c[3];
         ++n_eval;
-        if (!ray_splat64(g->T, px, py, -INFINITY, &u, &v, &zh, hx, hy, c)) continue;
+        const int obj = ray_splat64(g->T, px, py, -INFINITY, &u, &v, &zh, hx, hy, c);
+        double rho = obj ? u * u + v * v : INFINITY;
+        int scr = 0;
+        const double sx = px - g->cxp, sy = py - g->cyp;
+        if (p->lowpass) {
+            /* 2DGS low-pass filter: the larger of the object-space Gaussian and
+             * a screen-space one of variance 1/2 pixel^2 about the projected
+             * centre, rho = min(u^2 + v^2, 2 |x - c|^2); the screen term takes
+             * the centre's depth */
+            const double rs = 2.0 * (sx * sx + sy * sy);
+            if (obj && fabs(rho - rs) < 1e-6) flags |= FLAG_LOWPASS;
+            if (!(rho <= rs)) { rho = rs; zh = g->z; scr = 1; }
+        } else if (!obj) {
+            continue;
+        }
         if (fabs(zh - cam->near_plane) < 1e-5) flags |= FLAG_NEAR;
         if (!(zh > cam->near_plane)) continue;
-        double rho = u * u + v * v;
         double oG = opac[id] * exp(-0.5 * rho);
         if (fabs(oG - amin) < 1e-6) flags |= FLAG_ALPHA;
         if (fabs(oG - amax) < 1e-6) flags |= FLAG_CLAMP;
@@ -770,6 +876,7 @@ static void composite_pixel(const geo64 *geo, const double *opac, const double *
         contrib_t *e = &cb[n++];
         e->pos = j; e->id = id; e->alpha = alpha; e->T = T; e->w = alpha * T;
         e->u = u; e->v = v; e->oG = oG; e->zh = zh;
+        e->scr = scr; e->sx = sx; e->sy = sy;
         memcpy(e->hx, hx, sizeof hx); memcpy(e->hy, hy, sizeof hy); memcpy(e->c, c, sizeof c);
         if (fabs(g->cosang) < 2e-3) flags |= FLAG_GRAZE;
         for (int k = 0; k < 3; ++k) rgbacc[k] += e->w * rgb[3 * id + k];
@@ -1100,6 +1207,23 @@ void orc_render_backward(int64_t N, const double *means, const double *scales, c
                 g_opac[id] += dal * G;
                 if (g_abs) g_abs[10 * (int64_t)id + 9] += dala * G;
                 double drho = dal * (-0.5 * e->oG);
+                if (e->scr) {
+                    /* screen term: rho = 2 |x - c|^2 with c = (T1_2, T2_2) / Tw_2 */
+                    const geo64 *gg = &sp.geo[id];
+                    const double dcx = -4.0 * e->sx * drho, dcy = -4.0 * e->sy * drho, w2 = gg->T[2][2];
+                    double *d = dT + 9 * (int64_t)id;
+                    d[2] += dcx / w2;
+                    d[5] += dcy / w2;
+                    d[8] -= (dcx * gg->T[0][2] + dcy * gg->T[1][2]) / (w2 * w2);
+                    if (dTa) {
+                        const double ra = dala * 0.5 * e->oG, ax = 4.0 * fabs(e->sx) * ra, ay = 4.0 * fabs(e->sy) * ra;
+                        double *da = dTa + 9 * (int64_t)id;
+                        da[2] += ax / fabs(w2);
+                        da[5] += ay / fabs(w2);
+                        da[8] += (ax * fabs(gg->T[0][2]) + ay * fabs(gg->T[1][2])) / (w2 * w2);
+                    }
+                    continue;
+                }
                 double du = 2.0 * e->u * drho, dv = 2.0 * e->v * drho;
                 double gcv[3] = {du / e->c[2], dv / e->c[2], -(du * e->u + dv * e->v) / e->c[2]};
                 double dhx[3], dhy[3];
@@ -1274,9 +1398,17 @@ int64_t orc_check_conservative(int64_t N, const float *means, const float *scale
             if (q[0] > 0 && gg > 0) {
                 double X0 = (q[1] * q[4] - q[2] * q[3]) / gg, Y0 = (q[1] * q[3] - q[0] * q[4]) / gg;
                 double Fp = q[5] + q[3] * X0 + q[4] * Y0;
-                if (Fp >= 0) continue;
-                double hxx = sqrt(-Fp * q[2] / gg) + 2.0, hyy = sqrt(-Fp * q[0] / gg) + 2.0;
-                double lx = floor(X0 - hxx), hxp = ceil(X0 + hxx), ly = floor(Y0 - hyy), hyp = ceil(Y0 + hyy);
+                double lx = 1e30, hxp = -1e30, ly = 1e30, hyp = -1e30;
+                if (Fp < 0) {
+                    double hxx = sqrt(-Fp * q[2] / gg) + 2.0, hyy = sqrt(-Fp * q[0] / gg) + 2.0;
+                    lx = floor(X0 - hxx); hxp = ceil(X0 + hxx); ly = floor(Y0 - hyy); hyp = ceil(Y0 + hyy);
+                }
+                if (p->lowpass) { /* the screen disc 2 |x - c|^2 <= k^2, widened */
+                    double rr = sqrt(log(opac[i] / (double)p->alpha_min)) + 2.0;
+                    lx = fmin(lx, floor(g.cxp - rr)); hxp = fmax(hxp, ceil(g.cxp + rr));
+                    ly = fmin(ly, floor(g.cyp - rr)); hyp = fmax(hyp, ceil(g.cyp + rr));
+                }
+                if (lx > hxp) continue;
                 if (hxp < 0 || lx > W - 1 || hyp < 0 || ly > H - 1) continue;
                 x0 = lx < 0 ? 0 : (int)lx; x1 = hxp > W - 1 ? W - 1 : (int)hxp;
                 y0 = ly < 0 ? 0 : (int)ly; y1 = hyp > H - 1 ? H - 1 : (int)hyp;
@@ -1284,9 +1416,17 @@ int64_t orc_check_conservative(int64_t N, const float *means, const float *scale
         }
         for (int py = y0; py <= y1; ++py)
             for (int px = x0; px <= x1; ++px) {
-                double u, v, zh, hx[3], hy[3], c[3];
-                if (!ray_splat64(g.T, px + 0.5, py + 0.5, cam->near_plane, &u, &v, &zh, hx, hy, c)) continue;
-                double a = opac[i] * exp(-0.5 * (u * u + v * v));
+                double u = 0.0, v = 0.0, zh = 0.0, hx[3], hy[3], c[3];
+                const int obj = ray_splat64(g.T, px + 0.5, py + 0.5, -INFINITY, &u, &v, &zh, hx, hy, c);
+                double rho = obj ? u * u + v * v : INFINITY;
+                if (p->lowpass) {
+                    const double sx = px + 0.5 - g.cxp, sy = py + 0.5 - g.cyp, rs = 2.0 * (sx * sx + sy * sy);
+                    if (!(rho <= rs)) { rho = rs; zh = g.z; }
+                } else if (!obj) {
+                    continue;
+                }
+                if (!(zh > cam->near_plane)) continue;
+                double a = opac[i] * exp(-0.5 * rho);
                 if (a < p->alpha_min) continue;
                 ++checked;
                 if (!mark[(py / ts) * tiles_x + px / ts]) ++bad;
