@@ -104,6 +104,10 @@ typedef struct {
                            the backward's g_rgb then has the coefficients' shape and
                            g_means gains the direction term */
     int32_t sh_degree;  /* 0..3 (FSS_COLOR_SH) */
+    int32_t lowpass;    /* 1: the 2DGS screen-space low-pass filter, alpha = o exp(-rho/2)
+                           with rho = min(u^2 + v^2, 2 |x - c|^2), c the projected
+                           centre (the screen term takes the centre's depth); the
+                           binning adds the screen disc 2 |x - c|^2 <= k^2 */
 } fss_params;
 
 enum { FSS_SCHED_GRID = 0, FSS_SCHED_PERSISTENT = 1 };

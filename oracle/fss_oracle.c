@@ -99,7 +99,8 @@ enum {
     FLAG_CLAMP = 32, /* some |o f(u) - alpha_max| < 1e-6          */
     FLAG_GRAZE = 64, /* contributor seen nearly edge-on           */
     FLAG_MEDIAN = 128, /* some |T (1 - alpha) - 1/2| < 1e-6 (median depth) */
-    FLAG_LOWPASS = 256 /* low-pass: some |rho_obj - rho_screen| < 1e-6 (the derivative switches) */
+    FLAG_LOWPASS = 256 /* low-pass: some |rho_obj - rho_screen| < 1e-3 (the derivative switches; the
+                          binary32 centre moves rho_screen by up to ~1e-4 at a few pixels) */
 };
 
 #define DEG_EPS 1e-3 /* edge-on cull: |n . p_c| <= DEG_EPS |p_c| */
@@ -857,7 +858,7 @@ static void composite_pixel(const geo64 *geo, const double *opac, const double *
              * centre, rho = min(u^2 + v^2, 2 |x - c|^2); the screen term takes
              * the centre's depth */
             const double rs = 2.0 * (sx * sx + sy * sy);
-            if (obj && fabs(rho - rs) < 1e-6) flags |= FLAG_LOWPASS;
+            if (obj && fabs(rho - rs) < 1e-3) flags |= FLAG_LOWPASS;
             if (!(rho <= rs)) { rho = rs; zh = g->z; scr = 1; }
         } else if (!obj) {
             continue;

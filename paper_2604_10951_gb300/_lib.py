@@ -52,7 +52,8 @@ class fss_params(C.Structure):
                 ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("T_min", C.c_float),
                 ("feat_dtype", C.c_int32), ("out_dtype", C.c_int32), ("C", C.c_int32),
                 ("bg_rgb", C.c_float * 3), ("schedule", C.c_int32), ("select", C.c_int32),
-                ("renorm", C.c_int32), ("color_mode", C.c_int32), ("sh_degree", C.c_int32)]
+                ("renorm", C.c_int32), ("color_mode", C.c_int32), ("sh_degree", C.c_int32),
+                ("lowpass", C.c_int32)]
 
 
 class fss_aux_outputs(C.Structure):

@@ -62,6 +62,7 @@ fss_status check_params(const fss_params* p) {
         return fail(FSS_ERR_INVALID_ARG, "select %d", p->select);
     if (p->renorm != 0 && p->renorm != 1) return fail(FSS_ERR_INVALID_ARG, "renorm %d", p->renorm);
     if (p->renorm && p->K == 0) return fail(FSS_ERR_INVALID_ARG, "renorm needs K > 0");
+    if (p->lowpass != 0 && p->lowpass != 1) return fail(FSS_ERR_INVALID_ARG, "lowpass %d", p->lowpass);
     if (p->color_mode != FSS_COLOR_RGB && p->color_mode != FSS_COLOR_SH)
         return fail(FSS_ERR_INVALID_ARG, "color_mode %d", p->color_mode);
     if (p->color_mode == FSS_COLOR_SH && (p->sh_degree < 0 || p->sh_degree > 3))
@@ -109,6 +110,7 @@ RParams make_rparams(const fss_params* p, const Cams& cams, int64_t N, int64_t c
     r.feat_dtype = p->feat_dtype; r.out_dtype = p->out_dtype; r.C = p->C;
     r.select = p->select;
     r.renorm = p->renorm;
+    r.lowpass = p->lowpass;
     r.color_sh = p->color_mode == FSS_COLOR_SH;
     r.sh_deg = r.color_sh ? p->sh_degree : 0;
     for (int k = 0; k < 3; ++k) r.bg[k] = p->bg_rgb[k];

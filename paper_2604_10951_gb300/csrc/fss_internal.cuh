@@ -39,6 +39,7 @@ struct RParams {
     int32_t feat_dtype, out_dtype, C;
     int32_t select;  // FSS_SELECT_TOPW | FSS_SELECT_FRONT
     int32_t renorm;  // Top-K features divided by the selected weights' sum
+    int32_t lowpass;   // 2DGS screen-space low-pass filter
     int32_t color_sh;  // colours per (view, surfel) item from spherical harmonics
     int32_t sh_deg;
     float bg[3];
@@ -63,11 +64,14 @@ struct alignas(16) BinRec {
     float xc, yc;            // local origin (pixels)
     int16_t px0, px1, py0, py1;  // SnugBox pixel-centre range (inclusive)
     int16_t tx0, tx1, ty0, ty1;  // outer tile rectangle of the bin mode
-    int32_t flags;           // BR_VISIBLE | BR_UNBOUNDED
-    int32_t pad[3];
+    int32_t flags;           // BR_VISIBLE | BR_UNBOUNDED | BR_ELL | BR_LOWPASS
+    float rd2;               // low-pass filter: screen disc radius^2 (pixels^2)
+    int32_t pad[2];
 };
 static_assert(sizeof(BinRec) == 80, "BinRec layout");
-enum { BR_VISIBLE = 1, BR_UNBOUNDED = 2 };
+// BR_ELL: the cutoff ellipse has pixels (always set without the low-pass
+// filter); BR_LOWPASS: the screen disc of the low-pass filter joins it
+enum { BR_VISIBLE = 1, BR_UNBOUNDED = 2, BR_ELL = 4, BR_LOWPASS = 8 };
 
 // status block at the head of the workspace; everything from `counters` on
 // is cleared at the start of each frame, `err` only by fss_read_status

@@ -139,6 +139,31 @@ __device__ __forceinline__ bool pix_range(float lo, float hi, int n, int& a, int
     return a <= b;
 }
 
+// S20b: pixel interval [a, b] (clipped to [lo_clip, hi_clip]) of the
+// low-pass screen disc of radius^2 rd2 about the local origin on the strip
+// [Sa, Sb] of the other coordinate; a > b when it misses the strip
+__device__ __forceinline__ void disc_strip(float rd2, float Sa, float Sb, float origin, int lo_clip, int hi_clip,
+                                           int& a, int& b) {
+    a = 1;
+    b = 0;
+    const float Sn = Sa > 0.0f ? Sa : (Sb < 0.0f ? Sb : 0.0f);
+    const float s2 = fm(Sn, Sn);
+    if (!(s2 <= rd2)) return;
+    const float hw = fq(fs(rd2, s2));
+    const float fl = ceilf(fs(fa(-hw, origin), 0.5f)), fh = floorf(fs(fa(hw, origin), 0.5f));
+    if (!(fl <= fh) || fh < (float)lo_clip || fl > (float)hi_clip) return;
+    a = fl < (float)lo_clip ? lo_clip : (int)fl;
+    b = fh > (float)hi_clip ? hi_clip : (int)fh;
+}
+
+// union of an ellipse interval [a, b] (empty if a > b) with a disc interval
+__device__ __forceinline__ void hull_interval(int& a, int& b, int da, int db) {
+    if (da > db) return;
+    if (a > b) { a = da; b = db; return; }
+    a = min(a, da);
+    b = max(b, db);
+}
+
 // AccuTile, outer loop over tile rows: tile-column interval of row ty.  The
 // strip's extreme abscissae are the ellipse's left/right tangent points when
 // these fall inside the strip, else the roots of
@@ -147,6 +172,14 @@ __device__ __forceinline__ bool accu_row(const BinRec& r, int ts, int ty, int& t
     const int ra = max(ty * ts, (int)r.py0), rb = min(ty * ts + ts - 1, (int)r.py1);
     if (ra > rb) return false;
     const float Ya = fs(fa((float)ra, 0.5f), r.yc), Yb = fs(fa((float)rb, 0.5f), r.yc);
+    int da = 1, db = 0;  // S20b
+    if (r.flags & BR_LOWPASS) disc_strip(r.rd2, Ya, Yb, r.xc, r.px0, r.px1, da, db);
+    if (!(r.flags & BR_ELL)) {
+        if (da > db) return false;
+        ta = da / ts;
+        tb = db / ts;
+        return true;
+    }
     float ext[2];
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
@@ -163,10 +196,13 @@ __device__ __forceinline__ bool accu_row(const BinRec& r, int ts, int ty, int& t
         ext[side] = fdv(side == 0 ? fs(nb, sq) : fa(nb, sq), r.A);
     }
     const float fl = ceilf(fs(fa(ext[0], r.xc), 0.5f)), fh = floorf(fs(fa(ext[1], r.xc), 0.5f));
-    if (!(fl <= fh)) return false;
-    if (fh < (float)r.px0 || fl > (float)r.px1) return false;
-    const int a = fl < (float)r.px0 ? r.px0 : (int)fl;
-    const int b = fh > (float)r.px1 ? r.px1 : (int)fh;
+    int a = 1, b = 0;
+    if (fl <= fh && !(fh < (float)r.px0 || fl > (float)r.px1)) {
+        a = fl < (float)r.px0 ? r.px0 : (int)fl;
+        b = fh > (float)r.px1 ? r.px1 : (int)fh;
+    }
+    hull_interval(a, b, da, db);
+    if (a > b) return false;
     ta = a / ts;
     tb = b / ts;
     return true;
@@ -177,6 +213,14 @@ __device__ __forceinline__ bool accu_col(const BinRec& r, int ts, int tx, int& t
     const int ca = max(tx * ts, (int)r.px0), cb = min(tx * ts + ts - 1, (int)r.px1);
     if (ca > cb) return false;
     const float Xa = fs(fa((float)ca, 0.5f), r.xc), Xb = fs(fa((float)cb, 0.5f), r.xc);
+    int da = 1, db = 0;  // S20b
+    if (r.flags & BR_LOWPASS) disc_strip(r.rd2, Xa, Xb, r.yc, r.py0, r.py1, da, db);
+    if (!(r.flags & BR_ELL)) {
+        if (da > db) return false;
+        ta = da / ts;
+        tb = db / ts;
+        return true;
+    }
     float ext[2];
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
@@ -193,10 +237,13 @@ __device__ __forceinline__ bool accu_col(const BinRec& r, int ts, int tx, int& t
         ext[side] = fdv(side == 0 ? fs(nb, sq) : fa(nb, sq), r.C);
     }
     const float fl = ceilf(fs(fa(ext[0], r.yc), 0.5f)), fh = floorf(fs(fa(ext[1], r.yc), 0.5f));
-    if (!(fl <= fh)) return false;
-    if (fh < (float)r.py0 || fl > (float)r.py1) return false;
-    const int a = fl < (float)r.py0 ? r.py0 : (int)fl;
-    const int b = fh > (float)r.py1 ? r.py1 : (int)fh;
+    int a = 1, b = 0;
+    if (fl <= fh && !(fh < (float)r.py0 || fl > (float)r.py1)) {
+        a = fl < (float)r.py0 ? r.py0 : (int)fl;
+        b = fh > (float)r.py1 ? r.py1 : (int)fh;
+    }
+    hull_interval(a, b, da, db);
+    if (a > b) return false;
     ta = a / ts;
     tb = b / ts;
     return true;
@@ -271,7 +318,9 @@ __device__ __forceinline__ bool early_culls(const CamDev& cam, const RParams& P,
         const float uymax = fdv(yb, yb >= 0.0f ? zlo : zhi), uymin = fdv(ya, ya >= 0.0f ? zhi : zlo);
         const float pxmax = fa(fm(cam.fx, uxmax), cam.cx), pxmin = fa(fm(cam.fx, uxmin), cam.cx);
         const float pymax = fa(fm(cam.fy, uymax), cam.cy), pymin = fa(fm(cam.fy, uymin), cam.cy);
-        if (pxmax < -0.5f || pxmin > (float)cam.W + 0.5f || pymax < -0.5f || pymin > (float)cam.H + 0.5f)
+        // S5b': the low-pass filter's screen disc widens the margins
+        const float mg = P.lowpass ? fa(0.5f, fq(fm(fmaxf(kk, 0.0f), 0.5f))) : 0.5f;
+        if (pxmax < -mg || pxmin > fa((float)cam.W, mg) || pymax < -mg || pymin > fa((float)cam.H, mg))
             return false;
     }
     return true;
@@ -439,13 +488,30 @@ __global__ void __launch_bounds__(256, 4) k_project(const __grid_constant__ Cams
                 br.flags |= BR_UNBOUNDED;
                 px0 = 0; px1 = cam.W - 1; py0 = 0; py1 = cam.H - 1;
             } else {
-                // S16
-                if (!ellipse(q, br.X0, br.Y0, br.hx, br.hy)) break;
-                // S17
-                if (!pix_range(fs(fa(fs(br.X0, br.hx), xc), 0.5f), fs(fa(fa(br.X0, br.hx), xc), 0.5f), cam.W, px0, px1))
-                    break;
-                if (!pix_range(fs(fa(fs(br.Y0, br.hy), yc), 0.5f), fs(fa(fa(br.Y0, br.hy), yc), 0.5f), cam.H, py0, py1))
-                    break;
+                // S16, S17: the ellipse's pixel range
+                int e0 = 0, e1 = 0, f0 = 0, f1 = 0;
+                bool ell = ellipse(q, br.X0, br.Y0, br.hx, br.hy);
+                if (ell)
+                    ell = pix_range(fs(fa(fs(br.X0, br.hx), xc), 0.5f), fs(fa(fa(br.X0, br.hx), xc), 0.5f), cam.W, e0,
+                                    e1) &&
+                          pix_range(fs(fa(fs(br.Y0, br.hy), yc), 0.5f), fs(fa(fa(br.Y0, br.hy), yc), 0.5f), cam.H, f0,
+                                    f1);
+                // S17b: the low-pass screen disc's, then the union
+                int g0 = 0, g1 = 0, h0 = 0, h1 = 0;
+                bool disc = false;
+                if (P.lowpass) {
+                    br.flags |= BR_LOWPASS;
+                    br.rd2 = fm(kb, 0.5f);
+                    const float rd = fq(br.rd2);
+                    disc = pix_range(fs(fs(xc, rd), 0.5f), fs(fa(xc, rd), 0.5f), cam.W, g0, g1) &&
+                           pix_range(fs(fs(yc, rd), 0.5f), fs(fa(yc, rd), 0.5f), cam.H, h0, h1);
+                }
+                if (!ell && !disc) break;
+                if (ell) br.flags |= BR_ELL;
+                px0 = ell ? (disc ? min(e0, g0) : e0) : g0;
+                px1 = ell ? (disc ? max(e1, g1) : e1) : g1;
+                py0 = ell ? (disc ? min(f0, h0) : f0) : h0;
+                py1 = ell ? (disc ? max(f1, h1) : f1) : h1;
             }
             br.flags |= BR_VISIBLE;
             br.px0 = (int16_t)px0; br.px1 = (int16_t)px1; br.py0 = (int16_t)py0; br.py1 = (int16_t)py1;

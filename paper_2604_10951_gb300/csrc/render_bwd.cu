@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
 // ---------------------------------------------------------------------------
 // k_bwd_geo: back-to-front replay (Top-K and full accumulation)
 // ---------------------------------------------------------------------------
-template <int TS, bool FULL, int CMAX, typename FT, bool RN, bool SH>
+template <int TS, bool FULL, int CMAX, typename FT, bool VAR>
 __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cams cams,
                                                      const __grid_constant__ RParams P, const BwdArgs a) {
     constexpr int NT = TS * TS;
@@ -384,9 +384,10 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
     const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
     const int2 rg = a.ranges[t];
     const int64_t vbase = (int64_t)view * P.N;
-    // SH: the forward's item colours (a compile-time switch on the Top-K path,
-    // which keeps the plain instance's code as it is)
-    const float* __restrict__ rgbv = a.rgb + ((FULL ? P.color_sh : SH) ? 3 * vbase : 0);
+    // VAR instances carry the variants (renormalised Top-K, spherical-harmonic
+    // item colours, low-pass filter), read from the parameters; the plain
+    // instance keeps its code as it is
+    const float* __restrict__ rgbv = a.rgb + (VAR && P.color_sh ? 3 * vbase : 0);
     const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
     const FT* __restrict__ feats = reinterpret_cast<const FT*>(a.feats);
 
@@ -414,7 +415,7 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
                 next_pos = a.saved_pos[pix * K + kk];
                 next_dot = a.dots[pix * K + kk];
             }
-            if (RN) {  // entries 0..kk are the selected ones, front to back
+            if (VAR && P.renorm) {  // entries 0..kk are the selected ones, front to back
                 float ws = 0.0f, wd = 0.0f;
                 for (int k2 = 0; k2 <= kk; ++k2) {
                     const float wv = a.saved_w[pix * K + k2];
@@ -476,7 +477,8 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
             bool contrib = false;
             Hit h;
             const float4 oc = s_oc[j];
-            if (pos < nstop && eval_splat(s_r0[j], s_r1[j], s_r2[j], oc.x, pxf, pyf, P.alpha_min, cam.near_plane, h)) {
+            if (pos < nstop &&
+                eval_splat<VAR>(s_r0[j], s_r1[j], s_r2[j], oc.x, pxf, pyf, P.alpha_min, cam.near_plane, h, P.lowpass)) {
                 contrib = true;
                 const float alpha = fminf(h.alpha_raw, P.alpha_max);
                 const float Tj = T * rcp_approx(1.0f - alpha);
@@ -484,7 +486,7 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
                 float s = oc.y * gr + oc.z * gg + oc.w * gb;
                 if (!FULL) {
                     if (pos == next_pos) {
-                        s += RN ? fmaf(next_dot, rn_a, rn_b) : next_dot;
+                        s += VAR ? fmaf(next_dot, rn_a, rn_b) : next_dot;
                         --kk;
                         next_pos = kk >= 0 ? a.saved_pos[pix * K + kk] : -1;
                         next_dot = kk >= 0 ? a.dots[pix * K + kk] : 0.0f;
@@ -512,17 +514,22 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
                 if (h.alpha_raw < P.alpha_max) {
                     g[9] = dal * h.G;
                     const float drho = -0.5f * alpha * dal;
-                    const float du = 2.0f * h.u * drho, dv = 2.0f * h.v * drho;
-                    const float gc0 = du * h.inv, gc1 = dv * h.inv, gc2 = -(du * h.u + dv * h.v) * h.inv;
-                    g[0] = gc0 * h.X; g[1] = gc0 * h.Y; g[2] = gc0;
-                    g[3] = gc1 * h.X; g[4] = gc1 * h.Y; g[5] = gc1;
-                    g[6] = gc2 * h.X; g[7] = gc2 * h.Y; g[8] = gc2;
+                    if (VAR && h.scr) {  // low-pass screen term: rho = 2 |x - c|^2, d rho / d c = -4 (X, Y)
+                        g[13] = -4.0f * h.X * drho;
+                        g[14] = -4.0f * h.Y * drho;
+                    } else {
+                        const float du = 2.0f * h.u * drho, dv = 2.0f * h.v * drho;
+                        const float gc0 = du * h.inv, gc1 = dv * h.inv, gc2 = -(du * h.u + dv * h.v) * h.inv;
+                        g[0] = gc0 * h.X; g[1] = gc0 * h.Y; g[2] = gc0;
+                        g[3] = gc1 * h.X; g[4] = gc1 * h.Y; g[5] = gc1;
+                        g[6] = gc2 * h.X; g[7] = gc2 * h.Y; g[8] = gc2;
+                    }
                 }
                 T = Tj;
             }
             if (__any_sync(0xffffffffu, contrib)) {
                 reduce_scatter<16>(g);  // lane l holds value l >> 1
-                if ((lane & 1) == 0 && (lane >> 1) < 13) atomicAdd(&s_g[j * 16 + (lane >> 1)], g[0]);
+                if ((lane & 1) == 0 && (lane >> 1) < (VAR ? 15 : 13)) atomicAdd(&s_g[j * 16 + (lane >> 1)], g[0]);
                 if (FULL) {
 #pragma unroll
                     for (int c0 = 0; c0 < CMAX; c0 += 32) {
@@ -543,7 +550,7 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
             const float* v = s_g + 16 * j;
             bool nz = false;
 #pragma unroll
-            for (int k = 0; k < 13; ++k) nz |= v[k] != 0.0f;
+            for (int k = 0; k < (VAR ? 15 : 13); ++k) nz |= v[k] != 0.0f;
             if (!nz) continue;
             const int64_t sp = (int64_t)a.list[rg.x + b_start + j] - vbase;
             const int slot = a.splat_slot[sp];
@@ -551,7 +558,10 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
             red_add_v4(dst, v[0], v[1], v[2], v[3]);
             red_add_v4(dst + 4, v[4], v[5], v[6], v[7]);
             red_add_v4(dst + 8, v[8], v[9], v[10], v[11]);
-            atomicAdd(dst + 12, v[12]);
+            if (VAR)
+                red_add_v4(dst + 12, v[12], v[13], v[14], 0.0f);  // colour b, projected-centre gradient
+            else
+                atomicAdd(dst + 12, v[12]);
         }
         if (FULL) {
             const int c4 = C / 4;
@@ -573,15 +583,19 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
 // k_bwd_project: per surfel, d(adjugate rows) -> d(means, scales, quats)
 // ---------------------------------------------------------------------------
 // gradients of surfel s from its slot's per-view rows (slot < 0: zeros).
-// SH: the colour gradient of each view goes to the spherical-harmonic
-// coefficients (g_rgb [N, B, 3], accumulated in place by the surfel's own
-// thread) and, through the view direction d = (p - o) / |p - o|, to the
-// means: dd/dp = (I - d d^T) / |p - o|; a clamped channel passes nothing.
-template <bool SH>
+// VAR instances carry the variants, read from the parameters:
+//  - spherical-harmonic colours: each view's colour gradient goes to the
+//    coefficients (g_rgb [N, B, 3], accumulated in place by the surfel's own
+//    thread) and, through the view direction d = (p - o) / |p - o|, to the
+//    means: dd/dp = (I - d d^T) / |p - o|; a clamped channel passes nothing;
+//  - low-pass filter: the rows' projected-centre gradient (entries 13, 14)
+//    goes to the means through xc = fx pc_x / pc_z + cx, yc = fy pc_y / pc_z + cy.
+template <bool VAR>
 __device__ __forceinline__ void project_grad(const Cams& cams, const RParams& P, const BwdArgs& a, const float* sh,
                                              int64_t s, int slot) {
     float gm[3] = {0, 0, 0}, gs[2] = {0, 0}, gq[4] = {0, 0, 0, 0}, go = 0.0f, gc[3] = {0, 0, 0};
     const int nb = (P.sh_deg + 1) * (P.sh_deg + 1);
+    const bool SH = VAR && P.color_sh;
     float* gsh = SH && a.g_rgb ? a.g_rgb + s * nb * 3 : nullptr;
     if (gsh)
         for (int i = 0; i < nb * 3; ++i) gsh[i] = 0.0f;
@@ -630,10 +644,20 @@ __device__ __forceinline__ void project_grad(const Cams& cams, const RParams& P,
                 gm[1] += (gd[1] - dy * dd) * ir;
                 gm[2] += (gd[2] - dz * dd) * ir;
             }
+            const CamDev& cam = cams.c[v];
+            if (VAR && P.lowpass && (gv[13] != 0.f || gv[14] != 0.f)) {
+                float pc[3];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+                    pc[r] = cam.R[3 * r] * pm[0] + cam.R[3 * r + 1] * pm[1] + cam.R[3 * r + 2] * pm[2] + cam.t[r];
+                const float iz = 1.0f / pc[2], gx = gv[13] * cam.fx * iz, gy = gv[14] * cam.fy * iz;
+                const float dpc[3] = {gx, gy, -(gx * pc[0] + gy * pc[1]) * iz};
+#pragma unroll
+                for (int k = 0; k < 3; ++k) gm[k] += cam.R[k] * dpc[0] + cam.R[3 + k] * dpc[1] + cam.R[6 + k] * dpc[2];
+            }
             if (g0.x == 0.f && g0.y == 0.f && g0.z == 0.f && g0.w == 0.f && g1.x == 0.f && g1.y == 0.f &&
                 g1.z == 0.f && g1.w == 0.f && g2.x == 0.f)
                 continue;
-            const CamDev& cam = cams.c[v];
             const float4 r0 = a.rec[4 * ((int64_t)v * P.N + s)], r1 = a.rec[4 * ((int64_t)v * P.N + s) + 1];
             const float4 r3 = a.rec[4 * ((int64_t)v * P.N + s) + 3];
             const float xc = r0.w, yc = r1.w, sc = r3.w;
@@ -715,23 +739,23 @@ __device__ __forceinline__ void project_grad(const Cams& cams, const RParams& P,
     if (a.g_scales) { a.g_scales[2 * s] = gs[0]; a.g_scales[2 * s + 1] = gs[1]; }
     if (a.g_quats) for (int k = 0; k < 4; ++k) a.g_quats[4 * s + k] = gq[k];
     if (a.g_opac) a.g_opac[s] = go;
-    if (!SH && a.g_rgb) { a.g_rgb[3 * s] = gc[0]; a.g_rgb[3 * s + 1] = gc[1]; a.g_rgb[3 * s + 2] = gc[2]; }
+    if (!(VAR && P.color_sh) && a.g_rgb) { a.g_rgb[3 * s] = gc[0]; a.g_rgb[3 * s + 1] = gc[1]; a.g_rgb[3 * s + 2] = gc[2]; }
 }
 
 // Zeros for surfels culled in every view (one thread each), then the chain
 // rule for the surfels that have a slot, densely over the slots (a few
 // percent of the surfels are visible, so a thread per surfel would leave
 // most lanes of a warp idle through the long path).
-template <bool SH>
+template <bool VAR>
 __global__ void __launch_bounds__(256) k_bwd_project(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                                                      const BwdArgs a, const float* __restrict__ sh) {
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
     const bool err = a.st->err != 0;
     for (int64_t s = gtid; s < P.N; s += gstride)
-        if (err || a.splat_slot[s] < 0) project_grad<SH>(cams, P, a, sh, s, -1);
+        if (err || a.splat_slot[s] < 0) project_grad<VAR>(cams, P, a, sh, s, -1);
     const int64_t ns = err ? 0 : (int64_t)a.st->nslot;
-    for (int64_t sl = gtid; sl < ns; sl += gstride) project_grad<SH>(cams, P, a, sh, a.slot_surf[sl], (int)sl);
+    for (int64_t sl = gtid; sl < ns; sl += gstride) project_grad<VAR>(cams, P, a, sh, a.slot_surf[sl], (int)sl);
 }
 
 // ---------------------------------------------------------------------------
@@ -836,17 +860,17 @@ cudaError_t launch_feat(const Cams& cams, const RParams& P, const BwdArgs& a, cu
     return go(k_bwd_feat<32, FT>);
 }
 
-template <int TS, bool FULL, int CMAX, typename FT, bool RN = false, bool SH = false>
+template <int TS, bool FULL, int CMAX, typename FT, bool VAR = false>
 cudaError_t launch_geo_one(const Cams& cams, const RParams& P, const BwdArgs& a, cudaStream_t s) {
     constexpr int NB = FULL ? FBATCH : BB;
     const size_t smem = (size_t)NB * (4 * 16 + 8) + (size_t)NB * 16 * 4 + (FULL ? (size_t)NB * P.C * 8 : 0);  // staging, masks, partials, rows
-    cudaError_t e = set_smem((const void*)k_bwd_geo<TS, FULL, CMAX, FT, RN, SH>, smem);
+    cudaError_t e = set_smem((const void*)k_bwd_geo<TS, FULL, CMAX, FT, VAR>, smem);
     if (e != cudaSuccess) return e;
     int grid = cams.total_tiles;
-    if (a.persistent && (e = persistent_grid((const void*)k_bwd_geo<TS, FULL, CMAX, FT, RN, SH>, TS * TS, smem, grid)) !=
+    if (a.persistent && (e = persistent_grid((const void*)k_bwd_geo<TS, FULL, CMAX, FT, VAR>, TS * TS, smem, grid)) !=
                             cudaSuccess)
         return e;
-    k_bwd_geo<TS, FULL, CMAX, FT, RN, SH><<<grid, TS * TS, smem, s>>>(cams, P, a);
+    k_bwd_geo<TS, FULL, CMAX, FT, VAR><<<grid, TS * TS, smem, s>>>(cams, P, a);
     e = cudaGetLastError();
     if (e == cudaSuccess) kernel_mark(s);
     return e;
@@ -854,15 +878,13 @@ cudaError_t launch_geo_one(const Cams& cams, const RParams& P, const BwdArgs& a,
 
 template <int TS, typename FT>
 cudaError_t launch_geo(const Cams& cams, const RParams& P, const BwdArgs& a, cudaStream_t s) {
-    if (P.K > 0) {  // the renormalised and view-dependent-colour variants have their own instances
-        if (P.color_sh)
-            return P.renorm ? launch_geo_one<TS, false, 4, FT, true, true>(cams, P, a, s)
-                            : launch_geo_one<TS, false, 4, FT, false, true>(cams, P, a, s);
-        return P.renorm ? launch_geo_one<TS, false, 4, FT, true>(cams, P, a, s) : launch_geo_one<TS, false, 4, FT>(cams, P, a, s);
-    }
-    if (P.C <= 32) return launch_geo_one<TS, true, 32, FT>(cams, P, a, s);
-    if (P.C <= 64) return launch_geo_one<TS, true, 64, FT>(cams, P, a, s);
-    return launch_geo_one<TS, true, 128, FT>(cams, P, a, s);
+    // the variants (renormalised Top-K, spherical-harmonic colours, low-pass
+    // filter) have their own instances: no cost on the plain paths
+    const bool var = P.renorm || P.color_sh || P.lowpass;
+    if (P.K > 0) return var ? launch_geo_one<TS, false, 4, FT, true>(cams, P, a, s) : launch_geo_one<TS, false, 4, FT>(cams, P, a, s);
+    if (P.C <= 32) return var ? launch_geo_one<TS, true, 32, FT, true>(cams, P, a, s) : launch_geo_one<TS, true, 32, FT>(cams, P, a, s);
+    if (P.C <= 64) return var ? launch_geo_one<TS, true, 64, FT, true>(cams, P, a, s) : launch_geo_one<TS, true, 64, FT>(cams, P, a, s);
+    return var ? launch_geo_one<TS, true, 128, FT, true>(cams, P, a, s) : launch_geo_one<TS, true, 128, FT>(cams, P, a, s);
 }
 
 template <typename FT>
@@ -880,7 +902,7 @@ cudaError_t launch_all(const Cams& cams, const RParams& P, const BwdArgs& a, con
     else e = launch_geo<32, FT>(cams, P, a, s);
     if (e != cudaSuccess) return e;
     const int64_t nb = (P.N + 255) / 256;
-    if (P.color_sh)
+    if (P.color_sh || P.lowpass)
         k_bwd_project<true><<<(unsigned)std::max<int64_t>(1, nb), 256, 0, s>>>(cams, P, a, sh);
     else
         k_bwd_project<false><<<(unsigned)std::max<int64_t>(1, nb), 256, 0, s>>>(cams, P, a, nullptr);

@@ -31,10 +31,16 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // plane, or a non-finite intersection).
 struct Hit {
     float X, Y, u, v, inv, G, alpha_raw;  // G = exp(-(u^2+v^2)/2), alpha_raw = o G
+    bool scr;                             // low-pass: the screen-space term gave G
 };
 
+// LP instances also apply the 2DGS low-pass filter when `lowpass` is set:
+// rho = min(u^2 + v^2, 2 (X^2 + Y^2)), (X, Y) the pixel point about the
+// projected centre; the screen term takes the centre's depth, which passed
+// the near plane at binning, so it skips the near-plane test.
+template <bool LP = false>
 __device__ __forceinline__ bool eval_splat(const float4& A, const float4& B, const float4& Cq, float o, float pxf,
-                                           float pyf, float alpha_min, float near_plane, Hit& h) {
+                                           float pyf, float alpha_min, float near_plane, Hit& h, bool lowpass = false) {
     h.X = pxf - A.w;
     h.Y = pyf - B.w;
     const float c0 = fmaf(A.x, h.X, fmaf(A.y, h.Y, A.z));
@@ -43,10 +49,16 @@ __device__ __forceinline__ bool eval_splat(const float4& A, const float4& B, con
     h.inv = rcp_approx(c2);
     h.u = c0 * h.inv;
     h.v = c1 * h.inv;
-    const float rho = fmaf(h.u, h.u, h.v * h.v);
+    float rho = fmaf(h.u, h.u, h.v * h.v);
+    h.scr = false;
+    if (LP && lowpass) {
+        const float rs = 2.0f * fmaf(h.X, h.X, h.Y * h.Y);
+        h.scr = !(rho <= rs);  // also for a non-finite object term
+        rho = h.scr ? rs : rho;
+    }
     h.G = ex2_approx(NEG_HALF_LOG2E * rho);
     h.alpha_raw = o * h.G;
-    return (h.alpha_raw >= alpha_min) && (Cq.w * h.inv > near_plane);  // hit depth det / c2
+    return (h.alpha_raw >= alpha_min) && ((LP && h.scr) || Cq.w * h.inv > near_plane);  // hit depth det / c2
 }
 
 // Camera-space unit normal of a surfel from its render record, turned to face
@@ -164,7 +176,9 @@ __device__ __forceinline__ int2 pixel_of(int tid) {
 // A x^2 + 2(B y + D) x + (C y^2 + 2 E y + F) = 0 at the nearer strip edge;
 // the extent is widened by a small margin, so the mask may keep a warp
 // that misses but never drops one that is hit.  Skipping a warp therefore
-// changes no result.
+// changes no result.  With the low-pass filter the extent also covers the
+// screen disc of the binning record (radius^2 rd2 about the local origin),
+// widened by 0.1 % in radius^2 and 0.05 pixel.
 __device__ __forceinline__ uint32_t warp_block_mask(const BinRec* __restrict__ rp, int ts, int tile_x0, int tile_y0) {
     const int WX = ts >> 3;
     const float4 q0 = __ldg(reinterpret_cast<const float4*>(rp));       // A B C D
@@ -173,7 +187,10 @@ __device__ __forceinline__ uint32_t warp_block_mask(const BinRec* __restrict__ r
     const int2 q3 = __ldg(reinterpret_cast<const int2*>(rp) + 6);       // pixel box (int16 x 4)
     const int px0 = (int)(int16_t)(q3.x & 0xffff), px1 = q3.x >> 16;
     const int py0 = (int)(int16_t)(q3.y & 0xffff), py1 = q3.y >> 16;
-    const bool unbounded = (__ldg(&rp->flags) & BR_UNBOUNDED) != 0;
+    const int flags = __ldg(&rp->flags);
+    const bool unbounded = (flags & BR_UNBOUNDED) != 0;
+    const bool ell = (flags & BR_ELL) != 0;
+    const float rd2 = (flags & BR_LOWPASS) ? __ldg(&rp->rd2) : -1.0f;  // low-pass screen disc
     const int x0 = max(px0, tile_x0), x1 = min(px1, tile_x0 + ts - 1);
     const int y0 = max(py0, tile_y0), y1 = min(py1, tile_y0 + ts - 1);
     if (x0 > x1 || y0 > y1) return 0u;
@@ -186,6 +203,20 @@ __device__ __forceinline__ uint32_t warp_block_mask(const BinRec* __restrict__ r
         int ca = x0, cb = x1;
         if (!unbounded) {
             const float Ya = ((float)ra + 0.5f) - yc, Yb = ((float)rb + 0.5f) - yc;
+            // the low-pass disc's extent on the strip, widened like the ellipse's
+            int da = 1, db = 0;
+            const float Yn = Ya > 0.0f ? Ya : (Yb < 0.0f ? Yb : 0.0f);
+            if (Yn * Yn <= rd2 * 1.001f) {
+                const float hw = sqrtf(fmaxf(rd2 * 1.001f - Yn * Yn, 0.0f)) + 0.05f;
+                const float lo = ceilf(xc - hw - 0.5f), hi = floorf(xc + hw - 0.5f);
+                da = lo < (float)x0 ? x0 : (lo > (float)x1 ? x1 + 1 : (int)lo);
+                db = hi > (float)x1 ? x1 : (hi < (float)x0 ? x0 - 1 : (int)hi);
+            }
+            if (!ell) {
+                if (da > db) continue;
+                ca = da;
+                cb = db;
+            }
             float ext[2];
 #pragma unroll
             for (int side = 0; side < 2; ++side) {
@@ -201,10 +232,16 @@ __device__ __forceinline__ uint32_t warp_block_mask(const BinRec* __restrict__ r
                     ext[side] = (side == 0 ? -bb - sq : -bb + sq) / A;
                 }
             }
-            // comparisons are false for NaN: a degenerate extent restricts nothing
-            const float lo = ceilf(ext[0] + xc - 0.5f - margin), hi = floorf(ext[1] + xc - 0.5f + margin);
-            if (lo > (float)ca) ca = lo > (float)cb ? cb + 1 : (int)lo;
-            if (hi < (float)cb) cb = hi < (float)ca ? ca - 1 : (int)hi;
+            if (ell) {
+                // comparisons are false for NaN: a degenerate extent restricts nothing
+                const float lo = ceilf(ext[0] + xc - 0.5f - margin), hi = floorf(ext[1] + xc - 0.5f + margin);
+                if (lo > (float)ca) ca = lo > (float)cb ? cb + 1 : (int)lo;
+                if (hi < (float)cb) cb = hi < (float)ca ? ca - 1 : (int)hi;
+                if (da <= db) {
+                    if (ca > cb) { ca = da; cb = db; }
+                    else { ca = min(ca, da); cb = max(cb, db); }
+                }
+            }
             if (ca > cb) continue;
         }
         const int bx0 = (ca - tile_x0) >> 3, bx1 = (cb - tile_x0) >> 3;

@@ -82,7 +82,10 @@ __global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__
                 const int64_t sp = (int64_t)item - vbase;
                 s_oc[j] = make_float4(r[3].x, rgbv[3 * sp], rgbv[3 * sp + 1], rgbv[3 * sp + 2]);
                 s_wm[j] = a.masks[rg.x + b0 + j];
-                if (AUX) s_nrm[j] = facing_normal(r[2], r[0].w, r[1].w, cam);
+                if (AUX) {  // facing normal, and the centre depth for the low-pass screen term
+                    const float4 nf = facing_normal(r[2], r[0].w, r[1].w, cam);
+                    s_nrm[j] = make_float4(nf.x, nf.y, nf.z, r[3].y);
+                }
             }
             if (r0 < rpi) {
                 for (int j = r0; j < cnt; j += rpi) {
@@ -100,7 +103,8 @@ __global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__
                 ++n_eval;
                 Hit h;
                 const float4 oc = s_oc[j];
-                if (!eval_splat(s_r0[j], s_r1[j], s_r2[j], oc.x, pxf, pyf, P.alpha_min, cam.near_plane, h)) continue;
+                if (!eval_splat<AUX>(s_r0[j], s_r1[j], s_r2[j], oc.x, pxf, pyf, P.alpha_min, cam.near_plane, h, P.lowpass))
+                    continue;
                 const float alpha = fminf(h.alpha_raw, P.alpha_max);
                 const float Tn = T * (1.0f - alpha);
                 if (Tn < P.T_min) { done = true; break; }
@@ -111,7 +115,7 @@ __global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__
                 ++n_contrib;
                 if (AUX) {
                     const float4 nv = s_nrm[j];
-                    const float zh = s_r2[j].w * h.inv;  // hit depth, as in the near-plane test
+                    const float zh = h.scr ? nv.w : s_r2[j].w * h.inv;  // hit depth, as in the near-plane test
                     zs = fmaf(w, zh, zs);
                     nx = fmaf(w, nv.x, nx);
                     ny = fmaf(w, nv.y, ny);
@@ -178,7 +182,7 @@ namespace {
 template <int TS, typename FT>
 cudaError_t launch_full(const Cams& cams, const RParams& P, const FwdArgs& a, const AuxOut& x, int num_sms, cudaStream_t s) {
     constexpr int NT = TS * TS;
-    const bool aux = x.any();
+    const bool aux = x.any() || P.lowpass;  // the variant instances also carry the low-pass filter
     const size_t smem = (size_t)FBATCH * (4 * 16 + 8) + (size_t)FBATCH * P.C * 4 +
                         (aux ? (size_t)FBATCH * 16 : 0);  // staging, masks, rows (+ normals)
 #define FSS_FULL(CM)                                                                                         \

@@ -16,7 +16,8 @@
 //   channel-last output with consecutive lanes on consecutive 16-byte chunks.
 // Variants: FRONT takes the first K contributors instead of the K largest
 // weights; AUX also accumulates the sensor outputs (expected and median
-// depth, facing normal) over every contributor.
+// depth, facing normal) over every contributor and applies the low-pass
+// filter when the parameters ask for it.
 //
 // The accumulation is a sparse gather-weighted sum, not a dense contraction,
 // so no tensor cores are involved.
@@ -126,7 +127,10 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : 1) k_r
                 const int64_t sp = (int64_t)item - vbase;
                 s_oc[j] = make_float4(r[3].x, rgbv[3 * sp], rgbv[3 * sp + 1], rgbv[3 * sp + 2]);
                 s_wm[j] = a.masks[rg.x + b0 + j];
-                if (AUX) s_nrm[j] = facing_normal(r[2], r[0].w, r[1].w, cam);
+                if (AUX) {  // facing normal, and the centre depth for the low-pass screen term
+                    const float4 nf = facing_normal(r[2], r[0].w, r[1].w, cam);
+                    s_nrm[j] = make_float4(nf.x, nf.y, nf.z, r[3].y);
+                }
             }
             __syncthreads();
             if (done) continue;
@@ -135,7 +139,8 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : 1) k_r
                 ++n_eval;
                 Hit h;
                 const float4 oc = s_oc[j];
-                if (!eval_splat(s_r0[j], s_r1[j], s_r2[j], oc.x, pxf, pyf, P.alpha_min, cam.near_plane, h)) continue;
+                if (!eval_splat<AUX>(s_r0[j], s_r1[j], s_r2[j], oc.x, pxf, pyf, P.alpha_min, cam.near_plane, h, P.lowpass))
+                    continue;
                 const float alpha = fminf(h.alpha_raw, P.alpha_max);
                 const float Tn = T * (1.0f - alpha);
                 if (Tn < P.T_min) { done = true; break; }
@@ -146,7 +151,7 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : 1) k_r
                 ++n_contrib;
                 if (AUX) {
                     const float4 nv = s_nrm[j];
-                    const float zh = s_r2[j].w * h.inv;  // hit depth, as in the near-plane test
+                    const float zh = h.scr ? nv.w : s_r2[j].w * h.inv;  // hit depth, as in the near-plane test
                     zs = fmaf(w, zh, zs);
                     nx = fmaf(w, nv.x, nx);
                     ny = fmaf(w, nv.y, ny);
@@ -311,7 +316,7 @@ template <int TS, typename FT>
 cudaError_t launch_topk(const Cams& cams, const RParams& P, const FwdArgs& a, const AuxOut& x, int num_sms,
                         cudaStream_t s) {
     constexpr int NT = TS * TS;
-    const bool aux = x.any();
+    const bool aux = x.any() || P.lowpass;  // the variant instances also carry the low-pass filter
     auto smem = [aux](int kcap) {
         const size_t p1 = (size_t)BATCH * (4 * 16 + 4) + (aux ? (size_t)BATCH * 16 : 0);  // staging (+ normals)
         const int pc = (NT < 65536 / (kcap * 8 + 4)) ? NT : 65536 / (kcap * 8 + 4);

@@ -24,7 +24,7 @@ TORCH_DTYPES = {L.FSS_F32: torch.float32, L.FSS_BF16: torch.bfloat16}
 def make_params(C: int, K: int = 8, tile_size: int = 16, bin_mode="accu", stop_rule="tmin",
                 alpha_min: float = 1.0 / 255.0, alpha_max: float = 0.99, T_min: float = 1e-4,
                 feat_dtype=torch.float32, out_dtype=None, bg=(0.0, 0.0, 0.0),
-                schedule="grid", select="topw", renorm=False, sh_degree=None) -> L.fss_params:
+                schedule="grid", select="topw", renorm=False, sh_degree=None, lowpass=False) -> L.fss_params:
     p = L.fss_default_params()
     p.tile_size, p.K, p.C = int(tile_size), int(K), int(C)
     p.bin_mode = BIN_MODES[bin_mode] if isinstance(bin_mode, str) else int(bin_mode)
@@ -38,6 +38,7 @@ def make_params(C: int, K: int = 8, tile_size: int = 16, bin_mode="accu", stop_r
     p.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
     p.select = SELECTS[select] if isinstance(select, str) else int(select)
     p.renorm = int(bool(renorm))
+    p.lowpass = int(bool(lowpass))
     if sh_degree is not None:  # view-dependent colours: rgb arguments hold [N, (d+1)^2, 3] coefficients
         p.color_mode, p.sh_degree = L.FSS_COLOR_SH, int(sh_degree)
     return p

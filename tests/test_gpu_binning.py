@@ -17,8 +17,8 @@ pytestmark = pytest.mark.gpu
 MODES = {"aabb": O.AABB, "snug": O.SNUG, "accu": O.ACCU}
 
 
-def _check_view(run, scene, cam, ts, mode, view=0):
-    p = O.make_params(tile_size=ts, K=run.params.K)
+def _check_view(run, scene, cam, ts, mode, view=0, lowpass=0):
+    p = O.make_params(tile_size=ts, K=run.params.K, lowpass=lowpass)
     recf, reci, cnt = O.mirror_project(scene, cam, p, MODES[mode])
     N = scene.n
     sl = slice(view * N, (view + 1) * N)
@@ -37,7 +37,10 @@ def _check_view(run, scene, cam, ts, mode, view=0):
     _check_render_record(rec, recf, m, scene, cam)
     np.testing.assert_array_equal(bf[m][:, 0:6], recf[m, 14:20])      # conic A..F
     bounded = m & (reci[:, 2] == 0)
-    np.testing.assert_array_equal(bf[bounded][:, 6:10], recf[bounded, 20:24])  # X0, Y0, hx, hy
+    ell = bounded & ((flags & 4) != 0)  # the ellipse has pixels (always, without the low-pass filter)
+    if not lowpass:
+        np.testing.assert_array_equal(ell, bounded)
+    np.testing.assert_array_equal(bf[ell][:, 6:10], recf[ell, 20:24])  # X0, Y0, hx, hy
     np.testing.assert_array_equal((flags[m] & 2) != 0, reci[m, 2] == 1)       # unbounded
     np.testing.assert_array_equal(bi[m][:, 0:4], reci[m][:, [3, 4, 5, 6]])   # pixel range
     np.testing.assert_array_equal(bi[m][:, 4:8], reci[m][:, [7, 8, 9, 10]])  # tile rectangle
@@ -66,14 +69,14 @@ def _check_render_record(rec, recf, m, scene, cam):
         assert abs(rec[i, 11] - det) <= 1e-5 * abs(det), i
 
 
-def _check_lists(run, scene, cams, ts, mode):
+def _check_lists(run, scene, cams, ts, mode, lowpass=0):
     """Sorted per-tile lists of all views equal the oracle's, bit for bit."""
     tile_off = 0
     all_ranges = run.ranges()
     lists = run.lists()
     N = scene.n
     for v, cam in enumerate(cams):
-        p = O.make_params(tile_size=ts)
+        p = O.make_params(tile_size=ts, lowpass=lowpass)
         b = O.binning(scene, cam, p, MODES[mode])
         nt = O.n_tiles(cam, ts)
         rng = all_ranges[tile_off:tile_off + nt]
@@ -106,12 +109,13 @@ def test_room_view_binning_bit_exact():
     _check_lists(run, sc, cams, 16, "accu")
 
 
-def _check_masks(run, scene, cam, ts):
+def _check_masks(run, scene, cam, ts, lowpass=0):
     """Every pixel centre of a tile inside a listed surfel's binning ellipse
     (FP64 test on the bit-exact binary32 conic), or inside the pixel box of
-    an unbounded footprint, lies in a warp block that the pair's mask keeps
-    (warps own 8 x 4 pixel blocks, row-major over the tile)."""
-    p = O.make_params(tile_size=ts)
+    an unbounded footprint, or (low-pass filter) inside the screen disc
+    2 |x - c|^2 <= k^2 (1 + 2^-10), lies in a warp block that the pair's mask
+    keeps (warps own 8 x 4 pixel blocks, row-major over the tile)."""
+    p = O.make_params(tile_size=ts, lowpass=lowpass)
     recf, reci, _ = O.mirror_project(scene, cam, p, O.ACCU)
     rng, lists, masks = run.ranges(), run.lists(), run.masks()
     txn = (cam.width + ts - 1) // ts
@@ -130,7 +134,11 @@ def _check_masks(run, scene, cam, ts):
             X, Y = x + 0.5 - xc, y + 0.5 - yc
             q = A * X * X + 2 * B * X * Y + C * Y * Y + 2 * D * X + 2 * E * Y + F
             inbox = (x >= px0) & (x <= px1) & (y >= py0) & (y <= py1) & (x < cam.width) & (y < cam.height)
-            hit = inbox & (unb | (q <= 0))
+            ell = (A * C - B * B > 0) & (A > 0)
+            hit = inbox & (unb | ((q <= 0) & ell))
+            if lowpass:
+                kb = recf[ids, 1].astype(np.float64) * 1.0009765625
+                hit |= inbox & (2 * (X * X + Y * Y) <= kb)
             bit = (masks >> np.uint32((ly // 4) * (ts // 8) + lx // 8)) & 1
             assert not np.any(hit & (bit == 0)), (ts, lx, ly)
             covered += int(hit.sum())
