@@ -52,6 +52,13 @@ def parse():
 # distributed plumbing: one process per GPU, views sharded, no collective on
 # the data path (weak scaling); a barrier and a max-reduce of the time only
 # ---------------------------------------------------------------------------
+def shard_pose(step, rank, world, n_poses):
+    """Pose of a rank's step: the ranks take interleaved poses of the camera
+    stream (rank r renders poses r, r + world, ...), so together they render
+    different views and every pose equally often."""
+    return (step * world + rank) % n_poses
+
+
 class Dist:
     def __init__(self, backend):
         import torch
@@ -226,7 +233,7 @@ def run_ours(args):
         def step(self, i, events=None):
             fr, p, ws = self.frame, self.params, ptr(self.frame.ws)
             sp = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-            cams = cams_c[i % len(cams_c)]
+            cams = cams_c[shard_pose(i, D.rank, D.world, len(cams_c))]
             a = (p, cams, 1, N_SPLATS)
             rec = (lambda k: events[k].record()) if events else (lambda k: None)
             rec(0)
@@ -341,7 +348,7 @@ def run_ours(args):
                                              poses, flush)
         out["query_labels"] = queries(torch, dev, sc, means, scales, quats, opac, rgb, poses, flush)
     if D.rank == 0 and not args.no_extras:
-        out["cpu_baseline"] = cpu_baseline(sc, poses, sample_frames=1)
+        out["cpu_baseline"] = cpu_baseline(sc, poses)
     if D.rank == 0:
         print(json.dumps(out))
     D.close()
@@ -631,21 +638,38 @@ def queries(torch, dev, sc, means, scales, quats, opac, rgb, poses, flush, reps=
 
 def e2e(path, torch, dev, ptr, L, args):
     """Same step through the C ABI with host buffers: per step the targets go
-    host->device from pinned memory and the loss comes back."""
+    host->device from pinned memory and the loss comes back.  The copies run
+    on a second stream into two alternating device buffers, so step i+1's
+    targets travel while step i computes (the compute stream waits for its
+    buffer's copy, and a copy waits until the step two back has released its
+    buffer)."""
     F_h = path.F_tgt.cpu().pin_memory()
     r_h = torch.empty(path.frame.total_pix, 3).pin_memory()
     r_h.copy_(torch.rand(path.frame.total_pix, 3))
-    loss_h = torch.empty(1, dtype=torch.float64).pin_memory()
-    F_d, r_d = torch.empty_like(path.F_tgt), torch.empty(path.frame.total_pix, 3, device=dev)
+    loss_h = [torch.empty(1, dtype=torch.float64).pin_memory() for _ in range(2)]
+    F_d = [torch.empty_like(path.F_tgt) for _ in range(2)]
+    r_d = [torch.empty(path.frame.total_pix, 3, device=dev) for _ in range(2)]
+    copy_stream = torch.cuda.Stream(device=dev)
+    copied = [torch.cuda.Event() for _ in range(2)]
+    released = [torch.cuda.Event() for _ in range(2)]
+    compute = torch.cuda.current_stream()
+    for e in released:
+        e.record(compute)
     steps = max(8, args.steps // 4)
     old_F, old_r = path.F_tgt, path.rgb_tgt
 
     def step(i):
-        F_d.copy_(F_h, non_blocking=True)
-        r_d.copy_(r_h, non_blocking=True)
-        path.F_tgt, path.rgb_tgt = F_d, r_d
+        b = i & 1
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(released[b])
+            F_d[b].copy_(F_h, non_blocking=True)
+            r_d[b].copy_(r_h, non_blocking=True)
+            copied[b].record(copy_stream)
+        compute.wait_event(copied[b])
+        path.F_tgt, path.rgb_tgt = F_d[b], r_d[b]
         path.step(i)
-        loss_h.copy_(path.loss, non_blocking=True)
+        released[b].record(compute)
+        loss_h[b].copy_(path.loss, non_blocking=True)
 
     for i in range(3):
         step(i)
@@ -658,36 +682,82 @@ def e2e(path, torch, dev, ptr, L, args):
     path.F_tgt, path.rgb_tgt = old_F, old_r
     return {"value": round(steps / dt, 2), "unit": "frames/s",
             "h2d_bytes_per_step": int(F_h.numel() * F_h.element_size() + r_h.numel() * 4),
-            "d2h_bytes_per_step": 8}
+            "d2h_bytes_per_step": 8, "copies": "second stream, two alternating buffers"}
 
 
-def cpu_baseline(sc, poses, sample_frames=1):
-    """The FP64 checker as it stands on this host's cores, on a bounded
-    sample of the same workload (whole 640x480 frames, forward + backward)."""
-    import oracle as O
+BAND = 160  # rows per oracle step: ten 16-row tile rows, a third of a 640x480 frame
 
-    O.build()
-    p = O.make_params(K=K_TOP, stop_rule=O.EXACT_TOPK)
-    threads = O.num_threads()
-    rng = np.random.default_rng(0)
-    t0 = time.perf_counter()
-    for f in range(sample_frames):
-        cam = poses[f]
-        b = O.binning(sc, cam, p)
-        ref = O.render(sc, cam, p, binned=b, threads=threads)
-        gF = rng.normal(size=ref["F"].shape) * 1e-3
-        grgb = rng.normal(size=ref["rgb"].shape) * 1e-3
-        O.render_backward(sc, cam, p, gF, grgb, None, binned=b)
-    dt = time.perf_counter() - t0
-    return {"value": round(sample_frames / dt, 4), "unit": "frames/s", "cores": threads, "kind": "oracle",
-            "sample": f"{sample_frames} full 640x480 frame(s) of the same workload, FP64 forward "
-                      f"(OpenMP, {threads} threads) + backward (1 thread)", "seconds": round(dt, 2)}
+
+class OracleSteps:
+    """The FP64 checker as it stands, stepping through the bench's frames in
+    bands of BAND rows (each call of the checker also prepares the whole
+    scene, so a frame in three bands costs a little more than in one call):
+    step i renders (forward, OpenMP over the host cores)
+    and differentiates (backward, one thread) rows [b BAND, (b+1) BAND) of
+    pose f, with f, b = divmod(i, bands per frame); a frame's binning runs
+    at its first band and counts in that step.  A band camera is the pose
+    with height BAND and cy - b BAND, whose tiles are the frame's tile rows,
+    so its lists are a slice of the frame's: every frame costs one binning
+    and all its rows, as a whole frame does."""
+
+    def __init__(self, sc, poses):
+        import oracle as O
+
+        O.build()
+        self.O, self.sc, self.poses = O, sc, poses
+        self.p = O.make_params(K=K_TOP, stop_rule=O.EXACT_TOPK)
+        self.threads = O.num_threads()
+        self.nb = poses[0].height // BAND
+        self.frame, self.binned = None, None
+        self.rng = np.random.default_rng(0)
+
+    def step(self, i):
+        import dataclasses
+
+        O = self.O
+        f, b = divmod(i, self.nb)
+        cam = self.poses[f % len(self.poses)]
+        if self.frame != f:
+            self.binned = O.binning(self.sc, cam, self.p)
+            self.frame = f
+        bcam = dataclasses.replace(cam, height=BAND, cy=np.float32(cam.cy - b * BAND))
+        tx = (cam.width + 15) // 16
+        tr0 = b * BAND // 16
+        rng = self.binned["ranges"][tr0 * tx:(tr0 + BAND // 16) * tx]
+        bb = dict(self.binned, ranges=rng)
+        ref = O.render(self.sc, bcam, self.p, binned=bb, threads=self.threads)
+        gF = self.rng.normal(size=ref["F"].shape) * 1e-3
+        grgb = self.rng.normal(size=ref["rgb"].shape) * 1e-3
+        O.render_backward(self.sc, bcam, self.p, gF, grgb, None, binned=bb)
+
+    def sample(self, steps, warmup=0):
+        for i in range(warmup):
+            self.step(i)
+        self.frame = None  # the timed steps start with a fresh frame (its binning included)
+        t0 = time.perf_counter()
+        for i in range(steps):
+            self.step(i)
+        dt = time.perf_counter() - t0
+        frames = steps / self.nb
+        return {"value": round(frames / dt, 4), "unit": "frames/s", "cores": self.threads, "kind": "oracle",
+                "sample": f"{steps} bands of {BAND} rows ({frames:.1f} frames of 640x480 over the 16 poses, each "
+                          f"frame's binning once) of the same workload, FP64 forward (OpenMP, {self.threads} threads) "
+                          f"+ backward (1 thread)", "seconds": round(dt, 2)}
+
+
+def cpu_baseline(sc, poses, steps=15):
+    """The checker on a bounded sample of the bench's workload (about ten
+    seconds of CPU work: five frames in 160-row bands)."""
+    return OracleSteps(sc, poses).sample(steps)
 
 
 # ---------------------------------------------------------------------------
 # reference arm: the FP64 checker on the host cores
 # ---------------------------------------------------------------------------
 def run_reference(args):
+    """The reference arm: the FP64 checker, W untimed and K timed steps of
+    160-row bands of the bench's frames (OracleSteps), on rank 0 only (the
+    other ranks of a torchrun launch exit without work)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -695,14 +765,13 @@ def run_reference(args):
 
     sc = scenes.room_scene(n=N_SPLATS, C=C_FEAT, seed=SEED)
     poses = scenes.circle_poses(16)
-    for _ in range(args.warmup and 1):
-        pass
-    res = cpu_baseline(sc, poses, sample_frames=max(1, min(args.steps, 2)))
+    res = OracleSteps(sc, poses).sample(args.steps, args.warmup)
     out = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": "frames/s",
            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": round(1e3 / res["value"], 2), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "room 500k surfels, 640x480, C=64, K=8, forward+backward (FP64 checker)"},
+           "ms_per_step": round(res["seconds"] * 1e3 / max(1, args.steps), 2), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "room 500k surfels, 640x480 (fx=fy=525), C=64, K=8 Top-K, forward+backward "
+                                  "(FP64 checker, one step = a 160-row band of a frame)"},
            "cpu_baseline": res,
            "e2e": {"value": res["value"], "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))

@@ -179,6 +179,7 @@ __device__ __forceinline__ int2 pixel_of(int tid) {
 // changes no result.  With the low-pass filter the extent also covers the
 // screen disc of the binning record (radius^2 rd2 about the local origin),
 // widened by 0.1 % in radius^2 and 0.05 pixel.
+template <bool LP>
 __device__ __forceinline__ uint32_t warp_block_mask(const BinRec* __restrict__ rp, int ts, int tile_x0, int tile_y0) {
     const int WX = ts >> 3;
     const float4 q0 = __ldg(reinterpret_cast<const float4*>(rp));       // A B C D
@@ -189,8 +190,8 @@ __device__ __forceinline__ uint32_t warp_block_mask(const BinRec* __restrict__ r
     const int py0 = (int)(int16_t)(q3.y & 0xffff), py1 = q3.y >> 16;
     const int flags = __ldg(&rp->flags);
     const bool unbounded = (flags & BR_UNBOUNDED) != 0;
-    const bool ell = (flags & BR_ELL) != 0;
-    const float rd2 = (flags & BR_LOWPASS) ? __ldg(&rp->rd2) : -1.0f;  // low-pass screen disc
+    const bool ell = !LP || (flags & BR_ELL) != 0;
+    const float rd2 = LP && (flags & BR_LOWPASS) ? __ldg(&rp->rd2) : -1.0f;  // low-pass screen disc
     const int x0 = max(px0, tile_x0), x1 = min(px1, tile_x0 + ts - 1);
     const int y0 = max(py0, tile_y0), y1 = min(py1, tile_y0 + ts - 1);
     if (x0 > x1 || y0 > y1) return 0u;
@@ -206,7 +207,7 @@ __device__ __forceinline__ uint32_t warp_block_mask(const BinRec* __restrict__ r
             // the low-pass disc's extent on the strip, widened like the ellipse's
             int da = 1, db = 0;
             const float Yn = Ya > 0.0f ? Ya : (Yb < 0.0f ? Yb : 0.0f);
-            if (Yn * Yn <= rd2 * 1.001f) {
+            if (LP && Yn * Yn <= rd2 * 1.001f) {
                 const float hw = sqrtf(fmaxf(rd2 * 1.001f - Yn * Yn, 0.0f)) + 0.05f;
                 const float lo = ceilf(xc - hw - 0.5f), hi = floorf(xc + hw - 0.5f);
                 da = lo < (float)x0 ? x0 : (lo > (float)x1 ? x1 + 1 : (int)lo);

@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(256) k_tile_sort(const __grid_constant__ Cams 
             for (int j = 0; j < n; ++j) rank += sk[j] < key ? 1 : 0;
             const uint32_t item = (uint32_t)key;
             list[rg.x + rank] = item;
-            masks[rg.x + rank] = warp_block_mask(binrec + item, P.ts, tx0, ty0);
+            masks[rg.x + rank] = (P.lowpass ? warp_block_mask<true>(binrec + item, P.ts, tx0, ty0)
+                                           : warp_block_mask<false>(binrec + item, P.ts, tx0, ty0));
         }
         return;
     }
@@ -140,7 +141,8 @@ __global__ void __launch_bounds__(256) k_tile_sort(const __grid_constant__ Cams 
         for (int i = tid; i < n; i += blockDim.x) {
             const uint32_t item = (uint32_t)sk[i];
             list[rg.x + i] = item;
-            masks[rg.x + i] = warp_block_mask(binrec + item, P.ts, tx0, ty0);
+            masks[rg.x + i] = (P.lowpass ? warp_block_mask<true>(binrec + item, P.ts, tx0, ty0)
+                                           : warp_block_mask<false>(binrec + item, P.ts, tx0, ty0));
         }
         return;
     }
@@ -152,7 +154,8 @@ __global__ void __launch_bounds__(256) k_tile_sort(const __grid_constant__ Cams 
     for (int i = tid; i < n; i += blockDim.x) {
         const uint32_t item = (uint32_t)keys[i];
         list[rg.x + i] = item;
-        masks[rg.x + i] = warp_block_mask(binrec + item, P.ts, tx0, ty0);
+        masks[rg.x + i] = (P.lowpass ? warp_block_mask<true>(binrec + item, P.ts, tx0, ty0)
+                                           : warp_block_mask<false>(binrec + item, P.ts, tx0, ty0));
     }
 }
 
