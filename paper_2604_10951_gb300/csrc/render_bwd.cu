@@ -767,8 +767,10 @@ __global__ void __launch_bounds__(256) k_feat_out(const __grid_constant__ RParam
     const int nvec = P.C / E;
     const int64_t total = P.N * nvec;
     const bool err = a.st->err != 0;
+    const bool pow2 = (nvec & (nvec - 1)) == 0;  // the usual widths: a shift instead of a 64-bit division
+    const int sh = __ffs(nvec) - 1;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = i / nvec;
+        const int64_t s = pow2 ? (i >> sh) : i / nvec;
         const int vv = (int)(i - s * nvec);
         const int slot = err ? -1 : a.splat_slot[s];
         float v[E];
@@ -800,7 +802,7 @@ __global__ void __launch_bounds__(256) k_bwd_clear(const __grid_constant__ Cams 
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         if (i < g4 * cams.n) {
-            const int64_t v = i / g4, r = i - v * g4;
+            const int64_t v = cams.n == 1 ? 0 : i / g4, r = i - v * g4;
             reinterpret_cast<float4*>(a.grad_item + v * P.N * GRAD_STRIDE)[r] = z;
         } else {
             reinterpret_cast<float4*>(a.feat_acc)[i - g4 * cams.n] = z;
