@@ -146,7 +146,7 @@ fss_status fss_project_bin(const fss_params *params, const fss_camera *cams, int
                            void *workspace, int64_t pair_capacity, fss_stream_t stream);
 
 /*
- * Depth sort ("surfels are depth-sorted", Sec. 3.1): orders each tile's
+ * Depth sort (the depth order of the compositing, Sec. 3.1): orders each tile's
  * list by (binary32 bits of the surfel centre's camera depth, surfel index),
  * a total order, so the result is deterministic.
  */

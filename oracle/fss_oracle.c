@@ -11,9 +11,9 @@
  *   - surfel frame and the local-to-world map (Sec. 3.1, Eq. 1);
  *   - the homogeneous surfel-to-screen transform T with rows T1, T2, Tw
  *     (Sec. 3.2, x' = T u);
- *   - the ray-splat intersection u(x): the paper names it ("the 2D
- *     projection of the pixel onto the surfel's tangent space", Sec. 3.1,
- *     after Eq. 2) without a formula; it is derived here from x' = T u: the
+ *   - the ray-splat intersection u(x): the paper names it (the pixel's
+ *     projection into the surfel's tangent plane, Sec. 3.1, after Eq. 2)
+ *     without a formula; it is derived here from x' = T u: the
  *     two image lines through pixel x back-project to the planes
  *     (T1 - x Tw).u = 0 and (T2 - y Tw).u = 0, whose intersection is
  *     u ~ (T1 - x Tw) x (T2 - y Tw);
@@ -25,9 +25,9 @@
  *   - Precise Tile Intersection: the screen conic of the cutoff disc, its
  *     tight box (SnugBox) and per-row/column extents from the quadratic
  *     A x^2 + (2B y + 2D) x + (C y^2 + 2E y + F) = 0 (AccuTile)
- *     (Sec. 3.2, "Snugbox and AccuTile Application");
+ *     (Sec. 3.2, the SnugBox and AccuTile subsection);
  *   - analytic gradients of the rendered outputs (the paper trains through
- *     the renderer end to end, Sec. 3.1 "differentiable", Sec. 3.5; it
+ *     the differentiable renderer end to end, Sec. 3.1, Sec. 3.5; it
  *     prints no gradient formulas, so the chain rule of the forward is
  *     written out directly).
  *
@@ -767,7 +767,7 @@ static int pair_cmp(const void *pa, const void *pb)
 }
 
 /* Order pairs by (tile, binary32 bits of the surfel depth, surfel index)
- * ("surfels are depth-sorted", Sec. 3.1).  Depths are positive, so the bit
+ * (the depth order of the compositing, Sec. 3.1).  Depths are positive, so the bit
  * order is the numeric order. */
 void orc_sort_pairs(int64_t P, const int32_t *tiles, const int32_t *ids, const float *z,
                     int32_t *out_tiles, int32_t *out_ids)

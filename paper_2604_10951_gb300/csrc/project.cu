@@ -251,7 +251,7 @@ __device__ __forceinline__ bool accu_col(const BinRec& r, int ts, int tx, int& t
 
 // Outer lines of an item's tile set: rows if the tile span in y does not
 // exceed the span in x (or for the box modes), else columns (SnugBox's
-// "smaller span" traversal).
+// traversal over the smaller span).
 struct Lines {
     int n;          // number of outer lines
     int first;      // first outer coordinate

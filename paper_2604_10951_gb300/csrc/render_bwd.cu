@@ -1,7 +1,7 @@
 // Backward render for sm_103a: vector-Jacobian product of the forward
 // render (Eq. 2, Eq. 7) with the Top-K set, skips, stops and clamps held
-// fixed.  The paper trains through the renderer end to end (Sec. 3.1
-// "differentiable", Sec. 3.5) but prints no gradients; these are the chain
+// fixed.  The paper trains through the differentiable renderer end to end
+// (Sec. 3.1, Sec. 3.5) but prints no gradients; these are the chain
 // rule of the forward:
 //   s_j    = rgb_j . dL/dRGB + [j in K-set] c_j . dL/dF
 //   dL/da_j = T_j (s_j - S_j),  S_j = sum_{i>j} w_i s_i / T_{j+1} + bg.dL/dRGB + dL/dT

@@ -1,5 +1,5 @@
-// Depth sort of each tile's surfel list ("surfels are depth-sorted",
-// Sec. 3.1).
+// Depth sort of each tile's surfel list (the paper composites the surfels
+// in depth order, Sec. 3.1).
 //
 // Binning leaves every tile's range of the pair list filled in arbitrary
 // order (bounded items first, then the view's unbounded items are appended

@@ -6,7 +6,7 @@ blending, no selection), so the CUDA library and the FP64 checker can both
 consume what it produces without sharing any of the method.
 
 The paper measures on ScanNet-V2 / ScanNet++ rooms reconstructed with a
-surfel model (Sec. 4.1, "Datasets" and "Implementation Details").  Those
+surfel model (Sec. 4.1, its dataset and implementation paragraphs).  Those
 scenes are not available here; the room generator below stands in for them
 with the same structure: thin surfels lying on the surfaces of a closed
 indoor room plus compact objects, Kinect-like 640x480 intrinsics, and
