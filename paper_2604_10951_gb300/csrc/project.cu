@@ -290,24 +290,39 @@ __device__ __forceinline__ int view_of_item(int64_t item, int64_t N) {
 // test): the cheap culls, which remove most surfels of a view before the
 // rest of the chain.  Returns false when the item is culled; pc and o as
 // computed (o = 0 if the depth test failed first).
-__device__ __forceinline__ bool early_culls(const CamDev& cam, const RParams& P, const float* __restrict__ means,
-                                            const float* __restrict__ scales, const float* __restrict__ opac,
-                                            int64_t s, float pc[3], float& o) {
+// the surfel inputs the culls read, loaded together so that their latencies overlap
+struct CullIn {
+    float pm[3];
+    float o;
+    float2 sc;
+};
+__device__ __forceinline__ CullIn load_cull_in(const float* __restrict__ means, const float* __restrict__ scales,
+                                               const float* __restrict__ opac, int64_t s) {
+    CullIn c;
+    c.pm[0] = __ldg(means + 3 * s);
+    c.pm[1] = __ldg(means + 3 * s + 1);
+    c.pm[2] = __ldg(means + 3 * s + 2);
+    c.o = __ldg(opac + s);
+    c.sc = __ldg(reinterpret_cast<const float2*>(scales) + s);
+    return c;
+}
+
+__device__ __forceinline__ bool early_culls(const CamDev& cam, const RParams& P, const CullIn& in, float pc[3],
+                                            float& o) {
     float e[3];
-    const float pm[3] = {__ldg(means + 3 * s), __ldg(means + 3 * s + 1), __ldg(means + 3 * s + 2)};
-    mvec(cam.R, pm, e);
+    mvec(cam.R, in.pm, e);
 #pragma unroll
     for (int i = 0; i < 3; ++i) pc[i] = fa(e[i], cam.t[i]);
     o = 0.0f;
     if (!(pc[2] > cam.near_plane)) return false;
     // S5
-    o = __ldg(opac + s);
+    o = in.o;
     if (!(o >= P.alpha_min)) return false;
     // S5b: the binning disk lies in the sphere of radius
     // rho = sqrt(k^2 (1 + 2^-10)) max(r_u, r_v) about the centre; if that
     // sphere is in front of the camera and its projection's bounding box
     // misses every pixel centre by more than a pixel, no pixel can be reached.
-    const float2 scp = __ldg(reinterpret_cast<const float2*>(scales) + s);
+    const float2 scp = in.sc;
     const float kk = fm(fm(2.0f, ln32(fdv(o, P.alpha_min))), 1.0009765625f);
     const float rho = fa(fm(fm(fq(fmaxf(kk, 0.0f)), fmaxf(scp.x, scp.y)), 1.001f), 1e-6f);
     const float zlo = fs(pc[2], rho), zhi = fa(pc[2], rho);
@@ -327,6 +342,7 @@ __device__ __forceinline__ bool early_culls(const CamDev& cam, const RParams& P,
 }
 
 constexpr int PROJ_ITEMS = 1024;  // items per CTA of k_project
+constexpr int PROJ_THREADS = 256;
 
 // ---------------------------------------------------------------------------
 // k_project: (view, surfel) items, PROJ_ITEMS per CTA
@@ -343,7 +359,7 @@ constexpr int PROJ_ITEMS = 1024;  // items per CTA of k_project
 // ---------------------------------------------------------------------------
 constexpr uint32_t WIDE_TILES = 32;
 
-__global__ void __launch_bounds__(256, 4) k_project(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
+__global__ void __launch_bounds__(PROJ_THREADS, 4) k_project(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                                                  const float* __restrict__ means, const float* __restrict__ scales,
                                                  const float* __restrict__ quats, const float* __restrict__ opac,
                                                  float4* __restrict__ rec, BinRec* __restrict__ binrec,
@@ -357,15 +373,29 @@ __global__ void __launch_bounds__(256, 4) k_project(const __grid_constant__ Cams
     const int lane = threadIdx.x & 31;
     if (threadIdx.x == 0) s_nq = 0;
     __syncthreads();
-    // stage A: the cheap culls for PROJ_ITEMS items; survivors queued in shared memory
+    // stage A: the cheap culls for PROJ_ITEMS items (each thread's items loaded
+    // together first); survivors queued in shared memory
     const int64_t base = (int64_t)blockIdx.x * PROJ_ITEMS;
-    for (int k = threadIdx.x; k < PROJ_ITEMS; k += blockDim.x) {
+    constexpr int PER = PROJ_ITEMS / PROJ_THREADS;
+    CullIn in[PER];
+    int vw[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int64_t it = base + threadIdx.x + i * PROJ_THREADS;
+        vw[i] = 0;
+        if (it < P.n_items) {
+            vw[i] = view_of_item(it, P.N);
+            in[i] = load_cull_in(means, scales, opac, it - (int64_t)vw[i] * P.N);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int k = threadIdx.x + i * PROJ_THREADS;
         const int64_t it = base + k;
         bool keep = false;
         if (it < P.n_items) {
-            const int v = view_of_item(it, P.N);
             float pc[3], o;
-            keep = early_culls(cams.c[v], P, means, scales, opac, it - (int64_t)v * P.N, pc, o);
+            keep = early_culls(cams.c[vw[i]], P, in[i], pc, o);
         }
         const unsigned m = __ballot_sync(0xffffffffu, keep);
         int b = 0;
@@ -392,12 +422,13 @@ __global__ void __launch_bounds__(256, 4) k_project(const __grid_constant__ Cams
         br.px1 = br.py1 = br.tx1 = br.ty1 = 0;
         br.A = br.B = br.C = br.D = br.E = br.F = 0.0f;
         br.X0 = br.Y0 = br.hx = br.hy = br.xc = br.yc = 0.0f;
-        br.pad[0] = br.pad[1] = br.pad[2] = 0;
+        br.rd2 = 0.0f;
+        br.pad[0] = br.pad[1] = 0;
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
         do {
             // S3 (centre), S4, S5, S5b first: the order of the cull tests does not change the result
             float pc[3], o;
-            const bool pass = early_culls(cam, P, means, scales, opac, s, pc, o);
+            const bool pass = early_culls(cam, P, load_cull_in(means, scales, opac, s), pc, o);
             r3.y = pc[2];
             r3.x = o;
             if (!pass) break;
