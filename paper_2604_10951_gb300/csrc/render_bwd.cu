@@ -76,15 +76,21 @@ __device__ __forceinline__ void reduce_scatter(float* v) {
 //     16 bytes); each thread keeps EPT entries (list position, weight) in
 //     registers;
 //  2. the selected list positions get dense slot numbers (mark + scan) and
-//     a counting sort groups the entries by slot (warp-aggregated atomics);
+//     a counting sort groups the entries by slot (warp-aggregated atomics)
+//     into 8-byte records (slot, dL/dF row offset; weight);
 //  3. the selected surfels' feature rows are staged in shared memory in one
 //     parallel pass (over the counting-sort tables, which are dead by then);
-//  4. the slot-grouped entries are split into equal contiguous ranges, one
+//  4. the slot-grouped records are split into equal contiguous ranges, one
 //     per group of G lanes (G = 16-byte chunks per row, rounded up to a
-//     power of two, so a group reads whole rows without bank conflicts):
-//     two entries per step, the group forms each dot (shuffle-reduced) and
-//     accumulates w dL/dF, flushing one row of 16-byte vector reductions
-//     whenever its range moves on to the next surfel.
+//     power of two).  A group takes four records per step.  When, for every
+//     group of the warp, all four continue the group's current surfel (the
+//     common case: about 30 entries per surfel and chunk), the warp takes
+//     them without further checks; otherwise each record is checked, and a
+//     group flushes one row of 16-byte vector reductions whenever its range
+//     moves on to the next surfel.  The four partial dots are
+//     reduce-scattered over the group, so each sum costs one shuffle per
+//     lane and halving; packed FP32 FMAs (two products per instruction)
+//     form the dots and w dL/dF.
 // Shared memory holds everything the inner loop reads, so it runs without
 // global-memory latency; the equal ranges keep the warps balanced.
 // ---------------------------------------------------------------------------
@@ -95,22 +101,65 @@ constexpr int FEAT_UNION_BYTES = (PTAB + 2 * ECAP + 1) * 4;  // counting-sort ta
 constexpr int MAX_ROW_PASSES = 64;
 constexpr int STAGE_UNROLL = 4;  // global loads in flight per thread while staging
 
-// entry record: slot << 15 | chunk pixel << 5 | k
-__device__ __forceinline__ int ent_slot(int e) { return e >> 15; }
-__device__ __forceinline__ int ent_q(int e) { return (e >> 5) & 1023; }
+// entry record .x: slot << REC_ROW_BITS | offset of the entry's dL/dF row in
+// 16-byte units (slot < PTAB = 2^11, offset < 2^17: 28 bits); .y: weight bits
+constexpr int REC_ROW_BITS = 17;
+constexpr int REC_ROW_MASK = (1 << REC_ROW_BITS) - 1;
 
-template <int TS, typename FT>
+// Sums of four values v[0..3] over the G lanes of a group (G a power of two,
+// groups aligned in the warp), scattered: lanes swap halves of what is left
+// and add, so each halving costs one shuffle per value kept.  Afterwards the
+// lane holds the sums of the entries given by group_sum4_owned.
+template <int G>
+__device__ __forceinline__ void group_sum4(float (&v)[4], int sub) {
+    constexpr unsigned ALL = 0xffffffffu;
+    if constexpr (G >= 16) {
+#pragma unroll
+        for (int o = G >> 1; o >= 8; o >>= 1) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] += __shfl_xor_sync(ALL, v[j], o);
+        }
+    }
+    if constexpr (G >= 2) {  // four values -> two: lanes with the offset bit keep entries 2, 3
+        constexpr int o = G >= 8 ? 4 : G >> 1;
+        const bool up = (sub & o) != 0;
+        const float s0 = up ? v[0] : v[2], s1 = up ? v[1] : v[3];
+        const float k0 = up ? v[2] : v[0], k1 = up ? v[3] : v[1];
+        v[0] = k0 + __shfl_xor_sync(ALL, s0, o);
+        v[1] = k1 + __shfl_xor_sync(ALL, s1, o);
+    }
+    if constexpr (G >= 4) {  // two -> one: lanes with the offset bit keep the second
+        constexpr int o = G >= 8 ? 2 : 1;
+        const bool up = (sub & o) != 0;
+        const float sd = up ? v[0] : v[1], kp = up ? v[1] : v[0];
+        v[0] = kp + __shfl_xor_sync(ALL, sd, o);
+    }
+    if constexpr (G >= 8) v[0] += __shfl_xor_sync(ALL, v[0], 1);
+}
+
+// (first entry, count) whose sums the lane stores after group_sum4: one
+// lane per entry (G >= 4), two entries per lane (G = 2), all four (G = 1)
+template <int G>
+__device__ __forceinline__ int2 group_sum4_owned(int sub) {
+    if constexpr (G >= 8) return make_int2((sub >> 1) & 3, (sub & 1) == 0 && sub < 8 ? 1 : 0);
+    else if constexpr (G == 4) return make_int2(sub, 1);
+    else if constexpr (G == 2) return make_int2(2 * sub, 2);
+    else return make_int2(0, 4);
+}
+
+template <typename FT, int G>
 __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_constant__ Cams cams,
                                                               const __grid_constant__ RParams P, const BwdArgs a,
-                                                              int pch, int rowe, int G, int ucap) {
+                                                              int pch, int rowe, int ucap) {
     constexpr int E = FeatVec<FT>::E;
+    constexpr int gpw = 32 / G, ngroups = (BWD_FEAT_THREADS / 32) * gpw;  // groups of G lanes
     extern __shared__ __align__(16) unsigned char smem[];
     FT* s_df = reinterpret_cast<FT*>(smem);                                      // [pch][rowe]
-    int* s_ent = reinterpret_cast<int*>(smem + (((size_t)pch * rowe * sizeof(FT) + 15) & ~(size_t)15));
-    float* s_ew = reinterpret_cast<float*>(s_ent + ECAP);   // [ECAP] weights, grouped by slot
-    int* s_inv = reinterpret_cast<int*>(s_ew + ECAP);       // [ECAP] slot -> list position
+    int2* s_rec = reinterpret_cast<int2*>(smem + (((size_t)pch * rowe * sizeof(FT) + 15) & ~(size_t)15));  // [ECAP]
+    int* s_inv = reinterpret_cast<int*>(s_rec + ECAP);      // [ECAP] slot -> list position
     float* s_dot = reinterpret_cast<float*>(s_inv + ECAP);  // [ECAP] dots by entry (pixel * K + k)
-    int* s_gs = reinterpret_cast<int*>(s_dot + ECAP);       // [ucap] slot -> gradient slot (this row pass)
+    unsigned short* s_e = reinterpret_cast<unsigned short*>(s_dot + ECAP);  // [ECAP] record position -> entry
+    int* s_gs = reinterpret_cast<int*>(s_e + ECAP);         // [ucap] slot -> gradient slot (this row pass)
     unsigned char* uni = reinterpret_cast<unsigned char*>(s_gs + ((ucap + 3) & ~3));
     int* s_tab = reinterpret_cast<int*>(uni);  // [PTAB] position -> slot
     int* s_off = s_tab + PTAB;                 // [ECAP + 1] per-slot counts -> offsets
@@ -123,13 +172,15 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
 
     if (a.st->err) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int npx = TS * TS;
+    const int TS = P.ts, lts = TS == 8 ? 3 : TS == 16 ? 4 : 5, npx = TS * TS;
     const int K = P.K, C = P.C, nvec = C / E;
+    const int row16 = rowe * (int)sizeof(FT) / 16;  // padded row in 16-byte units
     const FastDiv divK(K), divV(nvec);
     const int rv = BWD_FEAT_THREADS / nvec, r0v = tid / nvec, v0 = tid - r0v * nvec;  // row-chunk mapping
-    const int sub = lane & (G - 1), gpw = 32 / G;                                      // groups of G lanes
-    const int gid = warp * gpw + lane / G, ngroups = (BWD_FEAT_THREADS / 32) * gpw;
+    const int sub = lane & (G - 1), gid = warp * gpw + lane / G;
     const bool chunk_live = sub < nvec;
+    const int2 own = group_sum4_owned<G>(sub);
+    const unsigned char* dfl = reinterpret_cast<const unsigned char*>(s_df) + sub * 16;  // this lane's chunk
     const FT* __restrict__ feats = reinterpret_cast<const FT*>(a.feats);
     const FT* __restrict__ dF = reinterpret_cast<const FT*>(a.d_feat);
     for (int t = next_tile_q(a.persistent, &a.st->work_feat, &s_tile, true); t < cams.total_tiles;
@@ -144,7 +195,8 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
         for (int pc0 = 0; pc0 < npx; pc0 += pch) {
             const int np = min(pch, npx - pc0), ne = np * K;
             // 1. this thread's entries (e = tid + i * BLOCK): list position and weight
-            int epos[EPT], eq[EPT];
+            // (the chunk pixel q and k follow from e; only these two stay live)
+            int epos[EPT];
             float ew[EPT];
             int lmax = 0;
 #pragma unroll
@@ -152,11 +204,9 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                 const int e = tid + i * BWD_FEAT_THREADS;
                 epos[i] = -1;
                 ew[i] = 0.0f;
-                eq[i] = 0;
                 if (e < ne) {
                     const int q = divK.div(e), k = e - q * K, p = pc0 + q;
-                    const int px = tx * TS + p % TS, py = ty * TS + p / TS;
-                    eq[i] = (q << 5) | k;
+                    const int px = tx * TS + (p & (TS - 1)), py = ty * TS + (p >> lts);
                     if (px < cam.W && py < cam.H) {
                         const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
                         epos[i] = a.saved_pos[pix * K + k];
@@ -178,7 +228,7 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                     uint4 val[STAGE_UNROLL];
 #pragma unroll
                     for (int u = 0; u < STAGE_UNROLL; ++u) {
-                        const int q = qb + u * rv, p = pc0 + q, px = tx * TS + p % TS, py = ty * TS + p / TS;
+                        const int q = qb + u * rv, p = pc0 + q, px = tx * TS + (p & (TS - 1)), py = ty * TS + (p >> lts);
                         val[u] = make_uint4(0u, 0u, 0u, 0u);
                         if (q < np && px < cam.W && py < cam.H)
                             val[u] = __ldg(reinterpret_cast<const uint4*>(
@@ -235,8 +285,9 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                     base = __shfl_sync(0xffffffffu, base, leader);
                     if (in) {
                         const int at = base + __popc(peers & ((1u << lane) - 1u));
-                        s_ent[at] = (eslot[i] << 15) | eq[i];
-                        s_ew[at] = ew[i];
+                        const int e = tid + i * BWD_FEAT_THREADS;
+                        s_rec[at] = make_int2((eslot[i] << REC_ROW_BITS) | (divK.div(e) * row16), __float_as_int(ew[i]));
+                        s_e[at] = (unsigned short)e;
                     }
                 }
                 const int npass = (U + ucap - 1) / ucap;  // <= MAX_ROW_PASSES (checked by the launcher)
@@ -270,76 +321,94 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                         }
                     }
                     __syncthreads();
-                    // 4. equal contiguous entry ranges per group of G lanes, two entries per
-                    // step (warp-uniform trip count; a range length of 2 mod 4 keeps the
-                    // groups' shared-memory reads on distinct banks)
-                    int len = (ee - eb + ngroups - 1) / ngroups;
-                    len = ((len + 1) & ~3) + 2;
-                    const int i0 = eb + gid * len, i1 = min(ee, i0 + len);
-                    int cur = -1;
-                    float f[E], acc[E];
+                    // 4. equal contiguous record ranges per group, starting at an even record
+                    // (records are read two at a time), four records per step (warp-uniform
+                    // trip count)
+                    const int ea = eb & ~1;
+                    const int len = (((ee - ea + ngroups - 1) / ngroups) + 3) & ~3;
+                    const int i0 = ea + gid * len, i1 = min(ee, i0 + len);
+                    int cur = -1;  // the group's current slot
+                    float2 f2[E / 2], acc2[E / 2];
 #pragma unroll
-                    for (int e = 0; e < E; ++e) { f[e] = 0.0f; acc[e] = 0.0f; }
-                    for (int st = 0; st < len; st += 2) {
-                        float dd[2];
-                        int en[2];
+                    for (int e = 0; e < E / 2; ++e) { f2[e] = make_float2(0.0f, 0.0f); acc2[e] = f2[e]; }
+                    // flush the current slot's w dL/dF, then move to `slot`
+                    auto next_slot = [&](int slot) {
+                        if (chunk_live) {
+                            if (cur >= 0) {
+                                float* dst = a.feat_acc + (int64_t)s_gs[cur - u0] * C + sub * E;
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int i = i0 + st + h;
-                            const bool live = i < i1;
-                            const int ent = live ? s_ent[i] : -1;
-                            en[h] = ent;
-                            const int slot = ent_slot(ent) - u0;
-                            if (live && slot != cur) {
-                                if (cur >= 0 && chunk_live) {
-                                    float* dst = a.feat_acc + (int64_t)s_gs[cur] * C + sub * E;
-#pragma unroll
-                                    for (int e = 0; e < E; e += 4) red_add_v4(dst + e, acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
-                                }
-                                cur = slot;
-                                if (chunk_live) FeatVec<FT>::lds(s_rows + (size_t)slot * rowe + sub * E, f);
-#pragma unroll
-                                for (int e = 0; e < E; ++e) acc[e] = 0.0f;
+                                for (int e = 0; e < E / 2; e += 2)
+                                    red_add_v4(dst + 2 * e, acc2[e].x, acc2[e].y, acc2[e + 1].x, acc2[e + 1].y);
                             }
-                            float d0 = 0.0f, d1 = 0.0f;
-                            if (live && chunk_live) {
-                                const float w = s_ew[i];
-                                float g[E];
-                                FeatVec<FT>::lds(s_df + (size_t)ent_q(ent) * rowe + sub * E, g);
+                            if (slot >= 0) {
+                                float fv[E];
+                                FeatVec<FT>::lds(s_rows + (size_t)(slot - u0) * rowe + sub * E, fv);
 #pragma unroll
-                                for (int e = 0; e < E; e += 2) {
-                                    d0 = fmaf(f[e], g[e], d0);
-                                    d1 = fmaf(f[e + 1], g[e + 1], d1);
-                                    acc[e] = fmaf(w, g[e], acc[e]);
-                                    acc[e + 1] = fmaf(w, g[e + 1], acc[e + 1]);
-                                }
+                                for (int e = 0; e < E / 2; ++e) f2[e] = make_float2(fv[2 * e], fv[2 * e + 1]);
                             }
-                            dd[h] = d0 + d1;
-                        }
-                        for (int o = G >> 1; o > 0; o >>= 1) {
-                            dd[0] += __shfl_xor_sync(0xffffffffu, dd[0], o);
-                            dd[1] += __shfl_xor_sync(0xffffffffu, dd[1], o);
-                        }
-                        if (sub == 0) {
 #pragma unroll
-                            for (int h = 0; h < 2; ++h)
-                                if (en[h] >= 0) s_dot[ent_q(en[h]) * K + (en[h] & 31)] = dd[h];
+                            for (int e = 0; e < E / 2; ++e) acc2[e] = make_float2(0.0f, 0.0f);
+                        }
+                        cur = slot;
+                    };
+                    // one record of the current slot: returns the lane's partial dot
+                    auto take = [&](int2 r, bool live) {
+                        float2 d = make_float2(0.0f, 0.0f);
+                        if (chunk_live && live) {
+                            float g[E];
+                            FeatVec<FT>::lds(reinterpret_cast<const FT*>(dfl + (size_t)(r.x & REC_ROW_MASK) * 16), g);
+                            const float w = __int_as_float(r.y);
+                            const float2 w2 = make_float2(w, w);
+#pragma unroll
+                            for (int e = 0; e < E / 2; ++e) {
+                                const float2 g2 = make_float2(g[2 * e], g[2 * e + 1]);
+                                d = __ffma2_rn(f2[e], g2, d);
+                                acc2[e] = __ffma2_rn(w2, g2, acc2[e]);
+                            }
+                        }
+                        return d.x + d.y;
+                    };
+                    for (int st = 0; st < len; st += 4) {
+                        const int i = i0 + st;
+                        int4 ra = make_int4(-1, 0, -1, 0), rb = ra;
+                        if (i < i1) ra = *reinterpret_cast<const int4*>(s_rec + i);
+                        if (i + 2 < i1) rb = *reinterpret_cast<const int4*>(s_rec + i + 2);
+                        const int2 r[4] = {make_int2(ra.x, ra.y), make_int2(ra.z, ra.w), make_int2(rb.x, rb.y),
+                                           make_int2(rb.z, rb.w)};
+                        float v[4];
+                        // steady: all four records continue the group's current slot (sorted
+                        // records: the fourth decides), or the group's range is used up
+                        const bool done = i >= i1;
+                        const bool steady = done || (i >= eb && i + 3 < i1 && (rb.z >> REC_ROW_BITS) == cur);
+                        if (__all_sync(0xffffffffu, steady)) {  // warp-uniform: no per-record checks
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) v[j] = take(r[j], !done);
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const bool live = i + j >= eb && i + j < i1;
+                                const int slot = r[j].x >> REC_ROW_BITS;
+                                if (live && slot != cur) next_slot(slot);
+                                v[j] = take(r[j], live);
+                            }
+                        }
+                        group_sum4<G>(v, sub);
+#pragma unroll
+                        for (int j = 0; j < (G >= 4 ? 1 : 4 / G); ++j) {
+                            const int at = i + own.x + j;
+                            if (j < own.y && at >= eb && at < i1) s_dot[s_e[at]] = v[j];
                         }
                     }
-                    if (cur >= 0 && chunk_live) {
-                        float* dst = a.feat_acc + (int64_t)s_gs[cur] * C + sub * E;
-#pragma unroll
-                        for (int e = 0; e < E; e += 4) red_add_v4(dst + e, acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
-                    }
+                    next_slot(-1);
                     __syncthreads();
                 }
                 // the dots of this pass's entries, written back in (pixel, k) order
 #pragma unroll
                 for (int i = 0; i < EPT; ++i) {
-                    if (eslot[i] >= 0) {
-                        const int e = tid + i * BWD_FEAT_THREADS, q = eq[i] >> 5, p = pc0 + q;
-                        const int64_t pix = cam.pix_off + (int64_t)(ty * TS + p / TS) * cam.W + tx * TS + p % TS;
-                        a.dots[pix * K + (eq[i] & 31)] = s_dot[e];
+                    if (epos[i] >= p0 && epos[i] < p0 + PTAB) {
+                        const int e = tid + i * BWD_FEAT_THREADS, q = divK.div(e), p = pc0 + q;
+                        const int64_t pix = cam.pix_off + (int64_t)(ty * TS + (p >> lts)) * cam.W + tx * TS + (p & (TS - 1));
+                        a.dots[pix * K + (e - q * K)] = s_dot[e];
                     }
                 }
             }
@@ -844,7 +913,7 @@ cudaError_t launch_feat(const Cams& cams, const RParams& P, const BwdArgs& a, cu
     const int npx = P.ts * P.ts;
     int pch = std::min(npx, ECAP / std::max(1, P.K));
     pch = (int)std::min<size_t>((size_t)pch, std::max<size_t>(32, (24 * 1024) / rowb));
-    const size_t smem = (((size_t)pch * rowb + 15) & ~(size_t)15) + (size_t)4 * ECAP * 4 +
+    const size_t smem = (((size_t)pch * rowb + 15) & ~(size_t)15) + (size_t)4 * ECAP * 4 + (size_t)2 * ECAP +
                         (size_t)((ucap + 3) & ~3) * 4 + FEAT_UNION_BYTES;
     auto go = [&](auto kern) {
         cudaError_t e2 = set_smem((const void*)kern, smem);
@@ -852,14 +921,19 @@ cudaError_t launch_feat(const Cams& cams, const RParams& P, const BwdArgs& a, cu
         int grid = cams.total_tiles;
         if (a.persistent && (e2 = persistent_grid((const void*)kern, BWD_FEAT_THREADS, smem, grid)) != cudaSuccess)
             return e2;
-        kern<<<grid, BWD_FEAT_THREADS, smem, s>>>(cams, P, a, pch, rowe, G, ucap);
+        kern<<<grid, BWD_FEAT_THREADS, smem, s>>>(cams, P, a, pch, rowe, ucap);
         e2 = cudaGetLastError();
         if (e2 == cudaSuccess) kernel_mark(s);
         return e2;
     };
-    if (P.ts == 8) return go(k_bwd_feat<8, FT>);
-    if (P.ts == 16) return go(k_bwd_feat<16, FT>);
-    return go(k_bwd_feat<32, FT>);
+    switch (G) {
+        case 1: return go(k_bwd_feat<FT, 1>);
+        case 2: return go(k_bwd_feat<FT, 2>);
+        case 4: return go(k_bwd_feat<FT, 4>);
+        case 8: return go(k_bwd_feat<FT, 8>);
+        case 16: return go(k_bwd_feat<FT, 16>);
+        default: return go(k_bwd_feat<FT, 32>);
+    }
 }
 
 template <int TS, bool FULL, int CMAX, typename FT, bool VAR = false>
