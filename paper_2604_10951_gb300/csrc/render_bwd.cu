@@ -99,7 +99,6 @@ constexpr int PTAB = 2048;  // list positions per pass
 constexpr int EPT = ECAP / BWD_FEAT_THREADS;  // entries per thread
 constexpr int FEAT_UNION_BYTES = (PTAB + 2 * ECAP + 1) * 4;  // counting-sort tables, then feature rows
 constexpr int MAX_ROW_PASSES = 64;
-constexpr int STAGE_UNROLL = 4;  // global loads in flight per thread while staging
 
 // entry record .x: slot << REC_ROW_BITS | offset of the entry's dL/dF row in
 // 16-byte units (slot < PTAB = 2^11, offset < 2^17: 28 bits); .y: weight bits
@@ -137,6 +136,19 @@ __device__ __forceinline__ void group_sum4(float (&v)[4], int sub) {
     if constexpr (G >= 8) v[0] += __shfl_xor_sync(ALL, v[0], 1);
 }
 
+// 16-byte asynchronous global -> shared copy (bytes = 0: zero fill), its
+// commit and the wait for all of this thread's copies
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// rows of zeros after the chunk's dL/dF rows: at least G 16-byte chunks, so
+// a lane without a record (or past the row) reads zeros
+__host__ __device__ constexpr int zero_rows(int G, int rowb) { return (G * 16 + rowb - 1) / rowb; }
+
 // (first entry, count) whose sums the lane stores after group_sum4: one
 // lane per entry (G >= 4), two entries per lane (G = 2), all four (G = 1)
 template <int G>
@@ -154,8 +166,9 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
     constexpr int E = FeatVec<FT>::E;
     constexpr int gpw = 32 / G, ngroups = (BWD_FEAT_THREADS / 32) * gpw;  // groups of G lanes
     extern __shared__ __align__(16) unsigned char smem[];
-    FT* s_df = reinterpret_cast<FT*>(smem);                                      // [pch][rowe]
-    int2* s_rec = reinterpret_cast<int2*>(smem + (((size_t)pch * rowe * sizeof(FT) + 15) & ~(size_t)15));  // [ECAP]
+    const int rowb = rowe * (int)sizeof(FT), zr = zero_rows(G, rowb);
+    FT* s_df = reinterpret_cast<FT*>(smem);  // [pch + zr][rowe]: the chunk's dL/dF rows, then zeros
+    int2* s_rec = reinterpret_cast<int2*>(smem + (((size_t)(pch + zr) * rowb + 15) & ~(size_t)15));  // [ECAP]
     int* s_inv = reinterpret_cast<int*>(s_rec + ECAP);      // [ECAP] slot -> list position
     float* s_dot = reinterpret_cast<float*>(s_inv + ECAP);  // [ECAP] dots by entry (pixel * K + k)
     unsigned short* s_e = reinterpret_cast<unsigned short*>(s_dot + ECAP);  // [ECAP] record position -> entry
@@ -174,8 +187,12 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int TS = P.ts, lts = TS == 8 ? 3 : TS == 16 ? 4 : 5, npx = TS * TS;
     const int K = P.K, C = P.C, nvec = C / E;
-    const int row16 = rowe * (int)sizeof(FT) / 16;  // padded row in 16-byte units
+    const int row16 = rowb / 16, zoff16 = pch * row16;  // padded row, first zero row (16-byte units)
     const FastDiv divK(K), divV(nvec);
+    // chunk pixel of entry e = tid + i * BLOCK: a constant step when K divides the block
+    const bool kdiv = BWD_FEAT_THREADS % K == 0;
+    const int q0 = divK.div(tid), qstep = BWD_FEAT_THREADS / K;
+    auto entry_q = [&](int i, int e) { return kdiv ? q0 + i * qstep : divK.div(e); };
     const int rv = BWD_FEAT_THREADS / nvec, r0v = tid / nvec, v0 = tid - r0v * nvec;  // row-chunk mapping
     const int sub = lane & (G - 1), gid = warp * gpw + lane / G;
     const bool chunk_live = sub < nvec;
@@ -183,6 +200,9 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
     const unsigned char* dfl = reinterpret_cast<const unsigned char*>(s_df) + sub * 16;  // this lane's chunk
     const FT* __restrict__ feats = reinterpret_cast<const FT*>(a.feats);
     const FT* __restrict__ dF = reinterpret_cast<const FT*>(a.d_feat);
+    for (int i = tid; i < zr * rowb / 16; i += BWD_FEAT_THREADS)
+        reinterpret_cast<uint4*>(s_df + (size_t)pch * rowe)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
     for (int t = next_tile_q(a.persistent, &a.st->work_feat, &s_tile, true); t < cams.total_tiles;
          t = next_tile_q(a.persistent, &a.st->work_feat, &s_tile, false)) {
         const int view = view_of_tile(cams, t);
@@ -194,6 +214,17 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
 
         for (int pc0 = 0; pc0 < npx; pc0 += pch) {
             const int np = min(pch, npx - pc0), ne = np * K;
+            // the chunk's dL/dF rows (zeros outside the image), copied asynchronously and
+            // waited for just before the inner loop, so that the copies overlap steps 1-3
+            if (r0v < rv) {
+                for (int q = r0v; q < np; q += rv) {
+                    const int p = pc0 + q, px = tx * TS + (p & (TS - 1)), py = ty * TS + (p >> lts);
+                    const bool in = px < cam.W && py < cam.H;
+                    const FT* src = in ? dF + (cam.pix_off + (int64_t)py * cam.W + px) * C + v0 * E : dF;
+                    cp_async16(s_df + (size_t)q * rowe + v0 * E, src, in ? 16 : 0);
+                }
+            }
+            cp_async_commit();
             // 1. this thread's entries (e = tid + i * BLOCK): list position and weight
             // (the chunk pixel q and k follow from e; only these two stay live)
             int epos[EPT];
@@ -205,7 +236,7 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                 epos[i] = -1;
                 ew[i] = 0.0f;
                 if (e < ne) {
-                    const int q = divK.div(e), k = e - q * K, p = pc0 + q;
+                    const int q = entry_q(i, e), k = e - q * K, p = pc0 + q;
                     const int px = tx * TS + (p & (TS - 1)), py = ty * TS + (p >> lts);
                     if (px < cam.W && py < cam.H) {
                         const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
@@ -221,26 +252,6 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                 }
             }
             if (tid == 0) s_max = 0;
-            // the chunk's dL/dF rows (zeros outside the image), STAGE_UNROLL loads in
-            // flight per thread before their shared-memory stores
-            if (r0v < rv) {
-                for (int qb = r0v; qb < np; qb += STAGE_UNROLL * rv) {
-                    uint4 val[STAGE_UNROLL];
-#pragma unroll
-                    for (int u = 0; u < STAGE_UNROLL; ++u) {
-                        const int q = qb + u * rv, p = pc0 + q, px = tx * TS + (p & (TS - 1)), py = ty * TS + (p >> lts);
-                        val[u] = make_uint4(0u, 0u, 0u, 0u);
-                        if (q < np && px < cam.W && py < cam.H)
-                            val[u] = __ldg(reinterpret_cast<const uint4*>(
-                                dF + (cam.pix_off + (int64_t)py * cam.W + px) * C + v0 * E));
-                    }
-#pragma unroll
-                    for (int u = 0; u < STAGE_UNROLL; ++u) {
-                        const int q = qb + u * rv;
-                        if (q < np) *reinterpret_cast<uint4*>(s_df + (size_t)q * rowe + v0 * E) = val[u];
-                    }
-                }
-            }
             __syncthreads();
             atomicMax(&s_max, lmax);
             __syncthreads();
@@ -286,7 +297,7 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                     if (in) {
                         const int at = base + __popc(peers & ((1u << lane) - 1u));
                         const int e = tid + i * BWD_FEAT_THREADS;
-                        s_rec[at] = make_int2((eslot[i] << REC_ROW_BITS) | (divK.div(e) * row16), __float_as_int(ew[i]));
+                        s_rec[at] = make_int2((eslot[i] << REC_ROW_BITS) | (entry_q(i, e) * row16), __float_as_int(ew[i]));
                         s_e[at] = (unsigned short)e;
                     }
                 }
@@ -320,6 +331,7 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                             }
                         }
                     }
+                    cp_async_wait_all();
                     __syncthreads();
                     // 4. equal contiguous record ranges per group, starting at an even record
                     // (records are read two at a time), four records per step (warp-uniform
@@ -352,19 +364,19 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                         cur = slot;
                     };
                     // one record of the current slot: returns the lane's partial dot
+                    // (no record: the zero row and weight 0, so the code has no branch)
                     auto take = [&](int2 r, bool live) {
+                        const bool on = chunk_live && live;
+                        float g[E];
+                        FeatVec<FT>::lds(reinterpret_cast<const FT*>(dfl + (size_t)(on ? r.x & REC_ROW_MASK : zoff16) * 16), g);
+                        const float w = on ? __int_as_float(r.y) : 0.0f;
+                        const float2 w2 = make_float2(w, w);
                         float2 d = make_float2(0.0f, 0.0f);
-                        if (chunk_live && live) {
-                            float g[E];
-                            FeatVec<FT>::lds(reinterpret_cast<const FT*>(dfl + (size_t)(r.x & REC_ROW_MASK) * 16), g);
-                            const float w = __int_as_float(r.y);
-                            const float2 w2 = make_float2(w, w);
 #pragma unroll
-                            for (int e = 0; e < E / 2; ++e) {
-                                const float2 g2 = make_float2(g[2 * e], g[2 * e + 1]);
-                                d = __ffma2_rn(f2[e], g2, d);
-                                acc2[e] = __ffma2_rn(w2, g2, acc2[e]);
-                            }
+                        for (int e = 0; e < E / 2; ++e) {
+                            const float2 g2 = make_float2(g[2 * e], g[2 * e + 1]);
+                            d = __ffma2_rn(f2[e], g2, d);
+                            acc2[e] = __ffma2_rn(w2, g2, acc2[e]);
                         }
                         return d.x + d.y;
                     };
@@ -406,12 +418,13 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
 #pragma unroll
                 for (int i = 0; i < EPT; ++i) {
                     if (epos[i] >= p0 && epos[i] < p0 + PTAB) {
-                        const int e = tid + i * BWD_FEAT_THREADS, q = divK.div(e), p = pc0 + q;
+                        const int e = tid + i * BWD_FEAT_THREADS, q = entry_q(i, e), p = pc0 + q;
                         const int64_t pix = cam.pix_off + (int64_t)(ty * TS + (p >> lts)) * cam.W + tx * TS + (p & (TS - 1));
                         a.dots[pix * K + (e - q * K)] = s_dot[e];
                     }
                 }
             }
+            cp_async_wait_all();  // (a chunk without selected entries never waited)
             __syncthreads();
         }
     }
@@ -913,7 +926,8 @@ cudaError_t launch_feat(const Cams& cams, const RParams& P, const BwdArgs& a, cu
     const int npx = P.ts * P.ts;
     int pch = std::min(npx, ECAP / std::max(1, P.K));
     pch = (int)std::min<size_t>((size_t)pch, std::max<size_t>(32, (24 * 1024) / rowb));
-    const size_t smem = (((size_t)pch * rowb + 15) & ~(size_t)15) + (size_t)4 * ECAP * 4 + (size_t)2 * ECAP +
+    const size_t smem = (((size_t)(pch + zero_rows(G, (int)rowb)) * rowb + 15) & ~(size_t)15) + (size_t)4 * ECAP * 4 +
+                        (size_t)2 * ECAP +
                         (size_t)((ucap + 3) & ~3) * 4 + FEAT_UNION_BYTES;
     auto go = [&](auto kern) {
         cudaError_t e2 = set_smem((const void*)kern, smem);
