@@ -104,6 +104,7 @@ constexpr int MAX_ROW_PASSES = 64;
 // 16-byte units (slot < PTAB = 2^11, offset < 2^17: 28 bits); .y: weight bits
 constexpr int REC_ROW_BITS = 17;
 constexpr int REC_ROW_MASK = (1 << REC_ROW_BITS) - 1;
+constexpr int DOT_UNSET = 0x7fa00001;  // signalling-NaN payload: a dot not formed
 
 // Sums of four values v[0..3] over the G lanes of a group (G a power of two,
 // groups aligned in the warp), scattered: lanes swap halves of what is left
@@ -179,7 +180,6 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
     int* s_cur = s_off + ECAP + 1;             // [ECAP] scatter cursors
     FT* s_rows = reinterpret_cast<FT*>(uni);   // [ucap][rowe] feature rows (after the counting sort)
     __shared__ int s_red[33];
-    __shared__ int s_max;
     __shared__ int s_tile;
     __shared__ int s_pass[MAX_ROW_PASSES + 1];
 
@@ -225,38 +225,39 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                 }
             }
             cp_async_commit();
-            // 1. this thread's entries (e = tid + i * BLOCK): list position and weight
-            // (the chunk pixel q and k follow from e; only these two stay live)
-            int epos[EPT];
-            float ew[EPT];
-            int lmax = 0;
+            // dots not yet formed read as a sentinel (a NaN payload that arithmetic does
+            // not produce), so the write-back needs no per-entry state
+            for (int e = tid; e < ne; e += BWD_FEAT_THREADS) s_dot[e] = __int_as_float(DOT_UNSET);
+            // list positions in passes of PTAB (one pass unless the tile's list is longer)
+            const int L = rg.y - rg.x;
+            for (int p0 = 0; p0 < L; p0 += PTAB) {
+                // 1. this thread's entries (e = tid + i * BLOCK) in this pass: list position
+                // and weight (the chunk pixel q and k follow from e)
+                int epos[EPT];
+                float ew[EPT];
 #pragma unroll
-            for (int i = 0; i < EPT; ++i) {
-                const int e = tid + i * BWD_FEAT_THREADS;
-                epos[i] = -1;
-                ew[i] = 0.0f;
-                if (e < ne) {
-                    const int q = entry_q(i, e), k = e - q * K, p = pc0 + q;
-                    const int px = tx * TS + (p & (TS - 1)), py = ty * TS + (p >> lts);
-                    if (px < cam.W && py < cam.H) {
-                        const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
-                        epos[i] = a.saved_pos[pix * K + k];
-                        ew[i] = a.saved_w[pix * K + k];
-                        if (P.renorm) {  // dL/dc = (w / W) dL/dF, W the selected weights' sum
-                            float ws = 0.0f;
-                            for (int k2 = 0; k2 < K; ++k2) ws += a.saved_w[pix * K + k2];
-                            ew[i] = ws > 0.0f ? ew[i] / ws : 0.0f;
+                for (int i = 0; i < EPT; ++i) {
+                    const int e = tid + i * BWD_FEAT_THREADS;
+                    epos[i] = -1;
+                    ew[i] = 0.0f;
+                    if (e < ne) {
+                        const int q = entry_q(i, e), k = e - q * K, p = pc0 + q;
+                        const int px = tx * TS + (p & (TS - 1)), py = ty * TS + (p >> lts);
+                        if (px < cam.W && py < cam.H) {
+                            const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
+                            const int pos = a.saved_pos[pix * K + k];
+                            if (pos >= p0 && pos < p0 + PTAB) {
+                                epos[i] = pos - p0;
+                                ew[i] = a.saved_w[pix * K + k];
+                                if (P.renorm) {  // dL/dc = (w / W) dL/dF, W the selected weights' sum
+                                    float ws = 0.0f;
+                                    for (int k2 = 0; k2 < K; ++k2) ws += a.saved_w[pix * K + k2];
+                                    ew[i] = ws > 0.0f ? ew[i] / ws : 0.0f;
+                                }
+                            }
                         }
-                        lmax = max(lmax, epos[i] + 1);
                     }
                 }
-            }
-            if (tid == 0) s_max = 0;
-            __syncthreads();
-            atomicMax(&s_max, lmax);
-            __syncthreads();
-            const int L = s_max;
-            for (int p0 = 0; p0 < L; p0 += PTAB) {
                 // 2. slots of the selected positions, then the entries grouped by slot
                 const int nt = min(PTAB, L - p0);  // positions in use (U <= nt)
                 for (int i = tid; i < nt; i += BWD_FEAT_THREADS) s_tab[i] = 0;
@@ -264,7 +265,7 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                 __syncthreads();
 #pragma unroll
                 for (int i = 0; i < EPT; ++i)
-                    if (epos[i] >= p0 && epos[i] < p0 + PTAB) s_tab[epos[i] - p0] = 1;
+                    if (epos[i] >= 0) s_tab[epos[i]] = 1;
                 __syncthreads();
                 const int U = block_exscan(s_tab, nt, s_red);  // s_tab[pos] = slot where marked
                 if (U == 0) continue;
@@ -275,8 +276,8 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                 int eslot[EPT];
 #pragma unroll
                 for (int i = 0; i < EPT; ++i) {
-                    const bool in = epos[i] >= p0 && epos[i] < p0 + PTAB;
-                    eslot[i] = in ? s_tab[epos[i] - p0] : -1;
+                    const bool in = epos[i] >= 0;
+                    eslot[i] = in ? s_tab[epos[i]] : -1;
                     // lanes with the same slot add their count once
                     const unsigned peers = __match_any_sync(0xffffffffu, in ? eslot[i] : -1 - lane);
                     if (in && lane == __ffs(peers) - 1) atomicAdd(&s_off[eslot[i]], __popc(peers));
@@ -414,14 +415,16 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                     next_slot(-1);
                     __syncthreads();
                 }
-                // the dots of this pass's entries, written back in (pixel, k) order
+            }
+            // the dots, written back in (pixel, k) order
 #pragma unroll
-                for (int i = 0; i < EPT; ++i) {
-                    if (epos[i] >= p0 && epos[i] < p0 + PTAB) {
-                        const int e = tid + i * BWD_FEAT_THREADS, q = entry_q(i, e), p = pc0 + q;
-                        const int64_t pix = cam.pix_off + (int64_t)(ty * TS + (p >> lts)) * cam.W + tx * TS + (p & (TS - 1));
-                        a.dots[pix * K + (e - q * K)] = s_dot[e];
-                    }
+            for (int i = 0; i < EPT; ++i) {
+                const int e = tid + i * BWD_FEAT_THREADS;
+                const float d = e < ne ? s_dot[e] : __int_as_float(DOT_UNSET);
+                if (__float_as_int(d) != DOT_UNSET) {
+                    const int q = entry_q(i, e), p = pc0 + q;
+                    const int64_t pix = cam.pix_off + (int64_t)(ty * TS + (p >> lts)) * cam.W + tx * TS + (p & (TS - 1));
+                    a.dots[pix * K + (e - q * K)] = d;
                 }
             }
             cp_async_wait_all();  // (a chunk without selected entries never waited)
