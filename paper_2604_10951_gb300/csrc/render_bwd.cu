@@ -308,30 +308,15 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                 for (int pi = 0; pi < npass; ++pi) {
                     const int u0 = pi * ucap, nu = min(ucap, U - u0);
                     const int eb = s_pass[pi], ee = s_pass[pi + 1];
-                    // 3. feature rows of slots [u0, u0 + nu) (over the counting-sort tables)
-                    for (int ib = tid; ib < nu * nvec; ib += 2 * BWD_FEAT_THREADS) {
-                        uint4 val[2];
-                        int64_t sp[2];
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int idx = ib + h * BWD_FEAT_THREADS;
-                            const int u = divV.div(idx);
-                            sp[h] = idx < nu * nvec ? (int64_t)a.list[rg.x + p0 + s_inv[u0 + u]] - vbase : -1;
-                        }
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int idx = ib + h * BWD_FEAT_THREADS, u = divV.div(idx), v = idx - u * nvec;
-                            if (sp[h] >= 0) val[h] = __ldg(reinterpret_cast<const uint4*>(feats + sp[h] * C + v * E));
-                        }
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const int idx = ib + h * BWD_FEAT_THREADS, u = divV.div(idx), v = idx - u * nvec;
-                            if (sp[h] >= 0) {
-                                *reinterpret_cast<uint4*>(s_rows + (size_t)u * rowe + v * E) = val[h];
-                                if (v == 0) s_gs[u] = a.splat_slot[sp[h]];
-                            }
-                        }
+                    // 3. feature rows of slots [u0, u0 + nu) (over the counting-sort tables),
+                    // copied asynchronously like the dL/dF rows
+                    for (int idx = tid; idx < nu * nvec; idx += BWD_FEAT_THREADS) {
+                        const int u = divV.div(idx), v = idx - u * nvec;
+                        const int64_t sp = (int64_t)a.list[rg.x + p0 + s_inv[u0 + u]] - vbase;
+                        cp_async16(s_rows + (size_t)u * rowe + v * E, feats + sp * C + v * E, 16);
+                        if (v == 0) s_gs[u] = a.splat_slot[sp];
                     }
+                    cp_async_commit();
                     cp_async_wait_all();
                     __syncthreads();
                     // 4. equal contiguous record ranges per group, starting at an even record
