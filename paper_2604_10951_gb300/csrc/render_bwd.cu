@@ -910,7 +910,8 @@ cudaError_t launch_feat(const Cams& cams, const RParams& P, const BwdArgs& a, cu
     const int rowe = P.C + 16 / (int)sizeof(FT);  // padded row, elements
     const size_t rowb = (size_t)rowe * sizeof(FT);
     const int ucap = (int)(FEAT_UNION_BYTES / rowb);  // feature rows per pass
-    if (ucap < 1 || (PTAB + ucap - 1) / ucap > MAX_ROW_PASSES) return cudaErrorInvalidValue;
+    // row passes per chunk: ceil(U / ucap), U <= ECAP (every slot has an entry)
+    if (ucap < 1 || (ECAP + ucap - 1) / ucap > MAX_ROW_PASSES) return cudaErrorInvalidValue;
     const int npx = P.ts * P.ts;
     int pch = std::min(npx, ECAP / std::max(1, P.K));
     pch = (int)std::min<size_t>((size_t)pch, std::max<size_t>(32, (24 * 1024) / rowb));
