@@ -5,6 +5,7 @@ pass logic branch on, against the oracle's FP64 analytic gradients:
   16-byte chunks in a group of four), 8, 16, 32;
 - K that does not divide the thread block (per-entry division) and K that does;
 - tile sizes 8 and 32;
+- full accumulation (K = 0) with 64- and 128-channel instances;
 - a tile whose list is longer than one pass of list positions (2048), with
   selected entries in both passes, and chunks with more distinct surfels than
   one pass of staged feature rows holds.
@@ -104,3 +105,13 @@ def test_feature_gradients_long_tile_list(dtype):
     ref = O.render(sc, cam, p, binned=b)
     pos = np.asarray(ref["pos"])[:16, :16]
     assert (pos >= 2048).any() and ((pos >= 0) & (pos < 2048)).any()
+
+
+@pytest.mark.parametrize("C,dtype,ts", [
+    (64, torch.float32, 16),     # full accumulation, 64-channel instance
+    (128, torch.float32, 16),    # 128-channel instance
+    (96, torch.bfloat16, 32),    # 128-channel instance, tile size 32, BF16
+])
+def test_full_accumulation_gradients_wide_features(C, dtype, ts):
+    sc, cam = scenes.tiny_scene(seed=31 + C, n=1000, C=C)
+    _check(sc, cam, 0, dtype, tile_size=ts, seed=C + 1)
