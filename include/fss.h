@@ -357,7 +357,11 @@ const char *fss_last_error(void);
  *   list; 13 unbounded items per view; 14 gradient slot per surfel (int32,
  *   -1 if culled in every view); 15 items spanning many tiles; 16 per-pair
  *   warp masks (uint32, written by fss_sort); 17 surfel of each gradient
- *   slot (int32).
+ *   slot (int32); 18 unit view direction and inverse distance per item
+ *   (float4, spherical-harmonic colours only); 19 colour per item (float
+ *   [3], spherical-harmonic colours only); 20 tile order (int32 [tiles]:
+ *   tiles by descending pair count, written by fss_project_bin; the tile
+ *   kernels take tiles in this order).
  * The workspace costs 24 bytes per unit of pair_capacity.
  */
 fss_status fss_workspace_region(const fss_params *params, const fss_camera *cams, int32_t n_cams, int64_t N,

@@ -32,7 +32,8 @@ REG_MASK = 16
 REG_SLOT_SURF = 17
 REG_DIR = 18
 REG_COLOR = 19
-N_REGIONS = 20
+REG_ORDER = 20
+N_REGIONS = 21
 
 EXPORTS = ["fss_default_params", "fss_workspace_size", "fss_saved_size", "fss_project_bin", "fss_sort",
            "fss_render_forward", "fss_render_backward", "fss_read_status", "fss_last_error",

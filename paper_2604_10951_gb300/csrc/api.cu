@@ -144,6 +144,7 @@ Layout make_layout(const RParams& P, const Cams& cams) {
     sz[REG_SLOT_SURF] = N * 4;
     sz[REG_DIR] = P.color_sh ? ni * 16 : 0;
     sz[REG_COLOR] = P.color_sh ? ni * 12 : 0;
+    sz[REG_ORDER] = (size_t)cams.total_tiles * 4;
     size_t off = 0;
     for (int r = 0; r < REG_COUNT_ALL; ++r) {
         L.off[r] = off;
@@ -178,6 +179,7 @@ fss_status prepare(const fss_params* params, const fss_camera* cams, int32_t n_c
     ctx.ws = reinterpret_cast<unsigned char*>(workspace);
     if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255))
         return fail(FSS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    ctx.cams.tile_order = workspace ? ctx.at<int32_t>(REG_ORDER) : nullptr;
     return FSS_OK;
 }
 
@@ -297,7 +299,8 @@ fss_status fss_project_bin(const fss_params* params, const fss_camera* cams, int
                                                ctx.at<int32_t>(REG_SLOT), ctx.at<int32_t>(REG_SLOT_SURF), stp);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_project");
     kernel_mark(st);
-    k_scan<<<1, 1024, 0, st>>>(ctx.cams, ctx.P, ctx.at<uint32_t>(REG_TILECNT), ctx.at<int2>(REG_RANGES), stp);
+    k_scan<<<1, 1024, 0, st>>>(ctx.cams, ctx.P, ctx.at<uint32_t>(REG_TILECNT), ctx.at<int2>(REG_RANGES),
+                               ctx.at<int32_t>(REG_ORDER), stp);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_scan");
     kernel_mark(st);
     // one resident wave: records run from the lowest threads up, tile emission

@@ -30,6 +30,7 @@ struct Cams {
     int32_t n;
     int32_t total_tiles;
     int64_t total_pix;
+    const int32_t* tile_order;  // [total_tiles] tiles by descending pair count (written by k_scan), or null
     CamDev c[FSS_MAX_CAMS];
 };
 
@@ -116,6 +117,7 @@ enum Region {
     REG_SLOT_SURF = 17,  // int32 [N]: surfel of each gradient slot
     REG_DIR = 18,    // float4 [items] (spherical-harmonic colours only): unit direction from the camera, 1/distance
     REG_COLOR = 19,  // float [items, 3] (spherical-harmonic colours only): each visible item's colour
+    REG_ORDER = 20,  // int32 [tiles]: the order the tile kernels take tiles in (heavy first)
     REG_COUNT_ALL
 };
 

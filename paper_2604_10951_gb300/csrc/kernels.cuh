@@ -20,7 +20,8 @@ __global__ void k_project(const __grid_constant__ Cams cams, const __grid_consta
                           uint32_t* __restrict__ unb_list, int32_t* __restrict__ splat_slot,
                           int32_t* __restrict__ slot_surf, Status* __restrict__ st);
 __global__ void k_scan(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
-                       uint32_t* __restrict__ tile_cnt, int2* __restrict__ ranges, Status* __restrict__ st);
+                       uint32_t* __restrict__ tile_cnt, int2* __restrict__ ranges, int32_t* __restrict__ order,
+                       Status* __restrict__ st);
 __global__ void k_emit(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                        const BinRec* __restrict__ binrec, const uint32_t* __restrict__ vis_list,
                        const uint32_t* __restrict__ wide_list, const uint32_t* __restrict__ unb_list,

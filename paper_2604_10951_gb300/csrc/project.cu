@@ -632,11 +632,19 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4) k_project(const __grid_consta
 
 // ---------------------------------------------------------------------------
 // k_scan: one CTA; per-tile totals (bounded pairs + the view's unbounded
-// items) -> exclusive scan -> ranges; tile_cnt becomes the emit cursor
+// items) -> exclusive scan -> ranges; tile_cnt becomes the emit cursor.
+// Then the heavy-first tile order: a counting sort of the tiles by pair
+// count, descending, in buckets of 16 pairs (the order within a bucket is
+// arbitrary).  The tile kernels take tiles in this order, so that the last
+// tiles to start are light ones: the work per tile varies severalfold, and
+// in index order a heavy tile starting late sets the kernel's end.
 // ---------------------------------------------------------------------------
+constexpr int ORDER_BUCKETS = 256;  // 32 lanes x 8
+__device__ __forceinline__ int order_bucket(int2 r) { return min(ORDER_BUCKETS - 1, (r.y - r.x) >> 4); }
+
 __global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                                                uint32_t* __restrict__ tile_cnt, int2* __restrict__ ranges,
-                                               Status* __restrict__ st) {
+                                               int32_t* __restrict__ order, Status* __restrict__ st) {
     __shared__ uint32_t warp_tot[32];
     __shared__ uint64_t carry_s;
     if (threadIdx.x == 0) carry_s = 0;
@@ -691,6 +699,34 @@ __global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ Cams cams
         st->pairs_needed = (int64_t)carry_s;
         if (carry_s > (uint64_t)P.pair_cap) st->err |= ERR_CAPACITY;
     }
+    // heavy-first order (a frame over capacity has empty ranges: any order)
+    __shared__ uint32_t ord[ORDER_BUCKETS];
+    for (int b = threadIdx.x; b < ORDER_BUCKETS; b += blockDim.x) ord[b] = 0u;
+    __syncthreads();
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) atomicAdd(&ord[order_bucket(ranges[t])], 1u);
+    __syncthreads();
+    if (wid == 0) {  // first position of each bucket, heaviest bucket first
+        uint32_t c[8], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            c[k] = ord[ORDER_BUCKETS - 1 - (8 * lane + k)];
+            sum += c[k];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        uint32_t run = incl - sum;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            ord[ORDER_BUCKETS - 1 - (8 * lane + k)] = run;
+            run += c[k];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) order[atomicAdd(&ord[order_bucket(ranges[t])], 1u)] = t;
 }
 
 // ---------------------------------------------------------------------------

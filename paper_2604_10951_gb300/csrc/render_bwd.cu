@@ -203,8 +203,8 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
     for (int i = tid; i < zr * rowb / 16; i += BWD_FEAT_THREADS)
         reinterpret_cast<uint4*>(s_df + (size_t)pch * rowe)[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
-    for (int t = next_tile_q(a.persistent, &a.st->work_feat, &s_tile, true); t < cams.total_tiles;
-         t = next_tile_q(a.persistent, &a.st->work_feat, &s_tile, false)) {
+    for (int t = next_tile_q(a.persistent, &a.st->work_feat, &s_tile, true, cams); t < cams.total_tiles;
+         t = next_tile_q(a.persistent, &a.st->work_feat, &s_tile, false, cams)) {
         const int view = view_of_tile(cams, t);
         const CamDev& cam = cams.c[view];
         const int lt = t - cam.tile_off;
@@ -442,8 +442,8 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t wbit = 1u << (tid >> 5);
     const int C = P.C, K = P.K;
-    for (int t = next_tile_q(a.persistent, &a.st->work_geo, &s_tile, true); t < cams.total_tiles;
-         t = next_tile_q(a.persistent, &a.st->work_geo, &s_tile, false)) {
+    for (int t = next_tile_q(a.persistent, &a.st->work_geo, &s_tile, true, cams); t < cams.total_tiles;
+         t = next_tile_q(a.persistent, &a.st->work_geo, &s_tile, false, cams)) {
     const int view = view_of_tile(cams, t);
     const CamDev& cam = cams.c[view];
     const int lt = t - cam.tile_off;

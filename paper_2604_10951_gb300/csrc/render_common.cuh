@@ -251,16 +251,23 @@ __device__ __forceinline__ uint32_t warp_block_mask(const BinRec* __restrict__ r
     return m;
 }
 
-// Next tile of a CTA: its own index (grid schedule), or the head of a
-// device work queue (persistent schedule).  Contains __syncthreads in the
-// persistent case, so it also separates consecutive tiles' use of shared
-// memory.
-__device__ __forceinline__ int next_tile_q(int persistent, uint32_t* queue, int* s_tile, bool first) {
-    if (!persistent) return first ? (int)blockIdx.x : INT_MAX;
-    __syncthreads();
-    if (threadIdx.x == 0) *s_tile = (int)atomicAdd(queue, 1u);
-    __syncthreads();
-    return *s_tile;
+// Next tile of a CTA: the tile at its own index (grid schedule) or at the
+// head of a device work queue (persistent schedule) in the heavy-first tile
+// order.  Contains __syncthreads in the persistent case, so it also
+// separates consecutive tiles' use of shared memory.
+__device__ __forceinline__ int next_tile_q(int persistent, uint32_t* queue, int* s_tile, bool first,
+                                           const Cams& cams) {
+    int i;
+    if (!persistent) {
+        i = first ? (int)blockIdx.x : INT_MAX;
+    } else {
+        __syncthreads();
+        if (threadIdx.x == 0) *s_tile = (int)atomicAdd(queue, 1u);
+        __syncthreads();
+        i = *s_tile;
+    }
+    // the i-th tile of the heavy-first order
+    return i < cams.total_tiles ? (cams.tile_order ? cams.tile_order[i] : i) : INT_MAX;
 }
 
 // exclusive scan of v[0, n) in shared memory by the whole CTA (n <= 8 *

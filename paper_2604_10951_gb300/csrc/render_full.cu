@@ -13,8 +13,8 @@ namespace fss {
 
 namespace {
 
-__device__ __forceinline__ int next_tile(const FwdArgs& a, int* s_tile, bool first) {
-    return next_tile_q(a.persistent, &a.st->work, s_tile, first);
+__device__ __forceinline__ int next_tile(const Cams& cams, const FwdArgs& a, int* s_tile, bool first) {
+    return next_tile_q(a.persistent, &a.st->work, s_tile, first, cams);
 }
 
 }  // namespace
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__
     const int nv = C / E;
     const int rpi = NT / nv;                         // staged rows per sweep
     const int r0 = tid / nv, vv0 = tid - r0 * nv;    // this thread's row offset and 16-byte chunk
-    for (int t = next_tile(a, &s_tile, true); t < cams.total_tiles; t = next_tile(a, &s_tile, false)) {
+    for (int t = next_tile(cams, a, &s_tile, true); t < cams.total_tiles; t = next_tile(cams, a, &s_tile, false)) {
         const int view = view_of_tile(cams, t);
         const CamDev& cam = cams.c[view];
         const int lt = t - cam.tile_off;

@@ -34,8 +34,8 @@ namespace fss {
 
 namespace topk_detail {
 
-__device__ __forceinline__ int next_tile(const FwdArgs& a, int* s_tile, bool first) {
-    return next_tile_q(a.persistent, &a.st->work, s_tile, first);
+__device__ __forceinline__ int next_tile(const Cams& cams, const FwdArgs& a, int* s_tile, bool first) {
+    return next_tile_q(a.persistent, &a.st->work, s_tile, first, cams);
 }
 
 }  // namespace topk_detail
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : 1) k_r
     const int nvec = P.C / E;
     const int ppi = NT / nvec;                         // pixels per phase-2 sweep
     const int q0 = tid / nvec, vv = tid - q0 * nvec;   // this thread's pixel offset and 16-byte chunk
-    for (int t = next_tile(a, &s_tile, true); t < cams.total_tiles; t = next_tile(a, &s_tile, false)) {
+    for (int t = next_tile(cams, a, &s_tile, true); t < cams.total_tiles; t = next_tile(cams, a, &s_tile, false)) {
         const int view = view_of_tile(cams, t);
         const CamDev& cam = cams.c[view];
         const int lt = t - cam.tile_off;
