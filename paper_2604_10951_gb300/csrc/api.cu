@@ -195,6 +195,50 @@ thread_local cudaEvent_t* g_mark_ev = nullptr;
 thread_local int g_mark_n = 0, g_mark_k = 0;
 }  // namespace
 
+bool kernel_marks_armed() { return g_mark_k < g_mark_n; }
+
+namespace {
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+constexpr int SIDE_DEVS = 64;
+thread_local SideStream g_side[SIDE_DEVS];  // per thread and device; kept until the process ends
+}  // namespace
+
+bool side_stream(cudaStream_t s, cudaStream_t& side, cudaEvent_t& fork, cudaEvent_t& join) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= SIDE_DEVS) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    SideStream& x = g_side[dev];
+    if (x.s == nullptr) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+            (void)cudaGetLastError();
+            return false;
+        }
+        cudaStream_t ns = nullptr;
+        cudaEvent_t ef = nullptr, ej = nullptr;
+        if (cudaStreamCreateWithFlags(&ns, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ef, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ej, cudaEventDisableTiming) != cudaSuccess) {
+            (void)cudaGetLastError();
+            if (ns) (void)cudaStreamDestroy(ns);
+            if (ef) (void)cudaEventDestroy(ef);
+            return false;
+        }
+        x.s = ns;
+        x.fork = ef;
+        x.join = ej;
+    }
+    side = x.s;
+    fork = x.fork;
+    join = x.join;
+    return true;
+}
+
 void kernel_mark(cudaStream_t s) {
     if (g_mark_k >= g_mark_n) return;
     // an external record becomes a node of a graph being captured; outside a

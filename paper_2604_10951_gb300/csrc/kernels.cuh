@@ -11,6 +11,15 @@ constexpr int SORT_CAP = 4096;  // longest tile list sorted in shared memory
 // launch; records the calling thread's next caller-supplied event, if any,
 // on the launch stream.
 void kernel_mark(cudaStream_t s);
+// True while that hook has events left: the timed launches then stay in the
+// launch stream, one after another.
+bool kernel_marks_armed();
+
+// A second stream of the calling thread on the current device, with a fork
+// and a join event, for work that may overlap the launch stream `s`.  False
+// when there is none (not created while `s` is being captured, or creation
+// failed): the caller then stays in `s`.
+bool side_stream(cudaStream_t s, cudaStream_t& side, cudaEvent_t& fork, cudaEvent_t& join);
 
 __global__ void k_project(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                           const float* __restrict__ means, const float* __restrict__ scales,
