@@ -241,6 +241,12 @@ fss_status fss_query_labels(int64_t N, int32_t n_queries, int32_t dim, const voi
  *   g_means [N,3], g_scales [N,2], g_quats [N,4], g_opac [N], g_rgb [N,3]
  *   (float32) and g_feat [N,C] (feat_dtype; FP32 accumulation inside).
  * Gradients are summed over all views of the call.
+ * Stream use: outside a graph capture, with K > 0 and g_feat given, the
+ * feature-gradient output pass runs in a second stream owned by the library
+ * (one per calling thread and device), forked from `stream` after the work
+ * it needs and joined back into `stream` before the call returns, so
+ * ordering on `stream` is as if everything ran there.  A call captured into
+ * a graph uses `stream` alone.
  */
 fss_status fss_render_backward(const fss_params *params, const fss_camera *cams, int32_t n_cams, int64_t N,
                                void *workspace, int64_t pair_capacity,
