@@ -203,3 +203,23 @@ def test_invalid_arguments_are_rejected_without_launch():
     p = make_params(C=16)
     with pytest.raises(L.FssError):
         L.fss_project_bin(p, cams, 1, sc.n, None, None, None, None, None, 1000, None)
+
+
+def test_tile_order_is_heavy_first_permutation():
+    """The tile order the tile kernels follow: a permutation of the tiles of
+    all views, with the pair-count bucket (16 pairs) never increasing."""
+    import torch
+    from paper_2604_10951_gb300 import _lib as L
+    from tests.gpu_util import GpuRun
+    sc = scenes.room_scene(n=100_000, C=8, seed=2)
+    cams = scenes.circle_poses(16)[3:5]
+    run = GpuRun(sc, cams, K=8, tile_size=16, render=False, cap=1 << 20)
+    torch.cuda.synchronize()
+    order = run.frame.region(L.REG_ORDER).view(torch.int32).cpu().numpy()
+    ranges = run.frame.region(L.REG_RANGES).view(torch.int32).cpu().numpy().reshape(-1, 2)
+    n_tiles = ranges.shape[0]
+    assert order.shape[0] == n_tiles
+    np.testing.assert_array_equal(np.sort(order), np.arange(n_tiles))
+    bucket = np.minimum(255, (ranges[:, 1] - ranges[:, 0]) >> 4)[order]
+    assert (np.diff(bucket) <= 0).all()
+    assert bucket[0] > bucket[-1]  # the frames have heavy and light tiles
