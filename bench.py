@@ -359,9 +359,9 @@ KERNELS = ["k_project", "k_scan", "k_emit", "k_tile_sort", "k_render_topk", "k_l
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch (camera pose 1) from the
 # ncu capture summarised in profiles/<kernel>_room500k_640x480_c64_k8.md; to be set
 # to None whenever the kernel changes after that capture
-NCU_TRAFFIC = {"k_render_topk": 26771456, "k_bwd_feat": 70470400, "k_bwd_geo": 38009600}
+NCU_TRAFFIC = {"k_render_topk": 27040768, "k_bwd_feat": 70487808, "k_bwd_geo": 38011904}
 # (smsp__inst_executed.sum, gpu__time_duration.sum in us) of the same captures
-NCU_ISSUE = {"k_render_topk": (85133445, 102.048), "k_bwd_feat": (67462191, 85.056), "k_bwd_geo": (88911732, 108.8)}
+NCU_ISSUE = {"k_render_topk": (85133445, 98.88), "k_bwd_feat": (67462191, 85.376), "k_bwd_geo": (88911244, 106.4)}
 # the query-label kernel's capture (profiles/k_query_labels_room500k_nq32_dim32.md): DRAM read + write
 NCU_QUERY_TRAFFIC = {"nq32_dim32_f32": 47276544}
 
