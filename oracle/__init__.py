@@ -29,6 +29,10 @@ TMIN, EXACT_TOPK = 0, 1
 FLAG_ALPHA, FLAG_TMIN, FLAG_TIE, FLAG_EXACT, FLAG_NEAR, FLAG_CLAMP, FLAG_GRAZE = 1, 2, 4, 8, 16, 32, 64
 FLAG_MEDIAN = 128
 FLAG_LOWPASS = 256
+# flags of the borderline decisions that a per-pixel flip mask can take the other way
+FLAGS_BORDER = FLAG_ALPHA | FLAG_TMIN | FLAG_TIE | FLAG_EXACT | FLAG_NEAR
+# flip-mask bit of the median-depth switch (bits 0..30: the other borderline decisions in order)
+FLIP_MEDIAN = 1 << 31
 
 
 class OrcCam(C.Structure):
@@ -74,10 +78,10 @@ def _load():
             lib.orc_ranges.argtypes = [i64, P, C.c_int32, P]
             lib.orc_ranges.restype = None
             lib.orc_render.argtypes = [i64, P, P, P, P, P, P, C.POINTER(OrcCam), C.POINTER(OrcParams), P, P, P, P,
-                                       P, P, P, P, P, P, P, P, P, P, C.c_int, P, P, P]
+                                       P, P, P, P, P, P, P, P, P, P, C.c_int, P, P, P, P, P, P]
             lib.orc_render.restype = None
             lib.orc_render_backward.argtypes = [i64, P, P, P, P, P, P, C.POINTER(OrcCam), C.POINTER(OrcParams),
-                                                P, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
+                                                P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
             lib.orc_render_backward.restype = None
             lib.orc_geometry.argtypes = [i64, P, P, P, P, C.POINTER(OrcCam), C.POINTER(OrcParams), P, P, P, P]
             lib.orc_geometry.restype = None
@@ -229,11 +233,24 @@ def binning(scene, cam, params, mode=None):
     return dict(recf=recf, reci=reci, count=cnt, tiles=st, ids=si, ranges=rng, P=int(st.shape[0]))
 
 
-def render(scene, cam, params, feats=None, binned=None, brute=False, visible=None, zkey=None, threads=0, sh=None):
+def _u32(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.uint32)
+
+
+def _u8(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.uint8)
+
+
+def render(scene, cam, params, feats=None, binned=None, brute=False, visible=None, zkey=None, threads=0, sh=None,
+           flip=None, only=None):
     """FP64 render.  Tiled over ``binned`` lists (computed if None) unless
     ``brute``; returns a dict of per-pixel outputs.  ``sh`` [N, B, 3]:
     view-dependent colours from spherical-harmonic coefficients instead of
-    ``scene.rgb``."""
+    ``scene.rgb``.  ``flip`` [H, W] (uint32): per-pixel masks that take the
+    pixel's borderline decisions the other way (bit b: the b-th one met;
+    FLIP_MEDIAN: the median-depth switch); ``only`` [H, W] (bool): render
+    just those pixels (the others' outputs stay zero).  "nborder" counts the
+    borderline decisions each pixel met."""
     lib = _load()
     m, s, q, o = _scene_arrays64(scene)
     rgb = _f64(scene.rgb) if sh is None else sh_colors(sh, scene.means, cam)
@@ -246,7 +263,12 @@ def render(scene, cam, params, feats=None, binned=None, brute=False, visible=Non
     out = dict(F=np.zeros((H, W, Cc)), rgb=np.zeros((H, W, 3)), T=np.zeros((H, W)),
                nstop=np.zeros((H, W), np.int32), ncontrib=np.zeros((H, W), np.int32),
                flags=np.zeros((H, W), np.int32), counters=np.zeros(2, np.int64),
-               depth=np.zeros((H, W)), depth_med=np.zeros((H, W)), normal=np.zeros((H, W, 3)))
+               depth=np.zeros((H, W)), depth_med=np.zeros((H, W)), normal=np.zeros((H, W, 3)),
+               nborder=np.zeros((H, W), np.int32))
+    flip = _u32(flip)
+    only = _u8(only)
+    assert flip is None or flip.size == H * W
+    assert only is None or only.size == H * W
     Kc = max(K, 1)
     out.update(ids=np.full((H, W, Kc), -1, np.int32), w=np.zeros((H, W, Kc)), pos=np.full((H, W, Kc), -1, np.int32))
     rng = None if brute else _i32(binned["ranges"])
@@ -258,7 +280,8 @@ def render(scene, cam, params, feats=None, binned=None, brute=False, visible=Non
                    _ptr(out["F"]), _ptr(out["rgb"]), _ptr(out["T"]),
                    _ptr(out["ids"]) if K else None, _ptr(out["w"]) if K else None, _ptr(out["pos"]) if K else None,
                    _ptr(out["nstop"]), _ptr(out["ncontrib"]), _ptr(out["flags"]), _ptr(out["counters"]), int(threads),
-                   _ptr(out["depth"]), _ptr(out["depth_med"]), _ptr(out["normal"]))
+                   _ptr(out["depth"]), _ptr(out["depth_med"]), _ptr(out["normal"]),
+                   _ptr(flip), _ptr(only), _ptr(out["nborder"]))
     if not K:
         for k in ("ids", "w", "pos"):
             out.pop(k)
@@ -267,13 +290,14 @@ def render(scene, cam, params, feats=None, binned=None, brute=False, visible=Non
 
 
 def render_backward(scene, cam, params, gF, grgb, gT=None, feats=None, binned=None, brute=False,
-                    visible=None, zkey=None, sh=None):
+                    visible=None, zkey=None, sh=None, flip=None):
     """Analytic FP64 gradients of sum(gF*F) + sum(grgb*rgb) + sum(gT*T), and
     under "abs" [N, 10] the same chain over magnitudes (means, scales, quats,
     opacity): a bound on the sum of |terms| that each geometric gradient
     entry adds up.  With ``sh`` [N, B, 3] the colours are view dependent: "sh"
     holds dL/dcoefficients, "rgb" the gradient of this view's colours, and
-    the direction term joins "means" (and its magnitude "abs")."""
+    the direction term joins "means" (and its magnitude "abs").  ``flip``
+    [H, W]: the per-pixel borderline outcomes, as in :func:`render`."""
     lib = _load()
     m, s, q, o = _scene_arrays64(scene)
     rgb = _f64(scene.rgb) if sh is None else sh_colors(sh, scene.means, cam)
@@ -295,7 +319,8 @@ def render_backward(scene, cam, params, gF, grgb, gT=None, feats=None, binned=No
                             C.byref(params), _ptr(rng), _ptr(sid), _ptr(vis), _ptr(zk),
                             _ptr(gF), _ptr(grgb), _ptr(gT),
                             _ptr(g["means"]), _ptr(g["scales"]), _ptr(g["quats"]), _ptr(g["opac"]),
-                            _ptr(g["rgb"]), _ptr(g["feat"]), _ptr(g["Tmat"]), _ptr(g["abs"]))
+                            _ptr(g["rgb"]), _ptr(g["feat"]), _ptr(g["Tmat"]), _ptr(g["abs"]),
+                            _ptr(_u32(flip)))
     if sh is not None:
         shc = _f64(sh)
         g["sh"] = np.zeros_like(shc)

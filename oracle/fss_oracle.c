@@ -53,6 +53,18 @@
  *     renorm = 1 divides that sum by the selected weights' sum W_K (the
  *     selected surfels' share of the pixel becomes 1), which the paper does
  *     not use and the GPU path offers as an option.
+ *
+ * Borderline decisions.  Where a discrete decision of Eq. 2 / Eq. 7 (skip
+ * below alpha_min, the near plane, the T_min stop, the exact Top-K stop,
+ * the K-th place of the selection, the median-depth switch) is taken
+ * within rounding distance of its threshold (the FLAG_* distances below),
+ * a binary32 evaluation may take it the other way, and both results are
+ * correct.  orc_render and orc_render_backward therefore accept a per-pixel
+ * flip mask: bit b takes the b-th borderline decision of the pixel's
+ * traversal (in traversal order, the selection's K-th place last) the other
+ * way, and bit FLIP_MEDIAN the median-depth switch.  A zero mask is the
+ * plain definition.  Nothing else changes, so each mask gives one of the
+ * results a correct evaluation may produce.
  */
 #define _GNU_SOURCE
 #include <math.h>
@@ -104,6 +116,20 @@ enum {
 };
 
 #define DEG_EPS 1e-3 /* edge-on cull: |n . p_c| <= DEG_EPS |p_c| */
+
+/* flip-mask bit of the median-depth switch; bits 0..30 are the traversal's
+ * and the selection's borderline decisions in the order they are met */
+#define FLIP_MEDIAN 0x80000000u
+
+/* A decision with outcome `taken`; when `borderline` it is the next
+ * borderline decision of the pixel (counted in *nb) and bit *nb of `flip`
+ * takes it the other way. */
+static int decide(int taken, int borderline, uint32_t flip, int *nb)
+{
+    if (!borderline) return taken;
+    const int b = (*nb)++;
+    return (b < 31 && ((flip >> b) & 1u)) ? !taken : taken;
+}
 
 /* ================================================================== */
 /* 1. FP64 geometry                                                     */
@@ -812,6 +838,7 @@ typedef struct {
     int32_t nsel;
     int32_t sel[32];     /* indices into the contributor array, front-to-back */
     int64_t n_eval;
+    int32_t nborder;     /* borderline decisions met (traversal and selection) */
 } pix_out;
 
 /* K largest weights, ties to the earlier position (Eq. 7 set definition). */
@@ -823,11 +850,13 @@ static int wt_before(const contrib_t *a, const contrib_t *b)
 static int cmp_int(const void *a, const void *b) { return *(const int *)a - *(const int *)b; }
 
 /* Composite one pixel over the candidate list `cand` (surfel indices in
- * depth order); contributors are written to `cb` (capacity n_cand). */
+ * depth order); contributors are written to `cb` (capacity n_cand).
+ * `flip` takes borderline decisions the other way (see decide()). */
 static void composite_pixel(const geo64 *geo, const double *opac, const double *rgb, const orc_cam *cam,
                             const orc_params *p, const int32_t *cand, int32_t n_cand, double px, double py,
-                            contrib_t *cb, pix_out *out)
+                            uint32_t flip, contrib_t *cb, pix_out *out)
 {
+    int nb = 0;
     const double amin = p->alpha_min, amax = p->alpha_max, tmin = p->T_min;
     const int K = p->K;
     double T = 1.0, rgbacc[3] = {0, 0, 0};
@@ -839,8 +868,9 @@ static void composite_pixel(const geo64 *geo, const double *opac, const double *
     for (int32_t j = 0; j < n_cand; ++j) {
         if (K > 0 && p->stop_rule == ORC_EXACT && p->select == 0 && ntop == K) {
             double wmin = topw[K - 1];
-            if (fabs(amax * T - wmin) <= 1e-6) flags |= FLAG_EXACT;
-            if (amax * T <= wmin) break;
+            const int border = fabs(amax * T - wmin) <= 1e-6;
+            if (border) flags |= FLAG_EXACT;
+            if (decide(amax * T <= wmin, border, flip, &nb)) break;
         }
         /* first-K selection: the set is final once K surfels contributed */
         if (K > 0 && p->stop_rule == ORC_EXACT && p->select == 1 && n == K) break;
@@ -863,17 +893,20 @@ static void composite_pixel(const geo64 *geo, const double *opac, const double *
         } else if (!obj) {
             continue;
         }
-        if (fabs(zh - cam->near_plane) < 1e-5) flags |= FLAG_NEAR;
-        if (!(zh > cam->near_plane)) continue;
+        const int bnear = fabs(zh - cam->near_plane) < 1e-5;
+        if (bnear) flags |= FLAG_NEAR;
+        if (decide(!(zh > cam->near_plane), bnear, flip, &nb)) continue;
         double oG = opac[id] * exp(-0.5 * rho);
-        if (fabs(oG - amin) < 1e-6) flags |= FLAG_ALPHA;
+        const int balpha = fabs(oG - amin) < 1e-6;
+        if (balpha) flags |= FLAG_ALPHA;
         if (fabs(oG - amax) < 1e-6) flags |= FLAG_CLAMP;
         double alpha = oG < amax ? oG : amax;
-        if (alpha < amin) continue;
+        if (decide(alpha < amin, balpha, flip, &nb)) continue;
         double Tn = T * (1.0 - alpha);
-        if (fabs(Tn - tmin) < 1e-8) flags |= FLAG_TMIN;
+        const int btmin = fabs(Tn - tmin) < 1e-8;
+        if (btmin) flags |= FLAG_TMIN;
         if (fabs(Tn - 0.5) < 1e-6) flags |= FLAG_MEDIAN;
-        if (Tn < tmin) break;
+        if (decide(Tn < tmin, btmin, flip, &nb)) break;
         contrib_t *e = &cb[n++];
         e->pos = j; e->id = id; e->alpha = alpha; e->T = T; e->w = alpha * T;
         e->u = u; e->v = v; e->oG = oG; e->zh = zh;
@@ -912,9 +945,14 @@ static void composite_pixel(const geo64 *geo, const double *opac, const double *
                 int tmp = idx[a]; idx[a] = idx[best]; idx[best] = tmp;
             }
             if (n > K) {
+                /* the K-th place against the best weight left out (ties to the earlier position) */
                 double wk = cb[idx[K - 1]].w, wbest_out = -1.0;
-                for (int b = K; b < n; ++b) if (cb[idx[b]].w > wbest_out) wbest_out = cb[idx[b]].w;
-                if (fabs(wk - wbest_out) <= 1e-6) flags |= FLAG_TIE;
+                int bout = -1;
+                for (int b = K; b < n; ++b)
+                    if (bout < 0 || wt_before(&cb[idx[b]], &cb[idx[bout]])) { bout = b; wbest_out = cb[idx[b]].w; }
+                const int btie = fabs(wk - wbest_out) <= 1e-6;
+                if (btie) flags |= FLAG_TIE;
+                if (decide(0, btie, flip, &nb)) { int tmp = idx[K - 1]; idx[K - 1] = idx[bout]; idx[bout] = tmp; }
             }
         }
         qsort(idx, (size_t)nsel, sizeof(int), cmp_int); /* front-to-back */
@@ -923,6 +961,7 @@ static void composite_pixel(const geo64 *geo, const double *opac, const double *
         free(idx);
     }
     out->flags = flags;
+    out->nborder = nb;
 }
 
 /* Candidate order for the brute-force renderer: every surfel that passes
@@ -976,6 +1015,10 @@ static void release(scene_prep *sp) { free(sp->geo); free(sp->order); }
  *   F[H*W*C], rgb[H*W*3], T[H*W], ids[H*W*K] (front-to-back, -1 padded),
  *   w[H*W*K], pos[H*W*K] (list position), nstop[H*W], ncontrib[H*W],
  *   flags[H*W]; counters[2] = (evaluations, contributions).
+ * flip[H*W] (may be NULL): per-pixel flip masks of the borderline decisions
+ * (see decide()); only[H*W] (may be NULL): render just the pixels where it
+ * is non-zero and leave the others' outputs untouched; nborder[H*W]: the
+ * borderline decisions each pixel met (the median switch not counted).
  */
 void orc_render(int64_t N, const double *means, const double *scales, const double *quats,
                 const double *opac, const double *rgb, const double *feats, const orc_cam *cam,
@@ -983,7 +1026,8 @@ void orc_render(int64_t N, const double *means, const double *scales, const doub
                 const int32_t *visible, const float *zkey,
                 double *F, double *out_rgb, double *out_T, int32_t *ids, double *wout, int32_t *pos,
                 int32_t *nstop, int32_t *ncontrib, int32_t *flags, int64_t *counters, int n_threads,
-                double *depth, double *depth_med, double *normal)
+                double *depth, double *depth_med, double *normal,
+                const uint32_t *flip, const uint8_t *only, int32_t *nborder)
 {
     const int W = cam->width, H = cam->height, ts = p->tile_size, C = p->C, K = p->K;
     const int tiles_x = (W + ts - 1) / ts;
@@ -1016,9 +1060,12 @@ void orc_render(int64_t N, const double *means, const double *scales, const doub
                 cand = sp.order;
                 n_cand = sp.n_order;
             }
-            pix_out o;
-            composite_pixel(sp.geo, opac, rgb, cam, p, cand, n_cand, px + 0.5, py + 0.5, cb, &o);
             const int64_t pix = (int64_t)py * W + px;
+            if (only && !only[pix]) continue;
+            const uint32_t fl = flip ? flip[pix] : 0u;
+            pix_out o;
+            composite_pixel(sp.geo, opac, rgb, cam, p, cand, n_cand, px + 0.5, py + 0.5, fl, cb, &o);
+            if (nborder) nborder[pix] = o.nborder;
             n_eval += o.n_eval;
             n_contrib += o.n_contrib;
             if (out_rgb) for (int k = 0; k < 3; ++k) out_rgb[3 * pix + k] = o.rgb[k];
@@ -1036,7 +1083,11 @@ void orc_render(int64_t N, const double *means, const double *scales, const doub
                     const contrib_t *e = &cb[i];
                     dz += e->w * e->zh;
                     for (int k = 0; k < 3; ++k) nn[k] += e->w * sp.geo[e->id].nf[k];
-                    if (!found && e->T * (1.0 - e->alpha) < 0.5) { zm = e->zh; found = 1; }
+                    if (found) continue;
+                    const double Tn = e->T * (1.0 - e->alpha);
+                    /* the switch within rounding distance of 1/2 may go the other way */
+                    const int below = Tn < 0.5;
+                    if ((fabs(Tn - 0.5) < 1e-6 && (fl & FLIP_MEDIAN)) ? !below : below) { zm = e->zh; found = 1; }
                 }
                 if (depth) depth[pix] = dz;
                 if (depth_med) depth_med[pix] = zm;
@@ -1098,7 +1149,9 @@ static void dframe(const double q[4], double dtu[4][3], double dtv[4][3])
  * selection set, skips, stops, clamps and binning are held fixed.
  * Outputs (accumulated, caller zeroes): g_means[N*3], g_scales[N*2],
  * g_quats[N*4], g_opac[N], g_rgb[N*3], g_feat[N*C], and optionally the
- * per-surfel derivative w.r.t. the rows of T, g_T[N*9].
+ * per-surfel derivative w.r.t. the rows of T, g_T[N*9].  flip[H*W] (may
+ * be NULL): the per-pixel borderline outcomes of orc_render, held fixed
+ * like every other decision.
  * g_abs[N*10] (optional, accumulated): the same chain evaluated over
  * magnitudes, per surfel (means 3, scales 2, quats 4, opacity 1): every
  * sum and product of the chain, from the upstream gradients through
@@ -1114,7 +1167,8 @@ void orc_render_backward(int64_t N, const double *means, const double *scales, c
                          const int32_t *visible, const float *zkey,
                          const double *gF, const double *grgb, const double *gT,
                          double *g_means, double *g_scales, double *g_quats, double *g_opac,
-                         double *g_rgb, double *g_feat, double *g_Tmat, double *g_abs)
+                         double *g_rgb, double *g_feat, double *g_Tmat, double *g_abs,
+                         const uint32_t *flip)
 {
     const int W = cam->width, H = cam->height, ts = p->tile_size, C = p->C, K = p->K;
     const int tiles_x = (W + ts - 1) / ts;
@@ -1147,9 +1201,9 @@ void orc_render_backward(int64_t N, const double *means, const double *scales, c
                 n_cand = sp.n_order;
             }
             const double x = px + 0.5, y = py + 0.5;
-            pix_out o;
-            composite_pixel(sp.geo, opac, rgb, cam, p, cand, n_cand, x, y, cb, &o);
             const int64_t pix = (int64_t)py * W + px;
+            pix_out o;
+            composite_pixel(sp.geo, opac, rgb, cam, p, cand, n_cand, x, y, flip ? flip[pix] : 0u, cb, &o);
             const double *gf = gF ? gF + pix * C : NULL;
             const double *gc = grgb + 3 * pix;
             const double gt = gT ? gT[pix] : 0.0;
