@@ -223,3 +223,49 @@ def test_tile_order_is_heavy_first_permutation():
     bucket = np.minimum(255, (ranges[:, 1] - ranges[:, 0]) >> 4)[order]
     assert (np.diff(bucket) <= 0).all()
     assert bucket[0] > bucket[-1]  # the frames have heavy and light tiles
+
+
+def _dense_tile_scene(n_small=5200, seed=0, C=16):
+    """32x32 camera at the origin looking +z (f = 32): n_small camera-facing
+    surfels of about 0.4 pixel at depths 2..3 with centres inside tile (0, 0)
+    (pixels 2..14), so that tile's list is longer than the 4096 keys the
+    shared-memory sorts take and the per-tile radix sort runs."""
+    rng = np.random.default_rng(seed)
+    z = rng.uniform(2.0, 3.0, n_small)
+    px = rng.uniform(2.0, 14.0, n_small)
+    py = rng.uniform(2.0, 14.0, n_small)
+    f, c = 32.0, 16.0
+    means = np.stack([(px - c) / f * z, (py - c) / f * z, z], axis=1)
+    log_scales = np.log(np.stack([0.4 * z / f, 0.4 * z / f], axis=1) * rng.uniform(0.8, 1.25, (n_small, 2)))
+    quats = np.tile([1.0, 0.0, 0.0, 0.0], (n_small, 1))
+    logits = rng.normal(-1.0, 0.5, n_small)
+    sc = scenes.Scene(means, log_scales, quats, logits, rng.uniform(0.0, 1.0, (n_small, 3)),
+                      rng.normal(0.0, 1.0, (n_small, C)))
+    vm = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0]], dtype=np.float32)
+    return sc, scenes.Camera(f, f, c, c, 32, 32, vm)
+
+
+def test_radix_sort_branch_for_a_tile_over_4096_pairs():
+    """A tile list of more than 4096 pairs (the per-tile LSD radix sort in
+    global scratch, with passes skipped where every key has the same digit):
+    order and warp masks bit-exact against the oracle, in a two-view call
+    (the second view's items have indices above N, so more digits vary), and
+    the features, colour, ids and gradients of the frame against the oracle."""
+    from tests.gpu_util import GpuRun
+    from tests.test_gpu_backward import _assert_close, _gpu_backward, _resolved, _upstream
+    from tests.test_gpu_render import _compare, _oracle
+    sc, cam = _dense_tile_scene()
+    run2 = GpuRun(sc, [cam, cam], K=8, render=False)
+    _check_lists(run2, sc, [cam, cam], 16, "accu")
+    r = run2.ranges()
+    assert r[0, 1] - r[0, 0] > 4096 and r[4, 1] - r[4, 0] > 4096  # tile (0, 0) of each view
+    run = GpuRun(sc, [cam], K=8)
+    _check_lists(run, sc, [cam], 16, "accu")
+    _check_masks(run, sc, cam, 16)
+    ref, S = _oracle(sc, cam, 8)
+    _compare(run.view(0), ref, S, 1e-4, 8)
+    p = O.make_params(K=8)
+    ref = _resolved(run, sc, cam, p)
+    gF, grgb, gT = _upstream(ref, sc.C, seed=9)
+    g_ref = O.render_backward(sc, cam, p, gF, grgb, gT, binned=ref["binned"], flip=ref["flip"])
+    _assert_close(_gpu_backward(run, gF, grgb, gT), g_ref)

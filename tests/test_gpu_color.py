@@ -17,9 +17,10 @@ import torch
 import oracle as O
 from paper_2604_10951_gb300 import scenes
 from tests._scenes import make_scene
+from tests.outcomes import oracle_ref
 from tests.gpu_util import GpuRun, dev
-from tests.test_gpu_backward import FLAGS, _assert_close, _upstream
-from tests.test_gpu_render import FLAGS_EXCLUDED
+from tests.test_gpu_backward import _assert_close, _resolved, _upstream
+from tests.test_gpu_render import _compare
 
 pytestmark = pytest.mark.gpu
 
@@ -43,11 +44,9 @@ def test_colours_against_oracle(deg):
     coef = _sh(sc.n, deg, deg)
     run = _run(sc, [cam], 4, deg, coef)
     p = O.make_params(K=4)
-    ref = O.render(sc, cam, p, binned=O.binning(sc, cam, p), sh=coef)
+    ref, S = oracle_ref(sc, cam, p, sh=coef)
     g = run.view(0)
-    ok = (ref["flags"] & FLAGS_EXCLUDED) == 0
-    np.testing.assert_allclose(g["rgb"][ok], ref["rgb"][ok], atol=2e-5, rtol=0)
-    np.testing.assert_allclose(g["T"][ok], ref["T"][ok], atol=2e-5, rtol=1e-4)
+    _compare(g, ref, S, 1e-4, 4)  # colours within 2e-5, features, T and ids
     plain = GpuRun(sc, [cam], K=4).view(0)  # the colour mode changes no feature, id or transmittance
     for k in ("F", "T", "ids"):
         np.testing.assert_array_equal(g[k], plain[k])
@@ -72,10 +71,9 @@ def test_gradients_against_oracle(K):
     coef = _sh(sc.n, deg, 11)
     run = _run(sc, [cam], K, deg, coef)
     p = O.make_params(K=K)
-    b = O.binning(sc, cam, p)
-    ref = O.render(sc, cam, p, binned=b, sh=coef)
+    ref = _resolved(run, sc, cam, p, sh=coef)
     gF, grgb, gT = _upstream(ref, sc.C, seed=3)
-    g_ref = O.render_backward(sc, cam, p, gF, grgb, gT, binned=b, sh=coef)
+    g_ref = O.render_backward(sc, cam, p, gF, grgb, gT, binned=ref["binned"], sh=coef, flip=ref["flip"])
     fr = run.frame
     N = sc.n
     out = dict(means=torch.empty(N, 3, device="cuda"), scales=torch.empty(N, 2, device="cuda"),

@@ -20,7 +20,7 @@ import torch
 import oracle as O
 from paper_2604_10951_gb300 import scenes
 from tests.gpu_util import GpuRun
-from tests.test_gpu_backward import _assert_close, _gpu_backward, _upstream
+from tests.test_gpu_backward import _assert_close, _gpu_backward, _resolved, _upstream
 
 pytestmark = pytest.mark.gpu
 
@@ -28,16 +28,16 @@ pytestmark = pytest.mark.gpu
 def _check(sc, cam, K, feat_dtype, tile_size=16, seed=0):
     run = GpuRun(sc, [cam], K=K, tile_size=tile_size, feat_dtype=feat_dtype)
     p = O.make_params(K=K, tile_size=tile_size)
-    b = O.binning(sc, cam, p)
     if feat_dtype == torch.bfloat16:
         feats = torch.as_tensor(sc.feats).bfloat16().double().numpy()
     else:
         feats = None
-    ref = O.render(sc, cam, p, feats=feats, binned=b)
+    ref = _resolved(run, sc, cam, p, tol=2e-2 if feat_dtype == torch.bfloat16 else 1e-4, feats=feats)
+    b = ref["binned"]
     gF, grgb, gT = _upstream(ref, sc.C, seed=seed)
     if feat_dtype == torch.bfloat16:
         gF = torch.as_tensor(gF).bfloat16().double().numpy()
-    g_ref = O.render_backward(sc, cam, p, gF, grgb, gT, feats=feats, binned=b)
+    g_ref = O.render_backward(sc, cam, p, gF, grgb, gT, feats=feats, binned=b, flip=ref["flip"])
     g = _gpu_backward(run, gF, grgb, gT, feat_dtype=feat_dtype)
     if feat_dtype == torch.bfloat16:
         _assert_close(g, g_ref, names=("means", "scales", "quats", "opac", "rgb"))

@@ -23,7 +23,8 @@ import oracle as O
 from paper_2604_10951_gb300 import scenes
 from paper_2604_10951_gb300.raster import Frame, make_params
 from tests.gpu_util import GpuRun, dev
-from tests.test_gpu_backward import FLAGS, _assert_close, _gpu_backward
+from tests.outcomes import upstream_mask
+from tests.test_gpu_backward import _assert_close, _gpu_backward, _resolved
 from tests.test_gpu_render import _compare, _oracle
 
 pytestmark = pytest.mark.gpu
@@ -39,10 +40,10 @@ def test_large_view_c128_bf16_against_oracle():
     run = GpuRun(sc, [cam], K=8, feat_dtype=torch.bfloat16, out_dtype=torch.bfloat16, cap=1 << 22)
     ref, S = _oracle(sc, cam, 8, feats=_bf16(sc.feats))
     g = run.view(0)
-    ok = _compare(g, ref, S, 2e-2, 8, max_flagged=0.01)
+    ok = _compare(g, ref, S, 2e-2, 8)
     err = (np.abs(g["F"] - ref["F"]) / S)[ok]
     print(f"1.5M surfels 1280x720 C=128: feature error / S max {err.max():.2e} mean {err.mean():.2e}, "
-          f"flagged pixels {(~ok).mean():.4f}, ids exact on all other pixels")
+          f"outcomes {ref['outcomes']}")
 
 
 def test_full_frame_backward_bf16_against_oracle():
@@ -50,22 +51,23 @@ def test_full_frame_backward_bf16_against_oracle():
     cam = scenes.circle_poses(16)[0]
     run = GpuRun(sc, [cam], K=8, feat_dtype=torch.bfloat16, stop_rule="exact_topk", cap=1 << 20)
     p = O.make_params(K=8, stop_rule=O.EXACT_TOPK)
-    b = O.binning(sc, cam, p)
     f16 = _bf16(sc.feats)
-    ref = O.render(sc, cam, p, feats=f16, binned=b)
+    ref = _resolved(run, sc, cam, p, tol=2e-2, feats=f16)
     rng = np.random.default_rng(7)
     H, W = ref["T"].shape
     gF = _bf16(rng.normal(size=(H, W, sc.C)))
     grgb = rng.normal(size=(H, W, 3))
-    bad = (ref["flags"] & FLAGS) != 0
+    bad = upstream_mask(ref)
     gF[bad] = 0
     grgb[bad] = 0
-    g_ref = O.render_backward(sc, cam, p, gF, grgb, None, feats=f16, binned=b)
+    g_ref = O.render_backward(sc, cam, p, gF, grgb, None, feats=f16, binned=ref["binned"], flip=ref["flip"])
     g = _gpu_backward(run, gF, grgb, None, feat_dtype=torch.bfloat16)
-    # whole-frame sums of ~10^2 FP32 terms per surfel and view: 1e-4 relative plus 1e-4 of the largest entry
-    _assert_close(g, g_ref, rel=1e-4, floor=1e-4, names=("means", "scales", "quats", "opac", "rgb"))
+    # the scope table's 1e-4 relative, plus 1e-5 of the largest entry
+    chain = _assert_close(g, g_ref, rel=1e-4, floor=1e-5, names=("means", "scales", "quats", "opac", "rgb"))
     # feature gradients are stored in BF16: 2^-8 relative rounding
     _assert_close(g, g_ref, rel=8e-3, floor=1e-4, names=("feat",))
+    print("outcomes", ref["outcomes"], "upstream zeroed at", int(bad.sum()), "pixels")
+    print("entries (total, passing only through the magnitude chain):", chain)
     for k in ("means", "scales", "quats", "opac", "rgb", "feat"):
         scale = np.abs(g_ref[k]).max()
         print(f"{k}: max |g - g_ref| / max|g_ref| = {np.abs(g[k] - g_ref[k]).max() / scale:.2e}")
@@ -126,10 +128,8 @@ def test_batched_twelve_views_one_million_surfels():
             ref, S = _oracle(sc, cam, 8, feats=_bf16(sc.feats), stop=O.EXACT_TOPK)
             h, w = fr.sizes[0]
             gv = dict(F=F1.float().cpu().numpy().reshape(h, w, -1), rgb=rgb1.cpu().numpy().reshape(h, w, 3),
-                      T=T1.cpu().numpy().reshape(h, w))
-            ok = (ref["flags"] & (O.FLAG_ALPHA | O.FLAG_TMIN | O.FLAG_TIE | O.FLAG_EXACT | O.FLAG_NEAR)) == 0
-            assert (np.abs(gv["F"] - ref["F"]) / S)[ok].max() <= 2e-2
-            np.testing.assert_array_equal(ids1.cpu().numpy().reshape(h, w, -1)[ok], ref["ids"][ok])
+                      T=T1.cpu().numpy().reshape(h, w), ids=ids1.cpu().numpy().reshape(h, w, -1))
+            _compare(gv, ref, S, 2e-2, 8)
         del one
     for x, y, m in zip(grads, acc, mag):
         # the same terms summed in another order (the FP32 summation-order bound, a few

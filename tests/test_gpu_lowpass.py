@@ -4,8 +4,11 @@ binary32 mirror with the screen disc (every bin mode), warp masks that keep
 every pixel of the disc, the forward against the FP64 oracle (features,
 colour, ids, the sensor depth with the centre depth for the screen term),
 and the gradients, whose screen-term part runs through the projected centre.
-Pixels within rounding distance of the switch between the two terms (the
-oracle's low-pass flag) are excluded like the other flagged decisions.
+Borderline decisions are resolved against the oracle's outcomes as in the
+other parity tests.  The switch between the two terms leaves the values
+continuous but not the derivative, so the sensor depth and the upstream
+gradients skip pixels within rounding distance of it (the oracle's low-pass
+flag).
 """
 import numpy as np
 import pytest
@@ -14,10 +17,11 @@ import torch
 import oracle as O
 from paper_2604_10951_gb300 import scenes
 from tests._scenes import make_scene
-from tests.gpu_util import GpuRun, dev, tol_scale
-from tests.test_gpu_backward import FLAGS, _assert_close, _gpu_backward, _upstream
+from tests.gpu_util import GpuRun, dev
+from tests.outcomes import oracle_ref
+from tests.test_gpu_backward import _assert_close, _gpu_backward, _resolved, _upstream
 from tests.test_gpu_binning import _check_lists, _check_masks, _check_view
-from tests.test_gpu_render import FLAGS_EXCLUDED, _compare
+from tests.test_gpu_render import _compare
 
 pytestmark = pytest.mark.gpu
 
@@ -58,9 +62,7 @@ def test_forward_against_oracle(K):
     sc, cam = _small(seed=2, f=0.15)
     run = GpuRun(sc, [cam], K=K, lowpass=True)
     p = O.make_params(K=K, lowpass=1)
-    b = O.binning(sc, cam, p)
-    ref = O.render(sc, cam, p, binned=b)
-    S = tol_scale(O, sc, cam, p, b)
+    ref, S = oracle_ref(sc, cam, p)
     ok = _compare(run.view(0), ref, S, 1e-4, K)
     plain = GpuRun(sc, [cam], K=K).view(0)
     assert np.abs(run.view(0)["T"] - plain["T"]).max() > 1e-2  # the filter changes the image
@@ -81,10 +83,8 @@ def test_gradients_against_oracle(K):
     sc, cam = _small(seed=3, n=1500, f=0.15)
     run = GpuRun(sc, [cam], K=K, lowpass=True)
     p = O.make_params(K=K, lowpass=1)
-    b = O.binning(sc, cam, p)
-    ref = O.render(sc, cam, p, binned=b)
-    ref["flags"] |= np.where((ref["flags"] & O.FLAG_LOWPASS) != 0, O.FLAG_ALPHA, 0).astype(ref["flags"].dtype)
-    gF, grgb, gT = _upstream(ref, sc.C, seed=4)
-    g_ref = O.render_backward(sc, cam, p, gF, grgb, gT, binned=b)
+    ref = _resolved(run, sc, cam, p)
+    gF, grgb, gT = _upstream(ref, sc.C, seed=4, extra_flags=O.FLAG_LOWPASS)
+    g_ref = O.render_backward(sc, cam, p, gF, grgb, gT, binned=ref["binned"], flip=ref["flip"])
     g = _gpu_backward(run, gF, grgb, gT)
     _assert_close(g, g_ref)

@@ -2,9 +2,12 @@
 
 Features: |F_gpu - F_ref| <= tol * S with S = sum_i w_i |c_i| + 1e-6 (the
 magnitude the sum is built from), tol = 1e-4 for FP32 storage and 2e-2 for
-BF16 storage.  RGB and T within 2e-5 absolute.  Top-K ids exact.  Pixels
-whose reference decisions lie within rounding distance of a threshold (the
-oracle's per-pixel flags) are excluded and counted.
+BF16 storage.  RGB and T within 2e-5 absolute.  Top-K ids, list positions
+and traversal lengths exact.  At pixels where a decision lies within
+rounding distance of its threshold (alpha_min, the near plane, the T_min
+and exact stops, the K-th place of the Top-K set), both outcomes are
+correct: the GPU's result must equal one of the oracle's outcomes there
+(tests/outcomes.py), and at most 0.1 % of the pixels may equal none.
 """
 import numpy as np
 import pytest
@@ -13,36 +16,29 @@ import torch
 import oracle as O
 from paper_2604_10951_gb300 import scenes
 from tests._scenes import ident_cam, make_scene
-from tests.gpu_util import GpuRun, tol_scale
+from tests.gpu_util import GpuRun
+from tests.outcomes import oracle_ref, settle
 
 pytestmark = pytest.mark.gpu
 
-FLAGS_EXCLUDED = O.FLAG_ALPHA | O.FLAG_TMIN | O.FLAG_TIE | O.FLAG_EXACT | O.FLAG_NEAR
+
+def _oracle(scene, cam, K, ts=16, feats=None, stop=O.TMIN, bg=(0, 0, 0), **kw):
+    p = O.make_params(K=K, tile_size=ts, stop_rule=stop, bg=bg, **kw)
+    return oracle_ref(scene, cam, p, feats=feats)
 
 
-def _oracle(scene, cam, K, ts=16, feats=None, stop=O.TMIN, bg=(0, 0, 0)):
-    p = O.make_params(K=K, tile_size=ts, stop_rule=stop, bg=bg)
-    b = O.binning(scene, cam, p)
-    out = O.render(scene, cam, p, feats=feats, binned=b)
-    S = tol_scale(O, scene if feats is None else _with_feats(scene, feats), cam, p, b)
-    return out, S
-
-
-def _with_feats(scene, feats):
-    return make_scene(scene.means, scene.scales, scene.quats, scene.opacities, scene.rgb, feats.astype(np.float32))
-
-
-def _compare(g, ref, S, tol, K, max_flagged=0.005):
-    ok = (ref["flags"] & FLAGS_EXCLUDED) == 0
-    assert (~ok).mean() <= max_flagged, (~ok).mean()
+def _compare(g, ref, S, tol, K):
+    """Every pixel against the oracle's outcome the GPU took (ref and S are
+    updated in place); returns the compared pixels."""
+    ok = settle(g, ref, S, tol, K)
     err = np.abs(g["F"] - ref["F"]) / S
     assert err[ok].max() <= tol, err[ok].max()
     np.testing.assert_allclose(g["rgb"][ok], ref["rgb"][ok], atol=2e-5, rtol=0)
     np.testing.assert_allclose(g["T"][ok], ref["T"][ok], atol=2e-5, rtol=1e-4)
     if K:
-        np.testing.assert_array_equal(g["ids"][ok], ref["ids"][ok])
-        np.testing.assert_array_equal(g["pos"][ok], ref["pos"][ok])
-        np.testing.assert_array_equal(g["nstop"][ok], ref["nstop"][ok])
+        for k in ("ids", "pos", "nstop"):
+            if k in g:
+                np.testing.assert_array_equal(g[k][ok], ref[k][ok], err_msg=k)
     return ok
 
 
@@ -114,7 +110,7 @@ def test_room_view_full_resolution():
     for K in (8, 0):
         run = GpuRun(sc, [cam], K=K, cap=1 << 20)
         ref, S = _oracle(sc, cam, K)
-        _compare(run.view(0), ref, S, 1e-4, K, max_flagged=0.01)
+        _compare(run.view(0), ref, S, 1e-4, K)
 
 
 def test_ragged_image_background_and_empty_scene():
@@ -145,9 +141,7 @@ def test_front_k_selection(K, stop):
     sc, cam = scenes.tiny_scene(seed=4)
     run = GpuRun(sc, [cam], K=K, stop_rule=stop, select="front")
     p = O.make_params(K=K, stop_rule=O.EXACT_TOPK if stop == "exact_topk" else O.TMIN, select=1)
-    b = O.binning(sc, cam, p)
-    ref = O.render(sc, cam, p, binned=b)
-    S = tol_scale(O, sc, cam, p, b)
+    ref, S = oracle_ref(sc, cam, p)
     _compare(run.view(0), ref, S, 1e-4, K)
 
 
@@ -160,9 +154,7 @@ def test_renormalised_topk(K, select, feat_dtype):
     run = GpuRun(sc, [cam], K=K, select=select, renorm=True, feat_dtype=feat_dtype)
     feats = torch.as_tensor(sc.feats).to(feat_dtype).double().numpy()
     p = O.make_params(K=K, select=1 if select == "front" else 0, renorm=1)
-    b = O.binning(sc, cam, p)
-    ref = O.render(sc, cam, p, feats=feats, binned=b)
-    S = tol_scale(O, _with_feats(sc, feats), cam, p, b)
+    ref, S = oracle_ref(sc, cam, p, feats=feats)
     _compare(run.view(0), ref, S, 1e-4 if feat_dtype == torch.float32 else 2e-2, K)
     plain = GpuRun(sc, [cam], K=K, select=select, feat_dtype=feat_dtype).view(0)
     g = run.view(0)

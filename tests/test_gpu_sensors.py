@@ -7,11 +7,11 @@ Tolerances follow the FP32 arithmetic of the kernels: the depth sum within
 1e-4 of itself (every term is positive), each normal component within
 1e-4 (1 - T) + 1e-6 (|n_i| = 1, so the sum of |w_i n_i| is at most
 sum w_i = 1 - T), the median depth within 1e-5 relative (one FP32 quotient
-det / c2).  Pixels whose reference decisions lie within rounding distance of
-a threshold are excluded, and for the median also the pixels whose
-transmittance passes within 1e-6 of 1/2.  Requesting the sensor outputs
-changes none of the other outputs: they are compared bit for bit with the
-plain forward call.
+det / c2).  Borderline decisions are resolved against the oracle's outcomes
+(tests/outcomes.py), and where the transmittance passes within 1e-6 of 1/2
+the median depth must equal one of the two outcomes of that switch.
+Requesting the sensor outputs changes none of the other outputs: they are
+compared bit for bit with the plain forward call.
 """
 import numpy as np
 import pytest
@@ -20,7 +20,7 @@ import torch
 import oracle as O
 from paper_2604_10951_gb300 import scenes
 from tests.gpu_util import GpuRun
-from tests.test_gpu_render import FLAGS_EXCLUDED
+from tests.outcomes import oracle_ref, settle
 
 pytestmark = pytest.mark.gpu
 
@@ -39,13 +39,20 @@ def _aux_run(run):
     return dict(F=F, rgb=rgb, T=T, ids=ids, depth=depth, med=med, nrm=nrm)
 
 
+def _ref(run, sc, cam, p, v=0, feats=None, tol=1e-4):
+    """The oracle's outputs with the outcomes the GPU took at borderline pixels."""
+    ref, S = oracle_ref(sc, cam, p, feats=feats)
+    settle(run.view(v), ref, S, tol, p.K)
+    return ref
+
+
 def _check(run, aux, ref, v=0):
     h, w = run.frame.sizes[v]
     a, b = run.frame.pix_off[v], run.frame.pix_off[v + 1]
     for k, plain in (("F", run.F), ("rgb", run.rgb_out), ("T", run.T), ("ids", run.ids)):
         if plain is not None:
             assert torch.equal(aux[k][a:b], plain[a:b]), k
-    ok = (ref["flags"] & FLAGS_EXCLUDED) == 0
+    ok = ~ref["unmatched"]
     d = aux["depth"][a:b].cpu().numpy().reshape(h, w)
     m = aux["med"][a:b].cpu().numpy().reshape(h, w)
     n = aux["nrm"][a:b].cpu().numpy().reshape(h, w, 3)
@@ -54,12 +61,22 @@ def _check(run, aux, ref, v=0):
     assert (e_d <= 1e-4 * ref["depth"][ok] + 1e-6).all(), e_d.max()
     e_n = np.abs(n - ref["normal"])[ok]
     assert (e_n <= 1e-4 * (1.0 - T[ok])[:, None] + 1e-6).all(), e_n.max()
-    okm = ok & ((ref["flags"] & O.FLAG_MEDIAN) == 0)
-    e_m = np.abs(m - ref["depth_med"])[okm]
-    assert (e_m <= 1e-5 * ref["depth_med"][okm]).all(), e_m.max()
-    assert ((m[okm] == 0) == (ref["depth_med"][okm] == 0)).all()
+    # the median switch: one outcome, or either of two where T passes within 1e-6 of 1/2
+    med = ref["depth_med"].copy()
+    sw = ok & ((ref["flags"] & O.FLAG_MEDIAN) != 0)
+    if sw.any():
+        c = ref["_ctx"]
+        alt = O.render(c["scene"], c["cam"], c["params"], feats=c["feats"], binned=c["binned"],
+                       flip=ref["flip"] | np.uint32(O.FLIP_MEDIAN), only=sw)["depth_med"]
+        close = lambda x, y: (np.abs(x - y) <= 1e-5 * np.abs(y)) & ((x == 0) == (y == 0))
+        take = sw & ~close(m, med) & close(m, alt)
+        med[take] = alt[take]
+    e_m = np.abs(m - med)[ok]
+    assert (e_m <= 1e-5 * med[ok]).all(), e_m.max()
+    assert ((m[ok] == 0) == (med[ok] == 0)).all()
     print(f"depth max rel {np.max(e_d / (ref['depth'][ok] + 1e-6)):.2e}, normal max abs {e_n.max():.2e}, "
-          f"median max abs {e_m.max() if e_m.size else 0:.2e}, excluded {(~okm).mean():.4f}")
+          f"median max abs {e_m.max() if e_m.size else 0:.2e}, median switches {int(sw.sum())}, "
+          f"outcomes {ref['outcomes']}")
     return ok
 
 
@@ -70,10 +87,10 @@ def test_sensor_outputs_tiny_scene(K, select, stop):
     run = GpuRun(sc, [cam], K=K, stop_rule=stop, select=select)
     p = O.make_params(K=K, stop_rule=O.EXACT_TOPK if stop == "exact_topk" else O.TMIN,
                       select=1 if select == "front" else 0)
-    ref = O.render(sc, cam, p, binned=O.binning(sc, cam, p))
+    ref = _ref(run, sc, cam, p)
     aux = _aux_run(run)
     ok = _check(run, aux, ref)
-    assert ok.mean() > 0.99
+    assert ok.mean() >= 0.999
     assert (ref["depth"] > 0).mean() > 0.3  # the tiny scene covers much of the view
 
 
@@ -84,11 +101,10 @@ def test_sensor_outputs_room_view_bf16():
     cam = scenes.circle_poses(16)[5]
     run = GpuRun(sc, [cam], K=8, feat_dtype=torch.bfloat16, stop_rule="exact_topk", cap=1 << 20)
     p = O.make_params(K=8, stop_rule=O.EXACT_TOPK)
-    ref = O.render(sc, cam, p, feats=torch.as_tensor(sc.feats).bfloat16().double().numpy(),
-                   binned=O.binning(sc, cam, p))
+    ref = _ref(run, sc, cam, p, feats=torch.as_tensor(sc.feats).bfloat16().double().numpy(), tol=2e-2)
     aux = _aux_run(run)
     ok = _check(run, aux, ref)
-    assert ok.mean() > 0.99
+    assert ok.mean() >= 0.999
 
 
 def test_sensor_outputs_batched_views_and_partial_requests():
@@ -100,8 +116,7 @@ def test_sensor_outputs_batched_views_and_partial_requests():
     aux = _aux_run(run)
     p = O.make_params(K=8, stop_rule=O.EXACT_TOPK)
     for v, cam in enumerate(cams):
-        ref = O.render(sc, cam, p, binned=O.binning(sc, cam, p))
-        _check(run, aux, ref, v)
+        _check(run, aux, _ref(run, sc, cam, p, v), v)
     fr = run.frame
     nrm = torch.zeros(fr.total_pix, 3, device="cuda")
     F, rgb, T, ids = fr.new_outputs()
