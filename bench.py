@@ -162,6 +162,158 @@ def measured_bf16_tflops():
 # ---------------------------------------------------------------------------
 # our implementation
 # ---------------------------------------------------------------------------
+def make_events(torch, n):
+    try:  # events that become graph nodes, so per-call times survive graph replay
+        return [torch.cuda.Event(enable_timing=True, external=True) for _ in range(n)]
+    except TypeError:
+        return None
+
+
+FWD_CALLS = ["project_bin", "sort", "render_forward"]
+STEP_CALLS = FWD_CALLS + ["loss", "render_backward"]
+FWD_KERNELS = ["k_project", "k_scan", "k_emit", "k_tile_sort"]
+# kernels per fwd+bwd step: project_bin 3 (project, scan, emit), sort 1, forward 1, loss 1,
+# backward 5 (clear, feature grads + dots, geometry replay, projection, feature rows)
+KERNELS = FWD_KERNELS + ["k_render_topk", "k_loss", "k_bwd_clear", "k_bwd_feat", "k_bwd_geo", "k_bwd_project",
+                         "k_feat_out"]
+
+
+class StepPath:
+    """Buffers and the step of one configuration, every call through the C
+    ABI, replayed as one CUDA graph per camera set: binning, sort, forward
+    render, and (``backward``) the L2-feature/L1-RGB loss and the backward
+    render.  ``cam_sets`` lists the camera sets the steps cycle over (one
+    view each, or several views rendered in one call)."""
+
+    def __init__(self, torch, L, dev, scene_t, cam_sets, N, C, K, dtype, stop, backward=True, ts=16,
+                 schedule="grid", rank=0, world=1, targets_seed=4):
+        from paper_2604_10951_gb300 import scenes
+        from paper_2604_10951_gb300.raster import Frame, make_cams, make_params
+
+        self.torch, self.L, self.dev = torch, L, dev
+        self.means, self.scales, self.quats, self.opac, self.rgb = scene_t["geo"]
+        self.feats = scene_t["feats"][dtype]
+        self.N, self.C, self.K, self.dtype = N, C, K, dtype
+        self.s = 2 if dtype == torch.bfloat16 else 4
+        self.ts, self.backward, self.rank, self.world = ts, backward, rank, world
+        self.params = make_params(C=C, K=K, tile_size=ts, bin_mode="accu", stop_rule=stop, feat_dtype=dtype,
+                                  out_dtype=dtype, schedule=schedule)
+        self.cam_sets = cam_sets
+        self.cams_c = [make_cams(cs) for cs in cam_sets]
+        self.n_cams = len(cam_sets[0])
+        self.frame = Frame(cam_sets[0], N, self.params, pair_capacity=1 << 20, device=dev)
+        cap = 0
+        for c in self.cams_c:  # size the pair capacity from every camera set, with margin
+            self.frame.cams = c
+            cap = max(cap, self.frame.bin_and_sort(self.means, self.scales, self.quats, self.opac))
+        self.frame._alloc(int(cap * 1.3) + 4096)
+        self.max_pairs = cap
+        self.F, self.rgb_o, self.T, self.ids = self.frame.new_outputs()
+        npx = self.frame.total_pix
+        self.npx = npx
+        self.render_kernel = "k_render_topk" if K else "k_render_full"
+        self.kernels = FWD_KERNELS + [self.render_kernel]
+        self.calls = FWD_CALLS
+        if backward:
+            F_t, rgb_t = scenes.targets(targets_seed, npx, C)
+            self.F_tgt = torch.as_tensor(F_t).to(dev).to(dtype)
+            self.rgb_tgt = torch.as_tensor(rgb_t).to(dev)
+            self.dF = torch.empty_like(self.F)
+            self.drgb = torch.empty_like(self.rgb_o)
+            self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
+            self.g = [torch.empty(N, k, device=dev) for k in (3, 2, 4)] + \
+                     [torch.empty(N, device=dev), torch.empty(N, 3, device=dev)]
+            self.gfeat = torch.empty(N, C, dtype=dtype, device=dev)
+            self.kernels = KERNELS if K else FWD_KERNELS + ["k_render_full", "k_loss", "k_bwd_clear", "k_bwd_geo",
+                                                             "k_bwd_project", "k_feat_out"]
+            self.calls = STEP_CALLS
+        self.graphs, self.gevents = [], []
+        self.ncu = False  # the ncu constants above describe this path's kernels (the main workload only)
+
+    @property
+    def n_sets(self):
+        return len(self.cams_c)
+
+    def step(self, i, events=None):
+        L, torch = self.L, self.torch
+        ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+        fr, p, ws = self.frame, self.params, ptr(self.frame.ws)
+        sp = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        cams = self.cams_c[shard_pose(i, self.rank, self.world, self.n_sets)]
+        a = (p, cams, self.n_cams, self.N)
+        rec = (lambda k: events[k].record()) if events else (lambda k: None)
+        rec(0)
+        L.fss_project_bin(*a, ptr(self.means), ptr(self.scales), ptr(self.quats), ptr(self.opac), ws, fr.cap, sp)
+        rec(1)
+        L.fss_sort(*a, ws, fr.cap, sp)
+        rec(2)
+        L.fss_render_forward(*a, ws, fr.cap, ptr(self.rgb), ptr(self.feats), ptr(self.F), ptr(self.rgb_o),
+                             ptr(self.T), ptr(self.ids), ptr(fr.saved), sp)
+        rec(3)
+        if not self.backward:
+            return
+        L.fss_loss_l2_l1(p, self.npx, ptr(self.F), ptr(self.rgb_o), ptr(self.F_tgt), ptr(self.rgb_tgt), 1.0, 1.0,
+                         ptr(self.dF), ptr(self.drgb), ptr(self.loss), sp)
+        rec(4)
+        L.fss_render_backward(*a, ws, fr.cap, ptr(self.means), ptr(self.scales), ptr(self.quats), ptr(self.opac),
+                              ptr(self.rgb), ptr(self.feats), ptr(fr.saved), ptr(self.T), ptr(self.dF),
+                              ptr(self.drgb), None, *(ptr(g) for g in self.g), ptr(self.gfeat), sp)
+        rec(5)
+
+    def capture(self):
+        """One graph per camera set: the whole step."""
+        torch = self.torch
+        for i in range(self.n_sets):
+            self.step(i)  # sets kernel attributes outside capture
+        torch.cuda.synchronize()
+        for i in range(self.n_sets):
+            g = torch.cuda.CUDAGraph()
+            ev = make_events(torch, len(self.calls) + 1)
+            with torch.cuda.graph(g):
+                self.step(i, ev)
+            self.graphs.append(g)
+            self.gevents.append(ev)
+        torch.cuda.synchronize()
+
+    def check(self):
+        for c in self.cams_c:
+            self.frame.cams = c
+            s, n = self.frame.read_status()
+            if s != self.L.FSS_OK:
+                raise RuntimeError(f"device status {s}: {self.L.last_error()}")
+
+    def time_steps(self, steps, warmup, flush, barrier=lambda: None):
+        torch = self.torch
+        if not self.graphs:
+            self.capture()
+        for i in range(warmup):
+            self.graphs[i % len(self.graphs)].replay()
+        torch.cuda.synchronize()
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(steps):
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+            ev[i][0].record()
+            self.graphs[i % len(self.graphs)].replay()
+            ev[i][1].record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        calls = {}
+        if self.gevents[0] is not None:  # last replay of each set's graph
+            used = self.gevents[:min(steps, len(self.gevents))]
+            for k, n in enumerate(self.calls):
+                calls[n] = float(np.mean([e[k].elapsed_time(e[k + 1]) for e in used]))
+        self.check()
+        return step_ms, calls, wall
+
+
+def percentiles(ms):
+    return {q: round(float(np.percentile(ms, v)), 4) for q, v in (("p10", 10), ("p50", 50), ("p90", 90))}
+
+
 def run_ours(args):
     import torch
 
@@ -170,22 +322,16 @@ def run_ours(args):
     from paper_2604_10951_gb300 import _lib as L
     from paper_2604_10951_gb300 import scenes
     from paper_2604_10951_gb300.build import build
-    from paper_2604_10951_gb300.raster import Frame, make_cams, make_params
 
     build()
     dev = torch.device("cuda", D.local)
     sc = scenes.room_scene(n=N_SPLATS, C=C_FEAT, seed=SEED)
     poses = scenes.circle_poses(16)
-    cams_c = [make_cams([c]) for c in poses]
     H, W = poses[0].height, poses[0].width
     npx = H * W
-    t32 = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev)
-    means, scales, quats, opac, rgb = (t32(x) for x in (sc.means, sc.scales, sc.quats, sc.opacities, sc.rgb))
-    feats = {torch.bfloat16: t32(sc.feats).bfloat16(), torch.float32: t32(sc.feats)}
-    F_tgt_np, rgb_tgt_np = scenes.targets(4, npx, C_FEAT)
-    rgb_tgt = t32(rgb_tgt_np)
-    F_tgt = {torch.bfloat16: t32(F_tgt_np).bfloat16(), torch.float32: t32(F_tgt_np)}
-    stream = torch.cuda.current_stream()
+    scene_t = device_scene(torch, dev, sc)
+    means, scales, quats, opac, rgb = scene_t["geo"]
+    feats = scene_t["feats"]
     ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -195,120 +341,16 @@ def run_ours(args):
         D.close()
         return
 
-    names = ["project_bin", "sort", "render_forward", "loss", "render_backward"]
-
-    def make_events():
-        try:  # events that become graph nodes, so per-call times survive graph replay
-            return [torch.cuda.Event(enable_timing=True, external=True) for _ in range(6)]
-        except TypeError:
-            return None
-
-    class Path:
-        """Buffers and the step of one configuration (all calls via the C ABI),
-        replayed as one CUDA graph per camera pose."""
-
-        def __init__(self, K, dtype, stop):
-            self.dtype = dtype
-            self.params = make_params(C=C_FEAT, K=K, tile_size=16, bin_mode="accu", stop_rule=stop,
-                                      feat_dtype=dtype, out_dtype=dtype)
-            self.frame = Frame([poses[0]], N_SPLATS, self.params, pair_capacity=1 << 20, device=dev)
-            cap = 0
-            for c in cams_c:  # size the pair capacity from the 16 poses, with margin
-                self.frame.cams = c
-                cap = max(cap, self.frame.bin_and_sort(means, scales, quats, opac))
-            self.frame._alloc(int(cap * 1.3) + 4096)
-            self.max_pairs = cap
-            self.F, self.rgb_o, self.T, self.ids = self.frame.new_outputs()
-            self.dF = torch.empty_like(self.F)
-            self.drgb = torch.empty_like(self.rgb_o)
-            self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
-            self.g = [torch.empty(N_SPLATS, k, device=dev) for k in (3, 2, 4)] + \
-                     [torch.empty(N_SPLATS, device=dev), torch.empty(N_SPLATS, 3, device=dev)]
-            self.gfeat = torch.empty(N_SPLATS, C_FEAT, dtype=dtype, device=dev)
-            self.feats = feats[dtype]
-            self.F_tgt = F_tgt[dtype]
-            self.rgb_tgt = rgb_tgt
-            self.graphs, self.gevents = [], []
-
-        def step(self, i, events=None):
-            fr, p, ws = self.frame, self.params, ptr(self.frame.ws)
-            sp = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-            cams = cams_c[shard_pose(i, D.rank, D.world, len(cams_c))]
-            a = (p, cams, 1, N_SPLATS)
-            rec = (lambda k: events[k].record()) if events else (lambda k: None)
-            rec(0)
-            L.fss_project_bin(*a, ptr(means), ptr(scales), ptr(quats), ptr(opac), ws, fr.cap, sp)
-            rec(1)
-            L.fss_sort(*a, ws, fr.cap, sp)
-            rec(2)
-            L.fss_render_forward(*a, ws, fr.cap, ptr(rgb), ptr(self.feats), ptr(self.F), ptr(self.rgb_o),
-                                 ptr(self.T), ptr(self.ids), ptr(fr.saved), sp)
-            rec(3)
-            L.fss_loss_l2_l1(p, npx, ptr(self.F), ptr(self.rgb_o), ptr(self.F_tgt), ptr(self.rgb_tgt), 1.0, 1.0,
-                             ptr(self.dF), ptr(self.drgb), ptr(self.loss), sp)
-            rec(4)
-            L.fss_render_backward(*a, ws, fr.cap, ptr(means), ptr(scales), ptr(quats), ptr(opac), ptr(rgb),
-                                  ptr(self.feats), ptr(fr.saved), ptr(self.T), ptr(self.dF), ptr(self.drgb), None,
-                                  *(ptr(g) for g in self.g), ptr(self.gfeat), sp)
-            rec(5)
-
-        def capture(self):
-            """One graph per pose: the whole step, 11 kernels and 4 memsets."""
-            for i in range(len(cams_c)):
-                self.step(i)  # sets kernel attributes outside capture
-            torch.cuda.synchronize()
-            for i in range(len(cams_c)):
-                g = torch.cuda.CUDAGraph()
-                ev = make_events()
-                with torch.cuda.graph(g):
-                    self.step(i, ev)
-                self.graphs.append(g)
-                self.gevents.append(ev)
-            torch.cuda.synchronize()
-
-        def check(self):
-            for c in cams_c:
-                self.frame.cams = c
-                s, n = self.frame.read_status()
-                if s != L.FSS_OK:
-                    raise RuntimeError(f"device status {s}: {L.last_error()}")
-
-        def time_steps(self, steps, warmup):
-            if not self.graphs:
-                self.capture()
-            for i in range(warmup):
-                self.graphs[i % len(self.graphs)].replay()
-            torch.cuda.synchronize()
-            D.barrier()
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for i in range(steps):
-                flush.zero_()  # L2 flush between timed steps (outside the events)
-                ev[i][0].record()
-                self.graphs[i % len(self.graphs)].replay()
-                ev[i][1].record()
-            torch.cuda.synchronize()
-            wall = time.perf_counter() - t0
-            step_ms = [a.elapsed_time(b) for a, b in ev]
-            calls = {}
-            if self.gevents[0] is not None:  # last replay of each pose's graph
-                used = self.gevents[:min(steps, len(self.gevents))]
-                for k, n in enumerate(names):
-                    calls[n] = float(np.mean([e[k].elapsed_time(e[k + 1]) for e in used]))
-            self.check()
-            return step_ms, calls, wall
-
-    ours = Path(K_TOP, torch.bfloat16, "exact_topk")
+    ours = StepPath(torch, L, dev, scene_t, [[c] for c in poses], N_SPLATS, C_FEAT, K_TOP, torch.bfloat16,
+                    "exact_topk", rank=D.rank, world=D.world)
+    ours.ncu = True
     with ClockSampler(D.local) as clk:
-        step_ms, calls, wall = ours.time_steps(args.steps, args.warmup)
+        step_ms, calls, wall = ours.time_steps(args.steps, args.warmup, flush, D.barrier)
     total_ms = D.max(float(np.sum(step_ms)))
     ms_step = total_ms / args.steps
     frames = args.steps * D.world
     value = frames / (total_ms / 1e3)
-    # kernels per step: project_bin 3 (project, scan, emit), sort 1, forward 1, loss 1,
-    # backward 5 (clear, feature grads + dots, geometry replay, projection, feature rows)
-    launches_per_step = 3 + 1 + 1 + 1 + 5
+    launches_per_step = len(KERNELS)
 
     out = {"metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": D.world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
@@ -321,7 +363,7 @@ def run_ours(args):
                       "global_batch": D.world, "seq_len": npx, "parallelism": f"views sharded x{D.world}",
                       "l2": "flushed between timed steps (512 MB write)"},
            "gpu_launches": launches_per_step * args.steps,
-           "step_ms": {q: round(float(np.percentile(step_ms, v)), 4) for q, v in (("p10", 10), ("p50", 50), ("p90", 90))},
+           "step_ms": percentiles(step_ms),
            "calls_ms": {k: round(v, 4) for k, v in calls.items()},
            "pairs_per_frame_max": ours.max_pairs}
     clocks = clk.summary()
@@ -329,33 +371,50 @@ def run_ours(args):
         out["clocks"] = clocks
     if not args.no_extras:
         # the plain FP32 full-accumulation path on the same frames
-        base = Path(0, torch.float32, "tmin")
-        b_ms, b_calls, _ = base.time_steps(max(8, args.steps // 4), 3)
+        base = StepPath(torch, L, dev, scene_t, [[c] for c in poses], N_SPLATS, C_FEAT, 0, torch.float32, "tmin",
+                        rank=D.rank, world=D.world)
+        b_ms, b_calls, _ = base.time_steps(max(32, args.steps // 4), 3, flush)
         b_ms_step = D.max(float(np.sum(b_ms))) / len(b_ms)
         out["fp32_full_path"] = {"ms_per_step": round(b_ms_step, 4), "frames_per_s": round(1e3 / b_ms_step, 2),
                                  "calls_ms": {k: round(v, 4) for k, v in b_calls.items()},
                                  "speedup_of_bf16_topk": round(b_ms_step / ms_step, 3)}
+        del base
         if calls:
             fwd_ms = calls["project_bin"] + calls["sort"] + calls["render_forward"]
             out["forward_only"] = {"ms": round(fwd_ms, 4), "frames_per_s": round(1e3 / fwd_ms, 2)}
-            out["roofline"], out["roofline_kernels"], out["kernel_us"], out["roofline_frame"] = \
-                roofline(ours, torch, L, flush)
-        out["e2e"] = e2e(ours, torch, dev, ptr, L, args)
-        del base
+        rf = path_roofline(ours, torch, L, flush, float(np.mean(step_ms)))
+        out["roofline"], out["roofline_kernels"], out["kernel_us"], out["roofline_frame"] = \
+            rf["main"], rf["rows"], rf["kernel_us"], rf["frame"]
+        out["kernel_us_hooked"], out["hook"] = rf["kernel_us_hooked"], rf["hook"]
+        out["e2e"] = e2e(ours, torch, dev, L, args)
+        out["e2e_sensor_fwd"] = e2e_sensor(torch, dev, L, scene_t, poses, args)
         out["ablation_fwd"] = ablation(torch, L, dev, means, scales, quats, opac, rgb, feats[torch.float32], poses,
                                        flush)
         out["variants_render_ms"] = variants(torch, dev, means, scales, quats, opac, rgb, feats[torch.bfloat16],
                                              poses, flush)
         out["query_labels"] = queries(torch, dev, sc, means, scales, quats, opac, rgb, poses, flush)
+        out["room_fwd_K"] = room_fwd_K(torch, L, dev, args, flush, D)
+        del ours
+        torch.cuda.empty_cache()
+        out["large_fwd"] = large_fwd(torch, L, dev, args, flush, D)
+        torch.cuda.empty_cache()
+        out["batched_fb"] = batched_fb(torch, L, dev, args, flush, D)
+        torch.cuda.empty_cache()
     if D.rank == 0 and not args.no_extras:
         out["cpu_baseline"] = cpu_baseline(sc, poses)
+        out["precision_vs_oracle"] = precision_sample()
     if D.rank == 0:
         print(json.dumps(out))
     D.close()
 
 
-KERNELS = ["k_project", "k_scan", "k_emit", "k_tile_sort", "k_render_topk", "k_loss", "k_bwd_clear", "k_bwd_feat",
-           "k_bwd_geo", "k_bwd_project", "k_feat_out"]
+def device_scene(torch, dev, sc):
+    t32 = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev)
+    geo = tuple(t32(x) for x in (sc.means, sc.scales, sc.quats, sc.opacities, sc.rgb))
+    f = t32(sc.feats)
+    return {"geo": geo, "feats": {torch.bfloat16: f.bfloat16(), torch.float32: f}}
+
+
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch (camera pose 1) from the
 # ncu capture summarised in profiles/<kernel>_room500k_640x480_c64_k8.md; to be set
 # to None whenever the kernel changes after that capture
@@ -367,15 +426,18 @@ NCU_QUERY_TRAFFIC = {"nq32_dim32_f32": 47276544}
 
 
 def kernel_times(path, torch, L, flush, rounds=4):
-    """Per-kernel durations (ms) over the 16 poses, from events that the library
-    records after each of its launches (fss_set_kernel_events), captured into
-    one graph per pose; L2 flushed before every replay."""
+    """Per-kernel durations (ms) averaged over the path's camera sets, from
+    events that the library records after each of its launches
+    (fss_set_kernel_events), captured into one graph per set; L2 flushed
+    before every replay.  Also the algorithmic bytes of each kernel for
+    those sets."""
     graphs, evs = [], []
-    for i in range(16):
+    names = path.kernels
+    for i in range(path.n_sets):
         # the first event is recorded by torch inside the capture (an external event
         # becomes a graph node); the others by the library after each launch
         ev = [torch.cuda.Event(enable_timing=True, external=True)] + \
-             [torch.cuda.Event(enable_timing=True) for _ in range(len(KERNELS))]
+             [torch.cuda.Event(enable_timing=True) for _ in range(len(names))]
         for e in ev:  # creates the CUDA events
             e.record()
         torch.cuda.synchronize()
@@ -387,7 +449,7 @@ def kernel_times(path, torch, L, flush, rounds=4):
             L.fss_set_kernel_events([])
         graphs.append(g)
         evs.append(ev)
-    sums = np.zeros(len(KERNELS))
+    sums = np.zeros(len(names))
     n = 0
     nbytes, sizes = {}, {}
     for r in range(rounds):
@@ -395,22 +457,33 @@ def kernel_times(path, torch, L, flush, rounds=4):
             flush.zero_()
             g.replay()
             torch.cuda.synchronize()
-            sums += [ev[k].elapsed_time(ev[k + 1]) for k in range(len(KERNELS))]
+            sums += [ev[k].elapsed_time(ev[k + 1]) for k in range(len(names))]
             n += 1
-            if r == 0:  # the pose's algorithmic bytes, averaged over the 16 poses
+            if r == 0:  # the set's algorithmic bytes, averaged over the sets
                 b, z = algorithmic_bytes(path, torch, L)
-                b.update(z.pop("rest"))
                 for k in b:
                     nbytes[k] = nbytes.get(k, 0.0) + b[k] / len(graphs)
                 for k in z:
                     sizes[k] = sizes.get(k, 0.0) + z[k] / len(graphs)
-    return dict(zip(KERNELS, (sums / n).tolist())), nbytes, {k: int(round(v)) for k, v in sizes.items()}
+    return dict(zip(names, (sums / n).tolist())), nbytes, {k: int(round(v)) for k, v in sizes.items()}
+
+
+def unique_rows(ids, sizes, pix_off, ts):
+    """U: per tile, the distinct surfels of its pixels' Top-K sets, summed over tiles."""
+    U = 0
+    for (h, w), a in zip(sizes, pix_off):
+        v = ids[a:a + h * w].reshape(h, w, -1)
+        for ty in range(0, h, ts):
+            for tx in range(0, w, ts):
+                blk = v[ty:ty + ts, tx:tx + ts].reshape(-1)
+                U += np.unique(blk[blk >= 0]).size
+    return U
 
 
 def algorithmic_bytes(path, torch, L):
-    """Unique bytes each of the three render kernels must move per launch for
-    the frame last rendered by `path`: reads of their inputs and writes of
-    their outputs once, nothing re-read."""
+    """Unique bytes each kernel of the step must move per launch for the
+    camera set last rendered by `path`: reads of its inputs and writes of its
+    outputs once, nothing re-read."""
     fr = path.frame
     ranges = fr.region(L.REG_RANGES).view(torch.int32).view(-1, 2).cpu().numpy()
     P = int((ranges[:, 1] - ranges[:, 0]).sum())
@@ -420,80 +493,171 @@ def algorithmic_bytes(path, torch, L):
     nslot = int(st[22])
     nvis = int(st[20]) + int(st[25])  # bounded visible items (narrow + wide)
     n_eval, n_contrib = int(cnt[0]), int(cnt[1])
-    H, W, ts = fr.sizes[0][0], fr.sizes[0][1], 16
-    ids = path.ids.cpu().numpy().reshape(H, W, -1)
-    U = 0
-    for ty in range(0, H, ts):
-        for tx in range(0, W, ts):
-            blk = ids[ty:ty + ts, tx:tx + ts].reshape(-1)
-            U += np.unique(blk[blk >= 0]).size
-    s, K, Cc, npx = 2, K_TOP, C_FEAT, H * W
-    N = N_SPLATS
-    # the other kernels of the step, for the per-frame total
-    rest = {
-        "k_project": N * 16 + nvis * (24 + 64 + 80 + 8),  # centres and opacities of all, the rest of the visible
+    s, K, Cc, npx, N, ts = path.s, path.K, path.C, path.npx, path.N, path.ts
+    V = path.n_cams
+    U = unique_rows(path.ids.cpu().numpy(), fr.sizes, fr.pix_off, ts) if K else 0
+    b = {
+        "k_project": V * N * 16 + nvis * (24 + 64 + 80 + 8),  # centres and opacities of all, the rest of the visible
         "k_scan": tiles * 12,
         "k_emit": nvis * (80 + 64 + 4) + P * 4,
         "k_tile_sort": P * (4 + 4 + 64 + 4 + 4),
-        "k_loss": npx * (2 * Cc * s + 24) + npx * (Cc * s + 12),
-        "k_bwd_clear": nslot * (64 + 4 * Cc),
-        "k_bwd_project": N * 52 + nslot * (64 + 48 + 40),
-        "k_feat_out": N * Cc * s + nslot * 4 * Cc,
     }
+    if K:
+        # ranges; per pair: list id, warp mask, adjugate rows, opacity, colour;
+        # selected rows once per tile; per pixel: features, rgb, T, ids, saved pos/w, nstop
+        b["k_render_topk"] = tiles * 8 + P * (4 + 4 + 48 + 4 + 12) + U * Cc * s + npx * (Cc * s + 12 + 4 + 4 * K * 3 + 4)
+    else:
+        # per pair the record and the feature row (staged once per tile); per pixel F, rgb, T, nstop
+        b["k_render_full"] = tiles * 8 + P * (4 + 4 + 48 + 4 + 12 + Cc * s) + npx * (Cc * s + 12 + 4 + 4)
+    if path.backward:
+        b.update({
+            "k_loss": npx * (2 * Cc * s + 24) + npx * (Cc * s + 12),
+            "k_bwd_clear": nslot * (64 + 4 * Cc),
+            "k_bwd_project": N * 52 + nslot * (V * 64 + 48 + 40),
+            "k_feat_out": N * Cc * s + nslot * 4 * Cc,
+        })
+        if K:
+            # per pixel: saved pos/w, dL/dF, dots written; selected rows (+ list id, slot) once
+            # per tile; the FP32 feature-gradient accumulators written once
+            b["k_bwd_feat"] = tiles * 8 + npx * (8 * K + Cc * s + 4 * K) + U * (Cc * s + 8) + nslot * Cc * 4
+            # per pixel: nstop, T, dL/drgb, saved pos, dots; per pair: list id, mask, record
+            # rows, colour; the per-(view, slot) gradient rows written once
+            b["k_bwd_geo"] = tiles * 8 + npx * (4 + 4 + 12 + 8 * K) + P * (4 + 4 + 64 + 12) + nslot * V * 64
+        else:
+            b["k_bwd_geo"] = tiles * 8 + npx * (4 + 4 + 12 + Cc * s) + P * (4 + 4 + 64 + 12 + Cc * s) \
+                + nslot * V * 64 + nslot * Cc * 4
     # FP32 operations of the forward: ~20 per evaluation (ray-splat solve,
     # density, opacity, depth test) + ~10 per contribution (compositing, K-set
     # test) + 2 C per selected row (feature accumulation); two MUFU ops per evaluation
-    flops_fwd = 20 * n_eval + 10 * n_contrib + 2 * Cc * min(K, 8) * npx
-    return {
-        # ranges; per pair: list id, warp mask, adjugate rows, opacity, colour;
-        # selected rows once per tile; per pixel: features, rgb, T, ids, saved pos/w, nstop
-        "k_render_topk": tiles * 8 + P * (4 + 4 + 48 + 4 + 12) + U * Cc * s
-        + npx * (Cc * s + 12 + 4 + 4 * K * 3 + 4),
-        # per pixel: saved pos/w, dL/dF, dots written; selected rows (+ list id, slot) once
-        # per tile; the FP32 feature-gradient accumulators written once
-        "k_bwd_feat": tiles * 8 + npx * (8 * K + Cc * s + 4 * K) + U * (Cc * s + 8) + nslot * Cc * 4,
-        # per pixel: nstop, T, dL/drgb, saved pos, dots; per pair: list id, mask, record
-        # rows, colour; the per-(view, slot) gradient rows written once
-        "k_bwd_geo": tiles * 8 + npx * (4 + 4 + 12 + 8 * K) + P * (4 + 4 + 64 + 12) + nslot * 64,
-    }, {"pairs": P, "unique_rows": U, "slots": nslot, "evaluations": n_eval, "contributions": n_contrib,
-        "flops_fwd": flops_fwd, "rest": rest}
+    flops_fwd = 20 * n_eval + 10 * n_contrib + 2 * Cc * (min(K, 8) * npx if K else n_contrib)
+    return b, {"pairs": P, "unique_rows": U, "slots": nslot, "evaluations": n_eval, "contributions": n_contrib,
+               "flops_fwd": flops_fwd}
 
 
-def roofline(path, torch, L, flush):
-    """Roofline of the dominant kernel (largest average duration): algorithmic
-    bytes per launch / its event-timed duration (both averaged over the 16
-    poses), against the measured HBM copy bandwidth; the other render kernels
-    alongside."""
+def hook_corrected(kt_raw, step_ms):
+    """Per-kernel times without the event hook's own cost: the hooked
+    kernel times sum to more than the hook-free step (each recorded event
+    adds a gap after its kernel), so the excess over the hook-free step's
+    mean is split evenly over the kernels and taken off each."""
+    tot = sum(kt_raw.values())
+    over = max(0.0, (tot - step_ms) / len(kt_raw))
+    return {k: max(v - over, 1e-6) for k, v in kt_raw.items()}, {
+        "hooked_sum_ms": round(tot, 5), "hook_free_step_ms": round(step_ms, 5),
+        "overhead_us_per_kernel": round(over * 1e3, 3),
+        "method": "per-kernel event times minus an even share of (hooked sum - hook-free step mean)"}
+
+
+def path_roofline(path, torch, L, flush, step_ms, rounds=4):
+    """Roofline of the path's dominant kernel (largest average duration):
+    algorithmic bytes per launch / its event-timed duration (both averaged
+    over the camera sets, the duration corrected for the hook), against the
+    measured HBM copy bandwidth; the render kernels alongside, and the frame
+    total."""
     peak, src = measured_peaks()
-    kt, nbytes, sizes = kernel_times(path, torch, L, flush)
+    raw, nbytes, sizes = kernel_times(path, torch, L, flush, rounds)
+    kt, hook = hook_corrected(raw, step_ms)
     rows = {}
     for k, b in nbytes.items():
-        if k not in ("k_render_topk", "k_bwd_feat", "k_bwd_geo"):
-            continue
         ach = b / (kt[k] * 1e-3) / 1e9
         rows[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-                   "traffic": NCU_TRAFFIC.get(k), "algorithmic_bytes": int(b), "ms": round(kt[k], 5)}
+                   "traffic": NCU_TRAFFIC.get(k) if path.ncu else None,
+                   "algorithmic_bytes": int(b), "ms": round(kt[k], 5)}
     # the forward's arithmetic against the FP32 peak: 152 SMs x 128 lanes x 2 flops x 2.07 GHz
     fp32_peak = 152 * 128 * 2 * 2.07e9
-    rows["k_render_topk"]["alu"] = {"flops": int(sizes["flops_fwd"]),
-                                    "achieved_tflops": round(sizes["flops_fwd"] / (kt["k_render_topk"] * 1e-3) / 1e12, 2),
-                                    "peak_tflops": round(fp32_peak / 1e12, 1),
-                                    "frac": round(sizes["flops_fwd"] / (kt["k_render_topk"] * 1e-3) / fp32_peak, 4)}
+    rk = path.render_kernel
+    rows[rk]["alu"] = {"flops": int(sizes["flops_fwd"]),
+                       "achieved_tflops": round(sizes["flops_fwd"] / (kt[rk] * 1e-3) / 1e12, 2),
+                       "peak_tflops": round(fp32_peak / 1e12, 1),
+                       "frac": round(sizes["flops_fwd"] / (kt[rk] * 1e-3) / fp32_peak, 4)}
     # warp-instruction issue of the ncu captures against 152 SMs x 4 schedulers x 2.07 GHz
     for k, v in NCU_ISSUE.items():
-        if k in rows and v is not None:
+        if k in rows and v is not None and path.ncu:
             rows[k]["issue_frac_ncu"] = round(v[0] / (v[1] * 1e-6) / (152 * 4 * 2.07e9), 3)
     dom = max(kt, key=kt.get)
-    main = dict(rows.get(dom, {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
-                               "traffic": None}), kernel=dom, peak_source=f"{src} (MEASURED_PEAKS.json hbm_gbs)")
+    main = dict(rows[dom], kernel=dom, peak_source=f"{src} (MEASURED_PEAKS.json hbm_gbs)")
     main.update({k: v for k, v in sizes.items() if k != "flops_fwd"})
     # per frame: all kernels' algorithmic bytes over the summed kernel times
-    tot_b = sum(nbytes.get(k, 0.0) for k in KERNELS)
+    tot_b = sum(nbytes.values())
     tot_t = sum(kt.values()) * 1e-3
     frame = {"algorithmic_bytes": int(tot_b), "kernel_ms": round(tot_t * 1e3, 4),
              "achieved": round(tot_b / tot_t / 1e9, 1), "peak": peak, "unit": "GB/s",
              "frac": round(tot_b / tot_t / 1e9 / peak, 4)}
-    return main, rows, {k: round(v * 1e3, 2) for k, v in kt.items()}, frame
+    render_rows = {k: v for k, v in rows.items() if k.startswith(("k_render", "k_bwd_feat", "k_bwd_geo"))}
+    return {"main": main, "rows": render_rows, "kernel_us": {k: round(v * 1e3, 2) for k, v in kt.items()},
+            "kernel_us_hooked": {k: round(v * 1e3, 2) for k, v in raw.items()}, "frame": frame, "hook": hook}
+
+
+def workload_line(path, torch, L, flush, steps, warmup, D, per="frames"):
+    """Timed graph replays of a path (L2 flushed between steps), its step
+    percentiles and its dominant kernel's roofline."""
+    ms, calls, _ = path.time_steps(steps, warmup, flush, D.barrier)
+    ms_step = D.max(float(np.sum(ms))) / len(ms)
+    rf = path_roofline(path, torch, L, flush, float(np.mean(ms)), rounds=2)
+    views = path.n_cams
+    return {"ms_per_step": round(ms_step, 4), f"{per}_per_s": round(views * 1e3 / ms_step, 2),
+            "steps": steps, "step_ms": percentiles(ms), "calls_ms": {k: round(v, 4) for k, v in calls.items()},
+            "roofline": rf["main"], "kernel_us": rf["kernel_us"], "pairs_per_step_max": path.max_pairs}
+
+
+def room_fwd_K(torch, L, dev, args, flush, D):
+    """The room forward workload (500k surfels, seed 1, FP32 C = 64 features,
+    640x480 over 16 poses): binning + sort + render, full accumulation and
+    Top-K K = 4, 8, 16 (exact stop), each step one graph replay."""
+    from paper_2604_10951_gb300 import scenes
+
+    sc = scenes.room_scene(n=N_SPLATS, C=C_FEAT, seed=1)
+    scene_t = device_scene(torch, dev, sc)
+    poses = [[c] for c in scenes.circle_poses(16)]
+    rows = {}
+    for K in (0, 4, 8, 16):
+        p = StepPath(torch, L, dev, scene_t, poses, N_SPLATS, C_FEAT, K, torch.float32,
+                     "exact_topk" if K else "tmin", backward=False, rank=D.rank, world=D.world)
+        rows["full" if K == 0 else f"K{K}"] = workload_line(p, torch, L, flush, max(32, args.steps // 4), 3, D)
+        del p
+    rows["workload"] = "room 500k surfels (seed 1), 640x480 f=525, FP32 C=64, forward (binning, sort, render)"
+    return rows
+
+
+def large_fwd(torch, L, dev, args, flush, D):
+    """The large forward workload: 1.5M surfels in the room generator (seed
+    2), BF16 C = 128 features, 1280x720 (f = 900) over 32 poses, Top-K K = 8."""
+    from paper_2604_10951_gb300 import scenes
+
+    sc = scenes.room_scene(n=1_500_000, C=128, seed=2)
+    scene_t = device_scene(torch, dev, sc)
+    poses = [[c] for c in scenes.circle_poses(32, 1280, 720, 900.0)]
+    p = StepPath(torch, L, dev, scene_t, poses, sc.n, 128, K_TOP, torch.bfloat16, "exact_topk", backward=False,
+                 rank=D.rank, world=D.world)
+    row = workload_line(p, torch, L, flush, max(64, args.steps // 4), 3, D)
+    row["workload"] = "large 1.5M surfels (seed 2), 1280x720 f=900, BF16 C=128, K=8 exact stop, forward"
+    return row
+
+
+def batched_fb(torch, L, dev, args, flush, D):
+    """The batched workload: 1M surfels (seed 6), BF16 C = 128, K = 8, 12
+    cameras of mixed size (4x 320x240, 4x 640x480, 4x 1280x720) rendered in
+    one call per step (forward + loss + backward), with the tile size,
+    schedule and stop rule the autotuner picks; one graph replay per step."""
+    from paper_2604_10951_gb300 import scenes
+    from paper_2604_10951_gb300.tune import Autotuner
+
+    sc = scenes.room_scene(n=1_000_000, C=128, seed=6)
+    scene_t = device_scene(torch, dev, sc)
+    cams = scenes.batched_cameras()
+    means, scales, quats, opac, rgb = scene_t["geo"]
+    t0 = time.perf_counter()
+    best = Autotuner().tune(cams, means, scales, quats, opac, rgb, scene_t["feats"][torch.bfloat16], K=K_TOP, reps=3)
+    tune_s = time.perf_counter() - t0
+    p = StepPath(torch, L, dev, scene_t, [cams], sc.n, 128, K_TOP, torch.bfloat16, best["stop_rule"],
+                 ts=best["tile_size"], schedule=best["schedule"])
+    row = workload_line(p, torch, L, flush, max(32, args.steps // 8), 3, D, per="views")
+    row["autotuner"] = {k: v for k, v in best.items() if k != "all"}
+    row["autotuner"]["seconds"] = round(tune_s, 1)
+    row["autotuner"]["candidates_ms"] = {f"ts{c['tile_size']}_{c['schedule']}_{c['stop_rule']}": round(c["ms"], 3)
+                                         for c in best["all"]}
+    row["workload"] = ("batched 1M surfels (seed 6), 12 views (4x 320x240, 4x 640x480, 4x 1280x720) in one call, "
+                       "BF16 C=128, K=8, forward + loss + backward, autotuned")
+    return row
 
 
 def ablation(torch, L, dev, means, scales, quats, opac, rgb, feats, poses, flush, reps=3):
@@ -636,7 +800,7 @@ def queries(torch, dev, sc, means, scales, quats, opac, rgb, poses, flush, reps=
     return rows
 
 
-def e2e(path, torch, dev, ptr, L, args):
+def e2e(path, torch, dev, L, args):
     """Same step through the C ABI with host buffers: per step the targets go
     host->device from pinned memory and the loss comes back.  The copies run
     on a second stream into two alternating device buffers, so step i+1's
@@ -644,7 +808,8 @@ def e2e(path, torch, dev, ptr, L, args):
     buffer's copy, and a copy waits until the step two back has released its
     buffer).  The compute of a step is the same CUDA graph of C ABI calls as
     the device-timed step, captured once per (pose, buffer); the waits on the
-    copies sit between the replays, on the compute stream."""
+    copies sit between the replays, on the compute stream.  At least 100
+    timed steps."""
     F_h = path.F_tgt.cpu().pin_memory()
     r_h = torch.empty(path.frame.total_pix, 3).pin_memory()
     r_h.copy_(torch.rand(path.frame.total_pix, 3))
@@ -656,7 +821,7 @@ def e2e(path, torch, dev, ptr, L, args):
     released = [torch.cuda.Event() for _ in range(2)]
     compute = torch.cuda.current_stream()
     old_F, old_r = path.F_tgt, path.rgb_tgt
-    n_poses = len(path.graphs) or 1
+    n_poses = path.n_sets
     graphs = [[], []]
     for b in range(2):  # one graph per (pose, buffer): the graph reads that buffer's targets
         path.F_tgt, path.rgb_tgt = F_d[b], r_d[b]
@@ -671,7 +836,7 @@ def e2e(path, torch, dev, ptr, L, args):
     torch.cuda.synchronize()
     for e in released:
         e.record(compute)
-    steps = max(8, args.steps // 4)
+    steps = max(100, args.steps)
 
     def step(i):
         b = i & 1
@@ -695,10 +860,100 @@ def e2e(path, torch, dev, ptr, L, args):
     dt = time.perf_counter() - t0
     path.F_tgt, path.rgb_tgt = old_F, old_r
     del graphs
-    return {"value": round(steps / dt, 2), "unit": "frames/s",
+    return {"value": round(steps / dt, 2), "unit": "frames/s", "steps": steps,
             "h2d_bytes_per_step": int(F_h.numel() * F_h.element_size() + r_h.numel() * 4),
             "d2h_bytes_per_step": 8,
             "copies": "second stream, two alternating buffers; compute as CUDA-graph replays of the C ABI calls"}
+
+
+def e2e_sensor(torch, dev, L, scene_t, poses, args):
+    """The simulator's sensor use (Sec. 4.4): per frame a forward render of
+    the room workload's view (binning, sort, BF16 Top-K K = 8 features, RGB,
+    expected depth through fss_render_forward_aux) whose features, colour
+    and depth come back to pinned host buffers.  The device->host copies run
+    on a second stream from two alternating output sets, so frame i's
+    outputs travel while frame i+1 renders; each frame's compute is one CUDA
+    graph of the C ABI calls per (pose, output set).  At least 100 frames."""
+    from paper_2604_10951_gb300.raster import Frame, make_cams, make_params
+
+    means, scales, quats, opac, rgb = scene_t["geo"]
+    feats = scene_t["feats"][torch.bfloat16]
+    p = make_params(C=C_FEAT, K=K_TOP, stop_rule="exact_topk", feat_dtype=torch.bfloat16)
+    fr = Frame([poses[0]], N_SPLATS, p, pair_capacity=1 << 20, device=dev)
+    cams_c = [make_cams([c]) for c in poses]
+    cap = 0
+    for c in cams_c:
+        fr.cams = c
+        cap = max(cap, fr.bin_and_sort(means, scales, quats, opac))
+    fr._alloc(int(cap * 1.3) + 4096)
+    npx = fr.total_pix
+    outs = []
+    for b in range(2):
+        F, rgb_o, T, ids = fr.new_outputs()
+        outs.append((F, rgb_o, T, ids, torch.empty(npx, device=dev)))
+    host = [(torch.empty(outs[0][0].shape, dtype=outs[0][0].dtype).pin_memory(), torch.empty(npx, 3).pin_memory(),
+             torch.empty(npx).pin_memory()) for _ in range(2)]
+    ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+
+    def compute(i, b):
+        sp = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        cams = cams_c[i % len(cams_c)]
+        a = (p, cams, 1, N_SPLATS)
+        ws = ptr(fr.ws)
+        F, rgb_o, T, ids, depth = outs[b]
+        L.fss_project_bin(*a, ptr(means), ptr(scales), ptr(quats), ptr(opac), ws, fr.cap, sp)
+        L.fss_sort(*a, ws, fr.cap, sp)
+        L.fss_render_forward_aux(*a, ws, fr.cap, ptr(rgb), ptr(feats), ptr(F), ptr(rgb_o), ptr(T), ptr(ids),
+                                 ptr(fr.saved), ptr(depth), None, None, sp)
+
+    graphs = [[], []]
+    for b in range(2):
+        for i in range(len(cams_c)):
+            compute(i, b)
+        torch.cuda.synchronize()
+        for i in range(len(cams_c)):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                compute(i, b)
+            graphs[b].append(g)
+    torch.cuda.synchronize()
+    copy_stream = torch.cuda.Stream(device=dev)
+    rendered = [torch.cuda.Event() for _ in range(2)]
+    drained = [torch.cuda.Event() for _ in range(2)]
+    main = torch.cuda.current_stream()
+    for e in drained:
+        e.record(copy_stream)
+
+    def frame(i):
+        b = i & 1
+        main.wait_event(drained[b])  # the copy of frame i - 2 has left this output set
+        graphs[b][i % len(cams_c)].replay()
+        rendered[b].record(main)
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(rendered[b])
+            F, rgb_o, T, ids, depth = outs[b]
+            hF, hr, hd = host[b]
+            hF.copy_(F, non_blocking=True)
+            hr.copy_(rgb_o, non_blocking=True)
+            hd.copy_(depth, non_blocking=True)
+            drained[b].record(copy_stream)
+
+    for i in range(3):
+        frame(i)
+    torch.cuda.synchronize()
+    steps = max(100, args.steps)
+    t0 = time.perf_counter()
+    for i in range(steps):
+        frame(i)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    s, _ = fr.read_status()
+    d2h = sum(int(t.numel() * t.element_size()) for t in host[0])
+    del graphs
+    return {"value": round(steps / dt, 2), "unit": "frames/s", "steps": steps, "h2d_bytes_per_step": 0,
+            "d2h_bytes_per_step": d2h, "status": int(s),
+            "outputs": "features [640x480, 64] BF16, RGB, expected depth to pinned host memory per frame",
+            "copies": "second stream, two alternating output sets; compute as CUDA-graph replays of the C ABI calls"}
 
 
 BAND = 160  # rows per oracle step: ten 16-row tile rows, a third of a 640x480 frame
@@ -765,6 +1020,21 @@ def cpu_baseline(sc, poses, steps=15):
     """The checker on a bounded sample of the bench's workload (about ten
     seconds of CPU work: five frames in 160-row bands)."""
     return OracleSteps(sc, poses).sample(steps)
+
+
+def precision_sample():
+    """Part of the checker's leg: the GPU path's error against the FP64
+    oracle per output and per gradient (tests/precision_report.py), FP32 and
+    BF16 feature storage, on one whole view of the room (500k surfels,
+    640x480, C = 64) and large (1.5M surfels, 1280x720, C = 128) workloads."""
+    from tests.precision_report import report
+
+    t0 = time.perf_counter()
+    out = report(("room", "large"))
+    out.pop("band_rows", None)
+    out["views"] = {"room": "pose 0 of 16, whole 640x480 frame", "large": "pose 7 of 32, whole 1280x720 frame"}
+    out["seconds"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 # ---------------------------------------------------------------------------
