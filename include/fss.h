@@ -36,6 +36,21 @@
  * Errors found on the device (too many tile-surfel pairs, a bounded wait
  * that ran out) are recorded in the workspace, make later kernels of the
  * same frame do nothing, and are returned by fss_read_status.
+ *
+ * Check build: the library compiled with -DFSS_CHECK_BOUNDS=1
+ * (libfss_check.so) checks, on the device, every index it takes from device
+ * data (tile ranges, pair-list entries, saved Top-K list positions,
+ * gradient slots, list counters) before using it.  A failed check skips the
+ * access, records its site and index, and makes fss_read_status return
+ * FSS_ERR_BOUNDS; nothing traps.  Its workspace (a larger
+ * fss_workspace_size) also holds a 256-byte canary after every region,
+ * written by fss_project_bin and verified by fss_read_status.  The API and
+ * results are otherwise those of the release build.
+ *
+ * Side streams: an eager (not captured) fss_render_backward may run part of
+ * its work in a second stream that the library creates once per calling
+ * thread and device, joined to `stream` before the call returns (also on
+ * errors); the thread's streams are destroyed when it exits.
  */
 #ifndef FSS_H
 #define FSS_H
@@ -55,7 +70,9 @@ typedef enum {
     FSS_ERR_UNSUPPORTED = 2,
     FSS_ERR_CAPACITY = 3, /* more tile-surfel pairs than pair_capacity */
     FSS_ERR_CUDA = 4,
-    FSS_ERR_TIMEOUT = 5   /* a bounded device-side wait gave up */
+    FSS_ERR_TIMEOUT = 5,  /* a bounded device-side wait gave up */
+    FSS_ERR_BOUNDS = 6    /* check build only (FSS_CHECK_BOUNDS): a device index check or a workspace
+                             canary failed; the refused access was skipped */
 } fss_status;
 
 enum { FSS_BIN_AABB = 0, FSS_BIN_SNUG = 1, FSS_BIN_ACCU = 2 };
@@ -300,9 +317,13 @@ fss_status fss_loss_l2_l1(const fss_params *params, int64_t n_pix, const void *f
  * fss_read_status, with the same arguments, on a workspace inside a
  * file-scope device array of FSS_STATIC_SCRATCH_BYTES.  The outputs equal
  * those calls' outputs on a caller workspace.  The call returns after
- * `stream` has finished the frame.  It returns FSS_ERR_CAPACITY (with
- * *num_pairs = pairs needed; retry with a larger pair_capacity) or FSS_OK
- * (with *num_pairs = pairs used); num_pairs may be NULL.
+ * `stream` has finished the frame.  Results: FSS_OK (with *num_pairs = pairs
+ * used; num_pairs may be NULL); FSS_ERR_CAPACITY (with *num_pairs = pairs
+ * needed; retry with a larger pair_capacity); FSS_ERR_INVALID_ARG or
+ * FSS_ERR_UNSUPPORTED for bad arguments or a frame over the limit below,
+ * before anything is launched; FSS_ERR_CUDA when a CUDA call fails;
+ * FSS_ERR_TIMEOUT as fss_read_status reports it; FSS_ERR_BOUNDS from the
+ * check build only.
  *
  * Limit: a frame whose fss_workspace_size(params, cams, n_cams, N,
  * pair_capacity) exceeds FSS_STATIC_SCRATCH_BYTES is rejected with
@@ -311,8 +332,11 @@ fss_status fss_loss_l2_l1(const fss_params *params, int64_t n_pix, const void *f
  * gradient regions, 4 K per pixel, and 20 bytes per pair must fit.
  *
  * Set-up: the first call on each device looks up the array's address
- * (cudaGetSymbolAddress, with that device current) and keeps it.  Make
- * that first call before any stream capture.
+ * (cudaGetSymbolAddress, with that device current) and keeps it for the
+ * life of the process.  Make that first call before any stream capture.
+ * A device reset (cudaDeviceReset) reloads the module at another address:
+ * it is not supported while this library is in use, for this call and for
+ * the library's per-thread side streams.
  *
  * Sharing: all calls on one device share the one array, so calls that
  * overlap in time race and corrupt each other's frames.  Overlap comes from

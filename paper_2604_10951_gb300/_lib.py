@@ -11,9 +11,9 @@ import ctypes as C
 import os
 import threading
 
-from .build import LIB
+from .build import LIB, LIB_CHECK
 
-FSS_OK, FSS_ERR_INVALID_ARG, FSS_ERR_UNSUPPORTED, FSS_ERR_CAPACITY, FSS_ERR_CUDA, FSS_ERR_TIMEOUT = range(6)
+FSS_OK, FSS_ERR_INVALID_ARG, FSS_ERR_UNSUPPORTED, FSS_ERR_CAPACITY, FSS_ERR_CUDA, FSS_ERR_TIMEOUT, FSS_ERR_BOUNDS = range(7)
 FSS_BIN_AABB, FSS_BIN_SNUG, FSS_BIN_ACCU = 0, 1, 2
 FSS_STOP_TMIN, FSS_STOP_EXACT_TOPK = 0, 1
 FSS_F32, FSS_BF16 = 0, 1
@@ -23,7 +23,7 @@ FSS_SELECT_TOPW, FSS_SELECT_FRONT = 0, 1
 FSS_MAX_CAMS = 64
 FSS_MAX_K = 32
 STATUS_NAMES = {0: "FSS_OK", 1: "FSS_ERR_INVALID_ARG", 2: "FSS_ERR_UNSUPPORTED", 3: "FSS_ERR_CAPACITY",
-                4: "FSS_ERR_CUDA", 5: "FSS_ERR_TIMEOUT"}
+                4: "FSS_ERR_CUDA", 5: "FSS_ERR_TIMEOUT", 6: "FSS_ERR_BOUNDS"}
 
 # workspace regions (fss_workspace_region)
 REG_STATUS, REG_REC, REG_BINREC, REG_COUNT, REG_RANGES, REG_LIST, REG_COUNTERS, REG_TILECNT = range(8)
@@ -71,14 +71,22 @@ _lib = None
 _lock = threading.Lock()
 
 
+def check_build() -> bool:
+    """True when the environment asks for the check build (FSS_CHECK_BOUNDS=1)."""
+    return os.environ.get("FSS_CHECK_BOUNDS", "0") == "1"
+
+
 def lib():
-    """The loaded library; raises if it has not been built."""
+    """The loaded library (the check build when FSS_CHECK_BOUNDS=1); raises
+    if it has not been built."""
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(LIB):
-                raise ImportError(f"libfss.so not built ({LIB}); run paper_2604_10951_gb300.build.build()")
-            L = C.CDLL(LIB)
+            path = LIB_CHECK if check_build() else LIB
+            if not os.path.exists(path):
+                raise ImportError(f"{os.path.basename(path)} not built ({path}); "
+                                  "run paper_2604_10951_gb300.build.build()")
+            L = C.CDLL(path)
             P, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
             pp, pc = C.POINTER(fss_params), C.POINTER(fss_camera)
             sig = {

@@ -149,7 +149,7 @@ Layout make_layout(const RParams& P, const Cams& cams) {
     for (int r = 0; r < REG_COUNT_ALL; ++r) {
         L.off[r] = off;
         L.size[r] = sz[r];
-        off += align256(sz[r]);
+        off += align256(sz[r]) + GUARD_BYTES;  // check build: the region's canary follows it
     }
     L.off[REG_COUNTERS] = L.off[REG_STATUS] + STATUS_CLEAR_OFF;
     L.size[REG_COUNTERS] = sizeof(((Status*)0)->counters);
@@ -185,6 +185,47 @@ fss_status prepare(const fss_params* params, const fss_camera* cams, int32_t n_c
 
 bool misaligned16(const void* p) { return p && (reinterpret_cast<uintptr_t>(p) & 15); }
 
+const char* const kRegionNames[REG_COUNT_ALL] = {
+    "status", "records", "binning records", "tile counts per item", "tile ranges", "pair list", "counters",
+    "tile cursors", "sort scratch", "gradient rows", "feature-gradient rows", "dots", "visible items",
+    "unbounded items", "gradient slots", "wide items", "warp masks", "slot surfels", "directions", "item colours",
+    "tile order"};
+const char* const kSiteNames[SITE_COUNT] = {"none", "tile id", "visible-item list slot", "gradient slot",
+                                            "tile range", "pair-list item", "sort scratch",
+                                            "saved list position", "feature row"};
+
+// check build: canary of region r (GUARD_BYTES after its aligned end)
+size_t guard_off(const Layout& L, int r) { return L.off[r] + align256(L.size[r]); }
+
+// check build: writes every region's canary and marks the status block
+cudaError_t arm_guards(const Ctx& ctx, cudaStream_t st) {
+    if (!GUARD_BYTES) return cudaSuccess;
+    for (int r = 0; r < REG_COUNT_ALL; ++r) {
+        if (r == REG_COUNTERS) continue;  // inside the status block
+        cudaError_t e = cudaMemsetAsync(ctx.ws + guard_off(ctx.L, r), GUARD_BYTE, GUARD_BYTES, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaMemsetAsync(ctx.ws + ctx.L.off[REG_STATUS] + offsetof(Status, guards), GUARD_BYTE, sizeof(uint32_t), st);
+}
+
+// check build: the first region whose canary was overwritten, or -1 (after a synchronising read)
+int broken_guard(const Ctx& ctx, cudaStream_t st, cudaError_t& e) {
+    e = cudaSuccess;
+    if (!GUARD_BYTES) return -1;
+    unsigned char buf[REG_COUNT_ALL][GUARD_BYTES ? GUARD_BYTES : 1];
+    for (int r = 0; r < REG_COUNT_ALL && e == cudaSuccess; ++r)
+        if (r != REG_COUNTERS)
+            e = cudaMemcpyAsync(buf[r], ctx.ws + guard_off(ctx.L, r), GUARD_BYTES, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return -1;
+    for (int r = 0; r < REG_COUNT_ALL; ++r) {
+        if (r == REG_COUNTERS) continue;
+        for (size_t k = 0; k < GUARD_BYTES; ++k)
+            if (buf[r][k] != GUARD_BYTE) return r;
+    }
+    return -1;
+}
+
 }  // namespace
 
 // Records `msg` as the calling thread's last error (for units outside this file).
@@ -203,7 +244,21 @@ struct SideStream {
     cudaEvent_t fork = nullptr, join = nullptr;
 };
 constexpr int SIDE_DEVS = 64;
-thread_local SideStream g_side[SIDE_DEVS];  // per thread and device; kept until the process ends
+// Per thread and device, created at the thread's first eager backward call on
+// the device and released when the thread exits (errors ignored: when the
+// process exits, the runtime may already be shutting down).
+struct SideStreams {
+    SideStream d[SIDE_DEVS];
+    ~SideStreams() {
+        for (SideStream& x : d) {
+            if (x.s) (void)cudaStreamDestroy(x.s);
+            if (x.fork) (void)cudaEventDestroy(x.fork);
+            if (x.join) (void)cudaEventDestroy(x.join);
+        }
+        (void)cudaGetLastError();
+    }
+};
+thread_local SideStreams g_side;
 }  // namespace
 
 bool side_stream(cudaStream_t s, cudaStream_t& side, cudaEvent_t& fork, cudaEvent_t& join) {
@@ -212,7 +267,7 @@ bool side_stream(cudaStream_t s, cudaStream_t& side, cudaEvent_t& fork, cudaEven
         (void)cudaGetLastError();
         return false;
     }
-    SideStream& x = g_side[dev];
+    SideStream& x = g_side.d[dev];
     if (x.s == nullptr) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
@@ -332,6 +387,7 @@ fss_status fss_project_bin(const fss_params* params, const fss_camera* cams, int
     }
     e = cudaMemsetAsync(ctx.ws + ctx.L.off[REG_TILECNT], 0, (size_t)ctx.cams.total_tiles * 4, st);
     if (e != cudaSuccess) return cuda_fail(e, "memset tile counts");
+    if ((e = arm_guards(ctx, st)) != cudaSuccess) return cuda_fail(e, "memset canaries");
     const int sms = num_sms_current();
     Status* stp = ctx.at<Status>(REG_STATUS);
     const int64_t items = ctx.P.n_items;
@@ -514,10 +570,19 @@ fss_status fss_read_status(const fss_params* params, const fss_camera* cams, int
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "read status");
     if (num_pairs) *num_pairs = h.pairs_needed;
+    if (GUARD_BYTES && h.guards == GUARD_WORD) {  // check build: the canaries of an armed workspace
+        const int r = broken_guard(ctx, st, e);
+        if (e != cudaSuccess) return cuda_fail(e, "read canaries");
+        if (r >= 0) return fail(FSS_ERR_BOUNDS, "the canary after workspace region %d (%s) was overwritten", r,
+                                kRegionNames[r]);
+    }
     if (h.err) {
         e = cudaMemsetAsync(ctx.ws + ctx.L.off[REG_STATUS], 0, sizeof(int32_t), st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "clear status");
+        if (h.err & ERR_BOUNDS)
+            return fail(FSS_ERR_BOUNDS, "device index check failed at %s: index %lld",
+                        h.bounds_site < SITE_COUNT ? kSiteNames[h.bounds_site] : "?", (long long)h.bounds_index);
         if (h.err & ERR_TIMEOUT) return fail(FSS_ERR_TIMEOUT, "a bounded device wait gave up");
         return fail(FSS_ERR_CAPACITY, "%lld tile-surfel pairs needed, capacity %lld", (long long)h.pairs_needed,
                     (long long)pair_capacity);

@@ -17,11 +17,14 @@ namespace fss {
 __device__ __forceinline__ uint32_t visible_item(int64_t i, uint32_t nvis, uint32_t nwide, const uint32_t* vis_list,
                                                  const uint32_t* wide_list, const uint32_t* unb_list, const Status* st,
                                                  int64_t N) {
+    Status* const stw = const_cast<Status*>(st);  // check build: failed index checks are recorded here
+    if (!in_bounds(stw, SITE_VIS_LIST, i, N * FSS_MAX_CAMS)) return ~0u;
     if (i < nvis) return vis_list[i];
     if (i < (int64_t)nvis + nwide) return wide_list[i - nvis];
     uint32_t k = (uint32_t)(i - nvis - nwide);
     int v = 0;
-    while (k >= st->unb_cnt[v]) k -= st->unb_cnt[v++];
+    while (v < FSS_MAX_CAMS && k >= st->unb_cnt[v]) k -= st->unb_cnt[v++];
+    if (!in_bounds(stw, SITE_VIS_LIST, v, FSS_MAX_CAMS) || !in_bounds(stw, SITE_VIS_LIST, k, N)) return ~0u;
     return unb_list[(int64_t)v * N + k];
 }
 
@@ -37,6 +40,7 @@ __global__ void __launch_bounds__(256) k_sh_dir(const __grid_constant__ Cams cam
     const int64_t n = (int64_t)nvis + nwide + nunb;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t item = visible_item(i, nvis, nwide, vis_list, wide_list, unb_list, st, P.N);
+        if (!in_bounds(const_cast<Status*>(st), SITE_ITEM, item, P.n_items)) continue;
         const int view = (int)((int64_t)item / P.N);
         const int64_t s = (int64_t)item - (int64_t)view * P.N;
         float ox, oy, oz;
@@ -61,6 +65,7 @@ __global__ void __launch_bounds__(256) k_sh_color(const __grid_constant__ Cams c
     const int nb = (P.sh_deg + 1) * (P.sh_deg + 1);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t item = visible_item(i, nvis, nwide, vis_list, wide_list, unb_list, st, P.N);
+        if (!in_bounds(const_cast<Status*>(st), SITE_ITEM, item, P.n_items)) continue;
         const int64_t s = (int64_t)item - (int64_t)((int64_t)item / P.N) * P.N;
         const float4 d = dir[item];
         float Y[16];

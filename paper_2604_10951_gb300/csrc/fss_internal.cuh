@@ -9,6 +9,18 @@
 
 #include "fss.h"
 
+// Debug build with device-side index checks (compiled with
+// -DFSS_CHECK_BOUNDS=1): every index that comes from device data (tile
+// ranges, list entries, saved list positions, gradient slots, counters) is
+// checked before use; a failed check records its site and index in the
+// status block, raises ERR_BOUNDS and skips the access, so the kernel never
+// faults and fss_read_status reports FSS_ERR_BOUNDS.  The workspace also
+// gets a 256-byte canary after every region, checked by fss_read_status.
+// Release builds compile every check away.
+#ifndef FSS_CHECK_BOUNDS
+#define FSS_CHECK_BOUNDS 0
+#endif
+
 namespace fss {
 
 // ---------------------------------------------------------------------------
@@ -77,8 +89,8 @@ enum { BR_VISIBLE = 1, BR_UNBOUNDED = 2, BR_ELL = 4, BR_LOWPASS = 8 };
 // status block at the head of the workspace; everything from `counters` on
 // is cleared at the start of each frame, `err` only by fss_read_status
 struct Status {
-    int32_t err;           // ERR_CAPACITY | ERR_TIMEOUT
-    int32_t pad0;
+    int32_t err;           // ERR_CAPACITY | ERR_TIMEOUT | ERR_BOUNDS
+    uint32_t guards;       // check build: GUARD_WORD once the workspace canaries are written
     int64_t pairs_needed;  // pairs of the last binning (the paper's RN-Total)
     uint64_t counters[8];  // 0 evaluations, 1 contributions, 2 pixels stopped early
     uint32_t nvis;         // bounded visible items listed by k_project
@@ -89,9 +101,68 @@ struct Status {
     uint32_t nwide;        // bounded visible items spanning many tiles
     uint32_t pad3[2];
     uint32_t unb_cnt[FSS_MAX_CAMS];  // unbounded items per view
+    uint32_t bounds_site;            // check build: first failed index check (BoundsSite), else 0
+    uint32_t pad4;
+    int64_t bounds_index;            // ... and the index it refused
 };
-enum { ERR_CAPACITY = 1, ERR_TIMEOUT = 2 };
+enum { ERR_CAPACITY = 1, ERR_TIMEOUT = 2, ERR_BOUNDS = 4 };
+
+// sites of the index checks of the check build (names in api.cu)
+enum BoundsSite : uint32_t {
+    SITE_NONE = 0,
+    SITE_TILE,        // a tile id from binning (tile counts, emit cursors)
+    SITE_VIS_LIST,    // a slot of the visible / wide / unbounded item lists
+    SITE_SLOT,        // a gradient slot or the surfel of one
+    SITE_RANGE,       // a tile's range of the pair list
+    SITE_ITEM,        // a (view, surfel) item read from the pair list
+    SITE_SORT_SCRATCH,  // the radix sort's global scratch
+    SITE_LIST_POS,    // a saved list position of a selected entry
+    SITE_FEAT_ROW,    // a feature row id
+    SITE_COUNT
+};
+
+// Check build: true if 0 <= i < n; otherwise records the site and index in
+// the status block (the first failure only), raises ERR_BOUNDS and returns
+// false so that the caller skips the access.  Release build: always true.
+__device__ __forceinline__ bool in_bounds(Status* st, BoundsSite site, int64_t i, int64_t n) {
+#if FSS_CHECK_BOUNDS
+    if (i >= 0 && i < n) return true;
+    if (atomicCAS(&st->bounds_site, 0u, (uint32_t)site) == 0u) st->bounds_index = i;
+    atomicOr(&st->err, ERR_BOUNDS);
+    return false;
+#else
+    (void)st; (void)site; (void)i; (void)n;
+    return true;
+#endif
+}
+// a condition that only the check build tests (true in release builds)
+#if FSS_CHECK_BOUNDS
+#define FSS_CHECKED(cond) (cond)
+#else
+#define FSS_CHECKED(cond) true
+#endif
+
+// a tile's range [x, y) of a pair list of capacity cap; an invalid range
+// becomes empty (check build)
+__device__ __forceinline__ int2 checked_range(const int2* ranges, int t, int64_t cap, Status* st) {
+    int2 rg = ranges[t];
+#if FSS_CHECK_BOUNDS
+    if (!(rg.x >= 0 && rg.x <= rg.y && (int64_t)rg.y <= cap)) {
+        in_bounds(st, SITE_RANGE, rg.y > cap ? (int64_t)rg.y : (int64_t)rg.x, rg.x < 0 ? 0 : cap + 1);
+        rg = make_int2(0, 0);
+    }
+#else
+    (void)cap; (void)st;
+#endif
+    return rg;
+}
 constexpr size_t STATUS_CLEAR_OFF = 16;  // offsetof(Status, counters)
+static_assert(STATUS_CLEAR_OFF == 16 && sizeof(int32_t) + sizeof(uint32_t) + sizeof(int64_t) == 16,
+              "err, guards and pairs_needed precede the per-frame part of the status block");
+// check build: a 256-byte canary of GUARD_BYTE after every workspace region
+constexpr size_t GUARD_BYTES = FSS_CHECK_BOUNDS ? 256 : 0;
+constexpr unsigned char GUARD_BYTE = 0xA5;
+constexpr uint32_t GUARD_WORD = 0xA5A5A5A5u;
 
 // ---------------------------------------------------------------------------
 // workspace layout (host computed, identical for every call of a frame)

@@ -591,7 +591,8 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4) k_project(const __grid_consta
                 if (!line_interval(br, L, P.ts, o, a, b)) continue;
                 for (int k = a; k <= b; ++k) {
                     const int tx = L.rows ? k : o, ty = L.rows ? o : k;
-                    atomicAdd(&tile_cnt[cam.tile_off + ty * cam.tiles_x + tx], 1u);
+                    const int tt = cam.tile_off + ty * cam.tiles_x + tx;
+                    if (in_bounds(st, SITE_TILE, tt, cams.total_tiles)) atomicAdd(&tile_cnt[tt], 1u);
                 }
                 cnt += (uint32_t)(b - a + 1);
             }
@@ -615,17 +616,21 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4) k_project(const __grid_consta
         bn = __shfl_sync(0xffffffffu, bn, 0);
         bw = __shfl_sync(0xffffffffu, bw, 0);
         bc = __shfl_sync(0xffffffffu, bc, 0);
-        if (narrow) vis_list[bn + __popc(mn & lt)] = (uint32_t)item;
-        if (wid) wide_list[bw + __popc(mw & lt)] = (uint32_t)item;
+        if (narrow && in_bounds(st, SITE_VIS_LIST, bn + __popc(mn & lt), P.n_items))
+            vis_list[bn + __popc(mn & lt)] = (uint32_t)item;
+        if (wid && in_bounds(st, SITE_VIS_LIST, bw + __popc(mw & lt), P.n_items))
+            wide_list[bw + __popc(mw & lt)] = (uint32_t)item;
         if (claim) {
             const int32_t sl = (int32_t)(bc + __popc(mc & lt));
-            splat_slot[claim_s] = sl;
-            slot_surf[sl] = (int32_t)claim_s;
+            if (in_bounds(st, SITE_SLOT, sl, P.N) && in_bounds(st, SITE_SLOT, claim_s, P.N)) {
+                splat_slot[claim_s] = sl;
+                slot_surf[sl] = (int32_t)claim_s;
+            }
         }
     }
     if (unb) {
         const uint32_t k = atomicAdd(&st->unb_cnt[view], 1u);
-        unb_list[(int64_t)view * P.N + k] = (uint32_t)item;
+        if (in_bounds(st, SITE_VIS_LIST, k, P.N)) unb_list[(int64_t)view * P.N + k] = (uint32_t)item;
     }
     }  // survivors
 }
@@ -823,11 +828,12 @@ constexpr int EMIT_BATCH = 8;
 
 // one slot in each of tiles tb[0, n) for `item`: all cursor atomics first, then the stores
 __device__ __forceinline__ void emit_batch(uint32_t* __restrict__ cursor, uint32_t* __restrict__ list,
-                                           const uint32_t* tb, int n, uint32_t item, int64_t cap) {
+                                           const uint32_t* tb, int n, uint32_t item, int64_t cap, int ntiles,
+                                           Status* st) {
     uint32_t pos[EMIT_BATCH];
 #pragma unroll
     for (int j = 0; j < EMIT_BATCH; ++j)
-        if (j < n) pos[j] = atomicAdd(&cursor[tb[j]], 1u);
+        if (j < n) pos[j] = in_bounds(st, SITE_TILE, tb[j], ntiles) ? atomicAdd(&cursor[tb[j]], 1u) : ~0u;
 #pragma unroll
     for (int j = 0; j < EMIT_BATCH; ++j)
         if (j < n && pos[j] < (uint32_t)cap) list[pos[j]] = item;
@@ -849,6 +855,7 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Cams cams,
                                               const float* __restrict__ scales, const float* __restrict__ quats,
                                               float4* __restrict__ rec, const Status* __restrict__ st, int max_lines) {
     if (st->err) return;
+    Status* const stw = const_cast<Status*>(st);  // check build: failed index checks are recorded here
     const int lane = threadIdx.x & 31;
     const uint32_t nvis = st->nvis, nwide = st->nwide;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -862,7 +869,8 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Cams cams,
         const int64_t ri = base + (lane >> 2);
         const bool valid = ri < nrec;
         uint32_t item = 0;
-        if (valid) {
+        bool ok = valid && in_bounds(stw, SITE_VIS_LIST, ri, P.n_items);
+        if (ok) {
             if (ri < nvis) {
                 item = vis_list[ri];
             } else if (ri < (int64_t)nvis + nwide) {
@@ -870,17 +878,21 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Cams cams,
             } else {
                 uint32_t k = (uint32_t)(ri - nvis - nwide);
                 int v = 0;
-                while (k >= st->unb_cnt[v]) k -= st->unb_cnt[v++];
-                item = unb_list[(int64_t)v * P.N + k];
+                while (FSS_CHECKED(v < cams.n) && k >= st->unb_cnt[v]) k -= st->unb_cnt[v++];
+                ok = in_bounds(stw, SITE_VIS_LIST, v, cams.n) && in_bounds(stw, SITE_VIS_LIST, k, P.N);
+                item = ok ? unb_list[(int64_t)v * P.N + k] : 0u;
             }
+            ok = ok && in_bounds(stw, SITE_ITEM, item, P.n_items);
         }
-        record_item_quad(cams, P, means, scales, quats, rec, item, valid);
+        record_item_quad(cams, P, means, scales, quats, rec, ok ? item : 0u, valid && ok);
     }
     // narrow items, from the highest threads down (so that they run beside the
     // records): tiles in batches of EMIT_BATCH, whose cursor atomics are in
     // flight together instead of one round trip each
     for (int64_t i = gstride - 1 - gtid; i < nvis; i += gstride) {
+        if (!in_bounds(stw, SITE_VIS_LIST, i, P.n_items)) break;
         const uint32_t item = vis_list[i];
+        if (!in_bounds(stw, SITE_ITEM, item, P.n_items)) continue;
         const BinRec r = binrec[item];
         const CamDev& cam = cams.c[view_of_item(item, P.N)];
         const Lines L = lines_of(r, P.bin_mode);
@@ -894,12 +906,12 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Cams cams,
                 const int tx = L.rows ? k : o, ty = L.rows ? o : k;
                 tb[nb++] = (uint32_t)(cam.tile_off + ty * cam.tiles_x + tx);
                 if (nb == EMIT_BATCH) {
-                    emit_batch(cursor, list, tb, nb, item, P.pair_cap);
+                    emit_batch(cursor, list, tb, nb, item, P.pair_cap, cams.total_tiles, stw);
                     nb = 0;
                 }
             }
         }
-        emit_batch(cursor, list, tb, nb, item, P.pair_cap);
+        emit_batch(cursor, list, tb, nb, item, P.pair_cap, cams.total_tiles, stw);
     }
     // wide items: one warp per (item, outer line), lanes over the line's tiles,
     // so that a surfel spanning many tiles is spread over many warps
@@ -908,7 +920,9 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Cams cams,
     for (int64_t u = gtid >> 5; u < units; u += warps) {
         const int64_t wi = u / max_lines;
         const int li = (int)(u - wi * max_lines);
+        if (!in_bounds(stw, SITE_VIS_LIST, wi, P.n_items)) break;
         const uint32_t item = wide_list[wi];
+        if (!in_bounds(stw, SITE_ITEM, item, P.n_items)) continue;
         const BinRec r = binrec[item];
         const Lines L = lines_of(r, P.bin_mode);
         if (li >= L.n) continue;  // warp-uniform
@@ -918,7 +932,9 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Cams cams,
         if (!line_interval(r, L, P.ts, o, a, b)) continue;
         for (int k = a + lane; k <= b; k += 32) {
             const int tx = L.rows ? k : o, ty = L.rows ? o : k;
-            const uint32_t pos = atomicAdd(&cursor[cam.tile_off + ty * cam.tiles_x + tx], 1u);
+            const int tt = cam.tile_off + ty * cam.tiles_x + tx;
+            if (!in_bounds(stw, SITE_TILE, tt, cams.total_tiles)) continue;
+            const uint32_t pos = atomicAdd(&cursor[tt], 1u);
             if (pos < (uint32_t)P.pair_cap) list[pos] = item;
         }
     }

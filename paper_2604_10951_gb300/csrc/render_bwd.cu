@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
         const CamDev& cam = cams.c[view];
         const int lt = t - cam.tile_off;
         const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-        const int2 rg = a.ranges[t];
+        const int2 rg = checked_range(a.ranges, t, P.pair_cap, a.st);
         const int64_t vbase = (int64_t)view * P.N;
 
         for (int pc0 = 0; pc0 < npx; pc0 += pch) {
@@ -245,7 +245,8 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                         const int px = tx * TS + (p & (TS - 1)), py = ty * TS + (p >> lts);
                         if (px < cam.W && py < cam.H) {
                             const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
-                            const int pos = a.saved_pos[pix * K + k];
+                            int pos = a.saved_pos[pix * K + k];
+                            if (pos >= 0 && !in_bounds(a.st, SITE_LIST_POS, pos, L)) pos = -1;
                             if (pos >= p0 && pos < p0 + PTAB) {
                                 epos[i] = pos - p0;
                                 ew[i] = a.saved_w[pix * K + k];
@@ -313,8 +314,12 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                     for (int idx = tid; idx < nu * nvec; idx += BWD_FEAT_THREADS) {
                         const int u = divV.div(idx), v = idx - u * nvec;
                         const int64_t sp = (int64_t)a.list[rg.x + p0 + s_inv[u0 + u]] - vbase;
-                        cp_async16(s_rows + (size_t)u * rowe + v * E, feats + sp * C + v * E, 16);
-                        if (v == 0) s_gs[u] = a.splat_slot[sp];
+                        const bool ok = in_bounds(a.st, SITE_ITEM, sp, P.N);  // check build: a zero row, no slot
+                        cp_async16(s_rows + (size_t)u * rowe + v * E, ok ? feats + sp * C + v * E : feats, ok ? 16 : 0);
+                        if (v == 0) {
+                            const int sl = ok ? a.splat_slot[sp] : -1;
+                            s_gs[u] = in_bounds(a.st, SITE_SLOT, sl, P.N) ? sl : -1;
+                        }
                     }
                     cp_async_commit();
                     cp_async_wait_all();
@@ -332,7 +337,7 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                     // flush the current slot's w dL/dF, then move to `slot`
                     auto next_slot = [&](int slot) {
                         if (chunk_live) {
-                            if (cur >= 0) {
+                            if (cur >= 0 && FSS_CHECKED(s_gs[cur - u0] >= 0)) {
                                 float* dst = a.feat_acc + (int64_t)s_gs[cur - u0] * C + sub * E;
 #pragma unroll
                                 for (int e = 0; e < E / 2; e += 2)
@@ -452,7 +457,7 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
     const int px = tx * TS + lp.x, py = ty * TS + lp.y;
     const bool inside = px < cam.W && py < cam.H;
     const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
-    const int2 rg = a.ranges[t];
+    const int2 rg = checked_range(a.ranges, t, P.pair_cap, a.st);
     const int64_t vbase = (int64_t)view * P.N;
     // VAR instances carry the variants (renormalised Top-K, spherical-harmonic
     // item colours, low-pass filter), read from the parameters; the plain
@@ -513,6 +518,11 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
         __syncthreads();
         for (int j = tid; j < cnt; j += NT) {
             const uint32_t item = a.list[rg.x + b_start + j];
+            if (!in_bounds(a.st, SITE_ITEM, (int64_t)item - vbase, P.N)) {  // check build: a dead record
+                s_oc[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                s_wm[j] = 0u;
+                continue;
+            }
             const float4* r = a.rec + 4 * (size_t)item;
             s_r0[j] = r[0];
             s_r1[j] = r[1];
@@ -527,6 +537,7 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
             const int nvec = C / E, rpi = NT / nvec, r0 = tid / nvec, vv = tid - r0 * nvec;
             for (int j = r0; r0 < rpi && j < cnt; j += rpi) {
                 const int64_t sp = (int64_t)a.list[rg.x + b_start + j] - vbase;
+                if (!FSS_CHECKED(sp >= 0 && sp < P.N)) continue;  // recorded by the staging loop
                 float f[E];
                 FeatVec<FT>::load(feats + sp * C + vv * E, f);
 #pragma unroll
@@ -623,7 +634,9 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
             for (int k = 0; k < (VAR ? 15 : 13); ++k) nz |= v[k] != 0.0f;
             if (!nz) continue;
             const int64_t sp = (int64_t)a.list[rg.x + b_start + j] - vbase;
+            if (!FSS_CHECKED(sp >= 0 && sp < P.N)) continue;  // recorded by the staging loop
             const int slot = a.splat_slot[sp];
+            if (!in_bounds(a.st, SITE_SLOT, slot, P.N)) continue;
             float* dst = a.grad_item + ((int64_t)view * P.N + slot) * GRAD_STRIDE;
             red_add_v4(dst, v[0], v[1], v[2], v[3]);
             red_add_v4(dst + 4, v[4], v[5], v[6], v[7]);
@@ -640,7 +653,9 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
                 const float* v = s_gf + j * C + 4 * q;
                 if (v[0] == 0.0f && v[1] == 0.0f && v[2] == 0.0f && v[3] == 0.0f) continue;
                 const int64_t sp = (int64_t)a.list[rg.x + b_start + j] - vbase;
+                if (!FSS_CHECKED(sp >= 0 && sp < P.N)) continue;  // recorded by the staging loop
                 const int slot = a.splat_slot[sp];
+                if (!in_bounds(a.st, SITE_SLOT, slot, P.N)) continue;
                 red_add_v4(a.feat_acc + (int64_t)slot * C + 4 * q, v[0], v[1], v[2], v[3]);
             }
         }
@@ -824,8 +839,12 @@ __global__ void __launch_bounds__(256) k_bwd_project(const __grid_constant__ Cam
     const bool err = a.st->err != 0;
     for (int64_t s = gtid; s < P.N; s += gstride)
         if (err || a.splat_slot[s] < 0) project_grad<VAR>(cams, P, a, sh, s, -1);
-    const int64_t ns = err ? 0 : (int64_t)a.st->nslot;
-    for (int64_t sl = gtid; sl < ns; sl += gstride) project_grad<VAR>(cams, P, a, sh, a.slot_surf[sl], (int)sl);
+    int64_t ns = err ? 0 : (int64_t)a.st->nslot;
+    if (ns > 0 && !in_bounds(a.st, SITE_SLOT, ns - 1, P.N)) ns = 0;
+    for (int64_t sl = gtid; sl < ns; sl += gstride) {
+        const int32_t s = a.slot_surf[sl];
+        if (in_bounds(a.st, SITE_SLOT, s, P.N)) project_grad<VAR>(cams, P, a, sh, s, (int)sl);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -842,7 +861,8 @@ __global__ void __launch_bounds__(256) k_feat_out(const __grid_constant__ RParam
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = pow2 ? (i >> sh) : i / nvec;
         const int vv = (int)(i - s * nvec);
-        const int slot = err ? -1 : a.splat_slot[s];
+        int slot = err ? -1 : a.splat_slot[s];
+        if (slot >= 0 && !in_bounds(a.st, SITE_SLOT, slot, P.N)) slot = -1;
         float v[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = 0.0f;
@@ -865,7 +885,8 @@ __global__ void __launch_bounds__(256) k_bwd_clear(const __grid_constant__ Cams 
         a.st->work_feat = 0u;
         a.st->work_geo = 0u;
     }
-    const int64_t ns = a.st->nslot;
+    int64_t ns = a.st->nslot;
+    if (ns > 0 && !in_bounds(a.st, SITE_SLOT, ns - 1, P.N)) ns = 0;
     const int64_t g4 = ns * (GRAD_STRIDE / 4);
     const int64_t f4 = ns * (P.C / 4);
     const int64_t total = g4 * cams.n + f4;
@@ -992,21 +1013,33 @@ cudaError_t launch_all(const Cams& cams, const RParams& P, const BwdArgs& a, con
         if ((e = cudaStreamWaitEvent(side, ev_fork, 0)) != cudaSuccess) return e;
         k_feat_out<FT><<<num_sms * 8, 256, 0, side>>>(P, a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = cudaEventRecord(ev_join, side)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(ev_join, side)) != cudaSuccess) {
+            (void)cudaStreamSynchronize(side);  // no join event: wait for the side stream's kernel here
+            return e;
+        }
     }
+    // from here on every return joins the side stream first, so that no work of
+    // this call is left running after it returns, even on an error
+    auto joined = [&](cudaError_t err) {
+        if (fork) {
+            const cudaError_t ej = cudaStreamWaitEvent(s, ev_join, 0);
+            if (err == cudaSuccess) err = ej;
+        }
+        return err;
+    };
     if (P.ts == 8) e = launch_geo<8, FT>(cams, P, a, s);
     else if (P.ts == 16) e = launch_geo<16, FT>(cams, P, a, s);
     else e = launch_geo<32, FT>(cams, P, a, s);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) return joined(e);
     const int64_t nb = (P.N + 255) / 256;
     if (P.color_sh || P.lowpass)
         k_bwd_project<true><<<(unsigned)std::max<int64_t>(1, nb), 256, 0, s>>>(cams, P, a, sh);
     else
         k_bwd_project<false><<<(unsigned)std::max<int64_t>(1, nb), 256, 0, s>>>(cams, P, a, nullptr);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return joined(e);
     kernel_mark(s);
     if (fork) {
-        if ((e = cudaStreamWaitEvent(s, ev_join, 0)) != cudaSuccess) return e;
+        if ((e = joined(cudaSuccess)) != cudaSuccess) return e;
     } else if (a.g_feat) {
         k_feat_out<FT><<<num_sms * 8, 256, 0, s>>>(P, a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

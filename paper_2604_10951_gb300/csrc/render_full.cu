@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__
         const int px = tx * TS + lp.x, py = ty * TS + lp.y;
         const bool inside = px < cam.W && py < cam.H;
         const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
-        const int2 rg = a.ranges[t];
+        const int2 rg = checked_range(a.ranges, t, P.pair_cap, a.st);
         const int n = rg.y - rg.x;
         const int64_t vbase = (int64_t)view * P.N;
         const float* __restrict__ rgbv = a.rgb + (P.color_sh ? 3 * vbase : 0);  // SH: item colours
@@ -75,6 +75,11 @@ __global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__
             const int cnt = min(FBATCH, n - b0);
             for (int j = tid; j < cnt; j += NT) {
                 const uint32_t item = a.list[rg.x + b0 + j];
+                if (!in_bounds(a.st, SITE_ITEM, (int64_t)item - vbase, P.N)) {  // check build: a dead record
+                    s_oc[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    s_wm[j] = 0u;
+                    continue;
+                }
                 const float4* r = a.rec + 4 * (size_t)item;
                 s_r0[j] = r[0];
                 s_r1[j] = r[1];
@@ -90,6 +95,7 @@ __global__ void __launch_bounds__(TS * TS) k_render_full(const __grid_constant__
             if (r0 < rpi) {
                 for (int j = r0; j < cnt; j += rpi) {
                     const int64_t sp = (int64_t)a.list[rg.x + b0 + j] - vbase;
+                    if (!FSS_CHECKED(sp >= 0 && sp < P.N)) continue;  // recorded by the staging loop
                     float f[E];
                     FeatVec<FT>::load(feats + (size_t)sp * C + vv0 * E, f);
 #pragma unroll

@@ -58,7 +58,7 @@ using topk_detail::next_tile;
 // largest weight is always slot KCAP - 1.  With the first-K selection the
 // K slots after the padding take the first K contributors in order.
 template <int TS, int KCAP, typename FT, bool FRONT, bool AUX>
-__global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : 1) k_render_topk(const __grid_constant__ Cams cams,
+__global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : (KCAP == 16 && TS <= 16 ? 512 / (TS * TS) : 1)) k_render_topk(const __grid_constant__ Cams cams,
                                                          const __grid_constant__ RParams P, const FwdArgs a,
                                                          const __grid_constant__ AuxOut x) {
     constexpr int NT = TS * TS;
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : 1) k_r
         const int px = tx * TS + lp.x, py = ty * TS + lp.y;
         const bool inside = px < cam.W && py < cam.H;
         const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
-        const int2 rg = a.ranges[t];
+        const int2 rg = checked_range(a.ranges, t, P.pair_cap, a.st);
         const int n = rg.y - rg.x;
         const int64_t vbase = (int64_t)view * P.N;
         const float* __restrict__ rgbv = a.rgb + (P.color_sh ? 3 * vbase : 0);  // SH: item colours
@@ -120,6 +120,11 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : 1) k_r
             const int cnt = min(BATCH, n - b0);
             for (int j = tid; j < cnt; j += NT) {
                 const uint32_t item = a.list[rg.x + b0 + j];
+                if (!in_bounds(a.st, SITE_ITEM, (int64_t)item - vbase, P.N)) {  // check build: a dead record
+                    s_oc[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    s_wm[j] = 0u;
+                    continue;
+                }
                 const float4* r = a.rec + 4 * (size_t)item;
                 s_r0[j] = r[0];
                 s_r1[j] = r[1];
@@ -279,6 +284,7 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : 1) k_r
                     for (int k = 0; k < c; ++k) {
                         const int id = s_id[q * KCAP + k];
                         const float w = s_w[q * KCAP + k];
+                        if (!in_bounds(a.st, SITE_FEAT_ROW, id, P.N)) continue;
                         float f[E];
                         FeatVec<FT>::load(feats + (size_t)id * P.C + vv * E, f);
 #pragma unroll

@@ -87,8 +87,9 @@ __global__ void __launch_bounds__(256) k_tile_sort(const __grid_constant__ Cams 
                                                    const Status* __restrict__ st) {
     __shared__ uint64_t sk[SORT_CAP];
     if (st->err) return;
+    Status* const stw = const_cast<Status*>(st);  // check build: failed index checks are recorded here
     const int t = blockIdx.x;  // index order: measured faster here than the heavy-first order
-    const int2 rg = ranges[t];
+    const int2 rg = checked_range(ranges, t, P.pair_cap, stw);
     const int n = rg.y - rg.x;
     if (n <= 0) return;
     const int view = view_of_tile(cams, t);
@@ -96,15 +97,21 @@ __global__ void __launch_bounds__(256) k_tile_sort(const __grid_constant__ Cams 
     const int lt = t - cam.tile_off;
     const int tx0 = (lt % cam.tiles_x) * P.ts, ty0 = (lt / cam.tiles_x) * P.ts;
     const int nu = (int)st->unb_cnt[view];
+    if (!in_bounds(stw, SITE_VIS_LIST, nu, ((int64_t)n < P.N ? (int64_t)n : P.N) + 1)) return;
     const int nb = n - nu;
     const uint32_t* ul = unb_list + (int64_t)view * P.N;
     const int tid = threadIdx.x;
+    // the i-th item of the tile (bounded items, then the view's unbounded ones), checked
+    auto item_at = [&](int i) -> uint32_t {
+        const uint32_t it = i < nb ? list[rg.x + i] : ul[i - nb];
+        return in_bounds(stw, SITE_ITEM, it, P.n_items) ? it : 0u;
+    };
     if (n <= (int)blockDim.x) {
         // short list: rank of each key = number of smaller keys (keys are
         // unique, so the ranks are a permutation); one barrier instead of a
         // network of them
         uint64_t key = ~0ull;
-        if (tid < n) key = make_key(rec, tid < nb ? list[rg.x + tid] : ul[tid - nb]);
+        if (tid < n) key = make_key(rec, item_at(tid));
         sk[tid] = key;
         __syncthreads();
         if (tid < n) {
@@ -122,7 +129,7 @@ __global__ void __launch_bounds__(256) k_tile_sort(const __grid_constant__ Cams 
         while (m < n) m <<= 1;
         for (int i = tid; i < m; i += blockDim.x) {
             uint64_t k = ~0ull;
-            if (i < n) k = make_key(rec, i < nb ? list[rg.x + i] : ul[i - nb]);
+            if (i < n) k = make_key(rec, item_at(i));
             sk[i] = k;
         }
         __syncthreads();
@@ -148,7 +155,7 @@ __global__ void __launch_bounds__(256) k_tile_sort(const __grid_constant__ Cams 
     }
     uint64_t* keys = scratch + rg.x;
     uint64_t* tmp = scratch + P.pair_cap + rg.x;
-    for (int i = tid; i < n; i += blockDim.x) keys[i] = make_key(rec, i < nb ? list[rg.x + i] : ul[i - nb]);
+    for (int i = tid; i < n; i += blockDim.x) keys[i] = make_key(rec, item_at(i));
     __syncthreads();
     block_radix_sort_global(keys, tmp, n);
     for (int i = tid; i < n; i += blockDim.x) {

@@ -76,9 +76,14 @@ extern "C" fss_status fss_forward_static(const fss_params* params, const fss_cam
         if ((s = static_workspace(&ws, msg, sizeof msg)) != FSS_OK) return fss::set_error(s, msg);
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    // The error word of the status block persists between frames; start clean
-    // (fss_project_bin clears the rest of the block, the slots and tile counts).
-    cudaError_t e = cudaMemsetAsync(ws, 0, sizeof(int32_t), st);
+    // The error word (the first word of the status block) persists between
+    // frames; start clean (fss_project_bin clears the rest of the block, the
+    // slots and the tile counts).
+    size_t status_off = 0;
+    if ((s = fss_workspace_region(params, cams, n_cams, N, pair_capacity, 0 /* the status block */, &status_off,
+                                  nullptr)) != FSS_OK)
+        return s;
+    cudaError_t e = cudaMemsetAsync(static_cast<unsigned char*>(ws) + status_off, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) {
         char msg[256];
         snprintf(msg, sizeof msg, "memset static status: %s", cudaGetErrorString(e));

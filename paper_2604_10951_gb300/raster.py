@@ -70,10 +70,19 @@ def _stream(stream=None):
 class Frame:
     """Workspace and per-pixel buffers for one set of cameras, N surfels and
     one parameter block.  One forward may be in flight per frame (the
-    backward pass reads the binning and the saved buffer it left)."""
+    backward pass reads the binning and the saved buffer it left).
+
+    ``deferred=True`` makes :meth:`forward` (and so :func:`render` under
+    autograd) asynchronous: it never waits for the device, so a training
+    step can run ahead of the host or be captured in a CUDA graph.  The pair
+    capacity is then fixed at construction; the caller calls :meth:`check`
+    after the step (or after several), which raises ``FssError`` with status
+    ``FSS_ERR_CAPACITY`` and the needed pair count if a frame overflowed.
+    The outputs and gradients of an overflowed step are incomplete: grow
+    the frame (:meth:`grow`) and run the step again."""
 
     def __init__(self, cams: Sequence, N: int, params: L.fss_params, pair_capacity: int = 1 << 20,
-                 device: Optional[torch.device] = None):
+                 device: Optional[torch.device] = None, deferred: bool = False):
         if not torch.cuda.is_available():
             raise RuntimeError("the rasterizer needs a CUDA device (sm_103a)")
         L.lib()
@@ -90,6 +99,7 @@ class Frame:
             self.pix_off.append(self.pix_off[-1] + h * w)
         self.saved = torch.empty(L.fss_saved_size(params, self.cams, self.n_cams), dtype=torch.uint8,
                                  device=self.device)
+        self.deferred = bool(deferred)
         self._alloc(pair_capacity)
 
     # -- workspace ------------------------------------------------------------
@@ -161,10 +171,33 @@ class Frame:
         return need
 
     def forward(self, means, scales, quats, opac, rgb, feats, grow: bool = True):
-        self.bin_and_sort(means, scales, quats, opac, grow)
+        if self.deferred:  # no host synchronisation: capacity is checked later by check()
+            self.project_bin(means, scales, quats, opac)
+            self.sort()
+        else:
+            self.bin_and_sort(means, scales, quats, opac, grow)
         F, rgb_o, T, ids = self.new_outputs()
         self.render_forward(rgb, feats, F, rgb_o, T, ids)
         return F, rgb_o, T, ids
+
+    def check(self, stream=None):
+        """Waits for the frame's last calls and reads the device status
+        (fss_read_status); raises FssError on capacity overflow (with the
+        needed pair count as ``.needed``) or a device-side error.  Returns
+        the pair count of the last binning."""
+        status, n = self.read_status(stream)
+        if status != L.FSS_OK:
+            err = L.FssError(status, L.last_error())
+            err.needed = n
+            raise err
+        self.num_pairs = n
+        return n
+
+    def grow(self, pairs: int):
+        """A new workspace for at least ``pairs`` tile-surfel pairs (with 25 %
+        margin).  Not while a step that uses the old one is in flight or
+        captured in a graph."""
+        self._alloc(int(pairs * 1.25) + 1024)
 
     def counters(self) -> torch.Tensor:
         return self.region(L.REG_COUNTERS).view(torch.int64)

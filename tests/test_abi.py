@@ -164,3 +164,40 @@ def test_colour_mode_arguments(lib):
     lib.fss_workspace_size(C.byref(p), _cam(), 1, 1000, 10, C.byref(out))
     # the colour mode adds a direction (16 B) and a colour (12 B) per item
     assert ws_sh - out.value >= 1000 * 28
+
+
+def test_status_values_match_the_header():
+    text = open(HEADER).read()
+    for name in ("FSS_ERR_INVALID_ARG", "FSS_ERR_UNSUPPORTED", "FSS_ERR_CAPACITY", "FSS_ERR_CUDA", "FSS_ERR_TIMEOUT",
+                 "FSS_ERR_BOUNDS"):
+        m = re.search(rf"{name} = (\d+)", text)
+        assert m and int(m.group(1)) == getattr(L, name), name
+        assert L.STATUS_NAMES[getattr(L, name)] == name
+
+
+def test_check_build_exports_the_abi_with_a_canary_after_every_region(lib):
+    """The check build (FSS_CHECK_BOUNDS=1) is the same ABI; its workspace
+    adds one 256-byte canary after each region, and its regions keep the
+    release sizes."""
+    from paper_2604_10951_gb300.build import LIB_CHECK
+    chk = C.CDLL(LIB_CHECK)
+    for name in _declared():
+        assert hasattr(chk, name), name
+    pp, pc = C.POINTER(L.fss_params), C.POINTER(L.fss_camera)
+    chk.fss_workspace_size.argtypes = [pp, pc, C.c_int32, C.c_int64, C.c_int64, C.POINTER(C.c_size_t)]
+    chk.fss_workspace_region.argtypes = [pp, pc, C.c_int32, C.c_int64, C.c_int64, C.c_int32,
+                                         C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
+    p = L.fss_default_params()
+    cams = _cam()
+    out = C.c_size_t()
+    assert chk.fss_workspace_size(C.byref(p), cams, 1, 1000, 5000, C.byref(out)) == L.FSS_OK
+    assert out.value == L.fss_workspace_size(p, cams, 1, 1000, 5000) + 256 * L.N_REGIONS
+    off, size = C.c_size_t(), C.c_size_t()
+    prev_end = 0
+    for r in range(L.N_REGIONS):
+        assert chk.fss_workspace_region(C.byref(p), cams, 1, 1000, 5000, r, C.byref(off), C.byref(size)) == L.FSS_OK
+        assert size.value == L.fss_workspace_region(p, cams, 1, 1000, 5000, r)[1]
+        if r != L.REG_COUNTERS:
+            assert off.value >= prev_end  # the previous region's canary lies between
+            prev_end = off.value + (size.value + 255) // 256 * 256 + 256
+    assert prev_end <= out.value

@@ -111,3 +111,34 @@ def test_static_forward_rejects_frames_over_the_limit():
     st, n, got, saved = _static(fr2, params, ins, cap=fr2.num_pairs)
     assert st == L.FSS_OK
     _assert_same(got, ref, saved, fr2.saved)
+
+
+def test_static_forward_calls_leave_device_memory_unchanged():
+    """After a first call (which loads the module and looks up the array),
+    further calls change neither the device's free memory (cudaMemGetInfo:
+    no allocation by the library, the runtime or a library it calls) nor
+    torch's allocated bytes; outputs are allocated before the calls."""
+    sc, cam = scenes.tiny_scene(seed=3, n=2000, C=16)
+    params = make_params(C=16, K=4)
+    ins = _inputs(sc, torch.float32)
+    fr, ref = _reference([cam], sc, params, ins)
+    cap = fr.num_pairs + 64
+    F, rgb_o, T, ids = fr.new_outputs()
+    saved = torch.empty_like(fr.saved)
+    means, scales, quats, opac, rgb, feats = ins
+
+    def call():
+        return L.fss_forward_static(params, fr.cams, fr.n_cams, fr.N, cap, _ptr(means), _ptr(scales), _ptr(quats),
+                                    _ptr(opac), _ptr(rgb), _ptr(feats), _ptr(F), _ptr(rgb_o), _ptr(T), _ptr(ids),
+                                    _ptr(saved), _stream())
+
+    assert call()[0] == L.FSS_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(5):
+        assert call()[0] == L.FSS_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0 and torch.cuda.memory_allocated() == alloc0
+    _assert_same((F, rgb_o, T, ids), ref, saved, fr.saved)
