@@ -137,15 +137,6 @@ __device__ __forceinline__ void group_sum4(float (&v)[4], int sub) {
     if constexpr (G >= 8) v[0] += __shfl_xor_sync(ALL, v[0], 1);
 }
 
-// 16-byte asynchronous global -> shared copy (bytes = 0: zero fill), its
-// commit and the wait for all of this thread's copies
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
-    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
 // rows of zeros after the chunk's dL/dF rows: at least G 16-byte chunks, so
 // a lane without a record (or past the row) reads zeros
 __host__ __device__ constexpr int zero_rows(int G, int rowb) { return (G * 16 + rowb - 1) / rowb; }

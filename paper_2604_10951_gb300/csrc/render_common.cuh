@@ -140,6 +140,15 @@ __device__ __forceinline__ void store_vec(void* out, int64_t elem, const float* 
     }
 }
 
+// 16-byte asynchronous global -> shared copy (bytes = 0: zero fill), its
+// commit and the wait for all of this thread's copies
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // Division by a divisor fixed for the whole kernel (d >= 1, 0 <= n < 2^24),
 // without the ~20-instruction integer division: a float reciprocal guess
 // corrected by one step either way.
@@ -343,7 +352,7 @@ template <typename KernelT>
 inline cudaError_t launch_tiles(KernelT kern, int threads, size_t smem, const Cams& cams, const RParams& P, const FwdArgs& a,
                                const AuxOut& x, int num_sms, cudaStream_t stream) {
     cudaError_t e = cudaSuccess;
-    if (smem > 48 * 1024) {
+    if (smem + 2048 > 48 * 1024) {  // above the default limit with the kernels' static shared memory (< 2 KB)
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
