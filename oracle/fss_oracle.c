@@ -866,12 +866,6 @@ static void composite_pixel(const geo64 *geo, const double *opac, const double *
     int ntop = 0;
     int64_t n_eval = 0;
     for (int32_t j = 0; j < n_cand; ++j) {
-        if (K > 0 && p->stop_rule == ORC_EXACT && p->select == 0 && ntop == K) {
-            double wmin = topw[K - 1];
-            const int border = fabs(amax * T - wmin) <= 1e-6;
-            if (border) flags |= FLAG_EXACT;
-            if (decide(amax * T <= wmin, border, flip, &nb)) break;
-        }
         /* first-K selection: the set is final once K surfels contributed */
         if (K > 0 && p->stop_rule == ORC_EXACT && p->select == 1 && n == K) break;
         const int32_t id = cand[j];
@@ -924,6 +918,16 @@ static void composite_pixel(const geo64 *geo, const double *opac, const double *
                 while (q > 0 && topw[q - 1] < e->w) { topw[q] = topw[q - 1]; --q; }
                 topw[q] = e->w;
             }
+        }
+        /* EXACT_TOPK stop: once the set is full, no later surfel can enter it when
+         * alpha_max T <= the smallest selected weight.  T and the set change only at a
+         * contribution, so the test is taken once per contribution (one decision,
+         * whatever number of candidates follow before the next contribution). */
+        if (K > 0 && p->stop_rule == ORC_EXACT && p->select == 0 && ntop == K) {
+            const double wmin = topw[K - 1];
+            const int border = fabs(amax * T - wmin) <= 1e-6;
+            if (border) flags |= FLAG_EXACT;
+            if (decide(amax * T <= wmin, border, flip, &nb)) break;
         }
     }
     for (int k = 0; k < 3; ++k) out->rgb[k] = rgbacc[k] + T * p->bg[k];
