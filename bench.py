@@ -400,7 +400,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         out["batched_fb"] = batched_fb(torch, L, dev, args, flush, D)
         torch.cuda.empty_cache()
-    if D.rank == 0 and not args.no_extras:
+    if D.rank == 0 and D.world == 1 and not args.no_extras:  # the checker's leg: rank 0 at N = 1 only
         out["cpu_baseline"] = cpu_baseline(sc, poses)
         out["precision_vs_oracle"] = precision_sample()
     if D.rank == 0:
