@@ -417,13 +417,13 @@ def device_scene(torch, dev, sc):
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch inside the step (camera
 # pose 0, the L2 contents the step's earlier kernels left; ncu --cache-control none),
-# summarised in profiles/instep_dram_room500k_640x480_c64_k8.md; to be set to None
-# whenever the kernel changes after that capture
+# from the in-step traffic summary under profiles/; to be set to None whenever the
+# kernel changes after that capture
 NCU_TRAFFIC = {"k_render_topk": 6969600 + 59221504, "k_bwd_feat": 42223872 + 28325888, "k_bwd_geo": 13252096 + 8844544}
 # (smsp__inst_executed.sum, gpu__time_duration.sum in us) of the one-kernel --set full
-# captures in profiles/<kernel>_room500k_640x480_c64_k8.md
+# captures summarised under profiles/
 NCU_ISSUE = {"k_render_topk": (85133445, 98.144), "k_bwd_feat": (67462191, 85.856), "k_bwd_geo": (88911000, 107.584)}
-# the query-label kernel's capture (profiles/k_query_labels_room500k_nq32_dim32.md): DRAM read + write
+# the query-label kernel's capture (summarised under profiles/): DRAM read + write
 NCU_QUERY_TRAFFIC = {"nq32_dim32_f32": 47276544}
 
 
