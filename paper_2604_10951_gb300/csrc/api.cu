@@ -131,7 +131,7 @@ Layout make_layout(const RParams& P, const Cams& cams) {
     sz[REG_RANGES] = (size_t)cams.total_tiles * 8;
     sz[REG_LIST] = cap * 4;
     sz[REG_COUNTERS] = 0;  // inside the status block
-    sz[REG_TILECNT] = (size_t)cams.total_tiles * 4;
+    sz[REG_TILECNT] = (size_t)cams.total_tiles * 4 * TC_STRIDE;
     sz[REG_SORTTMP] = cap * 16;
     sz[REG_GRAD_ITEM] = (size_t)cams.n * N * GRAD_STRIDE * 4;
     sz[REG_FEAT_ACC] = N * (size_t)P.C * 4;
@@ -385,7 +385,7 @@ fss_status fss_project_bin(const fss_params* params, const fss_camera* cams, int
         e = cudaMemsetAsync(ctx.ws + ctx.L.off[REG_SLOT], 0xff, (size_t)N * 4, st);
         if (e != cudaSuccess) return cuda_fail(e, "memset slots");
     }
-    e = cudaMemsetAsync(ctx.ws + ctx.L.off[REG_TILECNT], 0, (size_t)ctx.cams.total_tiles * 4, st);
+    e = cudaMemsetAsync(ctx.ws + ctx.L.off[REG_TILECNT], 0, (size_t)ctx.cams.total_tiles * 4 * TC_STRIDE, st);
     if (e != cudaSuccess) return cuda_fail(e, "memset tile counts");
     if ((e = arm_guards(ctx, st)) != cudaSuccess) return cuda_fail(e, "memset canaries");
     const int sms = num_sms_current();

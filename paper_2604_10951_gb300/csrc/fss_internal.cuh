@@ -167,6 +167,11 @@ constexpr uint32_t GUARD_WORD = 0xA5A5A5A5u;
 // ---------------------------------------------------------------------------
 // workspace layout (host computed, identical for every call of a frame)
 // ---------------------------------------------------------------------------
+// Per-tile pair counters (the emit cursors after the scan) sit one 32-byte
+// sector apart: every pair of the frame adds to one of them, and packed 32
+// to an L2 line the adds of the whole GPU queued on a few dozen lines.
+constexpr int TC_STRIDE = 8;
+
 enum Region {
     REG_STATUS = 0,
     REG_REC = 1,

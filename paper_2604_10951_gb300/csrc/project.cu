@@ -164,16 +164,28 @@ __device__ __forceinline__ void hull_interval(int& a, int& b, int da, int db) {
     b = max(b, db);
 }
 
-// AccuTile, outer loop over tile rows: tile-column interval of row ty.  The
-// strip's extreme abscissae are the ellipse's left/right tangent points when
+// AccuTile: the inner tile interval of one outer tile line (a row of tiles
+// when `rows`, else a column).  On a row strip [Ya, Yb] (local coordinates)
+// the ellipse's extreme abscissae are its left/right tangent points when
 // these fall inside the strip, else the roots of
-// A x^2 + 2(B y + D) x + (C y^2 + 2 E y + F) = 0 at the nearer strip edge.
-__device__ __forceinline__ bool accu_row(const BinRec& r, int ts, int ty, int& ta, int& tb) {
-    const int ra = max(ty * ts, (int)r.py0), rb = min(ty * ts + ts - 1, (int)r.py1);
+//   A x^2 + 2(B y + D) x + (C y^2 + 2 E y + F) = 0
+// at the nearer strip edge.  A column is the same with x and y exchanged
+// (A <-> C, D <-> E, and the centre, half extents and pixel ranges), so one
+// code path serves both, its operands picked by selects; both candidates of
+// each side are computed and one is selected.  The lanes of a warp,
+// holding different items and line kinds, then never split on these
+// branches (a divergent version measured ~1800 cycles per call).
+__device__ __forceinline__ bool accu_line(const BinRec& r, bool rows, int ts, int o, int& ta, int& tb) {
+    const float A = rows ? r.A : r.C, C = rows ? r.C : r.A, D = rows ? r.D : r.E, E = rows ? r.E : r.D;
+    const float X0 = rows ? r.X0 : r.Y0, hx = rows ? r.hx : r.hy;
+    const float xc = rows ? r.xc : r.yc, yc = rows ? r.yc : r.xc;
+    const int p0 = rows ? r.px0 : r.py0, p1 = rows ? r.px1 : r.py1;  // inner pixel range
+    const int q0 = rows ? r.py0 : r.px0, q1 = rows ? r.py1 : r.px1;  // outer pixel range
+    const int ra = max(o * ts, q0), rb = min(o * ts + ts - 1, q1);
     if (ra > rb) return false;
-    const float Ya = fs(fa((float)ra, 0.5f), r.yc), Yb = fs(fa((float)rb, 0.5f), r.yc);
+    const float Ya = fs(fa((float)ra, 0.5f), yc), Yb = fs(fa((float)rb, 0.5f), yc);
     int da = 1, db = 0;  // S20b
-    if (r.flags & BR_LOWPASS) disc_strip(r.rd2, Ya, Yb, r.xc, r.px0, r.px1, da, db);
+    if (r.flags & BR_LOWPASS) disc_strip(r.rd2, Ya, Yb, xc, p0, p1, da, db);
     if (!(r.flags & BR_ELL)) {
         if (da > db) return false;
         ta = da / ts;
@@ -183,65 +195,23 @@ __device__ __forceinline__ bool accu_row(const BinRec& r, int ts, int ty, int& t
     float ext[2];
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
-        const float Xs = side == 0 ? fs(r.X0, r.hx) : fa(r.X0, r.hx);
-        const float t = fa(fm(r.B, Xs), r.E);
-        const float Yt = fdv(-t, r.C);
-        if (Yt >= Ya && Yt <= Yb) { ext[side] = Xs; continue; }
+        const float Xs = side == 0 ? fs(X0, hx) : fa(X0, hx);
+        const float t = fa(fm(r.B, Xs), E);
+        const float Yt = fdv(-t, C);
+        const bool tangent = Yt >= Ya && Yt <= Yb;
         const float Y = Yt < Ya ? Ya : Yb;
-        const float bb = fa(fm(r.B, Y), r.D);
-        const float cc = fa(fa(fm(fm(r.C, Y), Y), fm(fm(2.0f, r.E), Y)), r.F);
-        float disc = fs(fm(bb, bb), fm(r.A, cc));
-        if (disc < 0.0f) disc = 0.0f;
+        const float bb = fa(fm(r.B, Y), D);
+        const float cc = fa(fa(fm(fm(C, Y), Y), fm(fm(2.0f, E), Y)), r.F);
+        float disc = fs(fm(bb, bb), fm(A, cc));
+        disc = disc < 0.0f ? 0.0f : disc;
         const float sq = fq(disc), nb = -bb;
-        ext[side] = fdv(side == 0 ? fs(nb, sq) : fa(nb, sq), r.A);
+        const float root = fdv(side == 0 ? fs(nb, sq) : fa(nb, sq), A);
+        ext[side] = tangent ? Xs : root;
     }
-    const float fl = ceilf(fs(fa(ext[0], r.xc), 0.5f)), fh = floorf(fs(fa(ext[1], r.xc), 0.5f));
-    int a = 1, b = 0;
-    if (fl <= fh && !(fh < (float)r.px0 || fl > (float)r.px1)) {
-        a = fl < (float)r.px0 ? r.px0 : (int)fl;
-        b = fh > (float)r.px1 ? r.px1 : (int)fh;
-    }
-    hull_interval(a, b, da, db);
-    if (a > b) return false;
-    ta = a / ts;
-    tb = b / ts;
-    return true;
-}
-
-// AccuTile, outer loop over tile columns: tile-row interval of column tx
-__device__ __forceinline__ bool accu_col(const BinRec& r, int ts, int tx, int& ta, int& tb) {
-    const int ca = max(tx * ts, (int)r.px0), cb = min(tx * ts + ts - 1, (int)r.px1);
-    if (ca > cb) return false;
-    const float Xa = fs(fa((float)ca, 0.5f), r.xc), Xb = fs(fa((float)cb, 0.5f), r.xc);
-    int da = 1, db = 0;  // S20b
-    if (r.flags & BR_LOWPASS) disc_strip(r.rd2, Xa, Xb, r.yc, r.py0, r.py1, da, db);
-    if (!(r.flags & BR_ELL)) {
-        if (da > db) return false;
-        ta = da / ts;
-        tb = db / ts;
-        return true;
-    }
-    float ext[2];
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-        const float Ys = side == 0 ? fs(r.Y0, r.hy) : fa(r.Y0, r.hy);
-        const float t = fa(fm(r.B, Ys), r.D);
-        const float Xt = fdv(-t, r.A);
-        if (Xt >= Xa && Xt <= Xb) { ext[side] = Ys; continue; }
-        const float X = Xt < Xa ? Xa : Xb;
-        const float bb = fa(fm(r.B, X), r.E);
-        const float cc = fa(fa(fm(fm(r.A, X), X), fm(fm(2.0f, r.D), X)), r.F);
-        float disc = fs(fm(bb, bb), fm(r.C, cc));
-        if (disc < 0.0f) disc = 0.0f;
-        const float sq = fq(disc), nb = -bb;
-        ext[side] = fdv(side == 0 ? fs(nb, sq) : fa(nb, sq), r.C);
-    }
-    const float fl = ceilf(fs(fa(ext[0], r.yc), 0.5f)), fh = floorf(fs(fa(ext[1], r.yc), 0.5f));
-    int a = 1, b = 0;
-    if (fl <= fh && !(fh < (float)r.py0 || fl > (float)r.py1)) {
-        a = fl < (float)r.py0 ? r.py0 : (int)fl;
-        b = fh > (float)r.py1 ? r.py1 : (int)fh;
-    }
+    const float fl = ceilf(fs(fa(ext[0], xc), 0.5f)), fh = floorf(fs(fa(ext[1], xc), 0.5f));
+    const bool hit = fl <= fh && !(fh < (float)p0 || fl > (float)p1);
+    int a = hit ? (fl < (float)p0 ? p0 : (int)fl) : 1;
+    int b = hit ? (fh > (float)p1 ? p1 : (int)fh) : 0;
     hull_interval(a, b, da, db);
     if (a > b) return false;
     ta = a / ts;
@@ -276,12 +246,58 @@ __device__ __forceinline__ bool line_interval(const BinRec& r, const Lines& L, i
         b = L.rows ? r.tx1 : r.ty1;
         return true;
     }
-    return L.rows ? accu_row(r, ts, o, a, b) : accu_col(r, ts, o, a, b);
+    return accu_line(r, L.rows, ts, o, a, b);
 }
 
 // view of item (items are view-major, view * N + surfel, < 2^32)
 __device__ __forceinline__ int view_of_item(int64_t item, int64_t N) {
     return N >= ((int64_t)1 << 32) || item < N ? 0 : (int)((uint32_t)item / (uint32_t)N);
+}
+
+// Tile work of a warp's items spread over its lanes.  The outer lines of
+// the 32 lanes' items are numbered in lane order ((lane, line) units) and
+// taken 32 at a time, one per lane, so that an item with many lines no
+// longer runs them one after another in its own lane while the others wait.
+// The warp's slices of shared memory hold each lane's binning record and
+// item, and the inclusive prefix of the line counts.
+struct WarpLines {
+    BinRec* br;      // [32]
+    uint32_t* item;  // [32]
+    int* pre;        // [32]
+};
+
+// every lane of the warp calls this with its own line count (0 for no
+// item) after writing its record and item; returns the warp's total
+__device__ __forceinline__ int warp_line_prefix(const WarpLines& w, int nl) {
+    const int lane = threadIdx.x & 31;
+    int incl = nl;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    w.pre[lane] = incl;
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, incl, 31);
+}
+
+// g(owner lane, item, camera, rows, outer line, first tile, last tile) for
+// every non-empty line interval of the warp's items (inner tiles a..b)
+template <typename G>
+__device__ __forceinline__ void warp_lines(const Cams& cams, const RParams& P, const WarpLines& w, int total, G&& g) {
+    const int lane = threadIdx.x & 31;
+    for (int u = lane; u < total; u += 32) {
+        int j = 0;  // owner: the first lane whose inclusive prefix exceeds u
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) j += w.pre[j + step - 1] <= u ? step : 0;
+        const BinRec r = w.br[j];
+        const Lines L = lines_of(r, P.bin_mode);
+        const int o = L.first + (u - (w.pre[j] - L.n));
+        int a, b;
+        if (!line_interval(r, L, P.ts, o, a, b)) continue;
+        const uint32_t item = w.item[j];
+        g(j, item, cams.c[view_of_item(item, P.N)], L.rows, o, a, b);
+    }
 }
 
 }  // namespace
@@ -369,6 +385,11 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4) k_project(const __grid_consta
                                                  int32_t* __restrict__ slot_surf, Status* __restrict__ st) {
     __shared__ uint32_t s_q[PROJ_ITEMS];
     __shared__ int s_nq;
+    __shared__ BinRec s_br[PROJ_THREADS];
+    __shared__ uint32_t s_item[PROJ_THREADS], s_cnt[PROJ_THREADS];
+    __shared__ int s_pre[PROJ_THREADS];
+    const int wb = threadIdx.x & ~31;
+    const WarpLines wl{s_br + wb, s_item + wb, s_pre + wb};
     if (st->err) return;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x == 0) s_nq = 0;
@@ -412,11 +433,11 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4) k_project(const __grid_consta
     bool vis = false, wide = false, unb = false, claim = false;
     int64_t claim_s = 0;
     int view = 0;
+    BinRec br;
     if (item < P.n_items) {
         view = view_of_item(item, P.N);
         const int64_t s = item - (int64_t)view * P.N;
         const CamDev& cam = cams.c[view];
-        BinRec br;
         br.flags = 0;
         br.px0 = br.py0 = br.tx0 = br.ty0 = 1;
         br.px1 = br.py1 = br.tx1 = br.ty1 = 0;
@@ -427,13 +448,15 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4) k_project(const __grid_consta
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
         do {
             // S3 (centre), S4, S5, S5b first: the order of the cull tests does not change the result
+            // (the rotation is loaded beside the cull inputs, so that the latencies overlap)
+            const CullIn ci = load_cull_in(means, scales, opac, s);
+            const float4 q4 = __ldg(reinterpret_cast<const float4*>(quats) + s);
             float pc[3], o;
-            const bool pass = early_culls(cam, P, load_cull_in(means, scales, opac, s), pc, o);
+            const bool pass = early_culls(cam, P, ci, pc, o);
             r3.y = pc[2];
             r3.x = o;
             if (!pass) break;
             // S1
-            const float4 q4 = __ldg(reinterpret_cast<const float4*>(quats) + s);
             const float qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
             const float n2 = fa(fa(fa(fm(qw, qw), fm(qx, qx)), fm(qy, qy)), fm(qz, qz));
             if (!(n2 > 0.0f)) break;
@@ -448,8 +471,7 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4) k_project(const __grid_consta
             tv[1] = fs(1.0f, fm(2.0f, fa(fm(x, x), fm(z, z))));
             tv[2] = fm(2.0f, fa(fm(y, z), fm(w, x)));
             // S3 (tangent columns)
-            const float2 sc2 = __ldg(reinterpret_cast<const float2*>(scales) + s);
-            const float su = sc2.x, sv = sc2.y;
+            const float su = ci.sc.x, sv = ci.sc.y;
             float au[3], av[3], e[3];
             mvec(cam.R, tu, e);
 #pragma unroll
@@ -582,23 +604,29 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4) k_project(const __grid_consta
             claim = atomicCAS(&splat_slot[s], -1, -2) == -1;
             claim_s = s;
         }
-        if (vis) {  // per-tile pair counts (S20 intervals)
-            const Lines L = lines_of(br, P.bin_mode);
-            uint32_t cnt = 0;
-            for (int li = 0; li < L.n; ++li) {
-                const int o = L.first + li;
-                int a, b;
-                if (!line_interval(br, L, P.ts, o, a, b)) continue;
-                for (int k = a; k <= b; ++k) {
-                    const int tx = L.rows ? k : o, ty = L.rows ? o : k;
-                    const int tt = cam.tile_off + ty * cam.tiles_x + tx;
-                    if (in_bounds(st, SITE_TILE, tt, cams.total_tiles)) atomicAdd(&tile_cnt[tt], 1u);
-                }
-                cnt += (uint32_t)(b - a + 1);
+    }
+    // per-tile pair counts (S20 intervals), the warp's lines spread over its lanes
+    {
+        const int lane = threadIdx.x & 31;
+        if (vis) wl.br[lane] = br;
+        wl.item[lane] = (uint32_t)item;
+        s_cnt[threadIdx.x] = 0u;
+        const int total = warp_line_prefix(wl, vis ? lines_of(br, P.bin_mode).n : 0);
+        warp_lines(cams, P, wl, total, [&](int j, uint32_t, const CamDev& cam, bool rows, int o, int a, int b) {
+            for (int k = a; k <= b; ++k) {
+                const int tx = rows ? k : o, ty = rows ? o : k;
+                const int tt = cam.tile_off + ty * cam.tiles_x + tx;
+                if (in_bounds(st, SITE_TILE, tt, cams.total_tiles)) atomicAdd(&tile_cnt[(size_t)tt * TC_STRIDE], 1u);
             }
+            atomicAdd(&s_cnt[wb + j], (uint32_t)(b - a + 1));
+        });
+        __syncwarp();
+        if (vis) {
+            const uint32_t cnt = s_cnt[threadIdx.x];
             count[item] = cnt;
             wide = cnt > WIDE_TILES;
         }
+        __syncwarp();  // the slices are reused by the warp's next survivors
     }
     // warp-aggregated appends (one global atomic per warp and counter, no CTA barrier)
     {
@@ -663,7 +691,7 @@ __global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ Cams cams
 #pragma unroll
         for (int k = 0; k < ITEMS; ++k) {
             const int t = base + threadIdx.x * ITEMS + k;
-            v[k] = t < nt ? tile_cnt[t] + st->unb_cnt[view_of_tile(cams, t)] : 0u;
+            v[k] = t < nt ? tile_cnt[(size_t)t * TC_STRIDE] + st->unb_cnt[view_of_tile(cams, t)] : 0u;
             sum += v[k];
         }
         uint32_t incl = sum;
@@ -693,7 +721,7 @@ __global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ Cams cams
                 run += v[k];
                 const bool fits = run <= (uint64_t)P.pair_cap;
                 ranges[t] = make_int2(fits ? (int)s0 : 0, fits ? (int)run : 0);
-                tile_cnt[t] = fits ? (uint32_t)s0 : 0u;  // emit cursor
+                tile_cnt[(size_t)t * TC_STRIDE] = fits ? (uint32_t)s0 : 0u;  // emit cursor
             }
         }
         __syncthreads();
@@ -803,10 +831,16 @@ __device__ void record_item_quad(const Cams& cams, const RParams& P, const float
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int i = 0; i < 3; ++i) d[c][i] = shfl_df(dj[i], q0 + c);
-    // adjugate row j: m_j = d_{j+1} x d_{j+2}
+    // adjugate row j: m_j = d_{j+1} x d_{j+2} (operands picked by selects: a
+    // dynamic index would put d in local memory)
     const int r = j < 3 ? j : 0;
-    df m[3];
-    dcross(d[(r + 1) % 3], d[(r + 2) % 3], m);
+    df da[3], db[3], m[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        da[i] = r == 0 ? d[1][i] : (r == 1 ? d[2][i] : d[0][i]);
+        db[i] = r == 0 ? d[2][i] : (r == 1 ? d[0][i] : d[1][i]);
+    }
+    dcross(da, db, m);
     float mx = j < 3 ? fmaxf(fmaxf(fabsf(m[0].hi), fabsf(m[1].hi)), fabsf(m[2].hi)) : 0.0f;
     mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1, 4));
     mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2, 4));
@@ -833,7 +867,7 @@ __device__ __forceinline__ void emit_batch(uint32_t* __restrict__ cursor, uint32
     uint32_t pos[EMIT_BATCH];
 #pragma unroll
     for (int j = 0; j < EMIT_BATCH; ++j)
-        if (j < n) pos[j] = in_bounds(st, SITE_TILE, tb[j], ntiles) ? atomicAdd(&cursor[tb[j]], 1u) : ~0u;
+        if (j < n) pos[j] = in_bounds(st, SITE_TILE, tb[j], ntiles) ? atomicAdd(&cursor[(size_t)tb[j] * TC_STRIDE], 1u) : ~0u;
 #pragma unroll
     for (int j = 0; j < EMIT_BATCH; ++j)
         if (j < n && pos[j] < (uint32_t)cap) list[pos[j]] = item;
@@ -844,7 +878,8 @@ __device__ __forceinline__ void emit_batch(uint32_t* __restrict__ cursor, uint32
 // tiles (slot order is arbitrary; the per-tile sort restores a total order)
 // and replaces the render records by their double-float versions.
 //   records:      one quad of lanes per narrow, wide or unbounded item;
-//   narrow items: one thread each, tiles in line order;
+//   narrow items: 32 per warp, their (item, outer line) units spread over
+//                 the lanes; each lane emits its line's tiles;
 //   wide items:   one warp per (item, outer line), lanes over the line's tiles;
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
@@ -854,9 +889,14 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Cams cams,
                                               uint32_t* __restrict__ list, const float* __restrict__ means,
                                               const float* __restrict__ scales, const float* __restrict__ quats,
                                               float4* __restrict__ rec, const Status* __restrict__ st, int max_lines) {
+    __shared__ BinRec s_br[256];
+    __shared__ uint32_t s_item[256];
+    __shared__ int s_pre[256];
     if (st->err) return;
     Status* const stw = const_cast<Status*>(st);  // check build: failed index checks are recorded here
     const int lane = threadIdx.x & 31;
+    const int wb = threadIdx.x & ~31;
+    const WarpLines wl{s_br + wb, s_item + wb, s_pre + wb};
     const uint32_t nvis = st->nvis, nwide = st->nwide;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
@@ -886,36 +926,40 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Cams cams,
         }
         record_item_quad(cams, P, means, scales, quats, rec, ok ? item : 0u, valid && ok);
     }
-    // narrow items, from the highest threads down (so that they run beside the
-    // records): tiles in batches of EMIT_BATCH, whose cursor atomics are in
-    // flight together instead of one round trip each
-    for (int64_t i = gstride - 1 - gtid; i < nvis; i += gstride) {
-        if (!in_bounds(stw, SITE_VIS_LIST, i, P.n_items)) break;
-        const uint32_t item = vis_list[i];
-        if (!in_bounds(stw, SITE_ITEM, item, P.n_items)) continue;
-        const BinRec r = binrec[item];
-        const CamDev& cam = cams.c[view_of_item(item, P.N)];
-        const Lines L = lines_of(r, P.bin_mode);
-        uint32_t tb[EMIT_BATCH];
-        int nb = 0;
-        for (int li = 0; li < L.n; ++li) {
-            const int o = L.first + li;
-            int a, b;
-            if (!line_interval(r, L, P.ts, o, a, b)) continue;
+    // narrow items, 32 per warp from the highest warps down (so that they run
+    // beside the records); each lane emits one line's tiles in batches of
+    // EMIT_BATCH, whose cursor atomics are in flight together
+    const int64_t warps = gstride >> 5;
+    for (int64_t c0 = (warps - 1 - (gtid >> 5)) * 32; c0 < nvis; c0 += warps * 32) {  // warp-uniform
+        const int64_t i = c0 + lane;
+        bool ok = i < nvis && in_bounds(stw, SITE_VIS_LIST, i, P.n_items);
+        const uint32_t item = ok ? vis_list[i] : 0u;
+        ok = ok && in_bounds(stw, SITE_ITEM, item, P.n_items);
+        int nl = 0;
+        if (ok) {
+            const BinRec r = binrec[item];
+            wl.br[lane] = r;
+            nl = lines_of(r, P.bin_mode).n;
+        }
+        wl.item[lane] = item;
+        const int total = warp_line_prefix(wl, nl);
+        warp_lines(cams, P, wl, total, [&](int, uint32_t it, const CamDev& cam, bool rows, int o, int a, int b) {
+            uint32_t tb[EMIT_BATCH];
+            int nb = 0;
             for (int k = a; k <= b; ++k) {
-                const int tx = L.rows ? k : o, ty = L.rows ? o : k;
+                const int tx = rows ? k : o, ty = rows ? o : k;
                 tb[nb++] = (uint32_t)(cam.tile_off + ty * cam.tiles_x + tx);
                 if (nb == EMIT_BATCH) {
-                    emit_batch(cursor, list, tb, nb, item, P.pair_cap, cams.total_tiles, stw);
+                    emit_batch(cursor, list, tb, nb, it, P.pair_cap, cams.total_tiles, stw);
                     nb = 0;
                 }
             }
-        }
-        emit_batch(cursor, list, tb, nb, item, P.pair_cap, cams.total_tiles, stw);
+            emit_batch(cursor, list, tb, nb, it, P.pair_cap, cams.total_tiles, stw);
+        });
+        __syncwarp();  // the slices are reused by the warp's next chunk
     }
     // wide items: one warp per (item, outer line), lanes over the line's tiles,
     // so that a surfel spanning many tiles is spread over many warps
-    const int64_t warps = gstride >> 5;
     const int64_t units = (int64_t)nwide * max_lines;
     for (int64_t u = gtid >> 5; u < units; u += warps) {
         const int64_t wi = u / max_lines;
@@ -934,7 +978,7 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Cams cams,
             const int tx = L.rows ? k : o, ty = L.rows ? o : k;
             const int tt = cam.tile_off + ty * cam.tiles_x + tx;
             if (!in_bounds(stw, SITE_TILE, tt, cams.total_tiles)) continue;
-            const uint32_t pos = atomicAdd(&cursor[tt], 1u);
+            const uint32_t pos = atomicAdd(&cursor[(size_t)tt * TC_STRIDE], 1u);
             if (pos < (uint32_t)P.pair_cap) list[pos] = item;
         }
     }
