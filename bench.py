@@ -171,8 +171,9 @@ def make_events(torch, n):
 
 FWD_CALLS = ["project_bin", "sort", "render_forward"]
 STEP_CALLS = FWD_CALLS + ["loss", "render_backward"]
-FWD_KERNELS = ["k_project", "k_scan", "k_emit", "k_tile_sort"]
-# kernels per fwd+bwd step: project_bin 3 (project, scan, emit), sort 1, forward 1, loss 1,
+FWD_KERNELS = ["k_project", "k_emit", "k_tile_sort"]
+# kernels per fwd+bwd step: project_bin 2 (project; emit, whose first CTA scans the tile counts), sort 1,
+# forward 1, loss 1,
 # backward 5 (clear, feature grads + dots, geometry replay, projection, feature rows)
 KERNELS = FWD_KERNELS + ["k_render_topk", "k_loss", "k_bwd_clear", "k_bwd_feat", "k_bwd_geo", "k_bwd_project",
                          "k_feat_out"]
@@ -500,8 +501,7 @@ def algorithmic_bytes(path, torch, L):
     U = unique_rows(path.ids.cpu().numpy(), fr.sizes, fr.pix_off, ts) if K else 0
     b = {
         "k_project": V * N * 16 + nvis * (24 + 64 + 80 + 8),  # centres and opacities of all, the rest of the visible
-        "k_scan": tiles * 12,
-        "k_emit": nvis * (80 + 64 + 4) + P * 4,
+        "k_emit": tiles * 12 + nvis * (80 + 64 + 4) + P * 4,
         "k_tile_sort": P * (4 + 4 + 64 + 4 + 4),
     }
     if K:

@@ -399,12 +399,9 @@ fss_status fss_project_bin(const fss_params* params, const fss_camera* cams, int
                                                ctx.at<int32_t>(REG_SLOT), ctx.at<int32_t>(REG_SLOT_SURF), stp);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_project");
     kernel_mark(st);
-    k_scan<<<1, 1024, 0, st>>>(ctx.cams, ctx.P, ctx.at<uint32_t>(REG_TILECNT), ctx.at<int2>(REG_RANGES),
-                               ctx.at<int32_t>(REG_ORDER), stp);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_scan");
-    kernel_mark(st);
     // one resident wave: records run from the lowest threads up, tile emission
-    // from the highest down, so both start at once
+    // from the highest down, so both start at once; one CTA scans the tile
+    // counts first
     int emit_per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&emit_per_sm, k_emit, 256, 0)) != cudaSuccess)
         return cuda_fail(e, "occupancy k_emit");
@@ -414,7 +411,8 @@ fss_status fss_project_bin(const fss_params* params, const fss_camera* cams, int
         max_lines = std::max(max_lines, std::max(ctx.cams.c[v].tiles_x, ctx.cams.c[v].tiles_y));
     k_emit<<<emit_blocks, 256, 0, st>>>(ctx.cams, ctx.P, ctx.at<BinRec>(REG_BINREC), ctx.at<uint32_t>(REG_VIS),
                                     ctx.at<uint32_t>(REG_WIDE), ctx.at<uint32_t>(REG_UNB),
-                                    ctx.at<uint32_t>(REG_TILECNT), ctx.at<uint32_t>(REG_LIST), means, scales, quats,
+                                    ctx.at<uint32_t>(REG_TILECNT), ctx.at<int2>(REG_RANGES),
+                                    ctx.at<int32_t>(REG_ORDER), ctx.at<uint32_t>(REG_LIST), means, scales, quats,
                                     ctx.at<float4>(REG_REC), stp, max_lines);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_emit");
     kernel_mark(st);

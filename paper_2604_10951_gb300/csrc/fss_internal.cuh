@@ -42,7 +42,7 @@ struct Cams {
     int32_t n;
     int32_t total_tiles;
     int64_t total_pix;
-    const int32_t* tile_order;  // [total_tiles] tiles by descending pair count (written by k_scan), or null
+    const int32_t* tile_order;  // [total_tiles] tiles by descending pair count (written by k_emit), or null
     CamDev c[FSS_MAX_CAMS];
 };
 
@@ -99,7 +99,8 @@ struct Status {
     uint32_t work_feat;    // work-queue heads of the backward tile kernels
     uint32_t work_geo;
     uint32_t nwide;        // bounded visible items spanning many tiles
-    uint32_t pad3[2];
+    uint32_t scan_ticket;  // k_emit: the first CTA to take it scans the tile counts
+    uint32_t scan_done;    // ... and sets this (release) once the ranges and cursors are written
     uint32_t unb_cnt[FSS_MAX_CAMS];  // unbounded items per view
     uint32_t bounds_site;            // check build: first failed index check (BoundsSite), else 0
     uint32_t pad4;

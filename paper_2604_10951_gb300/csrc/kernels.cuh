@@ -28,15 +28,13 @@ __global__ void k_project(const __grid_constant__ Cams cams, const __grid_consta
                           uint32_t* __restrict__ vis_list, uint32_t* __restrict__ wide_list,
                           uint32_t* __restrict__ unb_list, int32_t* __restrict__ splat_slot,
                           int32_t* __restrict__ slot_surf, Status* __restrict__ st);
-__global__ void k_scan(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
-                       uint32_t* __restrict__ tile_cnt, int2* __restrict__ ranges, int32_t* __restrict__ order,
-                       Status* __restrict__ st);
 __global__ void k_emit(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                        const BinRec* __restrict__ binrec, const uint32_t* __restrict__ vis_list,
                        const uint32_t* __restrict__ wide_list, const uint32_t* __restrict__ unb_list,
-                       uint32_t* __restrict__ cursor, uint32_t* __restrict__ list, const float* __restrict__ means,
-                       const float* __restrict__ scales, const float* __restrict__ quats, float4* __restrict__ rec,
-                       const Status* __restrict__ st, int max_lines);
+                       uint32_t* __restrict__ cursor, int2* __restrict__ ranges, int32_t* __restrict__ order,
+                       uint32_t* __restrict__ list, const float* __restrict__ means, const float* __restrict__ scales,
+                       const float* __restrict__ quats, float4* __restrict__ rec, Status* __restrict__ st,
+                       int max_lines);
 __global__ void k_tile_sort(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                             const float4* __restrict__ rec, const BinRec* __restrict__ binrec,
                             const int2* __restrict__ ranges, uint32_t* __restrict__ list,

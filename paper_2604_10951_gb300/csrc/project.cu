@@ -6,10 +6,11 @@
 //             compact list (unbounded conics to a per-view list instead).
 //             Also counts each item's tiles (AccuTile per-row or per-column
 //             intervals) into per-tile counters.
-// k_scan      per-tile exclusive scan -> tile ranges, total pairs, capacity.
-// k_emit      writes each item into a slot of each of its tiles (slot order
-//             is arbitrary; the per-tile sort restores a total order) and
-//             computes the double-float render records.
+// k_emit      computes the double-float render records; one of its CTAs
+//             scans the per-tile counts (tile ranges, total pairs, capacity,
+//             the heavy-first tile order) while the others build records;
+//             then writes each item into a slot of each of its tiles (slot
+//             order is arbitrary; the per-tile sort restores a total order).
 //
 // Every tile decision is taken in binary32 with the fixed operation order
 // that the FP64 checker's binning mirror also follows, so tile lists compare
@@ -664,10 +665,11 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4) k_project(const __grid_consta
 }
 
 // ---------------------------------------------------------------------------
-// k_scan: one CTA; per-tile totals (bounded pairs + the view's unbounded
-// items) -> exclusive scan -> ranges; tile_cnt becomes the emit cursor.
-// Then the heavy-first tile order: a counting sort of the tiles by pair
-// count, descending, in buckets of 16 pairs (the order within a bucket is
+// Tile scan, run by one CTA of k_emit (any block size, a multiple of 32):
+// per-tile totals (bounded pairs + the view's unbounded items) -> exclusive
+// scan -> ranges; the tile counters become the emit cursors.  Then the
+// heavy-first tile order: a counting sort of the tiles by pair count,
+// descending, in buckets of 16 pairs (the order within a bucket is
 // arbitrary).  The tile kernels take tiles in this order, so that the last
 // tiles to start are light ones: the work per tile varies severalfold, and
 // in index order a heavy tile starting late sets the kernel's end.
@@ -675,17 +677,16 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4) k_project(const __grid_consta
 constexpr int ORDER_BUCKETS = 256;  // 32 lanes x 8
 __device__ __forceinline__ int order_bucket(int2 r) { return min(ORDER_BUCKETS - 1, (r.y - r.x) >> 4); }
 
-__global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
-                                               uint32_t* __restrict__ tile_cnt, int2* __restrict__ ranges,
-                                               int32_t* __restrict__ order, Status* __restrict__ st) {
+__device__ void scan_tiles(const Cams& cams, const RParams& P, uint32_t* __restrict__ tile_cnt,
+                           int2* __restrict__ ranges, Status* __restrict__ st) {
     __shared__ uint32_t warp_tot[32];
     __shared__ uint64_t carry_s;
     if (threadIdx.x == 0) carry_s = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nt = cams.total_tiles;
-    constexpr int ITEMS = 4;
-    for (int base = 0; base < nt; base += 1024 * ITEMS) {
+    constexpr int ITEMS = 8;
+    for (int base = 0; base < nt; base += blockDim.x * ITEMS) {
         uint32_t v[ITEMS];
         uint32_t sum = 0;
 #pragma unroll
@@ -703,7 +704,7 @@ __global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ Cams cams
         if (lane == 31) warp_tot[wid] = incl;
         __syncthreads();
         if (wid == 0) {
-            uint32_t w = warp_tot[lane], wi = w;
+            uint32_t w = lane < nw ? warp_tot[lane] : 0u, wi = w;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
                 const uint32_t y = __shfl_up_sync(0xffffffffu, wi, off);
@@ -725,15 +726,21 @@ __global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ Cams cams
             }
         }
         __syncthreads();
-        if (threadIdx.x == 1023) carry_s = run;
+        if (threadIdx.x == blockDim.x - 1) carry_s = run;
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         st->pairs_needed = (int64_t)carry_s;
-        if (carry_s > (uint64_t)P.pair_cap) st->err |= ERR_CAPACITY;
+        if (carry_s > (uint64_t)P.pair_cap) atomicOr(&st->err, ERR_CAPACITY);
     }
-    // heavy-first order (a frame over capacity has empty ranges: any order)
+}
+
+// heavy-first order of the tiles from their ranges (a frame over capacity
+// has empty ranges: any order)
+__device__ void heavy_first_order(const Cams& cams, const int2* __restrict__ ranges, int32_t* __restrict__ order) {
     __shared__ uint32_t ord[ORDER_BUCKETS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nt = cams.total_tiles;
     for (int b = threadIdx.x; b < ORDER_BUCKETS; b += blockDim.x) ord[b] = 0u;
     __syncthreads();
     for (int t = threadIdx.x; t < nt; t += blockDim.x) atomicAdd(&ord[order_bucket(ranges[t])], 1u);
@@ -760,6 +767,20 @@ __global__ void __launch_bounds__(1024) k_scan(const __grid_constant__ Cams cams
     }
     __syncthreads();
     for (int t = threadIdx.x; t < nt; t += blockDim.x) order[atomicAdd(&ord[order_bucket(ranges[t])], 1u)] = t;
+}
+
+// Rounds of the bounded wait for the scanning CTA (each about 0.1-0.2 us of
+// sleep: about a second in all), after which the waiting CTA raises
+// ERR_TIMEOUT and returns.
+constexpr int SCAN_WAIT = 1 << 23;
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -877,7 +898,12 @@ __device__ __forceinline__ void emit_batch(uint32_t* __restrict__ cursor, uint32
 // k_emit: writes every bounded visible item into one slot of each of its
 // tiles (slot order is arbitrary; the per-tile sort restores a total order)
 // and replaces the render records by their double-float versions.
-//   records:      one quad of lanes per narrow, wide or unbounded item;
+//   scan:         the first CTA to take the ticket scans the per-tile counts
+//                 into ranges and emit cursors and publishes them (release
+//                 store of a flag); it never waits, so the others' bounded
+//                 wait for the flag ends however the CTAs are scheduled;
+//   records:      one quad of lanes per narrow, wide or unbounded item (they
+//                 need no ranges, so they run while the scan does);
 //   narrow items: 32 per warp, their (item, outer line) units spread over
 //                 the lanes; each lane emits its line's tiles;
 //   wide items:   one warp per (item, outer line), lanes over the line's tiles;
@@ -886,14 +912,25 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Cams cams,
                                               const BinRec* __restrict__ binrec, const uint32_t* __restrict__ vis_list,
                                               const uint32_t* __restrict__ wide_list,
                                               const uint32_t* __restrict__ unb_list, uint32_t* __restrict__ cursor,
+                                              int2* __restrict__ ranges, int32_t* __restrict__ order,
                                               uint32_t* __restrict__ list, const float* __restrict__ means,
                                               const float* __restrict__ scales, const float* __restrict__ quats,
-                                              float4* __restrict__ rec, const Status* __restrict__ st, int max_lines) {
+                                              float4* __restrict__ rec, Status* __restrict__ st, int max_lines) {
     __shared__ BinRec s_br[256];
     __shared__ uint32_t s_item[256];
     __shared__ int s_pre[256];
+    __shared__ int s_scanner, s_go;
     if (st->err) return;
-    Status* const stw = const_cast<Status*>(st);  // check build: failed index checks are recorded here
+    Status* const stw = st;
+    if (threadIdx.x == 0) s_scanner = atomicAdd(&st->scan_ticket, 1u) == 0u;
+    __syncthreads();
+    if (s_scanner) {
+        scan_tiles(cams, P, cursor, ranges, st);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) st_release(&st->scan_done, 1u);
+        heavy_first_order(cams, ranges, order);
+    }
     const int lane = threadIdx.x & 31;
     const int wb = threadIdx.x & ~31;
     const WarpLines wl{s_br + wb, s_item + wb, s_pre + wb};
@@ -926,6 +963,18 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Cams cams,
         }
         record_item_quad(cams, P, means, scales, quats, rec, ok ? item : 0u, valid && ok);
     }
+    // the emit cursors: published by the scanning CTA (bounded wait)
+    if (threadIdx.x == 0) {
+        bool done = s_scanner != 0;
+        for (int i = 0; !done && i < SCAN_WAIT; ++i) {
+            done = ld_acquire(&st->scan_done) != 0u;
+            if (!done) __nanosleep(128);
+        }
+        if (!done) atomicOr(&st->err, ERR_TIMEOUT);
+        s_go = done && !(ld_acquire(reinterpret_cast<const uint32_t*>(&st->err)) & ERR_CAPACITY);
+    }
+    __syncthreads();
+    if (!s_go) return;
     // narrow items, 32 per warp from the highest warps down (so that they run
     // beside the records); each lane emits one line's tiles in batches of
     // EMIT_BATCH, whose cursor atomics are in flight together

@@ -10,7 +10,7 @@ from tests.gpu_util import dev
 
 pytestmark = pytest.mark.gpu
 
-N_KERNELS = 3 + 1 + 1 + 4 + 1  # binning, sort, forward, backward (Top-K), feature rows
+N_KERNELS = 2 + 1 + 1 + 4 + 1  # binning (project; emit with the tile scan), sort, forward, backward, rows
 
 
 def _frame():
