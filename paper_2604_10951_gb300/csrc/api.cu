@@ -431,7 +431,7 @@ fss_status fss_sort(const fss_params* params, const fss_camera* cams, int32_t n_
     if (s != FSS_OK) return s;
     if (!workspace) return fail(FSS_ERR_INVALID_ARG, "workspace is NULL");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    k_tile_sort<<<ctx.cams.total_tiles, 256, 0, st>>>(ctx.cams, ctx.P, ctx.at<float4>(REG_REC),
+    k_tile_sort<<<ctx.cams.total_tiles, SORT_THREADS, 0, st>>>(ctx.cams, ctx.P, ctx.at<float4>(REG_REC),
                                                       ctx.at<BinRec>(REG_BINREC), ctx.at<int2>(REG_RANGES),
                                                       ctx.at<uint32_t>(REG_LIST), ctx.at<uint32_t>(REG_UNB),
                                                       ctx.at<uint64_t>(REG_SORTTMP), ctx.at<uint32_t>(REG_MASK),

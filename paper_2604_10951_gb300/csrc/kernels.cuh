@@ -5,7 +5,11 @@
 
 namespace fss {
 
-constexpr int SORT_CAP = 4096;  // longest tile list sorted in shared memory
+// Per-tile depth sort: CTAs of SORT_THREADS threads and lists of up to
+// SORT_CAP keys in shared memory (8 KB), so that eight CTAs fit on an SM and
+// the 1,200 tiles of a 640 x 480 frame sort in one wave
+constexpr int SORT_THREADS = 128;
+constexpr int SORT_CAP = 1024;
 
 // Measurement hook (fss_set_kernel_events): called right after every kernel
 // launch; records the calling thread's next caller-supplied event, if any,

@@ -29,12 +29,29 @@ __device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); 
 __device__ __forceinline__ float fdv(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ float fq(float a) { return __fsqrt_rn(a); }
 
+// frexpf and ldexpf for the chain below, from the binary32 layout: for a
+// normal x > 0, x = m 2^e with m in [1/2, 1) takes the exponent field and
+// the mantissa bits; x 2^k (one rounding, as ldexpf) is a multiply by the
+// exact power of two whenever 2^k is a normal number.  Other cases (zero,
+// subnormal, non-finite, exponents out of that range) call the library.
+__device__ __forceinline__ float frexp32(float x, int* e) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t be = (b >> 23) & 0xffu;
+    if (be == 0u || be == 0xffu || (b >> 31)) return frexpf(x, e);
+    *e = (int)be - 126;
+    return __uint_as_float((b & 0x807fffffu) | 0x3f000000u);
+}
+__device__ __forceinline__ float ldexp32(float x, int k) {
+    if (k < -126 || k > 127) return ldexpf(x, k);
+    return __fmul_rn(x, __uint_as_float((uint32_t)(k + 127) << 23));
+}
+
 // natural logarithm of x > 0 in binary32, the same operation sequence as the
 // checker's binning mirror: x = m 2^e with m in [sqrt(1/2), sqrt(2)),
 // ln m = 2 atanh(s), s = (m - 1)/(m + 1), series to s^9 (|s| <= 0.1716).
 __device__ __forceinline__ float ln32(float x) {
     int e;
-    float m = frexpf(x, &e);
+    float m = frexp32(x, &e);
     if (m < 0.70710677f) { m = fm(m, 2.0f); e = e - 1; }
     const float s = fdv(fs(m, 1.0f), fa(m, 1.0f));
     const float s2 = fm(s, s);
@@ -189,8 +206,8 @@ __device__ __forceinline__ bool accu_line(const BinRec& r, bool rows, int ts, in
     if (r.flags & BR_LOWPASS) disc_strip(r.rd2, Ya, Yb, xc, p0, p1, da, db);
     if (!(r.flags & BR_ELL)) {
         if (da > db) return false;
-        ta = da / ts;
-        tb = db / ts;
+        ta = da >> (__ffs(ts) - 1);
+        tb = db >> (__ffs(ts) - 1);
         return true;
     }
     float ext[2];
@@ -215,8 +232,8 @@ __device__ __forceinline__ bool accu_line(const BinRec& r, bool rows, int ts, in
     int b = hit ? (fh > (float)p1 ? p1 : (int)fh) : 0;
     hull_interval(a, b, da, db);
     if (a > b) return false;
-    ta = a / ts;
-    tb = b / ts;
+    ta = a >> (__ffs(ts) - 1);
+    tb = b >> (__ffs(ts) - 1);
     return true;
 }
 
@@ -520,11 +537,11 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4) k_project(const __grid_consta
             for (int i = 0; i < 9; ++i) mx = fabsf(m[i]) > mx ? fabsf(m[i]) : mx;
             if (!(mx > 0.0f)) break;
             int ex;
-            frexpf(mx, &ex);
+            frexp32(mx, &ex);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) m[i] = ldexpf(m[i], -ex);
-            det = ldexpf(det, -ex);
-            r3.w = ldexpf(1.0f, -ex);
+            for (int i = 0; i < 9; ++i) m[i] = ldexp32(m[i], -ex);
+            det = ldexp32(det, -ex);
+            r3.w = ldexp32(1.0f, -ex);
             r0 = make_float4(m[0], m[1], m[2], xc);
             r1 = make_float4(m[3], m[4], m[5], yc);
             r2 = make_float4(m[6], m[7], m[8], det);
@@ -571,7 +588,8 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4) k_project(const __grid_consta
             br.px0 = (int16_t)px0; br.px1 = (int16_t)px1; br.py0 = (int16_t)py0; br.py1 = (int16_t)py1;
             // S18
             const int ts = P.ts;
-            int tx0 = px0 / ts, tx1 = px1 / ts, ty0 = py0 / ts, ty1 = py1 / ts;
+            const int lts = __ffs(ts) - 1;  // tile sizes are powers of two; pixel indices are >= 0
+            int tx0 = px0 >> lts, tx1 = px1 >> lts, ty0 = py0 >> lts, ty1 = py1 >> lts;
             // S19
             if (P.bin_mode == FSS_BIN_AABB && !(br.flags & BR_UNBOUNDED)) {
                 float k2a = fm(2.0f, ln32(fdv(1.0f, P.alpha_min)));
@@ -591,7 +609,7 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4) k_project(const __grid_consta
                 }
                 ax0 = min(ax0, px0); ax1 = max(ax1, px1);
                 ay0 = min(ay0, py0); ay1 = max(ay1, py1);
-                tx0 = ax0 / ts; tx1 = ax1 / ts; ty0 = ay0 / ts; ty1 = ay1 / ts;
+                tx0 = ax0 >> lts; tx1 = ax1 >> lts; ty0 = ay0 >> lts; ty1 = ay1 >> lts;
             }
             br.tx0 = (int16_t)tx0; br.tx1 = (int16_t)tx1; br.ty0 = (int16_t)ty0; br.ty1 = (int16_t)ty1;
         } while (0);
@@ -601,8 +619,9 @@ __global__ void __launch_bounds__(PROJ_THREADS, 4) k_project(const __grid_consta
             float4* rr = rec + 4 * item;
             rr[0] = r0; rr[1] = r1; rr[2] = r2; rr[3] = r3;
             binrec[item] = br;
-            // one gradient slot per surfel visible in any view (-1 -> -2 claims it)
-            claim = atomicCAS(&splat_slot[s], -1, -2) == -1;
+            // one gradient slot per surfel visible in any view (-1 -> -2 claims it);
+            // with one view every item is a distinct surfel, so no round trip
+            claim = cams.n == 1 || atomicCAS(&splat_slot[s], -1, -2) == -1;
             claim_s = s;
         }
     }
@@ -868,15 +887,15 @@ __device__ void record_item_quad(const Cams& cams, const RParams& P, const float
     // lane 0: det(n2 T') from row 0
     const df det = dadd(dadd(dmul(d[0][0], m[0]), dmul(d[0][1], m[1])), dmul(d[0][2], m[2]));
     int ex = 0;
-    if (mx > 0.0f) frexpf(mx, &ex);
+    if (mx > 0.0f) frexp32(mx, &ex);
     // hit depth det(T') / c2: with M = 2^-ex n2^2 adj(T'), store 2^-ex det(n2 T') / n2
-    const float detr = __shfl_sync(0xffffffffu, ldexpf(fdv(det.hi, n2.hi), -ex), q0);
+    const float detr = __shfl_sync(0xffffffffu, ldexp32(fdv(det.hi, n2.hi), -ex), q0);
     if (!valid || !(mx > 0.0f)) return;  // after the last shuffle: every lane took part
     if (j < 3)
-        rr[j] = make_float4(ldexpf(m[0].hi, -ex), ldexpf(m[1].hi, -ex), ldexpf(m[2].hi, -ex),
+        rr[j] = make_float4(ldexp32(m[0].hi, -ex), ldexp32(m[1].hi, -ex), ldexp32(m[2].hi, -ex),
                             j == 0 ? xc : (j == 1 ? yc : detr));
     // total scale of M relative to adj(T' of the normalised surfel)
-    if (j == 0) rr[3].w = ldexpf(fm(n2.hi, n2.hi), -ex);
+    if (j == 0) rr[3].w = ldexp32(fm(n2.hi, n2.hi), -ex);
 }
 
 constexpr int EMIT_BATCH = 8;

@@ -24,6 +24,11 @@ __device__ __forceinline__ float rcp_approx(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // Ray-splat intersection and opacity of one staged surfel at pixel point
 // (pxf, pyf) (Eq. 2 density, alpha before the clamp).  Returns false when
@@ -188,6 +193,12 @@ __device__ __forceinline__ int2 pixel_of(int tid) {
 // changes no result.  With the low-pass filter the extent also covers the
 // screen disc of the binning record (radius^2 rd2 about the local origin),
 // widened by 0.1 % in radius^2 and 0.05 pixel.
+// The arithmetic is the approximate kind (reciprocal and square root to
+// about 2^-22 relative; the extents move by far less than the margin) and
+// has no branch inside a strip: the IEEE divide and square root each carry a
+// slow-path branch, which kept the strips' chains from overlapping (about
+// 900 cycles per strip where this takes a fraction).  The tangent points do
+// not depend on the strip and are formed once.
 template <bool LP>
 __device__ __forceinline__ uint32_t warp_block_mask(const BinRec* __restrict__ rp, int ts, int tile_x0, int tile_y0) {
     const int WX = ts >> 3;
@@ -207,55 +218,74 @@ __device__ __forceinline__ uint32_t warp_block_mask(const BinRec* __restrict__ r
     const float A = q0.x, B = q0.y, Cc = q0.z, D = q0.w, E = q1.x, F = q1.y;
     const float X0 = q1.z, hx = q2.x, xc = q2.z, yc = q2.w;
     const float margin = 0.05f + 1e-3f * hx;
+    const float iA = rcp_approx(A), iC = rcp_approx(Cc);
+    const float Xs[2] = {X0 - hx, X0 + hx};
+    const float Yt[2] = {-(B * Xs[0] + E) * iC, -(B * Xs[1] + E) * iC};
+    // pixel indices held as floats (exact), so a strip needs no conversion
+    const float fx0 = (float)x0, fx1 = (float)x1, fy0 = (float)y0, fy1 = (float)y1, ftx = (float)tile_x0;
+    const int by0 = (y0 - tile_y0) >> 2, by1 = (y1 - tile_y0) >> 2;
+    const float fs0 = (float)(tile_y0 + 4 * by0);  // first row of strip by0
     uint32_t m = 0u;
-    for (int by = (y0 - tile_y0) >> 2; by <= (y1 - tile_y0) >> 2; ++by) {
-        const int ra = max(y0, tile_y0 + 4 * by), rb = min(y1, tile_y0 + 4 * by + 3);
-        int ca = x0, cb = x1;
-        if (!unbounded) {
-            const float Ya = ((float)ra + 0.5f) - yc, Yb = ((float)rb + 0.5f) - yc;
-            // the low-pass disc's extent on the strip, widened like the ellipse's
-            int da = 1, db = 0;
-            const float Yn = Ya > 0.0f ? Ya : (Yb < 0.0f ? Yb : 0.0f);
-            if (LP && Yn * Yn <= rd2 * 1.001f) {
-                const float hw = sqrtf(fmaxf(rd2 * 1.001f - Yn * Yn, 0.0f)) + 0.05f;
-                const float lo = ceilf(xc - hw - 0.5f), hi = floorf(xc + hw - 0.5f);
-                da = lo < (float)x0 ? x0 : (lo > (float)x1 ? x1 + 1 : (int)lo);
-                db = hi > (float)x1 ? x1 : (hi < (float)x0 ? x0 - 1 : (int)hi);
-            }
-            if (!ell) {
-                if (da > db) continue;
-                ca = da;
-                cb = db;
-            }
-            float ext[2];
+    // strips of 4 pixel rows, four at a time (each side's tangent and root
+    // candidates are both formed and one is selected)
+    for (int g = 0; g <= by1 - by0; g += 4) {
+        const float fg = fs0 + (float)(4 * g);
 #pragma unroll
-            for (int side = 0; side < 2; ++side) {
-                const float Xs = side == 0 ? X0 - hx : X0 + hx;
-                const float Yt = -(B * Xs + E) / Cc;
-                if (Yt >= Ya && Yt <= Yb) {
-                    ext[side] = Xs;
-                } else {
-                    const float Y = Yt < Ya ? Ya : Yb;
+        for (int k = 0; k < 4; ++k) {
+            const int by = by0 + g + k;
+            const float fr = fg + 4.0f * k;
+            const float ra = fmaxf(fy0, fr), rb = fminf(fy1, fr + 3.0f);
+            float ca = fx0, cb = fx1;
+            bool keep = by <= by1;
+            if (!unbounded) {
+                const float Ya = (ra + 0.5f) - yc, Yb = (rb + 0.5f) - yc;
+                // the low-pass disc's extent on the strip, widened like the ellipse's
+                float da = 1.0f, db = 0.0f;
+                if (LP) {
+                    const float Yn = Ya > 0.0f ? Ya : (Yb < 0.0f ? Yb : 0.0f);
+                    const bool in = Yn * Yn <= rd2 * 1.001f;
+                    const float hw = sqrt_approx(fmaxf(rd2 * 1.001f - Yn * Yn, 0.0f)) + 0.05f;
+                    const float lo = ceilf(xc - hw - 0.5f), hi = floorf(xc + hw - 0.5f);
+                    da = in ? (lo < fx0 ? fx0 : (lo > fx1 ? fx1 + 1.0f : lo)) : 1.0f;
+                    db = in ? (hi > fx1 ? fx1 : (hi < fx0 ? fx0 - 1.0f : hi)) : 0.0f;
+                    if (!ell) {
+                        keep = keep && da <= db;
+                        ca = da;
+                        cb = db;
+                    }
+                }
+                float ext[2];
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    const float Y = Yt[side] < Ya ? Ya : Yb;
                     const float bb = B * Y + D;
                     const float cc = (Cc * Y + 2.0f * E) * Y + F;
-                    const float sq = sqrtf(fmaxf(bb * bb - A * cc, 0.0f));
-                    ext[side] = (side == 0 ? -bb - sq : -bb + sq) / A;
+                    const float sq = sqrt_approx(fmaxf(bb * bb - A * cc, 0.0f));
+                    const float root = (side == 0 ? -bb - sq : -bb + sq) * iA;
+                    ext[side] = Yt[side] >= Ya && Yt[side] <= Yb ? Xs[side] : root;
                 }
-            }
-            if (ell) {
-                // comparisons are false for NaN: a degenerate extent restricts nothing
-                const float lo = ceilf(ext[0] + xc - 0.5f - margin), hi = floorf(ext[1] + xc - 0.5f + margin);
-                if (lo > (float)ca) ca = lo > (float)cb ? cb + 1 : (int)lo;
-                if (hi < (float)cb) cb = hi < (float)ca ? ca - 1 : (int)hi;
-                if (da <= db) {
-                    if (ca > cb) { ca = da; cb = db; }
-                    else { ca = min(ca, da); cb = max(cb, db); }
+                if (ell) {
+                    // comparisons are false for NaN: a degenerate extent restricts nothing
+                    const float lo = ceilf(ext[0] + xc - 0.5f - margin), hi = floorf(ext[1] + xc - 0.5f + margin);
+                    ca = lo > ca ? (lo > cb ? cb + 1.0f : lo) : ca;
+                    cb = hi < cb ? (hi < ca ? ca - 1.0f : hi) : cb;
+                    if (da <= db) {
+                        const bool empty = ca > cb;
+                        ca = empty ? da : fminf(ca, da);
+                        cb = empty ? db : fmaxf(cb, db);
+                    }
                 }
+                keep = keep && ca <= cb;
             }
-            if (ca > cb) continue;
+            // the 8-pixel block columns that [ca, cb] meets
+            uint32_t bits = 0u;
+#pragma unroll
+            for (int bx = 0; bx < 4; ++bx) {
+                const float c0 = ftx + 8.0f * (float)bx;
+                bits |= (bx < WX && ca <= c0 + 7.0f && cb >= c0) ? (1u << bx) : 0u;
+            }
+            if (keep) m |= bits << (by * WX);
         }
-        const int bx0 = (ca - tile_x0) >> 3, bx1 = (cb - tile_x0) >> 3;
-        m |= ((2u << bx1) - (1u << bx0)) << (by * WX);
     }
     return m;
 }

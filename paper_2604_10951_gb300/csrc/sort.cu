@@ -7,8 +7,9 @@
 //   (binary32 bits of the item's camera depth) << 32 | item index,
 // which is unique, so the order is total and deterministic.  Depths are
 // positive, so their bit patterns order like the numbers.
-//   - up to blockDim.x keys: rank sort (each thread counts the smaller keys);
-//   - up to SORT_CAP keys: bitonic sort in shared memory;
+//   - up to SORT_CAP keys: 32-key chunks sorted by one warp each in
+//     registers, then merged by rank (place in the chunk plus a binary
+//     search in every other chunk);
 //   - longer lists: stable LSD radix sort (8-bit digits) by the same CTA
 //     in a global scratch range of the same offsets.
 // With the sorted item, each pair gets the mask of the tile's warps (8 x 4
@@ -27,19 +28,20 @@ __device__ __forceinline__ uint64_t make_key(const float4* __restrict__ rec, uin
     return ((uint64_t)__float_as_uint(z) << 32) | item;
 }
 
-// stable radix sort of keys[0, n) by one CTA of 256 threads; result in keys
+// stable radix sort of keys[0, n) by one CTA (a multiple of 32 threads, at
+// most 256); result in keys
 __device__ void block_radix_sort_global(uint64_t* keys, uint64_t* tmp, int n) {
     __shared__ uint32_t hist[256];
     __shared__ uint32_t offs[256];
     __shared__ int skip;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nt = blockDim.x, nw = nt >> 5;
     uint64_t* src = keys;
     uint64_t* dst = tmp;
     for (int pass = 0; pass < 8; ++pass) {
         const int shift = pass * 8;
-        hist[tid] = 0;
+        for (int d = tid; d < 256; d += nt) hist[d] = 0;
         __syncthreads();
-        for (int i = tid; i < n; i += 256) atomicAdd(&hist[(src[i] >> shift) & 255u], 1u);
+        for (int i = tid; i < n; i += nt) atomicAdd(&hist[(src[i] >> shift) & 255u], 1u);
         __syncthreads();
         if (tid == 0) {
             uint32_t run = 0;
@@ -52,7 +54,7 @@ __device__ void block_radix_sort_global(uint64_t* keys, uint64_t* tmp, int n) {
         }
         __syncthreads();
         if (skip) continue;  // every key has the same digit: order unchanged
-        for (int base = 0; base < n; base += 256) {
+        for (int base = 0; base < n; base += nt) {
             const int i = base + tid;
             const bool ok = i < n;
             const uint64_t k = ok ? src[i] : 0ull;
@@ -60,7 +62,7 @@ __device__ void block_radix_sort_global(uint64_t* keys, uint64_t* tmp, int n) {
             const unsigned peers = __match_any_sync(0xffffffffu, d);
             const int rank = __popc(peers & ((1u << lane) - 1u));
             const int leader = __ffs(peers) - 1;
-            for (int w = 0; w < 8; ++w) {  // warps in order keep the sort stable
+            for (int w = 0; w < nw; ++w) {  // warps in order keep the sort stable
                 if (wid == w && ok) {
                     dst[offs[d] + rank] = k;
                 }
@@ -73,19 +75,21 @@ __device__ void block_radix_sort_global(uint64_t* keys, uint64_t* tmp, int n) {
         uint64_t* t = src; src = dst; dst = t;
     }
     if (src != keys)
-        for (int i = tid; i < n; i += 256) keys[i] = src[i];
+        for (int i = tid; i < n; i += nt) keys[i] = src[i];
     __syncthreads();
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) k_tile_sort(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
+__global__ void __launch_bounds__(SORT_THREADS, 8) k_tile_sort(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                                                    const float4* __restrict__ rec, const BinRec* __restrict__ binrec,
                                                    const int2* __restrict__ ranges, uint32_t* __restrict__ list,
                                                    const uint32_t* __restrict__ unb_list,
                                                    uint64_t* __restrict__ scratch, uint32_t* __restrict__ masks,
                                                    const Status* __restrict__ st) {
-    __shared__ uint64_t sk[SORT_CAP];
+    __shared__ __align__(16) uint64_t sk[SORT_CAP];
+    __shared__ uint32_t smask[SORT_CAP];
+    __shared__ uint16_t spos[SORT_CAP];
     if (st->err) return;
     Status* const stw = const_cast<Status*>(st);  // check build: failed index checks are recorded here
     const int t = blockIdx.x;  // index order: measured faster here than the heavy-first order
@@ -106,50 +110,62 @@ __global__ void __launch_bounds__(256) k_tile_sort(const __grid_constant__ Cams 
         const uint32_t it = i < nb ? list[rg.x + i] : ul[i - nb];
         return in_bounds(stw, SITE_ITEM, it, P.n_items) ? it : 0u;
     };
-    if (n <= (int)blockDim.x) {
-        // short list: rank of each key = number of smaller keys (keys are
-        // unique, so the ranks are a permutation); one barrier instead of a
-        // network of them
-        uint64_t key = ~0ull;
-        if (tid < n) key = make_key(rec, item_at(tid));
-        sk[tid] = key;
-        __syncthreads();
-        if (tid < n) {
-            int rank = 0;
-            for (int j = 0; j < n; ++j) rank += sk[j] < key ? 1 : 0;
-            const uint32_t item = (uint32_t)key;
-            list[rg.x + rank] = item;
-            masks[rg.x + rank] = (P.lowpass ? warp_block_mask<true>(binrec + item, P.ts, tx0, ty0)
-                                           : warp_block_mask<false>(binrec + item, P.ts, tx0, ty0));
-        }
-        return;
-    }
     if (n <= SORT_CAP) {
-        int m = 1;
-        while (m < n) m <<= 1;
-        for (int i = tid; i < m; i += blockDim.x) {
+        // Lists in shared memory, in 32-key chunks (padding keys ~0 are larger
+        // than every key: depth bits < 0x7f800000):
+        //  A. each pair's key and warp mask (the mask does not depend on the
+        //     order, so it is formed here, beside the key's gather);
+        //  B. each warp sorts its chunks in registers (bitonic network over
+        //     the lanes), carrying each key's position in the list;
+        //  C. a key's rank is its place in its chunk plus, per other chunk,
+        //     the number of smaller keys there (a 32-way binary search); the
+        //     keys are unique, so the ranks are a permutation.
+        const int nch = (n + 31) >> 5, lane = tid & 31, w = tid >> 5;
+#pragma unroll 2
+        for (int i = tid; i < (nch << 5); i += SORT_THREADS) {
             uint64_t k = ~0ull;
-            if (i < n) k = make_key(rec, item_at(i));
+            if (i < n) {
+                const uint32_t item = item_at(i);
+                k = make_key(rec, item);
+                smask[i] = P.lowpass ? warp_block_mask<true>(binrec + item, P.ts, tx0, ty0)
+                                     : warp_block_mask<false>(binrec + item, P.ts, tx0, ty0);
+            }
             sk[i] = k;
         }
         __syncthreads();
-        for (int k = 2; k <= m; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = tid; i < (m >> 1); i += blockDim.x) {
-                    const int l = ((i & ~(j - 1)) << 1) | (i & (j - 1));  // j is a power of two
-                    const int r = l + j;
-                    const bool up = (l & k) == 0;
-                    const uint64_t a = sk[l], b = sk[r];
-                    if ((a > b) == up) { sk[l] = b; sk[r] = a; }
+        for (int c = w; c < nch; c += SORT_THREADS / 32) {
+            uint64_t k = sk[(c << 5) + lane];
+            int pos = (c << 5) + lane;
+#pragma unroll
+            for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+                for (int j = kk >> 1; j > 0; j >>= 1) {
+                    const uint64_t ok = __shfl_xor_sync(0xffffffffu, k, j);
+                    const int op = __shfl_xor_sync(0xffffffffu, pos, j);
+                    const bool keep_min = ((lane & kk) == 0) == ((lane & j) == 0);  // ascending runs
+                    const bool take = keep_min ? ok < k : ok > k;
+                    k = take ? ok : k;
+                    pos = take ? op : pos;
                 }
-                __syncthreads();
             }
+            sk[(c << 5) + lane] = k;
+            spos[(c << 5) + lane] = (uint16_t)pos;
         }
-        for (int i = tid; i < n; i += blockDim.x) {
-            const uint32_t item = (uint32_t)sk[i];
-            list[rg.x + i] = item;
-            masks[rg.x + i] = (P.lowpass ? warp_block_mask<true>(binrec + item, P.ts, tx0, ty0)
-                                           : warp_block_mask<false>(binrec + item, P.ts, tx0, ty0));
+        __syncthreads();
+        for (int q = tid; q < n; q += SORT_THREADS) {
+            const uint64_t k = sk[q];
+            const int c = q >> 5;
+            int rank = q & 31;
+            for (int c2 = 0; c2 < nch; ++c2) {
+                if (c2 == c) continue;
+                const uint64_t* a = sk + (c2 << 5);
+                int cnt = a[31] < k ? 32 : 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) cnt += (cnt < 32 && a[cnt + step - 1] < k) ? step : 0;
+                rank += cnt;
+            }
+            list[rg.x + rank] = (uint32_t)k;
+            masks[rg.x + rank] = smask[spos[q]];
         }
         return;
     }
