@@ -433,6 +433,7 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
     float* s_gf = s_f + (FULL ? NB * P.C : 0);  // FULL: [NB][C] feature gradients
     __shared__ int s_max;
     __shared__ int s_tile;
+    __shared__ uint32_t s_bits[NT / 32][BB / 32];  // per warp: the staged surfels its block meets
 
     if (a.st->err) return;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -539,9 +540,19 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
             }
         }
         __syncthreads();
-        for (int j = cnt - 1; j >= 0; --j) {
+        // this warp's staged surfels as bit words (the footprint misses the
+        // other ones): the loop below visits set bits only, last first
+#pragma unroll
+        for (int i = 0; i < NB / 32; ++i) {
+            const int j = 32 * i + lane;
+            const uint32_t word = __ballot_sync(0xffffffffu, j < cnt && (s_wm[j] & wbit));
+            if (lane == i) s_bits[tid >> 5][i] = word;
+        }
+        __syncwarp();
+        for (int i = ((cnt + 31) >> 5) - 1; i >= 0; --i) {
+        for (uint32_t bits = s_bits[tid >> 5][i]; bits != 0u; bits ^= 0x80000000u >> __clz(bits)) {
+            const int j = 32 * i + 31 - __clz(bits);
             const int pos = b_start + j;
-            if (!(s_wm[j] & wbit)) continue;  // warp-uniform: the footprint misses this warp's block
             float g[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) g[k] = 0.0f;
@@ -615,6 +626,7 @@ __global__ void __launch_bounds__(TS * TS) k_bwd_geo(const __grid_constant__ Cam
                     }
                 }
             }
+        }
         }
         __syncthreads();
         // flush one gradient row per staged surfel

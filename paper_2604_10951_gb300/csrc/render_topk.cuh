@@ -76,8 +76,9 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : (KCAP 
     unsigned long long* s_lab =  // AUX: per-pixel argmax keys
         reinterpret_cast<unsigned long long*>(smem + (((size_t)PC * KCAP * 8 + PC * 4 + 7) & ~(size_t)7));
     __shared__ int s_tile;
+    __shared__ uint32_t s_bits[NT / 32][BATCH / 32];  // per warp: the staged surfels its block meets
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t wbit = 1u << (tid >> 5);
     if (a.st->err) return;
     const int K = P.K;
@@ -138,9 +139,19 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : (KCAP 
                 }
             }
             __syncthreads();
+            // this warp's staged surfels as bit words (the footprint misses the
+            // other ones): the loop below visits set bits only
+#pragma unroll
+            for (int i = 0; i < BATCH / 32; ++i) {
+                const int j = 32 * i + lane;
+                const uint32_t word = __ballot_sync(0xffffffffu, j < cnt && (s_wm[j] & wbit));
+                if (lane == i) s_bits[tid >> 5][i] = word;
+            }
+            __syncwarp();
             if (done) continue;
-            for (int j = 0; j < cnt; ++j) {
-                if (!(s_wm[j] & wbit)) continue;  // warp-uniform: the footprint misses this warp's block
+            for (int i = 0; i < (cnt + 31) >> 5 && !done; ++i) {
+            for (uint32_t bits = s_bits[tid >> 5][i]; bits != 0u; bits &= bits - 1u) {
+                const int j = 32 * i + __ffs(bits) - 1;
                 ++n_eval;
                 Hit h;
                 const float4 oc = s_oc[j];
@@ -194,6 +205,7 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : (KCAP 
                     done = true;
                     break;
                 }
+            }
             }
         }
 
