@@ -87,6 +87,12 @@ struct FeatVec;
 template <>
 struct FeatVec<float> {
     static constexpr int E = 4;  // channels per 16-byte load
+    using Raw = float4;          // one 16-byte chunk as loaded
+    __device__ static __forceinline__ Raw raw(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+    __device__ static __forceinline__ void unpack2(const Raw& r, float2* o) {
+        o[0] = make_float2(r.x, r.y);
+        o[1] = make_float2(r.z, r.w);
+    }
     __device__ static __forceinline__ void load(const float* p, float* o) {
         const float4 v = __ldg(reinterpret_cast<const float4*>(p));
         o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
@@ -102,6 +108,13 @@ struct FeatVec<float> {
 template <>
 struct FeatVec<__nv_bfloat16> {
     static constexpr int E = 8;
+    using Raw = uint4;
+    __device__ static __forceinline__ Raw raw(const __nv_bfloat16* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
+    __device__ static __forceinline__ void unpack2(const Raw& r, float2* o) {
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o[k] = make_float2(__uint_as_float(w[k] << 16), __uint_as_float(w[k] & 0xffff0000u));
+    }
     __device__ static __forceinline__ void load(const __nv_bfloat16* p, float* o) {
         const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};

@@ -133,6 +133,11 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : (KCAP 
                 const int64_t sp = (int64_t)item - vbase;
                 s_oc[j] = make_float4(r[3].x, rgbv[3 * sp], rgbv[3 * sp + 1], rgbv[3 * sp + 2]);
                 s_wm[j] = a.masks[rg.x + b0 + j];
+                if (a.out_feat) {  // the feature row, into L2 while phase 1 runs (phase 2 gathers the selected ones)
+                    const char* row = reinterpret_cast<const char*>(feats + (size_t)sp * P.C);
+                    for (int off = 0; off < P.C * (int)sizeof(FT); off += 128)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(row + off));
+                }
                 if (AUX) {  // facing normal, and the centre depth for the low-pass screen term
                     const float4 nf = facing_normal(r[2], r[0].w, r[1].w, cam);
                     s_nrm[j] = make_float4(nf.x, nf.y, nf.z, r[3].y);
@@ -289,18 +294,27 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : (KCAP 
                     const int2 lq = pixel_of<TS>(p);  // pixel of the thread that selected row q
                     const int qx = tx * TS + lq.x, qy = ty * TS + lq.y;
                     if (qx >= cam.W || qy >= cam.H) continue;
-                    float acc[E];
+                    // the selected rows' chunks, weighted with packed FP32 pairs (lane for
+                    // lane fmaf) in the selection's front-to-back order
+                    float2 acc2[E / 2];
 #pragma unroll
-                    for (int e = 0; e < E; ++e) acc[e] = 0.0f;
+                    for (int e = 0; e < E / 2; ++e) acc2[e] = make_float2(0.0f, 0.0f);
                     const int c = s_n[q];
                     for (int k = 0; k < c; ++k) {
                         const int id = s_id[q * KCAP + k];
                         const float w = s_w[q * KCAP + k];
                         if (!in_bounds(a.st, SITE_FEAT_ROW, id, P.N)) continue;
-                        float f[E];
-                        FeatVec<FT>::load(feats + (size_t)id * P.C + vv * E, f);
+                        float2 f2[E / 2];
+                        FeatVec<FT>::unpack2(FeatVec<FT>::raw(feats + (size_t)id * P.C + vv * E), f2);
+                        const float2 w2 = make_float2(w, w);
 #pragma unroll
-                        for (int e = 0; e < E; ++e) acc[e] = fmaf(w, f[e], acc[e]);
+                        for (int e = 0; e < E / 2; ++e) acc2[e] = __ffma2_rn(w2, f2[e], acc2[e]);
+                    }
+                    float acc[E];
+#pragma unroll
+                    for (int e = 0; e < E / 2; ++e) {
+                        acc[2 * e] = acc2[e].x;
+                        acc[2 * e + 1] = acc2[e].y;
                     }
                     const int64_t qpix = cam.pix_off + (int64_t)qy * cam.W + qx;
                     if (a.out_feat) store_vec<E>(a.out_feat, qpix * P.C + vv * E, acc, P.out_dtype);
