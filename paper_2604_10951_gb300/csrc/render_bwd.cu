@@ -76,7 +76,7 @@ __device__ __forceinline__ void reduce_scatter(float* v) {
 //     16 bytes); each thread keeps EPT entries (list position, weight) in
 //     registers;
 //  2. the selected list positions get dense slot numbers (mark + scan) and
-//     a counting sort groups the entries by slot (warp-aggregated atomics)
+//     a counting sort groups the entries by slot (shared-memory atomics)
 //     into 8-byte records (slot, dL/dF row offset; weight);
 //  3. the selected surfels' feature rows are staged in shared memory in one
 //     parallel pass (over the counting-sort tables, which are dead by then);
@@ -268,11 +268,8 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                 int eslot[EPT];
 #pragma unroll
                 for (int i = 0; i < EPT; ++i) {
-                    const bool in = epos[i] >= 0;
-                    eslot[i] = in ? s_tab[epos[i]] : -1;
-                    // lanes with the same slot add their count once
-                    const unsigned peers = __match_any_sync(0xffffffffu, in ? eslot[i] : -1 - lane);
-                    if (in && lane == __ffs(peers) - 1) atomicAdd(&s_off[eslot[i]], __popc(peers));
+                    eslot[i] = epos[i] >= 0 ? s_tab[epos[i]] : -1;
+                    if (eslot[i] >= 0) atomicAdd(&s_off[eslot[i]], 1);
                 }
                 __syncthreads();
                 const int nsel = block_exscan(s_off, U, s_red);
@@ -281,14 +278,8 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                 __syncthreads();
 #pragma unroll
                 for (int i = 0; i < EPT; ++i) {
-                    const bool in = eslot[i] >= 0;
-                    const unsigned peers = __match_any_sync(0xffffffffu, in ? eslot[i] : -1 - lane);
-                    const int leader = __ffs(peers) - 1;
-                    int base = 0;
-                    if (in && lane == leader) base = atomicAdd(&s_cur[eslot[i]], __popc(peers));
-                    base = __shfl_sync(0xffffffffu, base, leader);
-                    if (in) {
-                        const int at = base + __popc(peers & ((1u << lane) - 1u));
+                    if (eslot[i] >= 0) {
+                        const int at = atomicAdd(&s_cur[eslot[i]], 1);
                         const int e = tid + i * BWD_FEAT_THREADS;
                         s_rec[at] = make_int2((eslot[i] << REC_ROW_BITS) | (entry_q(i, e) * row16), __float_as_int(ew[i]));
                         s_e[at] = (unsigned short)e;
