@@ -20,17 +20,37 @@ __global__ void __launch_bounds__(256) k_loss(int64_t n_pix, int C, const OT* __
     const float sf = 2.0f * wf / (float)(n_pix * C), sc = wc / (float)nc;
     float acc = 0.0f;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += stride) {
-        float a[E], b[E], g[E];
-        FeatVec<OT>::load(F + i * E, a);
-        FeatVec<OT>::load(Ft + i * E, b);
+    // U grid-stride steps at a time, their loads all issued first (enough
+    // bytes in flight for the copy rate); the sum keeps the steps' order
+    constexpr int U = 4;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < nf; i0 += U * stride) {
+        typename FeatVec<OT>::Raw ra[U], rb[U];
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const float d = a[e] - b[e];
-            acc = fmaf(d, d, acc);
-            g[e] = sf * d;
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < nf) {
+                ra[u] = FeatVec<OT>::raw(F + i * E);
+                rb[u] = FeatVec<OT>::raw(Ft + i * E);
+            }
         }
-        store_vec<E>(dF, i * E, g, sizeof(OT) == 4 ? FSS_F32 : FSS_BF16);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i >= nf) break;
+            float2 a2[E / 2], b2[E / 2];
+            FeatVec<OT>::unpack2(ra[u], a2);
+            FeatVec<OT>::unpack2(rb[u], b2);
+            float g[E];
+#pragma unroll
+            for (int e = 0; e < E / 2; ++e) {
+                const float d0 = a2[e].x - b2[e].x, d1 = a2[e].y - b2[e].y;
+                acc = fmaf(d0, d0, acc);
+                acc = fmaf(d1, d1, acc);
+                g[2 * e] = sf * d0;
+                g[2 * e + 1] = sf * d1;
+            }
+            store_vec<E>(dF, i * E, g, sizeof(OT) == 4 ? FSS_F32 : FSS_BF16);
+        }
     }
     float accf = acc * wf / (float)(n_pix * C), accc = 0.0f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += stride) {
