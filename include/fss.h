@@ -156,7 +156,10 @@ fss_status fss_saved_size(const fss_params *params, const fss_camera *cams, int3
  * pair_capacity pairs are needed, records FSS_ERR_CAPACITY and the needed
  * count (see fss_read_status); the following calls then do nothing.
  * Inputs are device pointers (layout above); culled surfels (camera depth
- * <= near, o < alpha_min, seen edge-on) produce no pairs.
+ * <= near, o < alpha_min, seen edge-on) produce no pairs.  One CTA of the
+ * emission kernel scans the per-tile counts while the others build render
+ * records; their wait for its result is bounded (FSS_ERR_TIMEOUT, see
+ * fss_test_hold_scan).
  */
 fss_status fss_project_bin(const fss_params *params, const fss_camera *cams, int32_t n_cams, int64_t N,
                            const float *means, const float *scales, const float *quats, const float *opac,
@@ -360,12 +363,26 @@ fss_status fss_forward_static(const fss_params *params, const fss_camera *cams, 
  * that they also become nodes of a captured CUDA graph.  The elapsed time
  * between consecutive events is then one kernel's duration.  n_events = 0
  * switches the hook off.  The array must stay valid while the hook is on.
- * Kernels per call: fss_project_bin 3 (project, scan, emit), fss_sort 1,
+ * Kernels per call: fss_project_bin 2 (project; emit, whose first CTA scans
+ * the tile counts), fss_sort 1,
  * fss_render_forward 1, fss_loss_l2_l1 1, fss_render_backward 4 for Top-K
  * (clear, feature gradients, geometry replay, projection) or 3 for K = 0,
  * plus 1 when g_feat is given (feature rows).
  */
 fss_status fss_set_kernel_events(void *const *events, int32_t n_events);
+
+/*
+ * Failure-detection test hook (the paper has no counterpart).  In
+ * fss_project_bin one CTA of the emission kernel scans the per-tile counts
+ * and publishes ranges and emission cursors with a flag; the other CTAs
+ * wait for the flag with a bounded wait (about a second of sleeping
+ * polls), after which they record FSS_ERR_TIMEOUT (see fss_read_status) and
+ * return without emitting tiles.  With hold != 0 the scanning CTA does not
+ * set the flag, so that the wait runs out; hold = 0 (the default) restores
+ * normal operation.  The setting is per device and process and takes effect
+ * for kernels launched after the call (which synchronises with the device).
+ */
+fss_status fss_test_hold_scan(int32_t hold);
 
 /* Message of the last error returned to the calling thread ("" if none). */
 const char *fss_last_error(void);
@@ -380,7 +397,8 @@ const char *fss_last_error(void);
  *   boxes, flags); 3 tile count per item (uint32); 4 tile ranges
  *   (int32 [tiles, 2]); 5 tile lists (uint32 item ids, sorted by fss_sort);
  *   6 counters (uint64 [8], inside the status block: evaluations,
- *   contributions); 7 per-tile pair counts, then emission cursors (uint32);
+ *   contributions); 7 per-tile pair counts, then emission cursors (uint32,
+ *   one per 32-byte sector);
  *   8 sort scratch (2 x uint64 per pair); 9 geometric gradient rows
  *   (float [views, N, 16]); 10 feature gradient accumulators (float [N, C]);
  *   11 per-(pixel, k) dot products (float [pixels, K]); 12 visible item

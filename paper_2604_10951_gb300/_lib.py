@@ -38,7 +38,7 @@ N_REGIONS = 21
 EXPORTS = ["fss_default_params", "fss_workspace_size", "fss_saved_size", "fss_project_bin", "fss_sort",
            "fss_render_forward", "fss_render_backward", "fss_read_status", "fss_last_error",
            "fss_workspace_region", "fss_loss_l2_l1", "fss_forward_static", "fss_set_kernel_events",
-           "fss_render_forward_aux", "fss_query_labels"]
+           "fss_render_forward_aux", "fss_query_labels", "fss_test_hold_scan"]
 FSS_STATIC_SCRATCH_BYTES = 64 << 20
 
 
@@ -104,6 +104,7 @@ def lib():
                 "fss_forward_static": [pp, pc, i32, i64, i64, P, P, P, P, P, P, P, P, P, P, P,
                                        C.POINTER(C.c_int64), P],
                 "fss_set_kernel_events": [C.POINTER(C.c_void_p), i32],
+                "fss_test_hold_scan": [i32],
                 "fss_render_forward_aux": [pp, pc, i32, i64, P, i64, P, P, P, P, P, P, P,
                                            C.POINTER(fss_aux_outputs), P],
                 "fss_query_labels": [i64, i32, i32, P, P, P, P, P, P, i32, P, P],
@@ -206,6 +207,11 @@ def fss_forward_static(params, cams, n_cams, N, pair_capacity, means, scales, qu
 
 
 _events_keepalive = None
+
+
+def fss_test_hold_scan(hold: bool):
+    """Failure-detection test hook: the binning's tile scan withholds its result (see include/fss.h)."""
+    check(lib().fss_test_hold_scan(1 if hold else 0))
 
 
 def fss_set_kernel_events(events):

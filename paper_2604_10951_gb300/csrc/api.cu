@@ -627,6 +627,11 @@ fss_status fss_query_labels(int64_t N, int32_t n_queries, int32_t dim, const voi
 
 const char* fss_last_error(void) { return g_err.c_str(); }
 
+fss_status fss_test_hold_scan(int32_t hold) {
+    const cudaError_t e = set_hold_scan(hold != 0);
+    return e == cudaSuccess ? FSS_OK : cuda_fail(e, "fss_test_hold_scan");
+}
+
 fss_status fss_set_kernel_events(void* const* events, int32_t n_events) {
     if (n_events < 0 || (n_events > 0 && !events)) return fail(FSS_ERR_INVALID_ARG, "events is NULL or n_events < 0");
     for (int32_t k = 0; k < n_events; ++k)

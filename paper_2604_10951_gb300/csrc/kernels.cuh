@@ -32,6 +32,7 @@ __global__ void k_project(const __grid_constant__ Cams cams, const __grid_consta
                           uint32_t* __restrict__ vis_list, uint32_t* __restrict__ wide_list,
                           uint32_t* __restrict__ unb_list, int32_t* __restrict__ splat_slot,
                           int32_t* __restrict__ slot_surf, Status* __restrict__ st);
+cudaError_t set_hold_scan(int hold);  // fss_test_hold_scan
 __global__ void k_emit(const __grid_constant__ Cams cams, const __grid_constant__ RParams P,
                        const BinRec* __restrict__ binrec, const uint32_t* __restrict__ vis_list,
                        const uint32_t* __restrict__ wide_list, const uint32_t* __restrict__ unb_list,

@@ -788,6 +788,12 @@ __device__ void heavy_first_order(const Cams& cams, const int2* __restrict__ ran
     for (int t = threadIdx.x; t < nt; t += blockDim.x) order[atomicAdd(&ord[order_bucket(ranges[t])], 1u)] = t;
 }
 
+// failure-detection test hook (fss_test_hold_scan): when set, the scanning
+// CTA keeps its result to itself, so the other CTAs' bounded wait runs out
+__device__ int g_hold_scan = 0;
+
+cudaError_t set_hold_scan(int hold) { return cudaMemcpyToSymbol(g_hold_scan, &hold, sizeof(int)); }
+
 // Rounds of the bounded wait for the scanning CTA (each about 0.1-0.2 us of
 // sleep: about a second in all), after which the waiting CTA raises
 // ERR_TIMEOUT and returns.
@@ -947,7 +953,7 @@ __global__ void __launch_bounds__(256) k_emit(const __grid_constant__ Cams cams,
         scan_tiles(cams, P, cursor, ranges, st);
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) st_release(&st->scan_done, 1u);
+        if (threadIdx.x == 0 && !g_hold_scan) st_release(&st->scan_done, 1u);
         heavy_first_order(cams, ranges, order);
     }
     const int lane = threadIdx.x & 31;

@@ -228,8 +228,9 @@ def test_tile_order_is_heavy_first_permutation():
 def _dense_tile_scene(n_small=5200, seed=0, C=16):
     """32x32 camera at the origin looking +z (f = 32): n_small camera-facing
     surfels of about 0.4 pixel at depths 2..3 with centres inside tile (0, 0)
-    (pixels 2..14), so that tile's list is longer than the 4096 keys the
-    shared-memory sorts take and the per-tile radix sort runs."""
+    (pixels 2..14): with 5,200 of them that tile's list is longer than the
+    1,024 keys the shared-memory sort takes and the per-tile radix sort runs;
+    with about 1,000 it fills nearly all 32 chunks of the shared-memory sort."""
     rng = np.random.default_rng(seed)
     z = rng.uniform(2.0, 3.0, n_small)
     px = rng.uniform(2.0, 14.0, n_small)
@@ -243,6 +244,23 @@ def _dense_tile_scene(n_small=5200, seed=0, C=16):
                       rng.normal(0.0, 1.0, (n_small, C)))
     vm = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0]], dtype=np.float32)
     return sc, scenes.Camera(f, f, c, c, 32, 32, vm)
+
+
+def test_chunked_sort_for_a_tile_of_nearly_1024_pairs():
+    """A tile list of close to the 1,024 keys of the shared-memory sort (32
+    warp-sorted chunks of 32 merged by rank, a ragged last chunk): order and
+    warp masks bit-exact against the oracle, and the frame's features, ids
+    and stop counts against the oracle."""
+    from tests.gpu_util import GpuRun
+    from tests.test_gpu_render import _compare, _oracle
+    sc, cam = _dense_tile_scene(n_small=1000, seed=1)
+    run = GpuRun(sc, [cam], K=8)
+    r = run.ranges()
+    assert 960 < r[0, 1] - r[0, 0] <= 1024 and (r[0, 1] - r[0, 0]) % 32 != 0
+    _check_lists(run, sc, [cam], 16, "accu")
+    _check_masks(run, sc, cam, 16)
+    ref, S = _oracle(sc, cam, 8)
+    _compare(run.view(0), ref, S, 1e-4, 8)
 
 
 def test_radix_sort_branch_for_a_tile_over_4096_pairs():
