@@ -28,9 +28,9 @@ __global__ void __launch_bounds__(256) k_loss(int64_t n_pix, int C, const OT* __
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t i = i0 + u * stride;
-            if (i < nf) {
-                ra[u] = FeatVec<OT>::raw(F + i * E);
-                rb[u] = FeatVec<OT>::raw(Ft + i * E);
+            if (i < nf) {  // read once: streaming loads, so that L2 keeps what the backward reads next
+                ra[u] = FeatVec<OT>::raw_cs(F + i * E);
+                rb[u] = FeatVec<OT>::raw_cs(Ft + i * E);
             }
         }
 #pragma unroll
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256) k_loss(int64_t n_pix, int C, const OT* __
     }
     float accf = acc * wf / (float)(n_pix * C), accc = 0.0f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += stride) {
-        const float d = rgb[i] - rgbt[i];
+        const float d = __ldcs(rgb + i) - __ldcs(rgbt + i);
         accc += fabsf(d);
         drgb[i] = d > 0.0f ? sc : (d < 0.0f ? -sc : 0.0f);
     }

@@ -89,6 +89,8 @@ struct FeatVec<float> {
     static constexpr int E = 4;  // channels per 16-byte load
     using Raw = float4;          // one 16-byte chunk as loaded
     __device__ static __forceinline__ Raw raw(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+    // streaming load (evict-first: read once, leaves L2 to the data read next)
+    __device__ static __forceinline__ Raw raw_cs(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
     __device__ static __forceinline__ void unpack2(const Raw& r, float2* o) {
         o[0] = make_float2(r.x, r.y);
         o[1] = make_float2(r.z, r.w);
@@ -110,6 +112,7 @@ struct FeatVec<__nv_bfloat16> {
     static constexpr int E = 8;
     using Raw = uint4;
     __device__ static __forceinline__ Raw raw(const __nv_bfloat16* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
+    __device__ static __forceinline__ Raw raw_cs(const __nv_bfloat16* p) { return __ldcs(reinterpret_cast<const uint4*>(p)); }
     __device__ static __forceinline__ void unpack2(const Raw& r, float2* o) {
         const uint32_t w[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll

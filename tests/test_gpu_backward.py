@@ -237,3 +237,34 @@ def test_backward_renormalised_topk(select):
     g_ref = O.render_backward(sc, cam, p, gF, grgb, gT, binned=ref["binned"], flip=ref["flip"])
     g = _gpu_backward(run, gF, grgb, gT)
     _assert_close(g, g_ref)
+
+
+@pytest.mark.parametrize("K,schedule", [(8, "grid"), (8, "persistent"), (0, "grid")])
+def test_repeated_backward_calls_start_from_zero(K, schedule):
+    """The backward's per-slot accumulators are cleared at the sort and again
+    by the backward's last kernels after they are read (and the persistent
+    work queues are reset there): backward calls repeated on one forward,
+    with and without the feature-gradient output, give the same gradients
+    each time (equal up to the order of the atomic sums)."""
+    from tests.gpu_util import GpuRun
+    sc, cam = scenes.tiny_scene(seed=12, n=2500, C=16)
+    run = GpuRun(sc, [cam], K=K, stop_rule="tmin", schedule=schedule)
+    rng = np.random.default_rng(3)
+    gF = rng.normal(0.0, 1.0, run.F.shape).astype(np.float32)
+    grgb = rng.normal(0.0, 1.0, run.rgb_out.shape).astype(np.float32)
+    first = _gpu_backward(run, gF, grgb, None)
+    fr, N = run.frame, run.scene.n
+    # a call without the feature-gradient output in between
+    outs = [torch.empty(N, 3, device="cuda"), torch.empty(N, 2, device="cuda"), torch.empty(N, 4, device="cuda"),
+            torch.empty(N, device="cuda"), torch.empty(N, 3, device="cuda")]
+    fr.render_backward(run.means, run.scales, run.quats, run.opac, run.rgb, run.feats, run.T,
+                       dev(gF.reshape(-1, gF.shape[-1])), dev(grgb.reshape(-1, 3)), None, *outs, None)
+    torch.cuda.synchronize()
+    for t, k in zip(outs, ("means", "scales", "quats", "opac", "rgb")):
+        scale = np.abs(first[k]).max()
+        assert np.abs(t.cpu().numpy() - first[k]).max() <= 1e-5 * scale, k
+    for _ in range(2):
+        again = _gpu_backward(run, gF, grgb, None)
+        for k, v in first.items():
+            scale = np.abs(v).max()
+            assert scale > 0 and np.abs(again[k] - v).max() <= 1e-5 * scale, k
