@@ -250,31 +250,33 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                         }
                     }
                 }
-                // 2. slots of the selected positions, then the entries grouped by slot
+                // 2. slots of the selected positions, then the entries grouped by slot: the
+                // entries per position are counted, and one exclusive scan of
+                // (count << 16 | count > 0) over the positions gives each position both its
+                // first record (high half) and its slot (low half: selected positions
+                // before it); counts <= ECAP and positions <= PTAB fit 16 bits each
                 const int nt = min(PTAB, L - p0);  // positions in use (U <= nt)
                 for (int i = tid; i < nt; i += BWD_FEAT_THREADS) s_tab[i] = 0;
-                for (int i = tid; i <= nt; i += BWD_FEAT_THREADS) s_off[i] = 0;
                 __syncthreads();
 #pragma unroll
                 for (int i = 0; i < EPT; ++i)
-                    if (epos[i] >= 0) s_tab[epos[i]] = 1;
+                    if (epos[i] >= 0) atomicAdd(&s_tab[epos[i]], 1 << 16);
                 __syncthreads();
-                const int U = block_exscan(s_tab, nt, s_red);  // s_tab[pos] = slot where marked
+                const int tot = block_exscan_marked(s_tab, nt, s_red);
+                const int U = tot & 0xffff, nsel = tot >> 16;
                 if (U == 0) continue;
                 for (int i = tid; i < nt; i += BWD_FEAT_THREADS) {
-                    const int nxt = i + 1 < nt ? s_tab[i + 1] : U;
-                    if (nxt - s_tab[i] == 1) s_inv[s_tab[i]] = i;
+                    const int pre = s_tab[i], nxt = i + 1 < nt ? s_tab[i + 1] : tot;
+                    if ((nxt & 0xffff) - (pre & 0xffff) == 1) {  // a selected position: its slot
+                        s_inv[pre & 0xffff] = i;
+                        s_off[pre & 0xffff] = pre >> 16;
+                        s_cur[pre & 0xffff] = pre >> 16;
+                    }
                 }
+                if (tid == 0) s_off[U] = nsel;
                 int eslot[EPT];
 #pragma unroll
-                for (int i = 0; i < EPT; ++i) {
-                    eslot[i] = epos[i] >= 0 ? s_tab[epos[i]] : -1;
-                    if (eslot[i] >= 0) atomicAdd(&s_off[eslot[i]], 1);
-                }
-                __syncthreads();
-                const int nsel = block_exscan(s_off, U, s_red);
-                for (int i = tid; i < U; i += BWD_FEAT_THREADS) s_cur[i] = s_off[i];
-                if (tid == 0) s_off[U] = nsel;
+                for (int i = 0; i < EPT; ++i) eslot[i] = epos[i] >= 0 ? s_tab[epos[i]] & 0xffff : -1;
                 __syncthreads();
 #pragma unroll
                 for (int i = 0; i < EPT; ++i) {

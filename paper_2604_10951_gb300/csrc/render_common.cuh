@@ -369,6 +369,49 @@ __device__ __forceinline__ int block_exscan(int* v, int n, int* red) {
     return total;
 }
 
+// block_exscan of v[i] | (v[i] != 0): the values' low bit also counts the
+// nonzero entries (for counts kept in the high bits)
+__device__ __forceinline__ int block_exscan_marked(int* v, int n, int* red) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    int loc[8], sum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int i = tid * per + k;
+        loc[k] = (k < per && i < n) ? (v[i] | (v[i] != 0 ? 1 : 0)) : 0;
+        sum += loc[k];
+    }
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) red[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int w = lane < nw ? red[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < nw) red[lane] = wi - w;
+        if (lane == 31) red[32] = wi;
+    }
+    __syncthreads();
+    int run = red[wid] + incl - sum;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int i = tid * per + k;
+        if (k < per && i < n) { v[i] = run; run += loc[k]; }
+    }
+    const int total = red[32];
+    __syncthreads();
+    return total;
+}
+
 __device__ __forceinline__ void warp_count(uint64_t* ctr, uint32_t v) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
