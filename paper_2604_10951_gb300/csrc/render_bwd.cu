@@ -205,17 +205,6 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
 
         for (int pc0 = 0; pc0 < npx; pc0 += pch) {
             const int np = min(pch, npx - pc0), ne = np * K;
-            // the chunk's dL/dF rows (zeros outside the image), copied asynchronously and
-            // waited for just before the inner loop, so that the copies overlap steps 1-3
-            if (r0v < rv) {
-                for (int q = r0v; q < np; q += rv) {
-                    const int p = pc0 + q, px = tx * TS + (p & (TS - 1)), py = ty * TS + (p >> lts);
-                    const bool in = px < cam.W && py < cam.H;
-                    const FT* src = in ? dF + (cam.pix_off + (int64_t)py * cam.W + px) * C + v0 * E : dF;
-                    cp_async16(s_df + (size_t)q * rowe + v0 * E, src, in ? 16 : 0);
-                }
-            }
-            cp_async_commit();
             // dots not yet formed read as a sentinel (a NaN payload that arithmetic does
             // not produce), so the write-back needs no per-entry state
             for (int e = tid; e < ne; e += BWD_FEAT_THREADS) s_dot[e] = __int_as_float(DOT_UNSET);
@@ -249,6 +238,20 @@ __global__ void __launch_bounds__(BWD_FEAT_THREADS, 4) k_bwd_feat(const __grid_c
                             }
                         }
                     }
+                }
+                if (p0 == 0) {
+                    // the chunk's dL/dF rows (zeros outside the image), copied asynchronously
+                    // once this thread's entries have arrived (issued first, they queued
+                    // the entry loads behind them) and waited for just before the inner loop
+                    if (r0v < rv) {
+                        for (int q = r0v; q < np; q += rv) {
+                            const int p = pc0 + q, px = tx * TS + (p & (TS - 1)), py = ty * TS + (p >> lts);
+                            const bool in = px < cam.W && py < cam.H;
+                            const FT* src = in ? dF + (cam.pix_off + (int64_t)py * cam.W + px) * C + v0 * E : dF;
+                            cp_async16(s_df + (size_t)q * rowe + v0 * E, src, in ? 16 : 0);
+                        }
+                    }
+                    cp_async_commit();
                 }
                 // 2. slots of the selected positions, then the entries grouped by slot: the
                 // entries per position are counted, and one exclusive scan of
