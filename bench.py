@@ -170,20 +170,20 @@ def make_events(torch, n):
 
 
 FWD_CALLS = ["project_bin", "sort", "render_forward"]
-STEP_CALLS = FWD_CALLS + ["loss", "render_backward"]
+STEP_CALLS = FWD_CALLS[:2] + ["render_forward_loss", "render_backward"]
 FWD_KERNELS = ["k_project", "k_emit", "k_tile_sort"]
 # kernels per fwd+bwd step: project_bin 2 (project; emit, whose first CTA scans the tile counts), sort 1,
-# forward 1, loss 1,
+# forward with the loss 1 (Top-K, K <= 8: the loss is evaluated in the render kernel),
 # backward 5 (clear, feature grads + dots, geometry replay, projection, feature rows)
-KERNELS = FWD_KERNELS + ["k_render_topk", "k_loss", "k_bwd_clear", "k_bwd_feat", "k_bwd_geo", "k_bwd_project",
-                         "k_feat_out"]
+BWD_KERNELS = ["k_bwd_clear", "k_bwd_feat", "k_bwd_geo", "k_bwd_project", "k_feat_out"]
+KERNELS = FWD_KERNELS + ["k_render_topk"] + BWD_KERNELS
 
 
 class StepPath:
     """Buffers and the step of one configuration, every call through the C
     ABI, replayed as one CUDA graph per camera set: binning, sort, forward
-    render, and (``backward``) the L2-feature/L1-RGB loss and the backward
-    render.  ``cam_sets`` lists the camera sets the steps cycle over (one
+    render, and (``backward``) the L2-feature/L1-RGB loss (in the forward
+    call, fss_render_forward_loss) and the backward render.  ``cam_sets`` lists the camera sets the steps cycle over (one
     view each, or several views rendered in one call)."""
 
     def __init__(self, torch, L, dev, scene_t, cam_sets, N, C, K, dtype, stop, backward=True, ts=16,
@@ -213,6 +213,7 @@ class StepPath:
         npx = self.frame.total_pix
         self.npx = npx
         self.render_kernel = "k_render_topk" if K else "k_render_full"
+        self.fused_loss = False
         self.kernels = FWD_KERNELS + [self.render_kernel]
         self.calls = FWD_CALLS
         if backward:
@@ -225,8 +226,10 @@ class StepPath:
             self.g = [torch.empty(N, k, device=dev) for k in (3, 2, 4)] + \
                      [torch.empty(N, device=dev), torch.empty(N, 3, device=dev)]
             self.gfeat = torch.empty(N, C, dtype=dtype, device=dev)
-            self.kernels = KERNELS if K else FWD_KERNELS + ["k_render_full", "k_loss", "k_bwd_clear", "k_bwd_geo",
-                                                             "k_bwd_project", "k_feat_out"]
+            # the loss runs inside the Top-K kernel for K <= 8, else as its own kernel
+            self.fused_loss = 0 < K <= 8
+            self.kernels = (FWD_KERNELS + [self.render_kernel] + ([] if self.fused_loss else ["k_loss"]) +
+                            [k for k in BWD_KERNELS if K or k != "k_bwd_feat"])
             self.calls = STEP_CALLS
         self.graphs, self.gevents = [], []
         self.ncu = False  # the ncu constants above describe this path's kernels (the main workload only)
@@ -248,18 +251,19 @@ class StepPath:
         rec(1)
         L.fss_sort(*a, ws, fr.cap, sp)
         rec(2)
-        L.fss_render_forward(*a, ws, fr.cap, ptr(self.rgb), ptr(self.feats), ptr(self.F), ptr(self.rgb_o),
-                             ptr(self.T), ptr(self.ids), ptr(fr.saved), sp)
-        rec(3)
         if not self.backward:
+            L.fss_render_forward(*a, ws, fr.cap, ptr(self.rgb), ptr(self.feats), ptr(self.F), ptr(self.rgb_o),
+                                 ptr(self.T), ptr(self.ids), ptr(fr.saved), sp)
+            rec(3)
             return
-        L.fss_loss_l2_l1(p, self.npx, ptr(self.F), ptr(self.rgb_o), ptr(self.F_tgt), ptr(self.rgb_tgt), 1.0, 1.0,
-                         ptr(self.dF), ptr(self.drgb), ptr(self.loss), sp)
-        rec(4)
+        L.fss_render_forward_loss(*a, ws, fr.cap, ptr(self.rgb), ptr(self.feats), ptr(self.F), ptr(self.rgb_o),
+                                  ptr(self.T), ptr(self.ids), ptr(fr.saved), ptr(self.F_tgt), ptr(self.rgb_tgt), 1.0,
+                                  1.0, ptr(self.dF), ptr(self.drgb), ptr(self.loss), sp)
+        rec(3)
         L.fss_render_backward(*a, ws, fr.cap, ptr(self.means), ptr(self.scales), ptr(self.quats), ptr(self.opac),
                               ptr(self.rgb), ptr(self.feats), ptr(fr.saved), ptr(self.T), ptr(self.dF),
                               ptr(self.drgb), None, *(ptr(g) for g in self.g), ptr(self.gfeat), sp)
-        rec(5)
+        rec(4)
 
     def capture(self):
         """One graph per camera set: the whole step."""
@@ -380,9 +384,13 @@ def run_ours(args):
                                  "calls_ms": {k: round(v, 4) for k, v in b_calls.items()},
                                  "speedup_of_bf16_topk": round(b_ms_step / ms_step, 3)}
         del base
-        if calls:
-            fwd_ms = calls["project_bin"] + calls["sort"] + calls["render_forward"]
-            out["forward_only"] = {"ms": round(fwd_ms, 4), "frames_per_s": round(1e3 / fwd_ms, 2)}
+        # the same frames forward only (binning, sort, render; one graph per pose)
+        fwd = StepPath(torch, L, dev, scene_t, [[c] for c in poses], N_SPLATS, C_FEAT, K_TOP, torch.bfloat16,
+                       "exact_topk", backward=False, rank=D.rank, world=D.world)
+        f_ms, _, _ = fwd.time_steps(max(64, args.steps // 4), 3, flush)
+        fwd_ms = D.max(float(np.sum(f_ms))) / len(f_ms)
+        out["forward_only"] = {"ms": round(fwd_ms, 4), "frames_per_s": round(1e3 / fwd_ms, 2)}
+        del fwd
         rf = path_roofline(ours, torch, L, flush, float(np.mean(step_ms)))
         out["roofline"], out["roofline_kernels"], out["kernel_us"], out["roofline_frame"] = \
             rf["main"], rf["rows"], rf["kernel_us"], rf["frame"]
@@ -512,8 +520,12 @@ def algorithmic_bytes(path, torch, L):
         # per pair the record and the feature row (staged once per tile); per pixel F, rgb, T, nstop
         b["k_render_full"] = tiles * 8 + P * (4 + 4 + 48 + 4 + 12 + Cc * s) + npx * (Cc * s + 12 + 4 + 4)
     if path.backward:
+        loss_b = npx * (2 * Cc * s + 24) + npx * (Cc * s + 12)  # F, F_t, rgb, rgb_t read; dL/dF, dL/drgb written
+        if path.fused_loss:  # in the render kernel: F is not read back
+            b["k_render_topk"] += loss_b - npx * (Cc * s + 12)
+        else:
+            b["k_loss"] = loss_b
         b.update({
-            "k_loss": npx * (2 * Cc * s + 24) + npx * (Cc * s + 12),
             "k_bwd_clear": nslot * (64 + 4 * Cc),
             "k_bwd_project": N * 52 + nslot * (V * 64 + 48 + 40),
             "k_feat_out": N * Cc * s + nslot * 4 * Cc,

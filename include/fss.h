@@ -299,6 +299,25 @@ fss_status fss_loss_l2_l1(const fss_params *params, int64_t n_pix, const void *f
                           void *d_feat, float *d_rgb, double *loss, fss_stream_t stream);
 
 /*
+ * fss_render_forward followed by fss_loss_l2_l1 on its outputs, in one call:
+ * the same forward arguments, then the loss's target, weights and outputs,
+ * over the n_pix pixels of all cameras (pixel order of the outputs).
+ * out_feat, out_rgb and every loss argument are required; feat_target and
+ * d_feat are 16-byte aligned, in params->out_dtype.  With the plain Top-K
+ * selection (0 < K <= 8, not FSS_SELECT_FRONT, no low-pass filter) and
+ * out_dtype == feat_dtype, the loss is evaluated inside the forward kernel
+ * on each pixel's feature chunk as it is stored, so F is not read back:
+ * d_feat and d_rgb equal those of the two separate calls bit for bit and
+ * *loss differs by the summation order only.  Otherwise the loss kernel runs
+ * after the render.  Errors as for the two calls.
+ */
+fss_status fss_render_forward_loss(const fss_params *params, const fss_camera *cams, int32_t n_cams, int64_t N,
+                                   void *workspace, int64_t pair_capacity, const float *rgb, const void *feats,
+                                   void *out_feat, float *out_rgb, float *out_T, int32_t *out_topk_id,
+                                   void *saved, const void *feat_target, const float *rgb_target, float w_feat,
+                                   float w_rgb, void *d_feat, float *d_rgb, double *loss, fss_stream_t stream);
+
+/*
  * Size of the device scratch array behind fss_forward_static: 64 MiB per
  * device, reserved when the library's module loads on that device.
  */

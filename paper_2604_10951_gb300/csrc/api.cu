@@ -450,10 +450,22 @@ fss_status fss_render_forward(const fss_params* params, const fss_camera* cams, 
                                   out_T, out_topk_id, saved, nullptr, stream);
 }
 
-fss_status fss_render_forward_aux(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N,
-                                  void* workspace, int64_t pair_capacity, const float* rgb, const void* feats,
-                                  void* out_feat, float* out_rgb, float* out_T, int32_t* out_topk_id, void* saved,
-                                  const fss_aux_outputs* aux, fss_stream_t stream) {
+namespace {
+
+// the training loss of fss_render_forward_loss
+struct LossIn {
+    const void* Ft;
+    const float* rgbt;
+    float wf, wc;
+    void* dF;
+    float* drgb;
+    double* loss;
+};
+
+fss_status render_forward_impl(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N,
+                               void* workspace, int64_t pair_capacity, const float* rgb, const void* feats,
+                               void* out_feat, float* out_rgb, float* out_T, int32_t* out_topk_id, void* saved,
+                               const fss_aux_outputs* aux, const LossIn* li, fss_stream_t stream) {
     Ctx ctx;
     fss_status s = prepare(params, cams, n_cams, N, pair_capacity, workspace, ctx);
     if (s != FSS_OK) return s;
@@ -498,9 +510,52 @@ fss_status fss_render_forward_aux(const fss_params* params, const fss_camera* ca
                                          reinterpret_cast<cudaStream_t>(stream));
         if (ec != cudaSuccess) return cuda_fail(ec, "k_sh_color");
     }
-    cudaError_t e = launch_render_forward(ctx.cams, ctx.P, a, x, num_sms_current(), reinterpret_cast<cudaStream_t>(stream));
+    const cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t n_pix = ctx.cams.total_pix;
+    // the loss in the Top-K kernel's phase 2: the plain selection with K <= 8 and
+    // the output in the feature type; otherwise the loss kernel after the render
+    const bool fused = li && params->K > 0 && params->K <= 8 && params->select != FSS_SELECT_FRONT &&
+                       !params->lowpass && !x.any() && params->out_dtype == params->feat_dtype;
+    if (fused) {
+        cudaError_t e = cudaMemsetAsync(li->loss, 0, sizeof(double), cs);
+        if (e != cudaSuccess) return cuda_fail(e, "memset loss");
+        if (n_pix > 0) {  // the scale factors exactly as the loss kernel forms them
+            x.loss = LossOut{li->Ft, li->rgbt, li->dF, li->drgb, li->loss, 2.0f * li->wf / (float)(n_pix * params->C),
+                             li->wf / (float)(n_pix * params->C), li->wc / (float)(n_pix * 3)};
+        }
+    }
+    cudaError_t e = launch_render_forward(ctx.cams, ctx.P, a, x, num_sms_current(), cs);
     if (e != cudaSuccess) return cuda_fail(e, "render_forward");
+    if (li && !fused) {
+        e = launch_loss(n_pix, params->C, params->out_dtype, out_feat, out_rgb, li->Ft, li->rgbt, li->wf, li->wc, li->dF,
+                        li->drgb, li->loss, num_sms_current(), cs);
+        if (e != cudaSuccess) return cuda_fail(e, "loss");
+    }
     return FSS_OK;
+}
+
+}  // namespace
+
+fss_status fss_render_forward_aux(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N,
+                                  void* workspace, int64_t pair_capacity, const float* rgb, const void* feats,
+                                  void* out_feat, float* out_rgb, float* out_T, int32_t* out_topk_id, void* saved,
+                                  const fss_aux_outputs* aux, fss_stream_t stream) {
+    return render_forward_impl(params, cams, n_cams, N, workspace, pair_capacity, rgb, feats, out_feat, out_rgb, out_T,
+                               out_topk_id, saved, aux, nullptr, stream);
+}
+
+fss_status fss_render_forward_loss(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N,
+                                   void* workspace, int64_t pair_capacity, const float* rgb, const void* feats,
+                                   void* out_feat, float* out_rgb, float* out_T, int32_t* out_topk_id, void* saved,
+                                   const void* feat_target, const float* rgb_target, float w_feat, float w_rgb,
+                                   void* d_feat, float* d_rgb, double* loss, fss_stream_t stream) {
+    if (!out_feat || !out_rgb || !feat_target || !rgb_target || !d_feat || !d_rgb || !loss)
+        return fail(FSS_ERR_INVALID_ARG, "NULL loss argument (out_feat, out_rgb, targets, gradients, loss)");
+    if (misaligned16(feat_target) || misaligned16(d_feat))
+        return fail(FSS_ERR_INVALID_ARG, "feature buffers must be 16-byte aligned");
+    const LossIn li{feat_target, rgb_target, w_feat, w_rgb, d_feat, d_rgb, loss};
+    return render_forward_impl(params, cams, n_cams, N, workspace, pair_capacity, rgb, feats, out_feat, out_rgb, out_T,
+                               out_topk_id, saved, nullptr, &li, stream);
 }
 
 fss_status fss_render_backward(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N,

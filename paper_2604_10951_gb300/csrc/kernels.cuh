@@ -67,13 +67,28 @@ struct FwdArgs {
     int persistent;
 };
 
-// sensor outputs of the forward render, each may be NULL.  A kernel parameter
-// of its own: a larger FwdArgs costs the main Top-K instance register spills.
+// training loss fused into the Top-K forward (its LOSS instances): the
+// definition and arithmetic of k_loss, on F as stored in the feature type
+struct LossOut {
+    const void* Ft;     // [pix, C] target features, feature type
+    const float* rgbt;  // [pix, 3]
+    void* dF;           // [pix, C] dL/dF, feature type
+    float* drgb;        // [pix, 3] dL/drgb
+    double* loss;       // one double, zeroed before the launch
+    float sf;           // 2 w_f / (n C): dL/dF = sf (F - F_t)
+    float lf;           // w_f / (n C): the feature term's weight on sum (F - F_t)^2
+    float sc;           // w_c / (3 n): dL/drgb = sc sign(rgb - rgb_t), and the weight on sum |rgb - rgb_t|
+};
+
+// sensor outputs of the forward render, each may be NULL, and the fused loss
+// (loss.loss NULL: none).  A kernel parameter of its own: a larger FwdArgs
+// costs the main Top-K instance register spills.
 struct AuxOut {
     float* depth;      // [pix] sum w z_hit
     float* depth_med;  // [pix] z_hit where T first drops below 1/2, else 0
     float* normal;     // [pix, 3] sum w n, camera-space normals facing the camera
     int32_t* label;    // [pix] argmax over the channels of the rendered features, -1 if none blended
+    LossOut loss;
     __host__ __device__ bool any() const { return depth || depth_med || normal || label; }
 };
 

@@ -100,6 +100,9 @@ struct FeatVec<float> {
         o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
     }
     __device__ static __forceinline__ float one(const float* p) { return __ldg(p); }
+    // E channels in pairs, as stored in this type (rounded like store_vec), and the 16-byte store
+    __device__ static __forceinline__ Raw pack(const float2* v) { return make_float4(v[0].x, v[0].y, v[1].x, v[1].y); }
+    __device__ static __forceinline__ void st(float* p, const Raw& r) { *reinterpret_cast<float4*>(p) = r; }
     // 16-byte shared-memory load
     __device__ static __forceinline__ void lds(const float* p, float* o) {
         const float4 v = *reinterpret_cast<const float4*>(p);
@@ -127,6 +130,16 @@ struct FeatVec<__nv_bfloat16> {
             o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
         }
     }
+    __device__ static __forceinline__ Raw pack(const float2* v) {
+        uint32_t w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v[k].x, v[k].y);
+            w[k] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        return make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    __device__ static __forceinline__ void st(__nv_bfloat16* p, const Raw& r) { *reinterpret_cast<uint4*>(p) = r; }
     __device__ static __forceinline__ float one(const __nv_bfloat16* p) {
         return __uint_as_float(((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p))) << 16);
     }

@@ -57,7 +57,7 @@ using topk_detail::next_tile;
 // KCAP the first KCAP - K slots hold +inf and never move, so the K-th
 // largest weight is always slot KCAP - 1.  With the first-K selection the
 // K slots after the padding take the first K contributors in order.
-template <int TS, int KCAP, typename FT, bool FRONT, bool AUX>
+template <int TS, int KCAP, typename FT, bool FRONT, bool AUX, bool LOSS = false>
 __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : (KCAP == 16 && TS <= 16 ? 512 / (TS * TS) : 1)) k_render_topk(const __grid_constant__ Cams cams,
                                                          const __grid_constant__ RParams P, const FwdArgs a,
                                                          const __grid_constant__ AuxOut x) {
@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : (KCAP 
         reinterpret_cast<unsigned long long*>(smem + (((size_t)PC * KCAP * 8 + PC * 4 + 7) & ~(size_t)7));
     __shared__ int s_tile;
     __shared__ uint32_t s_bits[NT / 32][BATCH / 32];  // per warp: the staged surfels its block meets
+    __shared__ float s_loss[LOSS ? NT / 32 : 1];        // LOSS: per-warp sums of a tile
 
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t wbit = 1u << (tid >> 5);
@@ -100,6 +101,12 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : (KCAP 
         const int n = rg.y - rg.x;
         const int64_t vbase = (int64_t)view * P.N;
         const float* __restrict__ rgbv = a.rgb + (P.color_sh ? 3 * vbase : 0);  // SH: item colours
+        if (LOSS && inside) {  // the pixel's targets, into L2 while phase 1 runs
+            const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
+            const char* ft = reinterpret_cast<const char*>(x.loss.Ft) + pix * P.C * (int64_t)sizeof(FT);
+            for (int off = 0; off < P.C * (int)sizeof(FT); off += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(ft + off));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(x.loss.rgbt + 3 * pix));
+        }
 
         float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
         bool done = !inside;
@@ -215,6 +222,13 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : (KCAP 
         }
 
         // per-pixel outputs; the K-set in front-to-back order
+        float lsum = 0.0f;  // LOSS: this thread's weighted loss terms in this tile (nothing live in phase 1)
+        float rt[3] = {0.0f, 0.0f, 0.0f};  // LOSS: the colour target, loaded ahead of the ranks
+        if (LOSS && inside) {
+            const float* r = x.loss.rgbt + 3 * (cam.pix_off + (int64_t)py * cam.W + px);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) rt[c] = __ldcs(r + c);
+        }
         int rank[KCAP], hid[KCAP];
         int hc = 0;
 #pragma unroll
@@ -231,6 +245,17 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : (KCAP 
                 a.out_rgb[3 * pix] = fmaf(T, P.bg[0], cr);
                 a.out_rgb[3 * pix + 1] = fmaf(T, P.bg[1], cg);
                 a.out_rgb[3 * pix + 2] = fmaf(T, P.bg[2], cb);
+                if (LOSS) {  // the colour term: |rgb - rgb_t| and its sign
+                    const float c3[3] = {fmaf(T, P.bg[0], cr), fmaf(T, P.bg[1], cg), fmaf(T, P.bg[2], cb)};
+                    float s1 = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float d = c3[c] - rt[c];
+                        s1 += fabsf(d);
+                        x.loss.drgb[3 * pix + c] = d > 0.0f ? x.loss.sc : (d < 0.0f ? -x.loss.sc : 0.0f);
+                    }
+                    lsum = fmaf(x.loss.sc, s1, lsum);
+                }
             }
             if (a.out_T) a.out_T[pix] = T;
             if (a.saved_nstop) a.saved_nstop[pix] = last + 1;
@@ -294,6 +319,10 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : (KCAP 
                     const int2 lq = pixel_of<TS>(p);  // pixel of the thread that selected row q
                     const int qx = tx * TS + lq.x, qy = ty * TS + lq.y;
                     if (qx >= cam.W || qy >= cam.H) continue;
+                    typename FeatVec<FT>::Raw ft{};  // LOSS: the target chunk, loaded during the gathers
+                    if (LOSS)
+                        ft = FeatVec<FT>::raw_cs(reinterpret_cast<const FT*>(x.loss.Ft) +
+                                                 (cam.pix_off + (int64_t)qy * cam.W + qx) * P.C + vv * E);
                     // the selected rows' chunks, weighted with packed FP32 pairs (lane for
                     // lane fmaf) in the selection's front-to-back order
                     float2 acc2[E / 2];
@@ -310,23 +339,46 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : (KCAP 
 #pragma unroll
                         for (int e = 0; e < E / 2; ++e) acc2[e] = __ffma2_rn(w2, f2[e], acc2[e]);
                     }
-                    float acc[E];
-#pragma unroll
-                    for (int e = 0; e < E / 2; ++e) {
-                        acc[2 * e] = acc2[e].x;
-                        acc[2 * e + 1] = acc2[e].y;
-                    }
                     const int64_t qpix = cam.pix_off + (int64_t)qy * cam.W + qx;
-                    if (a.out_feat) store_vec<E>(a.out_feat, qpix * P.C + vv * E, acc, P.out_dtype);
-                    if (AUX && x.label) {
-                        int eb = 0;
-                        float bv = acc[0];
+                    if constexpr (LOSS) {
+                        // F as stored (output type = feature type), then the feature term:
+                        // d = F - F_t (an FMA with -1: one rounding, as the subtraction),
+                        // sum d^2, dL/dF = sf d rounded once to the output type
+                        // (F with an evict-first store: the step does not read it again)
+                        using Raw = typename FeatVec<FT>::Raw;
+                        const Raw fr = FeatVec<FT>::pack(acc2);
+                        __stcs(reinterpret_cast<Raw*>(reinterpret_cast<FT*>(a.out_feat) + qpix * P.C + vv * E), fr);
+                        float2 f2[E / 2], t2[E / 2], g2[E / 2];
+                        FeatVec<FT>::unpack2(fr, f2);
+                        FeatVec<FT>::unpack2(ft, t2);
+                        const float2 m1 = make_float2(-1.0f, -1.0f), sf2 = make_float2(x.loss.sf, x.loss.sf);
+                        float2 q2 = make_float2(0.0f, 0.0f);
 #pragma unroll
-                        for (int e = 1; e < E; ++e) {
-                            eb = acc[e] > bv ? e : eb;
-                            bv = acc[e] > bv ? acc[e] : bv;
+                        for (int e = 0; e < E / 2; ++e) {
+                            const float2 d2 = __ffma2_rn(t2[e], m1, f2[e]);
+                            q2 = __ffma2_rn(d2, d2, q2);
+                            g2[e] = __fmul2_rn(sf2, d2);
                         }
-                        atomicMax(&s_lab[q], argmax_key(bv, vv * E + eb));
+                        FeatVec<FT>::st(reinterpret_cast<FT*>(x.loss.dF) + qpix * P.C + vv * E, FeatVec<FT>::pack(g2));
+                        lsum = fmaf(x.loss.lf, q2.x + q2.y, lsum);
+                    } else {
+                        float acc[E];
+#pragma unroll
+                        for (int e = 0; e < E / 2; ++e) {
+                            acc[2 * e] = acc2[e].x;
+                            acc[2 * e + 1] = acc2[e].y;
+                        }
+                        if (a.out_feat) store_vec<E>(a.out_feat, qpix * P.C + vv * E, acc, P.out_dtype);
+                        if (AUX && x.label) {
+                            int eb = 0;
+                            float bv = acc[0];
+#pragma unroll
+                            for (int e = 1; e < E; ++e) {
+                                eb = acc[e] > bv ? e : eb;
+                                bv = acc[e] > bv ? acc[e] : bv;
+                            }
+                            atomicMax(&s_lab[q], argmax_key(bv, vv * E + eb));
+                        }
                     }
                 }
                 if (AUX && x.label) {
@@ -339,6 +391,18 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : (KCAP 
                                 s_n[tid] > 0 ? argmax_channel(s_lab[tid]) : -1;
                     }
                 }
+            }
+        }
+        if constexpr (LOSS) {  // the tile's share of the loss, one double atomic per tile
+            float v = lsum;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) s_loss[tid >> 5] = v;
+            __syncthreads();  // (the next tile's writes come after its own barriers)
+            if (tid == 0) {
+                double t = 0.0;
+                for (int w = 0; w < NT / 32; ++w) t += s_loss[w];
+                atomicAdd(x.loss.loss, t);
             }
         }
     }
@@ -354,6 +418,8 @@ cudaError_t launch_topk(const Cams& cams, const RParams& P, const FwdArgs& a, co
         const int pc = (NT < 65536 / (kcap * 8 + 4)) ? NT : 65536 / (kcap * 8 + 4);
         return std::max(p1, (size_t)pc * (kcap * 8 + 4) + (aux ? (size_t)pc * 8 + 8 : 0));  // (+ argmax keys)
     };
+    // the fused loss: the plain selection with K <= 8, no sensor outputs (checked by the caller)
+    if (x.loss.loss) return launch_tiles(k_render_topk<TS, 8, FT, false, false, true>, NT, smem(8), cams, P, a, x, num_sms, s);
     // variants (first-K selection, sensor outputs) need unsorted or few slots: two capacities
     if (P.select == FSS_SELECT_FRONT) {
         if (aux) {
