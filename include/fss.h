@@ -384,7 +384,8 @@ fss_status fss_forward_static(const fss_params *params, const fss_camera *cams, 
  * switches the hook off.  The array must stay valid while the hook is on.
  * Kernels per call: fss_project_bin 2 (project; emit, whose first CTA scans
  * the tile counts), fss_sort 1,
- * fss_render_forward 1, fss_loss_l2_l1 1, fss_render_backward 4 for Top-K
+ * fss_render_forward 1, fss_loss_l2_l1 1, fss_render_forward_loss 1 when
+ * the loss runs in the render kernel (else 2), fss_render_backward 4 for Top-K
  * (clear, feature gradients, geometry replay, projection) or 3 for K = 0,
  * plus 1 when g_feat is given (feature rows).
  */
