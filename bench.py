@@ -428,10 +428,10 @@ def device_scene(torch, dev, sc):
 # pose 0, the L2 contents the step's earlier kernels left; ncu --cache-control none),
 # from the in-step traffic summary under profiles/; to be set to None whenever the
 # kernel changes after that capture
-NCU_TRAFFIC = {"k_render_topk": 8301312 + 56528640, "k_bwd_feat": 18149376 + 18669824, "k_bwd_geo": 12274432 + 11519232}
+NCU_TRAFFIC = {"k_render_topk": 53867776 + 100632576, "k_bwd_feat": 12216832 + 21090048, "k_bwd_geo": 12893440 + 9380352}
 # (smsp__inst_executed.sum, gpu__time_duration.sum in us) of the one-kernel --set full
 # captures summarised under profiles/
-NCU_ISSUE = {"k_render_topk": (70193242, 88.576), "k_bwd_feat": (61610201, 76.096), "k_bwd_geo": (82220205, 101.536)}
+NCU_ISSUE = {"k_render_topk": (77173426, 98.784), "k_bwd_feat": (61610201, 76.096), "k_bwd_geo": (82220205, 101.536)}
 # the query-label kernel's capture (summarised under profiles/): DRAM read + write
 NCU_QUERY_TRAFFIC = {"nq32_dim32_f32": 47276544}
 
