@@ -104,7 +104,8 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : (KCAP 
         if (LOSS && inside) {  // the pixel's targets, into L2 while phase 1 runs
             const int64_t pix = cam.pix_off + (int64_t)py * cam.W + px;
             const char* ft = reinterpret_cast<const char*>(x.loss.Ft) + pix * P.C * (int64_t)sizeof(FT);
-            for (int off = 0; off < P.C * (int)sizeof(FT); off += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(ft + off));
+            for (int off = 0; off < P.C * (int)sizeof(FT); off += 128)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(ft + off));
             asm volatile("prefetch.global.L2 [%0];" ::"l"(x.loss.rgbt + 3 * pix));
         }
 
@@ -419,7 +420,8 @@ cudaError_t launch_topk(const Cams& cams, const RParams& P, const FwdArgs& a, co
         return std::max(p1, (size_t)pc * (kcap * 8 + 4) + (aux ? (size_t)pc * 8 + 8 : 0));  // (+ argmax keys)
     };
     // the fused loss: the plain selection with K <= 8, no sensor outputs (checked by the caller)
-    if (x.loss.loss) return launch_tiles(k_render_topk<TS, 8, FT, false, false, true>, NT, smem(8), cams, P, a, x, num_sms, s);
+    if (x.loss.loss)
+        return launch_tiles(k_render_topk<TS, 8, FT, false, false, true>, NT, smem(8), cams, P, a, x, num_sms, s);
     // variants (first-K selection, sensor outputs) need unsorted or few slots: two capacities
     if (P.select == FSS_SELECT_FRONT) {
         if (aux) {
