@@ -112,3 +112,47 @@ def test_zero_weights_give_zero_loss_and_gradients():
     a, b = _run_both(scene, cams, K=8, feat_dtype=torch.bfloat16, wf=0.0, wc=0.0)
     assert b["loss"] == 0.0
     assert not b["dF"].float().abs().any() and not b["drgb"].abs().any()
+
+
+def test_empty_scene_with_background():
+    """No surfels: F = 0, rgb = background, T = 1 everywhere; the loss of those."""
+    from tests._scenes import make_scene
+    _, cams = _two_views()
+    empty = make_scene(np.zeros((0, 3)), np.zeros((0, 2)), np.zeros((0, 4)), np.zeros(0), C=32)
+    a, b = _run_both(empty, cams, K=8, feat_dtype=torch.bfloat16, bg=(0.25, 0.5, 0.75))
+    assert not b["F"].float().abs().any() and bool((b["T"] == 1.0).all())
+
+
+def test_graph_replay_equals_the_eager_call():
+    """The call captured in a CUDA graph (as the training step replays it) and
+    replayed on new targets gives the eager call's outputs on those targets."""
+    scene, cams = _two_views()
+    run = GpuRun(scene, cams, render=False, K=8, feat_dtype=torch.bfloat16, stop_rule="exact_topk")
+    fr = run.frame
+    npx, C = fr.total_pix, run.params.C
+    tgt = [tuple(dev(x, dt) for x, dt in zip(scenes.targets(s, npx, C), (torch.bfloat16, torch.float32)))
+           for s in (21, 22)]
+    Ft, rgbt = (torch.empty_like(t) for t in tgt[0])
+    outs = fr.new_outputs()
+    dF, drgb = torch.empty_like(outs[0]), torch.empty_like(outs[1])
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    call = lambda: fr.render_forward_loss(run.rgb, run.feats, *outs, Ft, rgbt, 1.0, 0.5, dF, drgb, loss)
+    Ft.copy_(tgt[0][0])
+    rgbt.copy_(tgt[0][1])
+    call()  # outside the capture first (kernel attributes)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        call()
+    Ft.copy_(tgt[1][0])
+    rgbt.copy_(tgt[1][1])
+    g.replay()
+    torch.cuda.synchronize()
+    got = [t.clone() for t in (*outs[:3], dF, drgb)] + [loss.item()]
+    call()
+    torch.cuda.synchronize()
+    ref = [t.clone() for t in (*outs[:3], dF, drgb)] + [loss.item()]
+    for x, y in zip(got[:-1], ref[:-1]):
+        assert torch.equal(x.view(torch.int16) if x.dtype == torch.bfloat16 else x,
+                           y.view(torch.int16) if y.dtype == torch.bfloat16 else y)
+    assert got[-1] == pytest.approx(ref[-1], rel=1e-6)
