@@ -170,13 +170,13 @@ def make_events(torch, n):
 
 
 FWD_CALLS = ["project_bin", "sort", "render_forward"]
-STEP_CALLS = FWD_CALLS[:2] + ["render_forward_loss", "render_backward"]
+STEP_CALLS = ["project_bin", "sort_render_forward_loss", "render_backward"]
 FWD_KERNELS = ["k_project", "k_emit", "k_tile_sort"]
-# kernels per fwd+bwd step: project_bin 2 (project; emit, whose first CTA scans the tile counts), sort 1,
-# forward with the loss 1 (Top-K, K <= 8: the loss is evaluated in the render kernel),
-# backward 5 (clear, feature grads + dots, geometry replay, projection, feature rows)
+# kernels per fwd+bwd step: project_bin 2 (project; emit, whose first CTA scans the tile counts), then the
+# sort, forward and loss in one kernel (Top-K, K <= 8: each CTA sorts its tile, renders it and evaluates the
+# loss on it), backward 5 (clear, feature grads + dots, geometry replay, projection, feature rows)
 BWD_KERNELS = ["k_bwd_clear", "k_bwd_feat", "k_bwd_geo", "k_bwd_project", "k_feat_out"]
-KERNELS = FWD_KERNELS + ["k_render_topk"] + BWD_KERNELS
+KERNELS = FWD_KERNELS[:2] + ["k_render_topk"] + BWD_KERNELS
 
 
 class StepPath:
@@ -228,7 +228,8 @@ class StepPath:
             self.gfeat = torch.empty(N, C, dtype=dtype, device=dev)
             # the loss runs inside the Top-K kernel for K <= 8, else as its own kernel
             self.fused_loss = 0 < K <= 8
-            self.kernels = (FWD_KERNELS + [self.render_kernel] + ([] if self.fused_loss else ["k_loss"]) +
+            self.kernels = (FWD_KERNELS[:2] + ([self.render_kernel] if self.fused_loss else
+                                               ["k_tile_sort", self.render_kernel, "k_loss"]) +
                             [k for k in BWD_KERNELS if K or k != "k_bwd_feat"])
             self.calls = STEP_CALLS
         self.graphs, self.gevents = [], []
@@ -249,21 +250,21 @@ class StepPath:
         rec(0)
         L.fss_project_bin(*a, ptr(self.means), ptr(self.scales), ptr(self.quats), ptr(self.opac), ws, fr.cap, sp)
         rec(1)
-        L.fss_sort(*a, ws, fr.cap, sp)
-        rec(2)
         if not self.backward:
+            L.fss_sort(*a, ws, fr.cap, sp)
+            rec(2)
             L.fss_render_forward(*a, ws, fr.cap, ptr(self.rgb), ptr(self.feats), ptr(self.F), ptr(self.rgb_o),
                                  ptr(self.T), ptr(self.ids), ptr(fr.saved), sp)
             rec(3)
             return
-        L.fss_render_forward_loss(*a, ws, fr.cap, ptr(self.rgb), ptr(self.feats), ptr(self.F), ptr(self.rgb_o),
-                                  ptr(self.T), ptr(self.ids), ptr(fr.saved), ptr(self.F_tgt), ptr(self.rgb_tgt), 1.0,
-                                  1.0, ptr(self.dF), ptr(self.drgb), ptr(self.loss), sp)
-        rec(3)
+        L.fss_sort_render_forward_loss(*a, ws, fr.cap, ptr(self.rgb), ptr(self.feats), ptr(self.F),
+                                       ptr(self.rgb_o), ptr(self.T), ptr(self.ids), ptr(fr.saved), ptr(self.F_tgt),
+                                       ptr(self.rgb_tgt), 1.0, 1.0, ptr(self.dF), ptr(self.drgb), ptr(self.loss), sp)
+        rec(2)
         L.fss_render_backward(*a, ws, fr.cap, ptr(self.means), ptr(self.scales), ptr(self.quats), ptr(self.opac),
                               ptr(self.rgb), ptr(self.feats), ptr(fr.saved), ptr(self.T), ptr(self.dF),
                               ptr(self.drgb), None, *(ptr(g) for g in self.g), ptr(self.gfeat), sp)
-        rec(4)
+        rec(3)
 
     def capture(self):
         """One graph per camera set: the whole step."""
@@ -428,10 +429,10 @@ def device_scene(torch, dev, sc):
 # pose 0, the L2 contents the step's earlier kernels left; ncu --cache-control none),
 # from the in-step traffic summary under profiles/; to be set to None whenever the
 # kernel changes after that capture
-NCU_TRAFFIC = {"k_render_topk": 53867776 + 100632576, "k_bwd_feat": 12216832 + 21090048, "k_bwd_geo": 12893440 + 9380352}
+NCU_TRAFFIC = {"k_render_topk": None, "k_bwd_feat": 12216832 + 21090048, "k_bwd_geo": 12893440 + 9380352}
 # (smsp__inst_executed.sum, gpu__time_duration.sum in us) of the one-kernel --set full
 # captures summarised under profiles/
-NCU_ISSUE = {"k_render_topk": (77173426, 98.784), "k_bwd_feat": (61610201, 76.096), "k_bwd_geo": (82220205, 101.536)}
+NCU_ISSUE = {"k_render_topk": None, "k_bwd_feat": (61610201, 76.096), "k_bwd_geo": (82220205, 101.536)}
 # the query-label kernel's capture (summarised under profiles/): DRAM read + write
 NCU_QUERY_TRAFFIC = {"nq32_dim32_f32": 47276544}
 
@@ -521,8 +522,8 @@ def algorithmic_bytes(path, torch, L):
         b["k_render_full"] = tiles * 8 + P * (4 + 4 + 48 + 4 + 12 + Cc * s) + npx * (Cc * s + 12 + 4 + 4)
     if path.backward:
         loss_b = npx * (2 * Cc * s + 24) + npx * (Cc * s + 12)  # F, F_t, rgb, rgb_t read; dL/dF, dL/drgb written
-        if path.fused_loss:  # in the render kernel: F is not read back
-            b["k_render_topk"] += loss_b - npx * (Cc * s + 12)
+        if path.fused_loss:  # the sort and the loss in the render kernel: F is not read back
+            b["k_render_topk"] += loss_b - npx * (Cc * s + 12) + b.pop("k_tile_sort")
         else:
             b["k_loss"] = loss_b
         b.update({

@@ -318,6 +318,23 @@ fss_status fss_render_forward_loss(const fss_params *params, const fss_camera *c
                                    float w_rgb, void *d_feat, float *d_rgb, double *loss, fss_stream_t stream);
 
 /*
+ * fss_sort followed by fss_render_forward_loss, in one call: the same
+ * arguments as fss_render_forward_loss, on a workspace that fss_project_bin
+ * has just filled (unsorted tile lists).  Where the loss runs inside the
+ * render kernel (the conditions above), each CTA of that kernel first sorts
+ * its own tile's list (the same order and warp masks as fss_sort, written to
+ * the workspace for the backward pass), so the sort needs no launch of its
+ * own; otherwise the sort kernel runs first.  Outputs, workspace contents
+ * and errors as for the two calls.
+ */
+fss_status fss_sort_render_forward_loss(const fss_params *params, const fss_camera *cams, int32_t n_cams, int64_t N,
+                                        void *workspace, int64_t pair_capacity, const float *rgb,
+                                        const void *feats, void *out_feat, float *out_rgb, float *out_T,
+                                        int32_t *out_topk_id, void *saved, const void *feat_target,
+                                        const float *rgb_target, float w_feat, float w_rgb, void *d_feat,
+                                        float *d_rgb, double *loss, fss_stream_t stream);
+
+/*
  * Size of the device scratch array behind fss_forward_static: 64 MiB per
  * device, reserved when the library's module loads on that device.
  */
@@ -385,7 +402,8 @@ fss_status fss_forward_static(const fss_params *params, const fss_camera *cams, 
  * Kernels per call: fss_project_bin 2 (project; emit, whose first CTA scans
  * the tile counts), fss_sort 1,
  * fss_render_forward 1, fss_loss_l2_l1 1, fss_render_forward_loss 1 when
- * the loss runs in the render kernel (else 2), fss_render_backward 4 for Top-K
+ * the loss runs in the render kernel (else 2), fss_sort_render_forward_loss 1
+ * when the loss runs in the render kernel (else 3), fss_render_backward 4 for Top-K
  * (clear, feature gradients, geometry replay, projection) or 3 for K = 0,
  * plus 1 when g_feat is given (feature rows).
  */

@@ -38,7 +38,8 @@ N_REGIONS = 21
 EXPORTS = ["fss_default_params", "fss_workspace_size", "fss_saved_size", "fss_project_bin", "fss_sort",
            "fss_render_forward", "fss_render_backward", "fss_read_status", "fss_last_error",
            "fss_workspace_region", "fss_loss_l2_l1", "fss_forward_static", "fss_set_kernel_events",
-           "fss_render_forward_aux", "fss_query_labels", "fss_test_hold_scan", "fss_render_forward_loss"]
+           "fss_render_forward_aux", "fss_query_labels", "fss_test_hold_scan", "fss_render_forward_loss",
+           "fss_sort_render_forward_loss"]
 FSS_STATIC_SCRATCH_BYTES = 64 << 20
 
 
@@ -110,6 +111,8 @@ def lib():
                 "fss_query_labels": [i64, i32, i32, P, P, P, P, P, P, i32, P, P],
                 "fss_render_forward_loss": [pp, pc, i32, i64, P, i64, P, P, P, P, P, P, P, P, P,
                                             C.c_float, C.c_float, P, P, P, P],
+                "fss_sort_render_forward_loss": [pp, pc, i32, i64, P, i64, P, P, P, P, P, P, P, P, P,
+                                                 C.c_float, C.c_float, P, P, P, P],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -190,6 +193,15 @@ def fss_render_forward_loss(params, cams, n_cams, N, workspace, pair_capacity, r
     return check(lib().fss_render_forward_loss(C.byref(params), cams, n_cams, N, workspace, pair_capacity, rgb, feats,
                                                out_feat, out_rgb, out_T, out_topk_id, saved, feat_target, rgb_target,
                                                float(w_feat), float(w_rgb), d_feat, d_rgb, loss, stream))
+
+
+def fss_sort_render_forward_loss(params, cams, n_cams, N, workspace, pair_capacity, rgb, feats, out_feat, out_rgb,
+                                 out_T, out_topk_id, saved, feat_target, rgb_target, w_feat, w_rgb, d_feat, d_rgb,
+                                 loss, stream):
+    return check(lib().fss_sort_render_forward_loss(C.byref(params), cams, n_cams, N, workspace, pair_capacity, rgb,
+                                                    feats, out_feat, out_rgb, out_T, out_topk_id, saved, feat_target,
+                                                    rgb_target, float(w_feat), float(w_rgb), d_feat, d_rgb, loss,
+                                                    stream))
 
 
 def fss_query_labels(N, n_queries, dim, f_ins, means, f_q, p_q, prec_q, labels, out_dtype, err, stream):

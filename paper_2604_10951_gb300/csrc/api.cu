@@ -424,13 +424,9 @@ fss_status fss_project_bin(const fss_params* params, const fss_camera* cams, int
     return FSS_OK;
 }
 
-fss_status fss_sort(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N, void* workspace,
-                    int64_t pair_capacity, fss_stream_t stream) {
-    Ctx ctx;
-    fss_status s = prepare(params, cams, n_cams, N, pair_capacity, workspace, ctx);
-    if (s != FSS_OK) return s;
-    if (!workspace) return fail(FSS_ERR_INVALID_ARG, "workspace is NULL");
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+namespace {
+
+fss_status launch_sort(Ctx& ctx, cudaStream_t st) {
     k_tile_sort<<<ctx.cams.total_tiles, SORT_THREADS, 0, st>>>(ctx.cams, ctx.P, ctx.at<float4>(REG_REC),
                                                       ctx.at<BinRec>(REG_BINREC), ctx.at<int2>(REG_RANGES),
                                                       ctx.at<uint32_t>(REG_LIST), ctx.at<uint32_t>(REG_UNB),
@@ -440,6 +436,17 @@ fss_status fss_sort(const fss_params* params, const fss_camera* cams, int32_t n_
     if (e != cudaSuccess) return cuda_fail(e, "k_tile_sort");
     kernel_mark(st);
     return FSS_OK;
+}
+
+}  // namespace
+
+fss_status fss_sort(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N, void* workspace,
+                    int64_t pair_capacity, fss_stream_t stream) {
+    Ctx ctx;
+    fss_status s = prepare(params, cams, n_cams, N, pair_capacity, workspace, ctx);
+    if (s != FSS_OK) return s;
+    if (!workspace) return fail(FSS_ERR_INVALID_ARG, "workspace is NULL");
+    return launch_sort(ctx, reinterpret_cast<cudaStream_t>(stream));
 }
 
 fss_status fss_render_forward(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N,
@@ -465,7 +472,7 @@ struct LossIn {
 fss_status render_forward_impl(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N,
                                void* workspace, int64_t pair_capacity, const float* rgb, const void* feats,
                                void* out_feat, float* out_rgb, float* out_T, int32_t* out_topk_id, void* saved,
-                               const fss_aux_outputs* aux, const LossIn* li, fss_stream_t stream) {
+                               const fss_aux_outputs* aux, const LossIn* li, bool sort, fss_stream_t stream) {
     Ctx ctx;
     fss_status s = prepare(params, cams, n_cams, N, pair_capacity, workspace, ctx);
     if (s != FSS_OK) return s;
@@ -522,7 +529,14 @@ fss_status render_forward_impl(const fss_params* params, const fss_camera* cams,
         if (n_pix > 0) {  // the scale factors exactly as the loss kernel forms them
             x.loss = LossOut{li->Ft, li->rgbt, li->dF, li->drgb, li->loss, 2.0f * li->wf / (float)(n_pix * params->C),
                              li->wf / (float)(n_pix * params->C), li->wc / (float)(n_pix * 3)};
+            if (sort)  // each CTA sorts its tile first (the same regions as the sort kernel)
+                x.sort = SortIn{ctx.at<BinRec>(REG_BINREC), ctx.at<uint32_t>(REG_LIST), ctx.at<uint32_t>(REG_MASK),
+                                ctx.at<uint32_t>(REG_UNB), ctx.at<uint64_t>(REG_SORTTMP)};
         }
+    }
+    if (sort && !x.sort.list) {  // the sort kernel first
+        const fss_status ss = launch_sort(ctx, cs);
+        if (ss != FSS_OK) return ss;
     }
     cudaError_t e = launch_render_forward(ctx.cams, ctx.P, a, x, num_sms_current(), cs);
     if (e != cudaSuccess) return cuda_fail(e, "render_forward");
@@ -541,7 +555,7 @@ fss_status fss_render_forward_aux(const fss_params* params, const fss_camera* ca
                                   void* out_feat, float* out_rgb, float* out_T, int32_t* out_topk_id, void* saved,
                                   const fss_aux_outputs* aux, fss_stream_t stream) {
     return render_forward_impl(params, cams, n_cams, N, workspace, pair_capacity, rgb, feats, out_feat, out_rgb, out_T,
-                               out_topk_id, saved, aux, nullptr, stream);
+                               out_topk_id, saved, aux, nullptr, false, stream);
 }
 
 fss_status fss_render_forward_loss(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N,
@@ -555,7 +569,21 @@ fss_status fss_render_forward_loss(const fss_params* params, const fss_camera* c
         return fail(FSS_ERR_INVALID_ARG, "feature buffers must be 16-byte aligned");
     const LossIn li{feat_target, rgb_target, w_feat, w_rgb, d_feat, d_rgb, loss};
     return render_forward_impl(params, cams, n_cams, N, workspace, pair_capacity, rgb, feats, out_feat, out_rgb, out_T,
-                               out_topk_id, saved, nullptr, &li, stream);
+                               out_topk_id, saved, nullptr, &li, false, stream);
+}
+
+fss_status fss_sort_render_forward_loss(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N,
+                                        void* workspace, int64_t pair_capacity, const float* rgb, const void* feats,
+                                        void* out_feat, float* out_rgb, float* out_T, int32_t* out_topk_id,
+                                        void* saved, const void* feat_target, const float* rgb_target, float w_feat,
+                                        float w_rgb, void* d_feat, float* d_rgb, double* loss, fss_stream_t stream) {
+    if (!out_feat || !out_rgb || !feat_target || !rgb_target || !d_feat || !d_rgb || !loss)
+        return fail(FSS_ERR_INVALID_ARG, "NULL loss argument (out_feat, out_rgb, targets, gradients, loss)");
+    if (misaligned16(feat_target) || misaligned16(d_feat))
+        return fail(FSS_ERR_INVALID_ARG, "feature buffers must be 16-byte aligned");
+    const LossIn li{feat_target, rgb_target, w_feat, w_rgb, d_feat, d_rgb, loss};
+    return render_forward_impl(params, cams, n_cams, N, workspace, pair_capacity, rgb, feats, out_feat, out_rgb, out_T,
+                               out_topk_id, saved, nullptr, &li, true, stream);
 }
 
 fss_status fss_render_backward(const fss_params* params, const fss_camera* cams, int32_t n_cams, int64_t N,

@@ -80,15 +80,27 @@ struct LossOut {
     float sc;           // w_c / (3 n): dL/drgb = sc sign(rgb - rgb_t), and the weight on sum |rgb - rgb_t|
 };
 
-// sensor outputs of the forward render, each may be NULL, and the fused loss
-// (loss.loss NULL: none).  A kernel parameter of its own: a larger FwdArgs
-// costs the main Top-K instance register spills.
+// the depth sort run by the Top-K forward on its own tile (its SORT
+// instances; sort_tile in sort.cuh): the workspace regions the sort kernel takes
+struct SortIn {
+    const BinRec* binrec;
+    uint32_t* list;  // sorted in place
+    uint32_t* masks;
+    const uint32_t* unb_list;
+    uint64_t* scratch;
+};
+
+// sensor outputs of the forward render, each may be NULL, the fused loss
+// (loss.loss NULL: none) and the fused sort (sort.list NULL: none).  A kernel
+// parameter of its own: a larger FwdArgs costs the main Top-K instance
+// register spills.
 struct AuxOut {
     float* depth;      // [pix] sum w z_hit
     float* depth_med;  // [pix] z_hit where T first drops below 1/2, else 0
     float* normal;     // [pix, 3] sum w n, camera-space normals facing the camera
     int32_t* label;    // [pix] argmax over the channels of the rendered features, -1 if none blended
     LossOut loss;
+    SortIn sort;
     __host__ __device__ bool any() const { return depth || depth_med || normal || label; }
 };
 

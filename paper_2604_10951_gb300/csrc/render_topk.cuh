@@ -26,6 +26,7 @@
 #include "fss_internal.cuh"
 #include "kernels.cuh"
 #include "render_common.cuh"
+#include "sort.cuh"
 
 #include <algorithm>
 #include <climits>
@@ -57,7 +58,7 @@ using topk_detail::next_tile;
 // KCAP the first KCAP - K slots hold +inf and never move, so the K-th
 // largest weight is always slot KCAP - 1.  With the first-K selection the
 // K slots after the padding take the first K contributors in order.
-template <int TS, int KCAP, typename FT, bool FRONT, bool AUX, bool LOSS = false>
+template <int TS, int KCAP, typename FT, bool FRONT, bool AUX, bool LOSS = false, bool SORT = false>
 __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : (KCAP == 16 && TS <= 16 ? 512 / (TS * TS) : 1)) k_render_topk(const __grid_constant__ Cams cams,
                                                          const __grid_constant__ RParams P, const FwdArgs a,
                                                          const __grid_constant__ AuxOut x) {
@@ -89,6 +90,14 @@ __global__ void __launch_bounds__(TS * TS, KCAP <= 8 ? 1024 / (TS * TS) : (KCAP 
     const int ppi = NT / nvec;                         // pixels per phase-2 sweep
     const int q0 = tid / nvec, vv = tid - q0 * nvec;   // this thread's pixel offset and 16-byte chunk
     for (int t = next_tile(cams, a, &s_tile, true); t < cams.total_tiles; t = next_tile(cams, a, &s_tile, false)) {
+        if constexpr (SORT) {  // this tile's depth sort first, in the staging area
+            __syncthreads();   // (the previous tile's last reads of the area)
+            sort_tile(cams, P, a.rec, x.sort.binrec, a.ranges, x.sort.list, x.sort.unb_list, x.sort.scratch,
+                      x.sort.masks, a.st, t, reinterpret_cast<uint64_t*>(smem),
+                      reinterpret_cast<uint32_t*>(smem + (size_t)SORT_CAP * 8),
+                      reinterpret_cast<uint16_t*>(smem + (size_t)SORT_CAP * 12));
+            __syncthreads();  // the sorted list and masks (global, written by this CTA) before staging
+        }
         const int view = view_of_tile(cams, t);
         const CamDev& cam = cams.c[view];
         const int lt = t - cam.tile_off;
@@ -419,7 +428,10 @@ cudaError_t launch_topk(const Cams& cams, const RParams& P, const FwdArgs& a, co
         const int pc = (NT < 65536 / (kcap * 8 + 4)) ? NT : 65536 / (kcap * 8 + 4);
         return std::max(p1, (size_t)pc * (kcap * 8 + 4) + (aux ? (size_t)pc * 8 + 8 : 0));  // (+ argmax keys)
     };
-    // the fused loss: the plain selection with K <= 8, no sensor outputs (checked by the caller)
+    // the fused loss (and sort): the plain selection with K <= 8, no sensor outputs (checked by the caller)
+    if (x.loss.loss && x.sort.list)
+        return launch_tiles(k_render_topk<TS, 8, FT, false, false, true, true>, NT,
+                            std::max(smem(8), SORT_SMEM_BYTES), cams, P, a, x, num_sms, s);
     if (x.loss.loss)
         return launch_tiles(k_render_topk<TS, 8, FT, false, false, true>, NT, smem(8), cams, P, a, x, num_sms, s);
     // variants (first-K selection, sensor outputs) need unsorted or few slots: two capacities

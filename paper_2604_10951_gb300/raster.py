@@ -145,6 +145,14 @@ class Frame:
                                   _ptr(rgb_target), w_feat, w_rgb, _ptr(d_feat), _ptr(d_rgb), _ptr(loss),
                                   _stream(stream))
 
+    def sort_render_forward_loss(self, rgb, feats, out_feat, out_rgb, out_T, out_ids, feat_target, rgb_target,
+                                 w_feat, w_rgb, d_feat, d_rgb, loss, stream=None):
+        """sort + render_forward_loss in one call, after project_bin (see fss_sort_render_forward_loss)."""
+        L.fss_sort_render_forward_loss(*self.args(), _ptr(self.ws), self.cap, _ptr(rgb), _ptr(feats), _ptr(out_feat),
+                                       _ptr(out_rgb), _ptr(out_T), _ptr(out_ids), _ptr(self.saved),
+                                       _ptr(feat_target), _ptr(rgb_target), w_feat, w_rgb, _ptr(d_feat), _ptr(d_rgb),
+                                       _ptr(loss), _stream(stream))
+
     def render_backward(self, means, scales, quats, opac, rgb, feats, out_T, d_feat, d_rgb, d_T, g_means, g_scales,
                         g_quats, g_opac, g_rgb, g_feat, stream=None):
         L.fss_render_backward(*self.args(), _ptr(self.ws), self.cap, _ptr(means), _ptr(scales), _ptr(quats),

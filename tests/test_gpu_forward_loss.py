@@ -156,3 +156,79 @@ def test_graph_replay_equals_the_eager_call():
         assert torch.equal(x.view(torch.int16) if x.dtype == torch.bfloat16 else x,
                            y.view(torch.int16) if y.dtype == torch.bfloat16 else y)
     assert got[-1] == pytest.approx(ref[-1], rel=1e-6)
+
+
+def _run_sorted(scene, cams, wf=1.0, wc=0.5, seed=11, **kw):
+    """fss_sort then fss_render_forward_loss, against fss_sort_render_forward_loss,
+    each on a fresh binning of the same frame: identical lists, warp masks,
+    forward outputs, saved buffers and gradients; the loss up to its order."""
+    run = GpuRun(scene, cams, render=False, **kw)
+    fr, p = run.frame, run.params
+    npx = fr.total_pix
+    Ft, rgbt = scenes.targets(seed, npx, p.C)
+    odt = torch.bfloat16 if p.out_dtype == L.FSS_BF16 else torch.float32
+    Ft, rgbt = dev(Ft, odt), dev(rgbt)
+    res = []
+    for fused in (False, True):
+        fr.project_bin(run.means, run.scales, run.quats, run.opac)
+        F, rgb, T, ids = fr.new_outputs()
+        dF = torch.full_like(F, float("nan"))
+        drgb = torch.full_like(rgb, float("nan"))
+        loss = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+        fr.saved.fill_(0xAB)
+        if fused:
+            fr.sort_render_forward_loss(run.rgb, run.feats, F, rgb, T, ids, Ft, rgbt, wf, wc, dF, drgb, loss)
+        else:
+            fr.sort()
+            fr.render_forward_loss(run.rgb, run.feats, F, rgb, T, ids, Ft, rgbt, wf, wc, dF, drgb, loss)
+        torch.cuda.synchronize()
+        s, _ = fr.read_status()
+        assert s == 0
+        res.append(dict(F=F, rgb=rgb, T=T, ids=ids, saved=fr.saved.clone(), dF=dF, drgb=drgb, loss=loss.item(),
+                        lists=run.lists().copy(), masks=run.masks().copy()))
+    a, b = res
+    np.testing.assert_array_equal(a["lists"], b["lists"])
+    np.testing.assert_array_equal(a["masks"], b["masks"])
+    for k in ("F", "rgb", "T", "ids", "saved", "dF", "drgb"):
+        if a[k] is None:
+            assert b[k] is None
+            continue
+        x, y = a[k].cpu(), b[k].cpu()
+        if x.dtype == torch.bfloat16:
+            x, y = x.view(torch.int16), y.view(torch.int16)
+        elif x.dtype == torch.float32:
+            x, y = x.view(torch.int32), y.view(torch.int32)
+        assert torch.equal(x, y), k
+    assert b["loss"] == pytest.approx(a["loss"], rel=1e-6)
+    return run
+
+
+@pytest.mark.parametrize("feat_dtype", [torch.bfloat16, torch.float32])
+@pytest.mark.parametrize("ts", [8, 16, 32])
+def test_sort_in_the_forward_two_ragged_views(feat_dtype, ts):
+    scene, cams = _two_views()
+    _run_sorted(scene, cams, K=8, tile_size=ts, feat_dtype=feat_dtype, stop_rule="exact_topk")
+
+
+@pytest.mark.parametrize("kw", [dict(K=4, schedule="persistent"), dict(K=16), dict(K=8, select="front"),
+                                dict(K=8, renorm=True), dict(K=0)])
+def test_sort_in_the_forward_schedules_and_variants(kw):
+    scene, cams = _two_views()
+    _run_sorted(scene, cams, **dict(dict(feat_dtype=torch.bfloat16), **kw))
+
+
+@pytest.mark.parametrize("n_small,views", [(1000, 1), (5200, 2)])
+def test_sort_in_the_forward_long_tile_lists(n_small, views):
+    """A tile of nearly 1,024 pairs (the shared-memory sort's last chunks) and
+    of over 4,096 (the radix sort in global scratch), the latter in two views."""
+    from tests.test_gpu_binning import _dense_tile_scene
+    sc, cam = _dense_tile_scene(n_small=n_small, seed=1)
+    run = _run_sorted(sc, [cam] * views, K=8, feat_dtype=torch.bfloat16)
+    r = run.ranges()
+    assert r[0, 1] - r[0, 0] > (4096 if n_small > 1024 else 960)
+
+
+def test_sort_in_the_forward_room_view():
+    scene = scenes.room_scene(n=200_000, C=64, seed=3)
+    cam = scenes.circle_poses(16)[9]
+    _run_sorted(scene, [cam], K=8, feat_dtype=torch.bfloat16, stop_rule="exact_topk", cap=1 << 20)
