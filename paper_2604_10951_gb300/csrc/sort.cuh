@@ -93,7 +93,7 @@ __device__ __noinline__ void block_radix_sort_global(uint64_t* keys, uint64_t* t
 // SORT_CAP entries of shared memory.  Returns with the list and masks in
 // global memory written by this CTA (the caller synchronises before reading
 // them back).
-__device__ __forceinline__ void sort_tile(const Cams& cams, const RParams& P, const float4* __restrict__ rec,
+static __device__ __noinline__ void sort_tile(const Cams& cams, const RParams& P, const float4* __restrict__ rec,
                                           const BinRec* __restrict__ binrec, const int2* __restrict__ ranges,
                                           uint32_t* list, const uint32_t* __restrict__ unb_list,
                                           uint64_t* __restrict__ scratch, uint32_t* masks, Status* stw, int t,
