@@ -17,7 +17,10 @@
 // Variants: FRONT takes the first K contributors instead of the K largest
 // weights; AUX also accumulates the sensor outputs (expected and median
 // depth, facing normal) over every contributor and applies the low-pass
-// filter when the parameters ask for it.
+// filter when the parameters ask for it; LOSS evaluates the training loss
+// (L2 on the features, L1 on the colour) and its gradients where F and rgb
+// are formed; SORT (with LOSS) first depth-sorts the CTA's own tile list
+// (sort_tile), so that no sort kernel runs before it.
 //
 // The accumulation is a sparse gather-weighted sum, not a dense contraction,
 // so no tensor cores are involved.
