@@ -204,21 +204,23 @@ def test_check_build_exports_the_abi_with_a_canary_after_every_region(lib):
 
 
 def test_forward_loss_arguments_are_checked_on_the_host(lib):
-    """fss_render_forward_loss needs out_feat, out_rgb and every loss buffer,
+    """fss_render_forward_loss (and with the sort, fss_sort_render_forward_loss)
+    needs out_feat, out_rgb and every loss buffer,
     16-byte aligned feature buffers and valid parameters; each is rejected
     before any launch."""
     p = L.fss_default_params()
     z = C.c_void_p(256)  # never dereferenced: every call below is rejected first
     ws = C.c_void_p(4096)
 
-    def call(params=p, out_feat=z, feat_target=z, d_feat=z, loss=z):
-        return lib.fss_render_forward_loss(C.byref(params), _cam(), 1, 10, ws, 100, z, z, out_feat, z, z, z, z,
-                                           feat_target, z, 1.0, 1.0, d_feat, z, loss, None)
+    for fn in (lib.fss_render_forward_loss, lib.fss_sort_render_forward_loss):
+        def call(params=p, out_feat=z, feat_target=z, d_feat=z, loss=z):
+            return fn(C.byref(params), _cam(), 1, 10, ws, 100, z, z, out_feat, z, z, z, z, feat_target, z, 1.0, 1.0,
+                      d_feat, z, loss, None)
 
-    assert call(out_feat=None) == L.FSS_ERR_INVALID_ARG
-    assert call(loss=None) == L.FSS_ERR_INVALID_ARG and "loss" in L.last_error()
-    assert call(feat_target=C.c_void_p(264)) == L.FSS_ERR_INVALID_ARG and "aligned" in L.last_error()
-    assert call(d_feat=C.c_void_p(72)) == L.FSS_ERR_INVALID_ARG
-    bad = L.fss_default_params()
-    bad.K = 33
-    assert call(params=bad) == L.FSS_ERR_UNSUPPORTED
+        assert call(out_feat=None) == L.FSS_ERR_INVALID_ARG
+        assert call(loss=None) == L.FSS_ERR_INVALID_ARG and "loss" in L.last_error()
+        assert call(feat_target=C.c_void_p(264)) == L.FSS_ERR_INVALID_ARG and "aligned" in L.last_error()
+        assert call(d_feat=C.c_void_p(72)) == L.FSS_ERR_INVALID_ARG
+        bad = L.fss_default_params()
+        bad.K = 33
+        assert call(params=bad) == L.FSS_ERR_UNSUPPORTED
