@@ -179,6 +179,18 @@ BWD_KERNELS = ["k_bwd_clear", "k_bwd_feat", "k_bwd_geo", "k_bwd_project", "k_fea
 KERNELS = FWD_KERNELS[:2] + ["k_render_topk"] + BWD_KERNELS
 
 
+def step_kernels(K, backward):
+    """The kernels one step of StepPath launches, in order: the forward path
+    (binning, sort, render), or the training step, where for the plain Top-K
+    selection with K <= 8 the render kernel also sorts its tile and
+    evaluates the loss, else the sort and the loss run as kernels of their own."""
+    render = "k_render_topk" if K else "k_render_full"
+    if not backward:
+        return FWD_KERNELS + [render]
+    fwd = [render] if 0 < K <= 8 else ["k_tile_sort", render, "k_loss"]
+    return FWD_KERNELS[:2] + fwd + [k for k in BWD_KERNELS if K or k != "k_bwd_feat"]
+
+
 class StepPath:
     """Buffers and the step of one configuration, every call through the C
     ABI, replayed as one CUDA graph per camera set: binning, sort, forward
@@ -214,7 +226,7 @@ class StepPath:
         self.npx = npx
         self.render_kernel = "k_render_topk" if K else "k_render_full"
         self.fused_loss = False
-        self.kernels = FWD_KERNELS + [self.render_kernel]
+        self.kernels = step_kernels(K, False)
         self.calls = FWD_CALLS
         if backward:
             F_t, rgb_t = scenes.targets(targets_seed, npx, C)
@@ -228,9 +240,7 @@ class StepPath:
             self.gfeat = torch.empty(N, C, dtype=dtype, device=dev)
             # the loss runs inside the Top-K kernel for K <= 8, else as its own kernel
             self.fused_loss = 0 < K <= 8
-            self.kernels = (FWD_KERNELS[:2] + ([self.render_kernel] if self.fused_loss else
-                                               ["k_tile_sort", self.render_kernel, "k_loss"]) +
-                            [k for k in BWD_KERNELS if K or k != "k_bwd_feat"])
+            self.kernels = step_kernels(K, True)
             self.calls = STEP_CALLS
         self.graphs, self.gevents = [], []
         self.ncu = False  # the ncu constants above describe this path's kernels (the main workload only)

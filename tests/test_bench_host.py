@@ -75,3 +75,54 @@ def test_reference_band_step_renders_the_frame_rows():
         np.testing.assert_array_equal(seen[b]["ids"], full["ids"][rows])
     res = st.sample(4, warmup=1)
     assert res["kind"] == "oracle" and res["value"] > 0 and f"bands of {bench.BAND} rows" in res["sample"]
+
+
+class _FakeFrame:
+    """The workspace regions that the bench's byte model reads, on the CPU:
+    tile ranges and the status block's counts."""
+
+    def __init__(self, torch, tiles=12, pairs_per_tile=5, sizes=((32, 48),)):
+        import paper_2604_10951_gb300._lib as L
+        self.L = L
+        r = np.zeros((tiles, 2), np.int32)
+        r[:, 0] = np.arange(tiles) * pairs_per_tile
+        r[:, 1] = r[:, 0] + pairs_per_tile
+        st = np.zeros(32, np.int32)
+        st[20], st[22], st[25] = 40, 30, 2  # narrow visible items, slots, wide items
+        self.regions = {L.REG_RANGES: torch.from_numpy(r.view(np.uint8).reshape(-1)),
+                        L.REG_STATUS: torch.from_numpy(st.view(np.uint8).reshape(-1))}
+        self.sizes = list(sizes)
+        self.pix_off = [0]
+        for h, w in self.sizes:
+            self.pix_off.append(self.pix_off[-1] + h * w)
+
+    def region(self, which):
+        return self.regions[which]
+
+
+class _FakePath:
+    def __init__(self, torch, K, backward, dtype_bytes=2, C=16):
+        self.frame = _FakeFrame(torch)
+        self.s, self.K, self.C, self.N, self.ts, self.n_cams = dtype_bytes, K, C, 100, 16, 1
+        self.npx = self.frame.pix_off[-1]
+        self.ids = torch.zeros(self.npx, max(K, 1), dtype=torch.int32) if K else None
+        self.backward = backward
+        self.fused_loss = backward and 0 < K <= 8
+        self.render_kernel = "k_render_topk" if K else "k_render_full"
+        self.kernels = bench.step_kernels(K, backward)  # as StepPath sets them
+
+
+@pytest.mark.parametrize("K,backward", [(8, True), (4, True), (0, True), (16, True), (8, False), (0, False)])
+def test_byte_model_covers_exactly_the_step_kernels(K, backward):
+    """Every kernel the step launches has algorithmic bytes and no other key
+    appears (the roofline divides one by the other's event time), for the
+    fused training step (sort and loss in the render kernel), the two-kernel
+    cases and the forward-only paths."""
+    import torch
+    path = _FakePath(torch, K, backward)
+    b, z = bench.algorithmic_bytes(path, torch, path.frame.L)
+    assert set(b) == set(path.kernels), (sorted(b), path.kernels)
+    assert all(v > 0 for v in b.values())
+    assert z["pairs"] == 60 and z["slots"] == 30
+    if backward and path.fused_loss:
+        assert bench.KERNELS == path.kernels and len(bench.KERNELS) == 8
